@@ -1,0 +1,209 @@
+"""CSR Hamiltonians, FP64, built by brute force (oracle; test infrastructure only).
+
+Common conventions (shared with the CUDA builder so that structure AND values
+agree bit for bit):
+  * Columns in each row are sorted ascending; the diagonal is always stored,
+    even when its value is zero.  Repeated (row, col) pairs are summed in the
+    order the terms are generated (only XXZ with L = 2 produces any).
+  * Diagonal values are accumulated term by term, left to right, starting from
+    +0.0, with no fused multiply-add (numpy never contracts a*b+c).
+
+XXZ (Eq. xxz, App. A):  H = J sum_i (S^x_i S^x_{i+1} + S^y_i S^y_{i+1}
+                                     + Delta S^z_i S^z_{i+1}) + sum_i h_i S^z_i.
+  Bit i = 1 means S^z_i = +1/2.  Bonds (i, i+1) for i = 0..L-2, plus (L-1, 0)
+  under periodic boundaries.  An antiparallel bond (i, j) couples the state to
+  the one with both spins flipped, with element J/2 (from (S+S- + S-S+)/2).
+  Diagonal: for each bond in order, +(J*Delta)*0.25 if parallel else
+  -(J*Delta)*0.25; then for i = 0..L-1, +h_i*0.5 if up else -(h_i*0.5).
+
+Quantum sun (Eq. qsun, App. A.2): dot of N spins in the top N bits, outer spin
+  j in bit j (j = 0..L-1).  H_dot = gamma R'/sqrt(2^N + 1) with
+  R' = (A + A^T)/sqrt(2); element (a, b) is computed as (A_ab + A_ba) * c,
+  c = gamma / (sqrt(2) * sqrt(2^N + 1)), and acts on the dot index of states
+  that share the outer configuration (the embedding R' (x) I).  Ray j flips
+  dot spin n(j) and outer spin j with element (g0 * alpha**u_j) * 0.25
+  (S = sigma/2, so S^x S^x has matrix element 1/4), u_j = j + noise_j.
+  Diagonal: H_dot[a, a], then for j = 0..L-1, +h_j*0.5 if up else -(h_j*0.5).
+
+Fermi-Hubbard (not in the paper; open chain):
+  H = -t sum_{i,sigma} (c+_{i,s} c_{i+1,s} + h.c.) + U sum_i n_i,up n_i,dn
+      + sum_i mu_i (n_i,up + n_i,dn).
+  Jordan-Wigner order: all up modes, then all down modes, so a hop of one
+  species between sites i and j carries (-1)^(occupied sites of that species
+  strictly between i and j); element -t times that sign.
+  Diagonal: for i = 0..L-1, + U*(n_up_i*n_dn_i); then for i = 0..L-1,
+  + mu_i*(n_up_i + n_dn_i) (the occupations as doubles).
+"""
+from dataclasses import dataclass
+import numpy as np
+import scipy.sparse as sp
+
+from . import basis as _basis
+
+PBC, OBC = 0, 1
+
+
+@dataclass
+class CSR:
+    D: int
+    indptr: np.ndarray    # int64[D+1]
+    indices: np.ndarray   # int64[nnz], ascending within each row
+    data: np.ndarray      # float64[nnz]
+
+    @property
+    def nnz(self):
+        return int(self.indptr[-1])
+
+    def scipy(self):
+        return sp.csr_matrix((self.data, self.indices, self.indptr), shape=(self.D, self.D))
+
+    def diag_mask(self):
+        rows = np.repeat(np.arange(self.D), np.diff(self.indptr))
+        return self.indices == rows
+
+    def dense(self):
+        return self.scipy().toarray()
+
+
+def csr_from_terms(D, rows, cols, vals):
+    """Sort (row, col) lexicographically (stable) and sum repeated pairs in order."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    if len(rows):
+        first = np.ones(len(rows), dtype=bool)
+        first[1:] = (rows[1:] != rows[:-1]) | (cols[1:] != cols[:-1])
+        if not np.all(first):
+            group = np.cumsum(first) - 1
+            summed = np.zeros(int(group[-1]) + 1)
+            for k in range(len(vals)):          # sequential, generation order
+                summed[group[k]] = summed[group[k]] + vals[k]
+            rows, cols, vals = rows[first], cols[first], summed
+    indptr = np.zeros(D + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=D), out=indptr[1:])
+    return CSR(D=D, indptr=indptr, indices=cols, data=vals)
+
+
+def _bonds(L, bc):
+    nb = L if bc == PBC else L - 1
+    return [(i, (i + 1) % L) for i in range(nb)]
+
+
+def xxz_hamiltonian(p):
+    """Eq. xxz in the S^z_tot sector with p.N up spins."""
+    L = p.L
+    states = _basis.xxz_basis(L, p.N)
+    D = len(states)
+    bonds = _bonds(L, p.bc)
+    jdq = (p.J * p.Delta) * 0.25
+    d = np.zeros(D)
+    for (i, j) in bonds:
+        par = ((states >> i) & 1) == ((states >> j) & 1)
+        d = d + np.where(par, jdq, -jdq)
+    for i in range(L):
+        hi = p.h[i] * 0.5
+        d = d + np.where(((states >> i) & 1) == 1, hi, -hi)
+    rows, cols, vals = [np.arange(D)], [np.arange(D)], [d]
+    half_j = p.J * 0.5
+    for (i, j) in bonds:
+        anti = ((states >> i) & 1) != ((states >> j) & 1)
+        r = np.nonzero(anti)[0]
+        t = states[r] ^ ((1 << i) | (1 << j))
+        rows.append(r)
+        cols.append(_basis.row_of(states, t))
+        vals.append(np.full(len(r), half_j))
+    H = csr_from_terms(D, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+    H.states = states
+    return H
+
+
+def qsun_dot_matrix(p):
+    """H_dot = gamma (A + A^T)/sqrt(2) / sqrt(2^N + 1) (App. A.2)."""
+    nd = 1 << p.N
+    c = p.gamma / (np.sqrt(2.0) * np.sqrt(nd + 1.0))
+    A = np.asarray(p.A, dtype=np.float64)
+    return (A + A.T) * c
+
+
+def qsun_ray_coefficients(p):
+    u = np.arange(p.L, dtype=np.float64) + p.u_noise
+    return (p.g0 * np.power(p.alpha, u)) * 0.25
+
+
+def qsun_hamiltonian(p):
+    """Eq. qsun on the full 2^(N+L) space."""
+    N, L = p.N, p.L
+    nd = 1 << N
+    D = 1 << (N + L)
+    states = _basis.qsun_basis(N, L)
+    dot = states >> L
+    outer = states & ((1 << L) - 1)
+    hd = qsun_dot_matrix(p)
+    d = hd[dot, dot].copy()
+    for j in range(L):
+        hj = p.h[j] * 0.5
+        d = d + np.where(((states >> j) & 1) == 1, hj, -hj)
+    rows, cols, vals = [states], [states], [d]
+    for b in range(nd):
+        m = dot != b
+        r = states[m]
+        rows.append(r)
+        cols.append((b << L) | outer[m])
+        vals.append(hd[dot[m], b])
+    coef = qsun_ray_coefficients(p)
+    for j in range(L):
+        flip = (1 << (L + int(p.n_of_j[j]))) | (1 << j)
+        rows.append(states)
+        cols.append(states ^ flip)
+        vals.append(np.full(D, coef[j]))
+    H = csr_from_terms(D, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+    H.states = states
+    return H
+
+
+def _between_mask(i, j):
+    lo, hi = min(i, j), max(i, j)
+    return ((1 << hi) - 1) & ~((1 << (lo + 1)) - 1)
+
+
+def hubbard_hamiltonian(p):
+    L = p.L
+    ups, dns = _basis.hubbard_basis(L, p.N_up, p.N_dn)
+    Du, Dd = len(ups), len(dns)
+    D = Du * Dd
+    rows_all = np.arange(D)
+    iu, idn = rows_all // Dd, rows_all % Dd
+    up, dn = ups[iu], dns[idn]
+    d = np.zeros(D)
+    for i in range(L):
+        d = d + p.U * (((up >> i) & 1) * ((dn >> i) & 1)).astype(np.float64)
+    for i in range(L):
+        d = d + p.mu[i] * (((up >> i) & 1) + ((dn >> i) & 1)).astype(np.float64)
+    rows, cols, vals = [rows_all], [rows_all], [d]
+    for (i, j) in _bonds(L, p.bc):
+        mask = (1 << i) | (1 << j)
+        between = _between_mask(i, j)
+        for spin in (0, 1):
+            occ = up if spin == 0 else dn
+            hop = ((occ >> i) & 1) != ((occ >> j) & 1)
+            r = rows_all[hop]
+            new = occ[hop] ^ mask
+            n_between = _basis.popcount(occ[hop] & between)
+            sign = np.where(n_between % 2 == 0, 1.0, -1.0)
+            if spin == 0:
+                c = _basis.row_of(ups, new) * Dd + idn[hop]
+            else:
+                c = iu[hop] * Dd + _basis.row_of(dns, new)
+            rows.append(r)
+            cols.append(c)
+            vals.append(-p.t * sign)
+    H = csr_from_terms(D, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+    H.ups, H.dns = ups, dns
+    return H
+
+
+def build(p):
+    """Dispatch on the parameter record's model kind (0 XXZ, 1 quantum sun, 2 Hubbard)."""
+    return {0: xxz_hamiltonian, 1: qsun_hamiltonian, 2: hubbard_hamiltonian}[p.kind](p)

@@ -1,0 +1,16 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module holds random draws and workload definitions only: no step of the
+method's arithmetic (no Hamiltonian construction, no filter, no Lanczos).
+Every random number comes from SplitMix64 (Steele, Lea & Flood, "Fast
+splittable pseudorandom number generators", OOPSLA 2014), used in counter form:
+the i-th output of a stream seeded with ``seed`` is ``mix64(seed + (i+1)*G)``
+with G = 0x9E3779B97F4A7C15.
+"""
+from .rng import splitmix64, uniform01, uniform_pm_half, normals
+from .workloads import (XXZParams, QSunParams, HubbardParams, xxz_params, qsun_params,
+                        hubbard_params, CONFIGS, config_seed)
+
+__all__ = ["splitmix64", "uniform01", "uniform_pm_half", "normals", "XXZParams",
+           "QSunParams", "HubbardParams", "xxz_params", "qsun_params", "hubbard_params",
+           "CONFIGS", "config_seed"]

@@ -1,0 +1,107 @@
+"""Synthetic workload definitions: model parameters and their seeded disorder.
+
+Models (paper App. A): the disordered XXZ chain (Eq. xxz), the quantum sun
+(Eq. qsun) and a 1D Fermi-Hubbard chain with random on-site potentials.  The
+draw order of every random array is fixed here so both sides of every parity
+test see identical inputs.  Seeds: realisation r of workload c uses
+seed = 1000*c + r.
+"""
+from dataclasses import dataclass, field
+import numpy as np
+
+from .rng import uniform01, normals
+
+XXZ, QSUN, HUBBARD = 0, 1, 2
+PBC, OBC = 0, 1
+
+
+@dataclass
+class XXZParams:
+    L: int
+    N: int                      # number of up spins (bit = 1)
+    J: float = 1.0
+    Delta: float = 1.0
+    W: float = 0.0
+    bc: int = PBC
+    seed: int = 0
+    h: np.ndarray = field(default=None, repr=False)   # fields h_i, i = 0..L-1
+    kind: int = XXZ
+
+
+@dataclass
+class QSunParams:
+    N: int                      # dot spins (top N bits of the state)
+    L: int                      # outer spins (bits 0..L-1)
+    g0: float = 1.0
+    alpha: float = 0.75
+    gamma: float = 1.0
+    zeta: float = 0.2
+    h0: float = 1.0             # field mean
+    wh: float = 0.5             # field half-width: h_j ~ U[h0-wh, h0+wh]
+    seed: int = 0
+    A: np.ndarray = field(default=None, repr=False)       # 2^N x 2^N raw normals
+    u_noise: np.ndarray = field(default=None, repr=False)  # u_j - j, U[-zeta, zeta]
+    n_of_j: np.ndarray = field(default=None, repr=False)   # dot spin coupled to j
+    h: np.ndarray = field(default=None, repr=False)        # fields h_j
+    kind: int = QSUN
+
+
+@dataclass
+class HubbardParams:
+    L: int
+    N_up: int
+    N_dn: int
+    t: float = 1.0
+    U: float = 1.0
+    W: float = 0.0
+    bc: int = OBC
+    seed: int = 0
+    mu: np.ndarray = field(default=None, repr=False)     # on-site potentials mu_i
+    kind: int = HUBBARD
+
+
+def xxz_params(L, N=None, J=1.0, Delta=1.0, W=0.0, bc=PBC, seed=0):
+    """h_i = W (2 u_i - 1), u_i = uniform01(seed, i), i = 0..L-1."""
+    N = L // 2 if N is None else N
+    h = W * (2.0 * uniform01(seed, np.arange(L)) - 1.0)
+    return XXZParams(L=L, N=N, J=J, Delta=Delta, W=W, bc=bc, seed=seed, h=h)
+
+
+def qsun_params(N=3, L=15, g0=1.0, alpha=0.75, gamma=1.0, zeta=0.2, h0=1.0, wh=0.5, seed=0):
+    """Draw order: A (row-major, Box-Muller normals), then u_j noise, n(j), h_j."""
+    nd = 1 << N
+    A = normals(seed, nd * nd).reshape(nd, nd)
+    off = 2 * ((nd * nd + 1) // 2)
+    u = uniform01(seed, off + np.arange(3 * L))
+    u_noise = zeta * (2.0 * u[:L] - 1.0)
+    n_of_j = np.minimum((u[L:2 * L] * N).astype(np.int64), N - 1)
+    h = h0 + wh * (2.0 * u[2 * L:] - 1.0)
+    return QSunParams(N=N, L=L, g0=g0, alpha=alpha, gamma=gamma, zeta=zeta, h0=h0, wh=wh,
+                      seed=seed, A=A, u_noise=u_noise, n_of_j=n_of_j, h=h)
+
+
+def hubbard_params(L, N_up=None, N_dn=None, t=1.0, U=1.0, W=0.0, bc=OBC, seed=0):
+    """mu_i = W (2 u_i - 1), u_i = uniform01(seed, i)."""
+    N_up = L // 2 if N_up is None else N_up
+    N_dn = L // 2 if N_dn is None else N_dn
+    mu = W * (2.0 * uniform01(seed, np.arange(L)) - 1.0)
+    return HubbardParams(L=L, N_up=N_up, N_dn=N_dn, t=t, U=U, W=W, bc=bc, seed=seed, mu=mu)
+
+
+def config_seed(config, r):
+    return 1000 * config + r
+
+
+# The five workloads (normalised target eps in [0,1]: lambda = Emin + eps (Emax - Emin)).
+CONFIGS = {
+    1: dict(name="xxz_L12", model="xxz", L=12, J=1.0, Delta=1.0, W=2.0, nev=20, eps=0.5,
+            block=8, precision="f64"),
+    2: dict(name="xxz_L20", model="xxz", L=20, J=1.0, Delta=1.0, W=(1.0, 3.0, 5.0), nev=100,
+            eps=0.5, block=32, precision=("f64", "f32")),
+    3: dict(name="qsun_N3_L15", model="qsun", N=3, L=15, g0=1.0, alpha=0.75, gamma=1.0,
+            nev=50, eps=0.5, block=16, precision="f32"),
+    4: dict(name="hubbard_L12", model="hubbard", L=12, N_up=6, N_dn=6, t=1.0, U=1.0, W=4.0,
+            nev=100, eps=0.5, block=64, precision="f32"),
+    5: dict(name="serving_mix", model="xxz", L=(14, 16, 18, 20, 22), W=(0.5, 8.0),
+            eps=(0.2, 0.8), nev=(20, 50, 200), requests=2000, precision="f32"),
+}

@@ -1,0 +1,189 @@
+"""Pins of the oracle's filter, DOS/K rule and (block) Lanczos (CPU only)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import pf_inputs as pi
+from oracle import hamiltonian as hm, dense, chebyshev as ch, dos, lanczos as lz
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _xxz12():
+    H = hm.xxz_hamiltonian(pi.xxz_params(12, W=2.0, seed=1001))
+    w, U = dense.eigh_dense(H)
+    return H, w, U
+
+
+@pytest.mark.parametrize("lam_t,K", [(0.0, 10), (0.3, 57), (-0.71, 200), (0.95, 33)])
+def test_filter_is_one_at_target(lam_t, K):
+    assert abs(ch.filter_value(lam_t, lam_t, K)[0] - 1.0) < 1e-12
+
+
+def test_filter_coefficients_definition():
+    a = ch.filter_coefficients(0.2, 7)
+    T = np.cos(np.arange(8) * math.acos(0.2))
+    c = np.array([1.0] + [2.0] * 7) * T
+    assert np.allclose(a, c / np.sum(c * T), rtol=0, atol=1e-15)
+
+
+def test_filter_against_closed_form_kernel():
+    # sum_{n=0}^K c_n T_n(x) with c_0 = 1, c_n = 2 T_n(y) equals the Dirichlet-type sum
+    # 1 + 2 sum cos(n t) cos(n p) = D_K(t - p) + D_K(t + p) - 1, D_K(u) = sin((K+1/2)u)/(2 sin(u/2)) * 2 / 2
+    K, y = 41, 0.37
+    p = math.acos(y)
+    def dirich(u):
+        return math.sin((K + 0.5) * u) / math.sin(u / 2.0) if abs(math.sin(u / 2)) > 1e-14 else 2 * K + 1.0
+    chi = 0.5 * (dirich(0.0) + dirich(2 * p))
+    for x in [-0.9, -0.2, 0.1, 0.36, 0.8]:
+        t = math.acos(x)
+        ref = 0.5 * (dirich(t - p) + dirich(t + p)) / chi
+        assert abs(ch.filter_value(x, y, K)[0] - ref) < 1e-12
+
+
+def test_window_edge_value_is_omega_reading():
+    # Eq. K_approx with the sinc reading of Omega: P(lam~ +- delta) ~= 0.176 for large K
+    for lam_t in (-0.6, 0.0, 0.3):
+        K = 1000
+        delta = dos.K_APPROX_CONSTANT * math.sqrt(1 - lam_t ** 2) / K
+        v = ch.filter_value([lam_t - delta, lam_t + delta], lam_t, K)
+        assert np.all(np.abs(v - dos.OMEGA) < 0.004)
+
+
+def test_expected_krylov_dim_printed_formula():
+    for l in open(os.path.join(GOLD, "expected_krylov_dim.txt")):
+        if not l.startswith("#"):
+            h, b, e, m = l.split()
+            assert dos.expected_krylov_dim(int(h), int(b), float(e)) == int(m)
+
+
+def test_clenshaw_equals_forward_sum_and_spectral_definition():
+    H, w, U = _xxz12()
+    Ec, dE = 0.5 * (w[-1] + w[0]), 0.5 * (w[-1] - w[0]) * 1.001
+    Ht = ch.rescale(H, Ec, dE)
+    V = lz.start_block(H.D, 4, 3)
+    a = ch.filter_coefficients(0.13, 150)
+    W1 = ch.clenshaw_apply(Ht, V, a)
+    W2 = ch.forward_chebyshev_sum(Ht, V, a)
+    Pdiag = ch.filter_value((w - Ec) / dE, 0.13, 150)
+    W3 = U @ (Pdiag[:, None] * (U.T @ V))
+    scale = np.abs(W3).max()
+    assert np.abs(W1 - W3).max() < 1e-12 * max(scale, 1)
+    assert np.abs(W2 - W3).max() < 1e-12 * max(scale, 1)
+
+
+def test_clenshaw_step_composes_to_apply():
+    H, w, _ = _xxz12()
+    Ht = ch.rescale(H, 0.1, 7.0)
+    V = lz.start_block(H.D, 3, 5)
+    a = ch.filter_coefficients(-0.2, 9)
+    b1 = np.zeros_like(V)
+    b2 = np.zeros_like(V)
+    for i in range(9, 0, -1):
+        b2, b1 = b1, ch.clenshaw_step(Ht, V, b1, b2, a[i], 2.0)
+    W = ch.clenshaw_step(Ht, V, b1, b2, a[0], 1.0)
+    assert np.abs(W - ch.clenshaw_apply(Ht, V, a)).max() < 1e-14
+
+
+def test_rescale_maps_spectrum():
+    H, w, _ = _xxz12()
+    Ec, dE = 0.3, 9.0
+    wt = np.linalg.eigvalsh(ch.rescale(H, Ec, dE).dense())
+    assert np.max(np.abs(wt - (w - Ec) / dE)) < 1e-14
+
+
+def test_exact_moments_equal_spectrum_moments():
+    H, w, _ = _xxz12()
+    Ht = ch.rescale(H, -0.4, 8.0)
+    mu, G = dos.exact_moments(Ht)
+    wt = (w + 0.4) / 8.0
+    assert abs(mu - wt.mean()) < 1e-14 and abs(G - wt.std()) < 1e-13
+
+
+def test_K_bisection_agrees_with_K_approx():
+    for lam_t in (-0.3, 0.0, 0.25):
+        delta = 0.003
+        kb = dos.bisect_K(lam_t, delta)
+        ka = dos.k_approx(lam_t, delta)
+        assert abs(kb - ka) / ka < 0.01
+
+
+@pytest.mark.parametrize("n", [6, 12, 20])
+def test_dense_eigh_against_jacobi(n):
+    H = hm.xxz_hamiltonian(pi.xxz_params(6 if n == 20 else 4 + (n == 12) * 2, W=1.5, seed=n))
+    A = H.dense()
+    wj, Qj = dense.jacobi_eigh(A)
+    w, _ = np.linalg.eigh(A)
+    assert np.max(np.abs(w - wj)) < 1e-13 * np.abs(w).max()
+    assert np.max(np.abs(A @ Qj - Qj * wj)) < 1e-12 * np.abs(w).max()
+
+
+def test_lanczos_extrema_against_dense():
+    H, w, _ = _xxz12()
+    b = lz.lanczos_extrema(H, tol=1e-10)
+    hn = max(abs(w[0]), abs(w[-1]))
+    assert abs(b["emin"] - w[0]) <= 1e-10 * hn and abs(b["emax"] - w[-1]) <= 1e-10 * hn
+
+
+def _solve_small(H, w, nev, s, eps, seed=2024, **kw):
+    b = lz.lanczos_extrema(H)
+    Ec, dE = lz.padded_interval(b["emin"], b["emax"], b["rmin"], b["rmax"])
+    lam = b["emin"] + eps * (b["emax"] - b["emin"])
+    Ht = ch.rescale(H, Ec, dE)
+    mu, G = dos.exact_moments(Ht)
+    nev_g = dos.guard_count(nev)
+    K = dos.choose_K((lam - Ec) / dE, nev_g, H.D, mu, G)
+    r = lz.polfed(H, lam, nev, K, s, Ec, dE, seed=seed, **kw)
+    return r, lam
+
+
+def test_polfed_oracle_matches_dense_xxz_L12():
+    H, w, _ = _xxz12()
+    r, lam = _solve_small(H, w, 20, 8, 0.5)
+    sel = dense.nearest(w, lam, 20)
+    hn = np.abs(w).max()
+    assert r["converged"]
+    assert np.max(np.abs(r["E"] - w[sel])) <= 1e-10 * hn
+    assert np.max(r["res"]) <= 1e-9 * hn
+
+
+@pytest.mark.parametrize("model", ["qsun", "hubbard"])
+def test_polfed_oracle_matches_dense_other_models(model):
+    if model == "qsun":
+        H = hm.qsun_hamiltonian(pi.qsun_params(N=3, L=7, seed=3001))
+    else:
+        H = hm.hubbard_hamiltonian(pi.hubbard_params(6, 3, 3, t=1.0, U=1.0, W=4.0, seed=4001))
+    w, _ = dense.eigh_dense(H)
+    r, lam = _solve_small(H, w, 12, 4, 0.45)
+    sel = dense.nearest(w, lam, 12)
+    hn = np.abs(w).max()
+    assert np.max(np.abs(r["E"] - w[sel])) <= 1e-10 * hn
+    assert np.max(r["res"]) <= 1e-9 * hn
+
+
+def test_block_lanczos_invariants():
+    H, w, _ = _xxz12()
+    b = lz.lanczos_extrema(H)
+    Ec, dE = lz.padded_interval(b["emin"], b["emax"], b["rmin"], b["rmax"])
+    r = lz.polfed(H, 0.0, 10, 120, 4, Ec, dE, check_first=6, check_every=1000, return_state=True)
+    V, HL, Ht, a = r["V"], r["HL"], r["Ht"], r["a"]
+    M = V.shape[1]
+    assert np.abs(V.T @ V - np.eye(M)).max() < 1e-13
+    PV = ch.clenshaw_apply(Ht, V, a)
+    HLx = V.T @ PV
+    # block tridiagonal projection, B upper triangular
+    assert np.abs(HL - HLx).max() < 1e-12
+    s = 4
+    for k in range(M // s - 1):
+        Bk = HL[(k + 1) * s:(k + 2) * s, k * s:(k + 1) * s]
+        assert np.abs(np.tril(Bk, -1)).max() == 0.0
+    # residual identity: ||P u - theta u|| = ||B_{m+1} tau_m|| (Sec. 2.2)
+    th, T = np.linalg.eigh(HL)
+    B = r["B"]
+    for j in (M - 1, M - 3, M - 7):
+        u = V @ T[:, j]
+        lhs = np.linalg.norm(ch.clenshaw_apply(Ht, u[:, None], a)[:, 0] - th[j] * u)
+        rhs = np.linalg.norm(B @ T[M - s:, j])
+        assert abs(lhs - rhs) < 1e-12

@@ -1,0 +1,160 @@
+"""Pins of the oracle's Hamiltonians: closed forms, brute force, counts (CPU only)."""
+import math
+import os
+import itertools
+
+import numpy as np
+import pytest
+
+import pf_inputs as pi
+from oracle import hamiltonian as hm, dense, basis
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_counts():
+    out = {}
+    for l in open(os.path.join(GOLD, "xxz_offdiag_counts.txt")):
+        if not l.startswith("#"):
+            L, D, n = map(int, l.split())
+            out[L] = (D, n)
+    return out
+
+
+@pytest.mark.parametrize("L", [4, 6, 8, 10, 12, 14, 16])
+def test_xxz_offdiag_count_matches_paper_closed_form(L):
+    D, noff = _golden_counts()[L]
+    H = hm.xxz_hamiltonian(pi.xxz_params(L, W=1.0, seed=5))
+    assert H.D == D
+    assert H.nnz - D == noff            # diagonal always stored
+
+
+def test_xxz_is_symmetric_bitwise_and_rows_sorted():
+    H = hm.xxz_hamiltonian(pi.xxz_params(12, W=2.0, seed=1001))
+    A = H.scipy()
+    assert (A != A.T).nnz == 0
+    for r in range(H.D):
+        c = H.indices[H.indptr[r]:H.indptr[r + 1]]
+        assert np.all(np.diff(c) > 0) and r in c
+
+
+@pytest.mark.parametrize("L,N", [(4, 2), (6, 3), (8, 4), (10, 5), (12, 6), (8, 3)])
+def test_xx_chain_free_fermion_closed_form(L, N):
+    H = hm.xxz_hamiltonian(pi.xxz_params(L, N=N, J=1.3, Delta=0.0, W=0.0))
+    w, _ = dense.eigh_dense(H)
+    assert np.max(np.abs(w - dense.xx_spectrum(L, N, 1.3))) < 1e-12
+
+
+def test_xxz_wrong_boundary_condition_is_detected():
+    # the open chain does NOT have the periodic closed form (guards the bond list)
+    H = hm.xxz_hamiltonian(pi.xxz_params(8, J=1.0, Delta=0.0, W=0.0, bc=hm.OBC))
+    w, _ = dense.eigh_dense(H)
+    assert np.max(np.abs(w - dense.xx_spectrum(8, 4))) > 0.1
+
+
+def test_heisenberg_ring_L4():
+    line = [l for l in open(os.path.join(GOLD, "known_spectra.txt")) if l.startswith("heisenberg_ring_L4_sz0")][0]
+    ref = np.array(list(map(float, line.split()[1:])))
+    w, _ = dense.eigh_dense(hm.xxz_hamiltonian(pi.xxz_params(4, J=1.0, Delta=1.0, W=0.0)))
+    assert np.max(np.abs(w - ref)) < 1e-13
+
+
+def test_xxz_diagonal_brute_force():
+    p = pi.xxz_params(10, J=0.7, Delta=1.9, W=3.0, seed=44)
+    H = hm.xxz_hamiltonian(p)
+    st = H.states
+    dg = H.data[H.diag_mask()]
+    for r, s in enumerate(st):
+        sz = [((s >> i) & 1) - 0.5 for i in range(p.L)]
+        e = sum(p.J * p.Delta * sz[i] * sz[(i + 1) % p.L] for i in range(p.L))
+        e += sum(p.h[i] * sz[i] for i in range(p.L))
+        assert abs(dg[r] - e) < 1e-13
+
+
+@pytest.mark.parametrize("L", [6, 8, 12])
+def test_xxz_trace_closed_form(L):
+    # Tr H / D = -J Delta L / (4 (L-1)) at S^z_tot = 0 with periodic bonds
+    p = pi.xxz_params(L, J=1.1, Delta=0.8, W=2.5, seed=9)
+    H = hm.xxz_hamiltonian(p)
+    tr = H.data[H.diag_mask()].sum() / H.D
+    assert abs(tr + p.J * p.Delta * L / (4.0 * (L - 1))) < 1e-12
+
+
+def test_xxz_L2_duplicates_are_summed():
+    H = hm.xxz_hamiltonian(pi.xxz_params(2, J=1.0, Delta=0.0, W=0.0))
+    assert H.nnz == 4
+    assert np.allclose(H.dense(), [[0, 1.0], [1.0, 0]])
+
+
+def test_qsun_structure_and_counts():
+    p = pi.qsun_params(N=3, L=7, seed=3)
+    H = hm.qsun_hamiltonian(p)
+    assert H.D == 1 << 10
+    assert np.all(np.diff(H.indptr) == (1 << 3) + 7)
+    A = H.scipy()
+    assert (A != A.T).nnz == 0
+
+
+def test_qsun_dot_only_spectrum_is_kronecker():
+    p = pi.qsun_params(N=2, L=3, g0=0.0, h0=0.0, wh=0.0, seed=11)
+    H = hm.qsun_hamiltonian(p)
+    w, _ = dense.eigh_dense(H)
+    A = p.A
+    hd = (A + A.T) / math.sqrt(2.0) * p.gamma / math.sqrt(5.0)
+    ref = np.sort(np.repeat(np.linalg.eigvalsh(hd), 1 << 3))
+    assert np.max(np.abs(w - ref)) < 1e-13
+
+
+def test_qsun_fields_and_rays_closed_forms():
+    # fields only: E = sum_j h_j (b_j - 1/2)
+    p = pi.qsun_params(N=1, L=4, gamma=0.0, g0=0.0, seed=2)
+    w, _ = dense.eigh_dense(hm.qsun_hamiltonian(p))
+    ref = sorted(sum(p.h[j] * (b[j] - 0.5) for j in range(4)) for b in itertools.product([0, 1], repeat=4) for _ in range(2))
+    assert np.max(np.abs(w - np.array(ref))) < 1e-13
+    # rays only, one dot spin: all S^x commute, E = sigma_d sum_j c_j sigma_j / 4
+    p = pi.qsun_params(N=1, L=3, gamma=0.0, g0=1.3, alpha=0.6, h0=0.0, wh=0.0, seed=8)
+    w, _ = dense.eigh_dense(hm.qsun_hamiltonian(p))
+    c = [p.g0 * p.alpha ** (j + p.u_noise[j]) for j in range(3)]
+    ref = sorted(sd * sum(c[j] * sj[j] for j in range(3)) / 4.0
+                 for sd in (-1, 1) for sj in itertools.product([-1, 1], repeat=3))
+    assert np.max(np.abs(w - np.array(ref))) < 1e-13
+
+
+def test_qsun_dot_normalisation_statistical():
+    # App. A.2: ||R_dot||^2 = Tr(R_dot^2)/D ~= 1 (expectation exactly 1 for (A+A^T)/sqrt 2 / sqrt(2^N+1))
+    vals = []
+    for s in range(300):
+        p = pi.qsun_params(N=3, L=1, seed=100 + s)
+        hd = hm.qsun_dot_matrix(p)
+        vals.append(np.sum(hd * hd) / 8.0)
+    assert abs(np.mean(vals) - 1.0) < 0.05
+
+
+@pytest.mark.parametrize("L,Nu,Nd", [(4, 2, 2), (5, 2, 3), (6, 3, 3)])
+def test_hubbard_free_fermions_open_chain(L, Nu, Nd):
+    H = hm.hubbard_hamiltonian(pi.hubbard_params(L, Nu, Nd, t=0.9, U=0.0, W=0.0))
+    w, _ = dense.eigh_dense(H)
+    assert np.max(np.abs(w - dense.hubbard_free_spectrum(L, Nu, Nd, 0.9))) < 1e-12
+
+
+def test_hubbard_dimer_closed_form():
+    U = 2.7
+    H = hm.hubbard_hamiltonian(pi.hubbard_params(2, 1, 1, t=1.0, U=U, W=0.0))
+    w, _ = dense.eigh_dense(H)
+    r = math.sqrt(U * U + 16.0)
+    assert np.max(np.abs(w - np.sort([0.0, U, (U - r) / 2, (U + r) / 2]))) < 1e-13
+
+
+def test_hubbard_atomic_limit_and_counts():
+    p = pi.hubbard_params(6, 3, 3, t=0.0, U=1.7, W=2.0, seed=7)
+    H = hm.hubbard_hamiltonian(p)
+    dg = H.data[H.diag_mask()]
+    Dd = len(H.dns)
+    for r in range(H.D):
+        up, dn = H.ups[r // Dd], H.dns[r % Dd]
+        e = sum(p.U * ((up >> i) & 1) * ((dn >> i) & 1) + p.mu[i] * (((up >> i) & 1) + ((dn >> i) & 1)) for i in range(6))
+        assert abs(dg[r] - e) < 1e-13
+    # off-diagonal count, open chain: per species (L-1) * 2 * binom(L-2, N-1) configs x other species
+    L, N = 6, 3
+    per = (L - 1) * 2 * math.comb(L - 2, N - 1) * math.comb(L, N)
+    assert H.nnz - H.D == 2 * per
