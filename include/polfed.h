@@ -1,0 +1,234 @@
+/*
+ * polfed.h -- C ABI of the B300 (sm_103a) POLFED hot path.
+ *
+ * POLFED computes the eigenpairs of a sparse real-symmetric Hamiltonian H that lie
+ * nearest a target energy lambda by running block Lanczos on the polynomial filter
+ * P(H~) = (1/chi) sum_{n=0..K} c_n T_n(H~) (paper, Sec. 3.2, Eq. transformation and
+ * Eq. transformationCoefficients), applied on the fly with the Clenshaw recurrence
+ * (Sec. 4.4, Eq. clenshaw_chebyshev_prod).  H~ = (H - E_c)/dE is H rescaled into
+ * [-1, 1] (Eq. rescaledMatrix).
+ *
+ * Conventions for every entry point:
+ *  - Return value: a pf_status.  No call aborts, traps or throws across this ABI.
+ *  - Pointers documented "device" must be CUDA device memory of the current device;
+ *    "host" pointers are ordinary host memory.  The caller owns every buffer it
+ *    passes in; the library never frees caller memory.
+ *  - Handles (pf_basis, pf_ham) are owned by the library and released with
+ *    pf_free_basis / pf_free_ham.  Their device memory comes from the allocator
+ *    installed by pf_set_allocator (default: cudaMallocAsync / cudaFreeAsync).
+ *  - Work is enqueued on the given stream.  Calls that return host scalars
+ *    synchronise that stream before returning.  A handle must not be used by two
+ *    threads at once; distinct handles are independent.
+ *  - Vector blocks are D x s, row-major (the s entries of a row are contiguous).
+ */
+#ifndef POLFED_H
+#define POLFED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* pf_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  PF_OK = 0,
+  PF_EINVAL = 1,    /* bad argument: shape, nev > D, K < 1, eps outside [0,1], ...  */
+  PF_ENOMEM = 2,    /* the allocator returned NULL                                    */
+  PF_ENOTCONV = 3,  /* not converged within the Krylov budget; outputs hold the best
+                       pairs found, with their residuals                              */
+  PF_ETIMEOUT = 4,  /* a device-side wait reached its iteration limit                 */
+  PF_ECUDA = 5,     /* a CUDA call failed; pf_last_cuda_error() names it              */
+  PF_ESTATE = 6,    /* call order violated (e.g. solve before pf_spectral_bounds)     */
+  PF_EBREAKDOWN = 7 /* Cholesky-QR breakdown the recovery path could not repair       */
+} pf_status;
+
+typedef enum { PF_MODEL_XXZ = 0, PF_MODEL_QSUN = 1, PF_MODEL_HUBBARD = 2 } pf_model_kind;
+typedef enum { PF_BC_PERIODIC = 0, PF_BC_OPEN = 1 } pf_boundary;
+typedef enum { PF_F64 = 0, PF_F32 = 1 } pf_precision;
+
+/* Model description (paper App. A).
+ *  XXZ (Eq. xxz): L sites, N up spins (S^z_tot sector), couplings J, Delta, fields h_i.
+ *     Bit i of a basis state is 1 when spin i is up; basis = L-bit integers with
+ *     popcount N in ascending order; row = rank in that order.
+ *  Quantum sun (Eq. qsun): N dot spins in the top N bits, L outer spins in bits
+ *     0..L-1; D = 2^(N+L), row = state.  H_dot = gamma (A + A^T)/sqrt(2)/sqrt(2^N+1);
+ *     ray j couples dot spin n(j) and outer spin j with g0 alpha^(j + u_noise_j)/4.
+ *  Fermi-Hubbard (not in the paper): L sites, N_up / N_dn fermions, hopping t,
+ *     interaction U, potentials mu_i; row = rank_up * D_dn + rank_dn; Jordan-Wigner
+ *     order: all up modes, then all down modes.                                     */
+typedef struct {
+  int32_t kind;     /* pf_model_kind                                   */
+  int32_t L;        /* sites (XXZ, Hubbard) or outer spins (quantum sun) */
+  int32_t N;        /* XXZ: up spins; quantum sun: dot spins            */
+  int32_t N_up, N_dn;
+  int32_t bc;       /* pf_boundary (XXZ, Hubbard)                       */
+  double J, Delta;  /* XXZ                                              */
+  double t, U;      /* Hubbard                                          */
+  double g0, alpha, gamma; /* quantum sun                               */
+} pf_model;
+
+/* Disorder and random couplings, host arrays (copied during the call).          */
+typedef struct {
+  const double* h;        /* XXZ and quantum-sun fields, [L]                        */
+  const double* mu;       /* Hubbard on-site potentials, [L]                        */
+  const double* A;        /* quantum-sun raw normals, [2^N * 2^N] row-major         */
+  const double* u_noise;  /* quantum-sun exponent noise u_j - j, [L]                */
+  const int32_t* n_of_j;  /* quantum-sun dot spin coupled to outer spin j, [L]      */
+} pf_params;
+
+typedef struct pf_basis pf_basis;
+typedef struct pf_ham pf_ham;
+
+/* Device-memory hook.  alloc(ctx, bytes, stream) returns device memory or NULL;
+ * release(ctx, ptr, stream) returns it.  Passing NULL for both restores the
+ * default (cudaMallocAsync / cudaFreeAsync on the call's stream).             */
+typedef void* (*pf_alloc_fn)(void* ctx, size_t bytes, pf_stream_t stream);
+typedef void (*pf_free_fn)(void* ctx, void* ptr, pf_stream_t stream);
+pf_status pf_set_allocator(pf_alloc_fn alloc, pf_free_fn release, void* ctx);
+
+const char* pf_status_str(pf_status s);
+const char* pf_last_cuda_error(void);   /* thread-local text of the last CUDA failure */
+
+/* ---------------------------------------------------------------------------
+ * (a1) Basis enumeration.  Sec. 2 intro / App. A.2: the S^z sector of L spins with
+ * N up has dimension binom(L, N).  Unranking uses the combinatorial number system.
+ *   m   : host, model description.
+ *   out : receives a new handle.
+ * Errors: PF_EINVAL for L outside [1, 32] (XXZ/Hubbard; N+L <= 30 for the quantum
+ * sun), N outside [0, L]; PF_ENOMEM; PF_ECUDA.                                  */
+pf_status pf_build_basis(const pf_model* m, pf_basis** out, pf_stream_t stream);
+/* D; for Hubbard also the up/down table lengths (else 0).  Synchronises.        */
+pf_status pf_basis_info(const pf_basis* b, int64_t* D, int64_t* D_up, int64_t* D_dn);
+/* Device pointer to the state table: XXZ states[D]; Hubbard up[D_up] followed by
+ * dn[D_dn]; quantum sun: NULL (row = state).  Owned by the handle.             */
+pf_status pf_basis_states(const pf_basis* b, const uint32_t** states);
+void pf_free_basis(pf_basis* b);
+
+/* ---------------------------------------------------------------------------
+ * (a2) Hamiltonian construction: CSR of H (count pass, scan, fill), FP64 values.
+ * Eq. xxz, Eq. qsun, Hubbard as above.  Columns ascending in each row; diagonal
+ * always stored; repeated (row, col) terms summed in generation order.  Diagonal
+ * values are summed term by term without fused multiply-add, so they agree bit for
+ * bit with a plain left-to-right FP64 sum.
+ *   b, m : the basis built from the same model; p: host disorder arrays.
+ * Errors: PF_EINVAL (model/basis mismatch, missing arrays); PF_ENOMEM; PF_ECUDA.   */
+pf_status pf_build_hamiltonian(const pf_basis* b, const pf_model* m, const pf_params* p,
+                               pf_ham** out, pf_stream_t stream);
+/* D, nnz, and ||H|| = max(|Emin|, |Emax|) once pf_spectral_bounds ran (else 0).  */
+pf_status pf_ham_info(const pf_ham* H, int64_t* D, int64_t* nnz, double* norm_est);
+/* Device CSR arrays (row_ptr int64[D+1], col int32[nnz], val float64[nnz]) of H. */
+pf_status pf_ham_csr(const pf_ham* H, const int64_t** row_ptr, const int32_t** col,
+                     const double** val);
+void pf_free_ham(pf_ham* H);
+
+/* ---------------------------------------------------------------------------
+ * (a3) Spectral bounds by FP64 block Lanczos on H (Sec. 2.1-2.2, Eq. lan_criterion),
+ * stopping when both extreme Ritz pairs have residual <= tol * max|theta|.  Then
+ * sets the rescaling (Eq. rescaledMatrix) on the handle, over the interval padded
+ * by the residuals and 1e-3 of the half-width, and writes H~ in FP64 and FP32.
+ *   tol <= 0 selects 1e-10.  emin/emax/rmin/rmax: host outputs (rmin/rmax may be NULL).
+ * Synchronises.  Errors: PF_ENOTCONV, PF_ENOMEM, PF_ECUDA.                         */
+pf_status pf_spectral_bounds(pf_ham* H, double tol, double* emin, double* emax, double* rmin,
+                             double* rmax, pf_stream_t stream);
+/* Set the rescaling directly (E_c, dE) and write H~ values; for tests and for callers
+ * that know their bounds.                                                          */
+pf_status pf_set_rescale(pf_ham* H, double Ec, double dE, pf_stream_t stream);
+/* Rescaling and the device arrays of H~ values (FP64 and FP32, CSR order).         */
+pf_status pf_ham_rescaled(const pf_ham* H, double* Ec, double* dE, const double** val64,
+                          const float** val32);
+
+/* Exact moments of the spectrum of H~ from traces: mu~ = Tr H~ / D,
+ * G~^2 = Tr H~^2 / D - mu~^2 (Eq. dos_gaussian uses them).  Synchronises.          */
+pf_status pf_ham_moments(pf_ham* H, double* mu_t, double* G_t, pf_stream_t stream);
+
+/* (a4) Filter coefficients a_n = c_n/chi, n = 0..K (Eq. transformation,
+ * Eq. transformationCoefficients), computed on the device.  coeffs: host [K+1].     */
+pf_status pf_filter_coefficients(double lam_t, int32_t K, double* coeffs, pf_stream_t stream);
+
+/* Degree K from the Gaussian DOS with exact moments (Eq. dos_gaussian, Eq. Nev,
+ * Eq. K_approx): K = ceil(2.655 sqrt(1 - lam~^2) * 2 rho(lam~) / nev_g),
+ * nev_g = ceil(1.2 nev).  target_eps: lambda = Emin + eps (Emax - Emin).  Synchronises. */
+pf_status pf_choose_K(pf_ham* H, double target_eps, int32_t nev, int32_t* K, pf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * (a5) One fused Clenshaw step (Eq. clenshaw_chebyshev_prod):
+ *     out = a * V + alpha * (H~ B1) - beta * B2
+ * with alpha = 2 for b_i (i >= 1) and alpha = 1 for the closing line P V = a_0 V +
+ * H~ b_1 - b_2.  beta in {0, 1}; B2 may be NULL when beta = 0; out may alias B2
+ * (b_i overwrites b_{i+2}); out must not alias V or B1.  alpha = 0 skips the SpMM
+ * (B1 may then be NULL).  If use_H is nonzero the unscaled H is used instead of H~
+ * (then only precision PF_F64 is allowed).
+ *   prec: PF_F64 (double blocks, FP64 values) or PF_F32 (float blocks, FP32 values).
+ *   s   : block width, one of 1, 2, 4, 8, 16, 32, 64.
+ * Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ECUDA.                             */
+pf_status pf_clenshaw_step(const pf_ham* H, int32_t prec, int32_t s, const void* V,
+                           const void* B1, const void* B2, void* out, double a, double alpha,
+                           double beta, int32_t use_H, pf_stream_t stream);
+
+/* W = P(H~) V for a D x s block: the whole recurrence, K steps, with two internal
+ * D x s auxiliary blocks.  coeffs: host [K+1].  V and W are double blocks for
+ * PF_F64; for PF_F32 they are float blocks.                                        */
+pf_status pf_filter_apply(const pf_ham* H, int32_t prec, int32_t s, const void* V, void* W,
+                          const double* coeffs, int32_t K, pf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * (a6-a10) The solve: block Lanczos on P(H~) with full reorthogonalisation (two
+ * classical Gram-Schmidt passes), shifted Cholesky QR, the block-tridiagonal
+ * Lanczos matrix, periodic convergence checks (Eq. blocklan_criterion), Ritz
+ * extraction with a Rayleigh-Ritz in H on the converged block, residuals
+ * ||H u - E u|| (Sec. 4.3), and, for PF_F32, FP64 refinement passes.
+ */
+typedef struct {
+  int32_t block;          /* s: 1..64, power of two; 0 = 32                          */
+  int32_t precision;      /* pf_precision of the filter recurrence                   */
+  int32_t nev_guard;      /* Ritz pairs converged; 0 = ceil(1.2 nev)                  */
+  int32_t check_first;    /* first check at this block step; 0 = rule (see DESIGN)   */
+  int32_t check_every;    /* check interval in block steps; 0 = rule                 */
+  int32_t max_blocks;     /* Krylov budget in blocks; 0 = from eta                    */
+  double eta;             /* over-allocation of the expected Krylov size; 0 = 1.5    */
+  double tol;             /* P-space tolerance on ||B tau|| (FP64 filter); 0 = 1e-10 */
+  double tol_f32;         /* same for the FP32 filter stage; 0 = 1e-7                */
+  double res_tol;         /* final acceptance ||Hu - Eu|| <= res_tol ||H||; 0 = 1e-9 */
+  int32_t refine_passes;  /* FP32 path: max FP64 filter passes; <0 = none, 0 = 3     */
+  int32_t refine_K;       /* degree of the refinement filter; 0 = K                  */
+  uint64_t seed;          /* start block: v[r,c] = SplitMix64(seed, r*s+c) - 1/2     */
+  int32_t use_abs_target; /* nonzero: target is target_abs (absolute energy)         */
+  double target_abs;
+} pf_solve_opts;
+
+typedef struct {
+  int32_t status, K, blocks, krylov_dim, nev_guard, converged, checks, refine_passes;
+  int64_t filter_steps;        /* Clenshaw steps executed (all precisions)           */
+  int64_t filter_steps_f64;    /* of which FP64                                        */
+  double emin, emax, Ec, dE, lambda, lambda_t, hnorm;
+  double max_residual;         /* max ||Hu - Eu|| over the returned pairs              */
+  double ms_filter, ms_orth, ms_qr, ms_check, ms_extract, ms_refine, ms_total;
+} pf_report;
+
+/* Fill o with the defaults listed in pf_solve_opts.                                */
+void pf_default_opts(pf_solve_opts* o);
+
+/*   H          : handle with bounds set (pf_spectral_bounds or pf_set_rescale).
+ *   target_eps : normalised energy, lambda = Emin + eps (Emax - Emin), eps in [0,1]
+ *                (ignored when o->use_abs_target).
+ *   nev        : eigenpairs returned, 1 <= nev <= D.  K: filter degree >= 1.
+ *   evals      : host [nev], ascending.      resid: host [nev], ||H u - E u||.
+ *   evecs      : device, D x nev column-major (may be NULL).
+ *   rep        : host, may be NULL.
+ * Synchronises.  Errors: PF_EINVAL, PF_ESTATE, PF_ENOMEM, PF_ENOTCONV (outputs written),
+ * PF_EBREAKDOWN, PF_ECUDA.                                                        */
+pf_status pf_polfed_solve(pf_ham* H, double target_eps, int32_t nev, int32_t K,
+                          const pf_solve_opts* o, double* evals, double* evecs, double* resid,
+                          pf_report* rep, pf_stream_t stream);
+
+/* Start block as the solve draws it: v[r,c] = uniform(SplitMix64(seed, r*s+c)) - 1/2,
+ * uniform = top 53 bits * 2^-53 (Steele, Lea & Flood 2014).  out: device double [D*s]. */
+pf_status pf_start_block(int64_t D, int32_t s, uint64_t seed, double* out, pf_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POLFED_H */

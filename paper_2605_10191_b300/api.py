@@ -1,0 +1,283 @@
+"""Python binding of libpolfed (argument marshalling only; every step runs in the CUDA library).
+
+PyTorch supplies device memory (through the allocator hook) and streams.  Vector
+blocks are torch tensors of shape (D, s), row-major, float64 or float32, on the
+current CUDA device.
+"""
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import check, lib
+
+_ALLOC_REFS = []
+
+
+def _install_torch_allocator():
+    """Route the library's device allocations through PyTorch's caching allocator."""
+    if _ALLOC_REFS:
+        return
+
+    def _alloc(ctx, nbytes, stream):
+        try:
+            dev = torch.cuda.current_device()
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or None))
+        except Exception:
+            return None
+
+    def _free(ctx, ptr, stream):
+        if ptr:
+            torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = L.ALLOC_FN(_alloc), L.FREE_FN(_free)
+    _ALLOC_REFS.extend([a, f])
+    check(lib().pf_set_allocator(a, f, None), "pf_set_allocator")
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _dbl_arr(x):
+    if x is None:
+        return None, None
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class _DevView:
+    """Non-owning __cuda_array_interface__ wrapper of a library-owned device array."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (ptr, False),
+                                         "version": 2, "strides": None}
+
+
+def _copy_device(ptr, n, typestr, torch_dtype):
+    if n == 0:
+        return torch.empty(0, dtype=torch_dtype, device="cuda")
+    t = torch.as_tensor(_DevView(ptr, (n,), typestr), device="cuda")
+    return t.clone()
+
+
+@dataclass
+class Model:
+    kind: int
+    L: int
+    N: int = 0
+    N_up: int = 0
+    N_dn: int = 0
+    bc: int = 0
+    J: float = 1.0
+    Delta: float = 1.0
+    t: float = 1.0
+    U: float = 0.0
+    g0: float = 1.0
+    alpha: float = 0.75
+    gamma: float = 1.0
+    h: object = None
+    mu: object = None
+    A: object = None
+    u_noise: object = None
+    n_of_j: object = None
+
+    @staticmethod
+    def from_params(p):
+        """From a parameter record with the attribute names of pf_inputs.workloads."""
+        k = p.kind
+        if k == L.PF_MODEL_XXZ:
+            return Model(kind=k, L=p.L, N=p.N, bc=p.bc, J=p.J, Delta=p.Delta, h=p.h)
+        if k == L.PF_MODEL_QSUN:
+            return Model(kind=k, L=p.L, N=p.N, g0=p.g0, alpha=p.alpha, gamma=p.gamma, h=p.h, A=p.A,
+                         u_noise=p.u_noise, n_of_j=p.n_of_j)
+        if k == L.PF_MODEL_HUBBARD:
+            return Model(kind=k, L=p.L, N_up=p.N_up, N_dn=p.N_dn, bc=p.bc, t=p.t, U=p.U, mu=p.mu)
+        raise ValueError(f"unknown model kind {k}")
+
+    def c_model(self):
+        return L.pf_model(kind=self.kind, L=self.L, N=self.N, N_up=self.N_up, N_dn=self.N_dn, bc=self.bc,
+                          J=self.J, Delta=self.Delta, t=self.t, U=self.U, g0=self.g0, alpha=self.alpha,
+                          gamma=self.gamma)
+
+
+class Basis:
+    def __init__(self, model, stream=None):
+        _install_torch_allocator()
+        self.model = model
+        h = C.c_void_p()
+        check(lib().pf_build_basis(C.byref(model.c_model()), C.byref(h), _stream(stream)), "pf_build_basis")
+        self.handle = h
+        D, Du, Dd = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().pf_basis_info(h, C.byref(D), C.byref(Du), C.byref(Dd)), "pf_basis_info")
+        self.D, self.D_up, self.D_dn = D.value, Du.value, Dd.value
+
+    def states(self):
+        """Copy of the state table (XXZ: [D]; Hubbard: up table then down table) as int64."""
+        p = C.c_void_p()
+        check(lib().pf_basis_states(self.handle, C.byref(p)), "pf_basis_states")
+        n = self.D if self.model.kind == L.PF_MODEL_XXZ else (self.D_up + self.D_dn
+                                                              if self.model.kind == L.PF_MODEL_HUBBARD else 0)
+        if not p.value:
+            return torch.empty(0, dtype=torch.int64, device="cuda")
+        return _copy_device(p.value, n, "<u4", torch.int32).to(torch.int64) & 0xFFFFFFFF
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None):
+                lib().pf_free_basis(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+@dataclass
+class SolveResult:
+    evals: np.ndarray
+    resid: np.ndarray
+    evecs: torch.Tensor
+    report: dict
+    status: int
+
+
+class Hamiltonian:
+    """CSR Hamiltonian on the device (FP64) with its rescaled copies H~ (FP64, FP32)."""
+
+    def __init__(self, model, stream=None):
+        _install_torch_allocator()
+        self.model = model
+        self.basis = Basis(model, stream)
+        arrays = [_dbl_arr(model.h), _dbl_arr(model.mu), _dbl_arr(model.A), _dbl_arr(model.u_noise)]
+        nj = None
+        if model.n_of_j is not None:
+            nj = np.ascontiguousarray(np.asarray(model.n_of_j, dtype=np.int32))
+        self._keep = (arrays, nj)
+        prm = L.pf_params(h=arrays[0][1], mu=arrays[1][1], A=arrays[2][1], u_noise=arrays[3][1],
+                          n_of_j=nj.ctypes.data_as(C.POINTER(C.c_int32)) if nj is not None else None)
+        h = C.c_void_p()
+        check(lib().pf_build_hamiltonian(self.basis.handle, C.byref(model.c_model()), C.byref(prm), C.byref(h),
+                                         _stream(stream)), "pf_build_hamiltonian")
+        self.handle = h
+        D, nnz, nrm = C.c_int64(), C.c_int64(), C.c_double()
+        check(lib().pf_ham_info(h, C.byref(D), C.byref(nnz), C.byref(nrm)), "pf_ham_info")
+        self.D, self.nnz = D.value, nnz.value
+
+    @staticmethod
+    def from_params(p, stream=None):
+        return Hamiltonian(Model.from_params(p), stream)
+
+    def __del__(self):
+        try:
+            if getattr(self, "handle", None):
+                lib().pf_free_ham(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+    # ---- structure and values
+    def csr(self):
+        rp, col, val = C.c_void_p(), C.c_void_p(), C.c_void_p()
+        check(lib().pf_ham_csr(self.handle, C.byref(rp), C.byref(col), C.byref(val)), "pf_ham_csr")
+        torch.cuda.current_stream().synchronize()
+        return (_copy_device(rp.value, self.D + 1, "<i8", torch.int64),
+                _copy_device(col.value, self.nnz, "<i4", torch.int32),
+                _copy_device(val.value, self.nnz, "<f8", torch.float64))
+
+    def rescaled(self):
+        Ec, dE, v64, v32 = C.c_double(), C.c_double(), C.c_void_p(), C.c_void_p()
+        check(lib().pf_ham_rescaled(self.handle, C.byref(Ec), C.byref(dE), C.byref(v64), C.byref(v32)),
+              "pf_ham_rescaled")
+        torch.cuda.current_stream().synchronize()
+        return (Ec.value, dE.value, _copy_device(v64.value, self.nnz, "<f8", torch.float64),
+                _copy_device(v32.value, self.nnz, "<f4", torch.float32))
+
+    def norm(self):
+        D, nnz, nrm = C.c_int64(), C.c_int64(), C.c_double()
+        check(lib().pf_ham_info(self.handle, C.byref(D), C.byref(nnz), C.byref(nrm)), "pf_ham_info")
+        return nrm.value
+
+    # ---- bounds, rescaling, moments, K
+    def spectral_bounds(self, tol=1e-10, stream=None):
+        a, b, ra, rb = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+        check(lib().pf_spectral_bounds(self.handle, tol, C.byref(a), C.byref(b), C.byref(ra), C.byref(rb),
+                                       _stream(stream)), "pf_spectral_bounds")
+        return a.value, b.value, ra.value, rb.value
+
+    def set_rescale(self, Ec, dE, stream=None):
+        check(lib().pf_set_rescale(self.handle, float(Ec), float(dE), _stream(stream)), "pf_set_rescale")
+
+    def moments(self, stream=None):
+        mu, G = C.c_double(), C.c_double()
+        check(lib().pf_ham_moments(self.handle, C.byref(mu), C.byref(G), _stream(stream)), "pf_ham_moments")
+        return mu.value, G.value
+
+    def choose_K(self, eps, nev, stream=None):
+        K = C.c_int32()
+        check(lib().pf_choose_K(self.handle, float(eps), int(nev), C.byref(K), _stream(stream)), "pf_choose_K")
+        return K.value
+
+    # ---- kernels
+    def clenshaw_step(self, V, B1, B2, out, a, alpha, beta, use_H=False, stream=None):
+        prec = L.PF_F64 if V.dtype == torch.float64 else L.PF_F32
+        s = V.shape[1]
+        check(lib().pf_clenshaw_step(self.handle, prec, s, _ptr(V), _ptr(B1), _ptr(B2), _ptr(out), float(a),
+                                     float(alpha), float(beta), int(bool(use_H)), _stream(stream)),
+              "pf_clenshaw_step")
+        return out
+
+    def filter_apply(self, V, coeffs, W=None, stream=None):
+        prec = L.PF_F64 if V.dtype == torch.float64 else L.PF_F32
+        W = torch.empty_like(V) if W is None else W
+        c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+        check(lib().pf_filter_apply(self.handle, prec, V.shape[1], _ptr(V), _ptr(W),
+                                    c.ctypes.data_as(C.POINTER(C.c_double)), len(c) - 1, _stream(stream)),
+              "pf_filter_apply")
+        return W
+
+    # ---- the solve
+    def solve(self, eps, nev, K, block=32, precision="f64", return_vectors=True, target_abs=None, stream=None,
+              raise_on_notconv=True, **opts):
+        o = L.pf_solve_opts()
+        lib().pf_default_opts(C.byref(o))
+        o.block = block
+        o.precision = L.PF_F64 if precision == "f64" else L.PF_F32
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        if target_abs is not None:
+            o.use_abs_target = 1
+            o.target_abs = float(target_abs)
+        evals = np.zeros(nev)
+        resid = np.zeros(nev)
+        evecs = torch.empty((nev, self.D), dtype=torch.float64, device="cuda") if return_vectors else None
+        rep = L.pf_report()
+        st = lib().pf_polfed_solve(self.handle, float(eps), int(nev), int(K), C.byref(o),
+                                   evals.ctypes.data_as(C.POINTER(C.c_double)), _ptr(evecs),
+                                   resid.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep), _stream(stream))
+        if st not in (L.PF_OK, L.PF_ENOTCONV) or (st == L.PF_ENOTCONV and raise_on_notconv):
+            check(st, "pf_polfed_solve")
+        # evecs buffer is D x nev column-major == (nev, D) row-major; expose as (D, nev)
+        return SolveResult(evals=evals, resid=resid, evecs=evecs.t() if evecs is not None else None,
+                           report=rep.as_dict(), status=st)
+
+
+def filter_coefficients(lam_t, K, stream=None):
+    _install_torch_allocator()
+    c = np.zeros(K + 1)
+    check(lib().pf_filter_coefficients(float(lam_t), int(K), c.ctypes.data_as(C.POINTER(C.c_double)),
+                                       _stream(stream)), "pf_filter_coefficients")
+    return c
+
+
+def start_block(D, s, seed, stream=None):
+    out = torch.empty((D, s), dtype=torch.float64, device="cuda")
+    check(lib().pf_start_block(int(D), int(s), C.c_uint64(seed), _ptr(out), _stream(stream)), "pf_start_block")
+    return out

@@ -1,0 +1,166 @@
+// Internal definitions shared by the CUDA translation units of libpolfed.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+#include <stdio.h>
+#include <vector>
+#include "../../include/polfed.h"
+
+#define PF_MAX_S 64
+
+namespace pf {
+
+// ---------------------------------------------------------------- errors
+void set_cuda_error(cudaError_t e, const char* where);
+
+#define PF_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) {                            \
+      ::pf::set_cuda_error(_e, #call);                  \
+      return PF_ECUDA;                                  \
+    }                                                   \
+  } while (0)
+
+#define PF_LAUNCH_CHECK(name)                           \
+  do {                                                  \
+    cudaError_t _e = cudaGetLastError();                \
+    if (_e != cudaSuccess) {                            \
+      ::pf::set_cuda_error(_e, name);                   \
+      return PF_ECUDA;                                  \
+    }                                                   \
+  } while (0)
+
+#define PF_TRY(expr)                                    \
+  do {                                                  \
+    pf_status _s = (expr);                              \
+    if (_s != PF_OK) return _s;                         \
+  } while (0)
+
+// ---------------------------------------------------------------- memory
+void* dev_alloc(size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
+
+// RAII owner of one device allocation (internal scratch).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  pf_status alloc(size_t nbytes, cudaStream_t stream) {
+    release();
+    st = stream;
+    bytes = nbytes;
+    if (nbytes == 0) return PF_OK;
+    p = dev_alloc(nbytes, stream);
+    return p ? PF_OK : PF_ENOMEM;
+  }
+  void release() {
+    if (p) dev_free(p, st);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---------------------------------------------------------------- handles
+struct Basis {
+  pf_model m;
+  int64_t D = 0, D_up = 0, D_dn = 0;
+  uint32_t* states = nullptr;   // device
+  uint64_t* binom = nullptr;    // device, 33 x 33, binom[n*33+k]
+  cudaStream_t st = 0;
+};
+
+struct Ham {
+  pf_model m;
+  int64_t D = 0, nnz = 0;
+  int64_t* row_ptr = nullptr;   // device [D+1]
+  int32_t* col = nullptr;       // device [nnz]
+  double* val = nullptr;        // device [nnz], H
+  double* val_t = nullptr;      // device [nnz], H~ (FP64)
+  float* val32 = nullptr;       // device [nnz], H~ (FP32)
+  int has_rescale = 0, has_bounds = 0;
+  double Ec = 0, dE = 1, emin = 0, emax = 0, rmin = 0, rmax = 0, hnorm = 0;
+  cudaStream_t st = 0;
+};
+
+// binomial table n, k <= 32 (host)
+void host_binom(uint64_t* tab /*33*33*/);
+
+// ---------------------------------------------------------------- device helpers
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block-wide sum (power-of-two blockDim <= 1024); result valid in all threads.
+template <typename T>
+__device__ T block_sum(T v, T* sh /* >= 32 */) {
+  v = warp_sum(v);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  T r = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
+  if (w == 0) r = warp_sum(r);
+  if (threadIdx.x == 0) sh[0] = r;
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------- cross-unit API
+// Clenshaw step on raw CSR arrays (clenshaw.cu)
+pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* col, const void* val,
+                            int prec, int s, const void* V, const void* B1, const void* B2, void* out,
+                            double a, double alpha, double beta, cudaStream_t st);
+// W = P V for a D x s block (K steps); aux buffers are two D x s blocks of the filter type.
+pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs_host,
+                           const void* coeffs_dev, int K, void* aux0, void* aux1, cudaStream_t st);
+
+// Dense tall-skinny kernels (dense.cu).  Blocked storage: nb blocks, each D x s row-major,
+// block b at X + b*D*s.
+// C[nbX*s x nbY*s] (row-major, ldc = nbY*s) = X^T Y  (two-stage deterministic reduction)
+pf_status gram(int64_t D, int s, const double* X, int nbX, const double* Y, int nbY, double* C,
+               double* scratch, size_t scratch_elems, cudaStream_t st);
+size_t gram_scratch_elems(int64_t D, int s, int nbX, int nbY);
+// Y(nbY blocks) = beta*Y + alpha * X(nbX blocks) * C, C row-major (nbX*s) x (nbY*s), ldc >= nbY*s.
+// Y may equal X only when nbX == nbY == 1.
+pf_status tsgemm(int64_t D, int s, const double* X, int nbX, const double* C, int ldc, double* Y, int nbY,
+                 double alpha, double beta, cudaStream_t st);
+// Column norms of R = A - B*diag(e) for nb blocks (norms[nb*s]); B may be NULL (then ||A||)
+pf_status colnorms(int64_t D, int s, const double* A, const double* B, const double* e, int nb, double* norms,
+                   double* scratch, size_t scratch_elems, cudaStream_t st);
+// Conversions between double and float blocks
+pf_status convert_d2f(const double* x, float* y, int64_t n, cudaStream_t st);
+pf_status convert_f2d(const float* x, double* y, int64_t n, cudaStream_t st);
+// Small dense helpers on one CTA
+// Shifted Cholesky of G (n x n, row-major), writes upper R (row-major) with G + shift*I = R^T R;
+// Rinv = R^{-1} (upper); status[0] = 0 ok, 1 = not positive definite.
+pf_status small_chol_inv(const double* G, int n, double shift_rel, double* R, double* Rinv, int* status,
+                         cudaStream_t st);
+// Rout = A * B (n x n, upper triangular products, row-major)
+pf_status small_matmul(const double* A, const double* B, double* C, int n, cudaStream_t st);
+
+// Symmetric eigensolver for a dense n x n matrix (eig.cu).  Computes the eigenvalues with
+// indices [lo, hi) of the ascending order and their eigenvectors (columns of Z, ldz = n).
+struct EigWork;
+size_t eig_workspace_bytes(int nmax, int qmax);
+pf_status sym_eig_range(const double* A, int lda, int n, int lo, int hi, double* w_host, double* Z_dev,
+                        void* work, size_t work_bytes, cudaStream_t st);
+
+// Seeded start block (solver.cu)
+pf_status start_block_raw(int64_t D, int s, uint64_t seed, double* out, cudaStream_t st);
+
+}  // namespace pf

@@ -1,0 +1,348 @@
+// Symmetric eigensolver for the projected (Lanczos) matrix H_L, FP64, on the device.
+//
+// Used by the convergence checks (Eq. blocklan_criterion needs eigenvectors t_j of H_L)
+// and by the Rayleigh-Ritz steps.  Only selected eigenpairs are computed:
+//   1. Householder tridiagonalisation A = Q T Q^T (reflectors kept in A's columns),
+//      three or four launches per column: reflector, p = tau A22 v, w = p - (tau/2)(p.v) v,
+//      and the rank-2 update A22 -= v w^T + w v^T of the full trailing block.
+//   2. Bisection with Sturm counts for each requested index (one thread per index).
+//   3. Inverse iteration on T - lambda I (tridiagonal LU with partial pivoting), one
+//      thread per cluster of close eigenvalues; members of a cluster are kept
+//      orthogonal by modified Gram-Schmidt against the earlier members.
+//   4. Back-transformation z = H_0 H_1 ... H_{n-3} y, one CTA per eigenvector.
+#include "common.cuh"
+#include <cmath>
+#include <algorithm>
+
+namespace pf {
+
+struct EigLayout {
+  size_t aw, d, e, tau, p, w, y, lu, cl, total;
+};
+
+static EigLayout eig_layout(int n, int q) {
+  EigLayout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o += (bytes + 255) & ~(size_t)255; return r; };
+  L.aw = take((size_t)n * n * 8);
+  L.d = take((size_t)n * 8);
+  L.e = take((size_t)n * 8);
+  L.tau = take((size_t)n * 8);
+  L.p = take((size_t)2 * n * 8);
+  L.w = take((size_t)q * 8);
+  L.y = take((size_t)n * q * 8);
+  L.lu = take((size_t)q * 6 * n * 8);
+  L.cl = take((size_t)(q + 2) * 4 * 2);
+  L.total = o;
+  return L;
+}
+
+size_t eig_workspace_bytes(int nmax, int qmax) { return eig_layout(nmax, qmax).total; }
+
+// Aw (column-major n x n) = A (row-major, lda); A is symmetric.
+__global__ void eig_copy_kernel(const double* A, int lda, int n, double* Aw) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * n) return;
+  int c = (int)(i / n), r = (int)(i % n);
+  Aw[i] = 0.5 * (A[(int64_t)r * lda + c] + A[(int64_t)c * lda + r]);
+}
+
+// Reflector for column j: x = Aw[j+1.., j].  H x = beta e1, H = I - tau v v^T, v_0 = 1.
+__global__ void house_kernel(double* Aw, int n, int j, double* d, double* e, double* tau) {
+  __shared__ double sh[32];
+  const int m = n - j - 1;
+  double* x = Aw + (int64_t)j * n + j + 1;
+  double sig = 0.0;
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
+  sig = block_sum(sig, sh);
+  const double alpha = x[0];
+  double beta, t, scale;
+  if (sig == 0.0) {
+    beta = alpha;
+    t = 0.0;
+    scale = 0.0;
+  } else {
+    double nrm = sqrt(alpha * alpha + sig);
+    beta = alpha <= 0.0 ? nrm : -nrm;
+    t = (beta - alpha) / beta;
+    scale = 1.0 / (alpha - beta);
+  }
+  __syncthreads();
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] *= scale;
+  if (threadIdx.x == 0) {
+    x[0] = 1.0;
+    d[j] = Aw[(int64_t)j * n + j];
+    e[j] = beta;
+    tau[j] = t;
+  }
+}
+
+// p_i = tau_j * sum_l A22[l, i] v_l, i < m.  One warp per i (column i of A22 is contiguous).
+__global__ void symv_kernel(const double* Aw, int n, int j, const double* tau, double* p) {
+  const int m = n - j - 1;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= m) return;
+  const double* v = Aw + (int64_t)j * n + j + 1;
+  const double* col = Aw + (int64_t)(j + 1 + warp) * n + j + 1;
+  double s = 0.0;
+  for (int l = lane; l < m; l += 32) s = fma(col[l], v[l], s);
+  s = warp_sum(s);
+  if (lane == 0) p[warp] = tau[j] * s;
+}
+
+// w = p - (tau/2)(p.v) v, written to p + n (one CTA).
+__global__ void wvec_kernel(const double* Aw, int n, int j, const double* tau, double* p) {
+  __shared__ double sh[32];
+  const int m = n - j - 1;
+  const double* v = Aw + (int64_t)j * n + j + 1;
+  double g = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) g = fma(p[i], v[i], g);
+  g = block_sum(g, sh);
+  const double c = 0.5 * tau[j] * g;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) p[n + i] = p[i] - c * v[i];
+}
+
+// A22[l, i] -= v_l w_i + w_l v_i over the full trailing block.
+__global__ void rank2_kernel(double* Aw, int n, int j, const double* p) {
+  const int m = n - j - 1;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)m * m) return;
+  const int i = (int)(idx / m), l = (int)(idx % m);
+  const double* v = Aw + (int64_t)j * n + j + 1;
+  const double* w = p + n;
+  double* a = Aw + (int64_t)(j + 1 + i) * n + j + 1 + l;
+  *a -= v[l] * w[i] + w[l] * v[i];
+}
+
+__global__ void tri_finish_kernel(const double* Aw, int n, double* d, double* e, double* tau) {
+  if (threadIdx.x != 0) return;
+  if (n == 1) {
+    d[0] = Aw[0];
+    return;
+  }
+  d[n - 2] = Aw[(int64_t)(n - 2) * n + n - 2];
+  d[n - 1] = Aw[(int64_t)(n - 1) * n + n - 1];
+  e[n - 2] = Aw[(int64_t)(n - 2) * n + n - 1];
+  tau[n - 2] = 0.0;
+}
+
+// Sturm count: number of eigenvalues of T below x.
+__device__ int sturm_count(const double* d, const double* e, int n, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void bisect_kernel(const double* d, const double* e, int n, const int* idx, int q, double* w) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= q) return;
+  double gl = d[0], gu = d[0], maxe2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i < n - 1 ? fabs(e[i]) : 0.0);
+    gl = fmin(gl, d[i] - r);
+    gu = fmax(gu, d[i] + r);
+    if (i < n - 1) maxe2 = fmax(maxe2, e[i] * e[i]);
+  }
+  const double tn = fmax(fabs(gl), fabs(gu));
+  gl -= 2.0 * 2.2e-16 * tn * n + 1e-300;
+  gu += 2.0 * 2.2e-16 * tn * n + 1e-300;
+  const double pivmin = 2.3e-308 * fmax(1.0, maxe2);
+  const int k = idx[t];
+  double lo = gl, hi = gu;
+  for (int it = 0; it < 256; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid == lo || mid == hi) break;
+    if (hi - lo <= 2.2e-16 * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
+    if (sturm_count(d, e, n, mid, pivmin) >= k + 1) hi = mid;
+    else lo = mid;
+  }
+  w[t] = 0.5 * (lo + hi);
+}
+
+__device__ __forceinline__ double hash_unit(uint64_t a) {
+  uint64_t z = a + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+}
+
+// One thread per cluster [cs[c], cs[c+1]) of selected eigenvalues.
+__global__ void inviter_kernel(const double* d, const double* e, int n, const double* w, const int* cs, int ncl,
+                               double* Y, double* lu, double tnorm) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncl) return;
+  double* dl = lu + (int64_t)c * 6 * n;
+  double* dd = dl + n;
+  double* du = dd + n;
+  double* du2 = du + n;
+  double* b = du2 + n;
+  double* piv = b + n;    // 0/1 flags stored as doubles
+  const double eps = 2.2e-16;
+  const double pertol = 10.0 * eps * tnorm;
+  double lam_prev = -1e300;
+  for (int p = cs[c]; p < cs[c + 1]; ++p) {
+    double lam = w[p];
+    if (p > cs[c] && lam - lam_prev < pertol) lam = lam_prev + pertol;
+    lam_prev = lam;
+    // factor T - lam I with partial pivoting
+    for (int i = 0; i < n; ++i) {
+      dd[i] = d[i] - lam;
+      if (i < n - 1) {
+        dl[i] = e[i];
+        du[i] = e[i];
+      }
+      du2[i] = 0.0;
+      piv[i] = 0.0;
+    }
+    for (int i = 0; i < n - 1; ++i) {
+      if (fabs(dd[i]) >= fabs(dl[i])) {
+        double f = dd[i] != 0.0 ? dl[i] / dd[i] : 0.0;
+        dl[i] = f;
+        dd[i + 1] -= f * du[i];
+      } else {
+        double f = dd[i] / dl[i];
+        dd[i] = dl[i];
+        dl[i] = f;
+        double tmp = du[i];
+        du[i] = dd[i + 1];
+        dd[i + 1] = tmp - f * dd[i + 1];
+        if (i < n - 2) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -f * du[i + 1];
+        }
+        piv[i] = 1.0;
+      }
+    }
+    for (int i = 0; i < n; ++i)
+      if (dd[i] == 0.0) dd[i] = pertol > 0 ? pertol : 1e-300;
+    double* y = Y + (int64_t)p * n;
+    for (int i = 0; i < n; ++i) y[i] = hash_unit(((uint64_t)p << 32) ^ (uint64_t)i);
+    for (int it = 0; it < 4; ++it) {
+      for (int i = 0; i < n; ++i) b[i] = y[i];
+      // L solve with the row interchanges
+      for (int i = 0; i < n - 1; ++i) {
+        if (piv[i] != 0.0) {
+          double tmp = b[i];
+          b[i] = b[i + 1];
+          b[i + 1] = tmp - dl[i] * b[i];
+        } else {
+          b[i + 1] -= dl[i] * b[i];
+        }
+      }
+      // U solve
+      b[n - 1] /= dd[n - 1];
+      if (n > 1) b[n - 2] = (b[n - 2] - du[n - 2] * b[n - 1]) / dd[n - 2];
+      for (int i = n - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
+      // orthogonalise against earlier members of the cluster (twice)
+      for (int pass = 0; pass < 2; ++pass)
+        for (int q = cs[c]; q < p; ++q) {
+          const double* z = Y + (int64_t)q * n;
+          double g = 0.0;
+          for (int i = 0; i < n; ++i) g = fma(z[i], b[i], g);
+          for (int i = 0; i < n; ++i) b[i] -= g * z[i];
+        }
+      double nrm = 0.0;
+      for (int i = 0; i < n; ++i) nrm = fma(b[i], b[i], nrm);
+      nrm = sqrt(nrm);
+      if (!(nrm > 0.0)) nrm = 1.0;
+      for (int i = 0; i < n; ++i) y[i] = b[i] / nrm;
+    }
+  }
+}
+
+// z = H_0 H_1 ... H_{n-3} y for the column of Y given by blockIdx.x; Z column-major, ldz.
+__global__ void backtransform_kernel(const double* Aw, const double* tau, int n, const double* Y, double* Z, int ldz) {
+  extern __shared__ double ys[];
+  __shared__ double sh[32];
+  const int c = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = Y[(int64_t)c * n + i];
+  __syncthreads();
+  for (int j = n - 3; j >= 0; --j) {
+    const double t = tau[j];
+    if (t == 0.0) continue;
+    const int m = n - j - 1;
+    const double* v = Aw + (int64_t)j * n + j + 1;
+    double g = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) g = fma(v[i], ys[j + 1 + i], g);
+    g = block_sum(g, sh);
+    const double f = t * g;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) ys[j + 1 + i] -= f * v[i];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) Z[(int64_t)c * ldz + i] = ys[i];
+}
+
+pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, int q, double* w_host, double* Z,
+                         int ldz, void* work, size_t work_bytes, cudaStream_t st) {
+  if (n < 1 || q < 1 || q > n || ldz < n) return PF_EINVAL;
+  EigLayout L = eig_layout(n, q);
+  if (L.total > work_bytes) return PF_EINVAL;
+  char* wb = (char*)work;
+  double* Aw = (double*)(wb + L.aw);
+  double* d = (double*)(wb + L.d);
+  double* e = (double*)(wb + L.e);
+  double* tau = (double*)(wb + L.tau);
+  double* p = (double*)(wb + L.p);
+  double* w = (double*)(wb + L.w);
+  double* Y = (double*)(wb + L.y);
+  double* lu = (double*)(wb + L.lu);
+  int* cl = (int*)(wb + L.cl);
+  int* idx_dev = cl + (q + 2);
+  const int64_t nn = (int64_t)n * n;
+  eig_copy_kernel<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>(A, lda, n, Aw);
+  PF_LAUNCH_CHECK("eig_copy_kernel");
+  for (int j = 0; j + 2 < n; ++j) {
+    const int m = n - j - 1;
+    house_kernel<<<1, 256, 0, st>>>(Aw, n, j, d, e, tau);
+    symv_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Aw, n, j, tau, p);
+    wvec_kernel<<<1, 256, 0, st>>>(Aw, n, j, tau, p);
+    rank2_kernel<<<(unsigned)ceil_div((int64_t)m * m, 256), 256, 0, st>>>(Aw, n, j, p);
+  }
+  tri_finish_kernel<<<1, 32, 0, st>>>(Aw, n, d, e, tau);
+  PF_LAUNCH_CHECK("tridiagonalisation");
+  PF_CUDA(cudaMemcpyAsync(idx_dev, idx_host, q * sizeof(int), cudaMemcpyHostToDevice, st));
+  bisect_kernel<<<(unsigned)ceil_div(q, 64), 64, 0, st>>>(d, e, n, idx_dev, q, w);
+  PF_LAUNCH_CHECK("bisect_kernel");
+  PF_CUDA(cudaMemcpyAsync(w_host, w, q * sizeof(double), cudaMemcpyDeviceToHost, st));
+  std::vector<double> dh(n), eh(n);
+  PF_CUDA(cudaMemcpyAsync(dh.data(), d, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PF_CUDA(cudaMemcpyAsync(eh.data(), e, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PF_CUDA(cudaStreamSynchronize(st));
+  double tnorm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double r = fabs(dh[i]) + (i > 0 ? fabs(eh[i - 1]) : 0.0) + (i < n - 1 ? fabs(eh[i]) : 0.0);
+    tnorm = std::max(tnorm, r);
+  }
+  // clusters: consecutive requested indices whose eigenvalues are within 1e-3 ||T||
+  std::vector<int> cs;
+  cs.push_back(0);
+  for (int i = 1; i < q; ++i) {
+    bool same = idx_host[i] == idx_host[i - 1] + 1 && (w_host[i] - w_host[i - 1]) <= 1e-3 * tnorm;
+    if (!same) cs.push_back(i);
+  }
+  cs.push_back(q);
+  const int ncl = (int)cs.size() - 1;
+  PF_CUDA(cudaMemcpyAsync(cl, cs.data(), cs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  inviter_kernel<<<(unsigned)ceil_div(ncl, 32), 32, 0, st>>>(d, e, n, w, cl, ncl, Y, lu, tnorm);
+  PF_LAUNCH_CHECK("inviter_kernel");
+  const size_t smem = (size_t)n * sizeof(double);
+  if (smem > 48 * 1024) {
+    if (smem > 200 * 1024) return PF_EINVAL;
+    PF_CUDA(cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  }
+  backtransform_kernel<<<q, 256, smem, st>>>(Aw, tau, n, Y, Z, ldz);
+  PF_LAUNCH_CHECK("backtransform_kernel");
+  PF_CUDA(cudaStreamSynchronize(st));   // the host cluster vectors go out of scope
+  return PF_OK;
+}
+
+}  // namespace pf

@@ -1,0 +1,669 @@
+// (a3) spectral bounds, (a4) coefficients, (a6-a10) the POLFED block-Lanczos solve.
+//
+// Block Lanczos (paper Sec. 2.2 and Sec. 4.3) on an operator Op:
+//     W_k = Op V_k;  A_k = V_k^T W_k;
+//     W_k -= V_{1:k} (V_{1:k}^T W_k)     twice (classical Gram-Schmidt, full reorth.);
+//     W_k = V_{k+1} B_{k+1}              shifted Cholesky QR (three passes);
+//     H_L: A_k on the diagonal, B_{k+1} below, B_{k+1}^T above.
+// Convergence (Eq. blocklan_criterion): at checkpoints the selected eigenpairs (theta_j,
+// t_j) of H_L must satisfy ||B_{k+1} tau_kj|| <= tol, tau_kj the last block of t_j.
+//   Op = H (FP64)            spectral bounds, selected pairs = the two extremes;
+//   Op = P(H~) (Clenshaw)    the solve, selected pairs = the nev_g largest theta.
+// Extraction (Sec. 4.3): U = V_{1:m} T_sel, then a Rayleigh-Ritz with H on span(U)
+// (separates Ritz vectors whose filter values nearly coincide), residuals
+// ||H u - E u||, and the nev pairs nearest lambda.  With the FP32 filter the Krylov
+// basis and everything after the filter stay FP64, and FP64 filter passes
+// (U <- P(H~) U, Cholesky QR, Rayleigh-Ritz) refine the pairs until
+// ||H u - E u|| <= res_tol ||H||.
+#include "common.cuh"
+#include <cmath>
+#include <algorithm>
+#include <numeric>
+
+namespace pf {
+
+pf_status set_rescale(Ham* H, double Ec, double dE, cudaStream_t st);
+pf_status ham_moments(Ham* H, double* mu_t, double* G_t, cudaStream_t st);
+pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, int q, double* w_host, double* Z,
+                         int ldz, void* work, size_t work_bytes, cudaStream_t st);
+
+// ------------------------------------------------------------------ small kernels
+__device__ __forceinline__ double splitmix_unit(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void start_block_kernel(int64_t n, uint64_t seed, double* out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = splitmix_unit(seed, (uint64_t)i) - 0.5;
+}
+
+pf_status start_block_raw(int64_t D, int s, uint64_t seed, double* out, cudaStream_t st) {
+  const int64_t n = D * s;
+  start_block_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(n, seed, out);
+  PF_LAUNCH_CHECK("start_block_kernel");
+  return PF_OK;
+}
+
+// a_n = c_n / chi, c_0 = 1, c_n = 2 cos(n arccos lam~), chi = sum_n c_n cos(n arccos lam~)
+__global__ void coeff_kernel(double lam_t, int K, double* c, double* t) {
+  const double th = acos(lam_t);
+  for (int n = threadIdx.x; n <= K; n += blockDim.x) {
+    double T = cos((double)n * th);
+    t[n] = T;
+    c[n] = (n == 0 ? 1.0 : 2.0) * T;
+  }
+}
+__global__ void coeff_norm_kernel(int K, double* c, const double* t) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int n = threadIdx.x; n <= K; n += blockDim.x) s += c[n] * t[n];
+  s = block_sum(s, sh);
+  for (int n = threadIdx.x; n <= K; n += blockDim.x) c[n] /= s;
+}
+
+static pf_status filter_coefficients_dev(double lam_t, int K, double* host, cudaStream_t st) {
+  DevBuf b;
+  PF_TRY(b.alloc((size_t)2 * (K + 1) * sizeof(double), st));
+  coeff_kernel<<<1, 1024, 0, st>>>(lam_t, K, b.as<double>(), b.as<double>() + K + 1);
+  coeff_norm_kernel<<<1, 1024, 0, st>>>(K, b.as<double>(), b.as<double>() + K + 1);
+  PF_LAUNCH_CHECK("coeff_kernel");
+  PF_CUDA(cudaMemcpyAsync(host, b.p, (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PF_CUDA(cudaStreamSynchronize(st));
+  return PF_OK;
+}
+
+// HL[(k+1)s.., k s..] = B, HL[k s.., (k+1)s..] = B^T, and optionally the diagonal block A (symmetrised).
+__global__ void hl_store_kernel(double* HL, int ld, int k, int s, const double* A, const double* B) {
+  for (int i = threadIdx.x; i < s * s; i += blockDim.x) {
+    int a = i / s, b = i % s;
+    if (A) HL[(int64_t)(k * s + a) * ld + k * s + b] = 0.5 * (A[a * s + b] + A[b * s + a]);
+    if (B) {
+      HL[(int64_t)((k + 1) * s + a) * ld + k * s + b] = B[a * s + b];
+      HL[(int64_t)(k * s + b) * ld + (k + 1) * s + a] = B[a * s + b];
+    }
+  }
+}
+
+// res[j] = || B * Z[n-s:n, j] || for the q columns of Z (column-major, ldz)
+__global__ void block_resid_kernel(const double* B, int s, const double* Z, int ldz, int n, int q, double* res) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= q) return;
+  const double* tau = Z + (int64_t)j * ldz + (n - s);
+  double acc = 0.0;
+  for (int a = 0; a < s; ++a) {
+    double r = 0.0;
+    for (int b = a; b < s; ++b) r = fma(B[a * s + b], tau[b], r);
+    acc = fma(r, r, acc);
+  }
+  res[j] = sqrt(acc);
+}
+
+// C (n x q row-major, ldc) = Z (n x q column-major, ldz) with column order perm (C col c = Z col perm[c])
+__global__ void z_to_rowmajor_kernel(const double* Z, int ldz, int n, int q, const int* perm, double* C, int ldc) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * q) return;
+  int r = (int)(i / q), c = (int)(i % q);
+  C[(int64_t)r * ldc + c] = Z[(int64_t)perm[c] * ldz + r];
+}
+
+// evecs[:, j] (column-major D x nev) = U column sel[j] (blocked D x s storage)
+__global__ void gather_cols_kernel(int64_t D, int s, const double* U, const int* sel, int nev, double* out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= D * nev) return;
+  int j = (int)(i / D);
+  int64_t r = i % D;
+  int c = sel[j];
+  out[i] = U[(int64_t)(c / s) * D * s + r * s + (c % s)];
+}
+
+// ------------------------------------------------------------------ workspace
+struct Solver {
+  const Ham* H = nullptr;
+  cudaStream_t st = 0;
+  int64_t D = 0;
+  int s = 0, max_blocks = 0, Mcap = 0;
+  DevBuf V, HL, W, tmp, aux0, aux1, V32, W32, small, gscr, eigw, Z, Cg;
+  size_t gscr_elems = 0, eig_bytes = 0;
+  int qmax = 0;
+  // small: A, B, G, R, Rinv, R2.., status
+  double *Ab, *Bb, *Gb, *Rb, *Rib, *R1, *R2, *R3, *T1, *res;
+  int* stat;
+  pf_report rep;
+  cudaEvent_t ev[2];
+};
+
+static pf_status solver_init(Solver& S, const Ham* H, int s, int max_blocks, int qmax, bool f32, cudaStream_t st) {
+  S.H = H;
+  S.st = st;
+  S.D = H->D;
+  S.s = s;
+  S.max_blocks = max_blocks;
+  S.Mcap = (max_blocks + 1) * s;
+  S.qmax = qmax;
+  const int64_t blk = S.D * s;
+  PF_TRY(S.V.alloc((size_t)(max_blocks + 1) * blk * 8, st));
+  PF_TRY(S.HL.alloc((size_t)S.Mcap * S.Mcap * 8, st));
+  PF_CUDA(cudaMemsetAsync(S.HL.p, 0, (size_t)S.Mcap * S.Mcap * 8, st));
+  PF_TRY(S.W.alloc(blk * 8, st));
+  PF_TRY(S.tmp.alloc(blk * 8, st));
+  if (f32) {
+    PF_TRY(S.aux0.alloc(blk * 4, st));
+    PF_TRY(S.aux1.alloc(blk * 4, st));
+    PF_TRY(S.V32.alloc(blk * 4, st));
+    PF_TRY(S.W32.alloc(blk * 4, st));
+  } else {
+    PF_TRY(S.aux0.alloc(blk * 8, st));
+    PF_TRY(S.aux1.alloc(blk * 8, st));
+  }
+  // Gram scratch: the largest of (max_blocks+1) x 1 blocks and qmax/s x qmax/s blocks
+  int qb = (qmax + s - 1) / s;
+  size_t g1 = gram_scratch_elems(S.D, s, max_blocks + 1, 1);
+  size_t g2 = gram_scratch_elems(S.D, s, qb, qb);
+  size_t g3 = (size_t)256 * (qb + 2) * s;   // colnorms
+  S.gscr_elems = std::max(std::max(g1, g2), g3);
+  PF_TRY(S.gscr.alloc(S.gscr_elems * 8, st));
+  const int nsm = 10;
+  PF_TRY(S.small.alloc((size_t)nsm * s * s * 8 + (size_t)(qmax + S.Mcap) * 8 + 64, st));
+  double* b = S.small.as<double>();
+  S.Ab = b; S.Bb = b + s * s; S.Gb = b + 2 * s * s; S.Rb = b + 3 * s * s; S.Rib = b + 4 * s * s;
+  S.R1 = b + 5 * s * s; S.R2 = b + 6 * s * s; S.R3 = b + 7 * s * s; S.T1 = b + 8 * s * s;
+  S.res = b + nsm * s * s;
+  S.stat = (int*)(S.res + qmax + S.Mcap);
+  S.eig_bytes = eig_workspace_bytes(S.Mcap, std::max(qmax, 2));
+  PF_TRY(S.eigw.alloc(S.eig_bytes, st));
+  PF_TRY(S.Z.alloc((size_t)S.Mcap * std::max(qmax, 2) * 8, st));
+  // coefficient matrix for CGS (Mcap x s) and for Ritz rotation (Mcap x qmax)
+  PF_TRY(S.Cg.alloc((size_t)S.Mcap * std::max(qmax, s) * 8, st));
+  memset(&S.rep, 0, sizeof(S.rep));
+  return PF_OK;
+}
+
+static double* blockp(const Solver& S, int k) { return S.V.as<double>() + (int64_t)k * S.D * S.s; }
+
+// Shifted Cholesky QR, three passes (shift only in the first).  In: X (D x s, FP64, may be
+// overwritten), out: Q (D x s), R (s x s upper, into S.Bb).  Returns PF_EBREAKDOWN when the
+// factorisation fails.
+static pf_status chol_qr3(Solver& S, double* X, double* Q) {
+  const int s = S.s;
+  const double u = 1.1102230246251565e-16;
+  const double shift = 11.0 * ((double)S.D * s + (double)s * (s + 1)) * u;
+  double* Rs[3] = {S.R1, S.R2, S.R3};
+  double* src = X;
+  for (int pass = 0; pass < 3; ++pass) {
+    PF_TRY(gram(S.D, s, src, 1, src, 1, S.Gb, S.gscr.as<double>(), S.gscr_elems, S.st));
+    PF_TRY(small_chol_inv(S.Gb, s, pass == 0 ? shift : 0.0, Rs[pass], S.Rib, S.stat, S.st));
+    PF_TRY(tsgemm(S.D, s, src, 1, S.Rib, s, S.tmp.as<double>(), 1, 1.0, 0.0, S.st));
+    PF_CUDA(cudaMemcpyAsync(Q, S.tmp.p, (size_t)S.D * s * 8, cudaMemcpyDeviceToDevice, S.st));
+    src = Q;
+    int bad = 0;
+    PF_CUDA(cudaMemcpyAsync(&bad, S.stat, sizeof(int), cudaMemcpyDeviceToHost, S.st));
+    PF_CUDA(cudaStreamSynchronize(S.st));
+    if (bad) return PF_EBREAKDOWN;
+  }
+  // R = R3 R2 R1
+  PF_TRY(small_matmul(S.R3, S.R2, S.T1, s, S.st));
+  PF_TRY(small_matmul(S.T1, S.R1, S.Bb, s, S.st));
+  return PF_OK;
+}
+
+enum OpKind { OP_H = 0, OP_FILTER64 = 1, OP_FILTER32 = 2 };
+
+static pf_status apply_op(Solver& S, OpKind op, const double* Vk, double* Wk, const double* coeffs, int K) {
+  const Ham* H = S.H;
+  if (op == OP_H) {
+    return clenshaw_step_raw(S.D, H->row_ptr, H->col, H->val, PF_F64, S.s, Vk, Vk, nullptr, Wk, 0.0, 1.0, 0.0, S.st);
+  }
+  if (op == OP_FILTER64) {
+    S.rep.filter_steps += K + 1;
+    S.rep.filter_steps_f64 += K + 1;
+    return filter_apply_raw(H, PF_F64, S.s, Vk, Wk, coeffs, nullptr, K, S.aux0.p, S.aux1.p, S.st);
+  }
+  S.rep.filter_steps += K + 1;
+  const int64_t n = S.D * S.s;
+  PF_TRY(convert_d2f(Vk, S.V32.as<float>(), n, S.st));
+  PF_TRY(filter_apply_raw(H, PF_F32, S.s, S.V32.p, S.W32.p, coeffs, nullptr, K, S.aux0.p, S.aux1.p, S.st));
+  return convert_f2d(S.W32.as<float>(), Wk, n, S.st);
+}
+
+struct LanczosResult {
+  int blocks = 0;      // number of Krylov blocks in the basis (M = blocks * s)
+  bool converged = false;
+  std::vector<double> theta;   // selected Ritz values (ascending)
+  std::vector<int> idx;        // their indices in the ascending order of H_L's spectrum
+  std::vector<double> resid;
+};
+
+// Runs block Lanczos from the start block already in V[0].  select: 0 = extremes, 1 = top q.
+static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K, int select, int q, int min_M,
+                               double tol, bool tol_relative, int check_first, int check_every, LanczosResult& out) {
+  const int s = S.s;
+  const int64_t D = S.D;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float ms = 0;
+  int k = 0;
+  for (;;) {
+    double* Vk = blockp(S, k);
+    double* W = S.W.as<double>();
+    cudaEventRecord(e0, S.st);
+    PF_TRY(apply_op(S, op, Vk, W, coeffs, K));
+    cudaEventRecord(e1, S.st);
+    // A_k = V_k^T W
+    PF_TRY(gram(D, s, Vk, 1, W, 1, S.Ab, S.gscr.as<double>(), S.gscr_elems, S.st));
+    hl_store_kernel<<<1, 256, 0, S.st>>>(S.HL.as<double>(), S.Mcap, k, s, S.Ab, nullptr);
+    PF_LAUNCH_CHECK("hl_store_kernel");
+    // full reorthogonalisation, two classical Gram-Schmidt passes
+    for (int pass = 0; pass < 2; ++pass) {
+      PF_TRY(gram(D, s, S.V.as<double>(), k + 1, W, 1, S.Cg.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
+      PF_TRY(tsgemm(D, s, S.V.as<double>(), k + 1, S.Cg.as<double>(), s, W, 1, -1.0, 1.0, S.st));
+    }
+    // full: the basis spans the whole space, so B_{k+1} = 0 exactly.  cap: no room for
+    // another block; B_{k+1} comes from the Cholesky factor of W^T W alone (enough for
+    // ||B tau||), and the iteration stops.
+    const bool full = (int64_t)(k + 1) * s >= D;
+    const bool cap = (int64_t)(k + 2) * s > D;
+    const bool exhausted = full || cap;
+    if (full) {
+      PF_CUDA(cudaMemsetAsync(S.Bb, 0, (size_t)s * s * 8, S.st));
+    } else if (cap) {
+      const double u = 1.1102230246251565e-16;
+      PF_TRY(gram(D, s, W, 1, W, 1, S.Gb, S.gscr.as<double>(), S.gscr_elems, S.st));
+      PF_TRY(small_chol_inv(S.Gb, s, 11.0 * ((double)D * s + (double)s * (s + 1)) * u, S.Bb, S.Rib, S.stat, S.st));
+    } else {
+      pf_status qs = chol_qr3(S, W, blockp(S, k + 1));
+      if (qs != PF_OK) return qs;
+    }
+    hl_store_kernel<<<1, 256, 0, S.st>>>(S.HL.as<double>(), S.Mcap, k, s, nullptr, S.Bb);
+    PF_LAUNCH_CHECK("hl_store_kernel");
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    S.rep.ms_filter += ms;
+    ++k;
+    const int M = k * s;
+    const bool last = (k + 1 > S.max_blocks) || exhausted;
+    const bool enough = (select == 0 ? M >= 2 : M >= q) && M >= min_M;
+    const bool at_check = (k >= check_first && ((k - check_first) % check_every == 0)) || last;
+    if (enough && at_check) {
+      std::vector<int> idx;
+      if (select == 0) {
+        idx.push_back(0);
+        if (M > 1) idx.push_back(M - 1);
+      } else {
+        for (int i = M - q; i < M; ++i) idx.push_back(i);
+      }
+      const int nq = (int)idx.size();
+      std::vector<double> th(nq), res(nq);
+      PF_TRY(sym_eig_select(S.HL.as<double>(), S.Mcap, M, idx.data(), nq, th.data(), S.Z.as<double>(), M,
+                            S.eigw.p, S.eig_bytes, S.st));
+      block_resid_kernel<<<(unsigned)ceil_div(nq, 64), 64, 0, S.st>>>(S.Bb, s, S.Z.as<double>(), M, M, nq, S.res);
+      PF_LAUNCH_CHECK("block_resid_kernel");
+      PF_CUDA(cudaMemcpyAsync(res.data(), S.res, nq * 8, cudaMemcpyDeviceToHost, S.st));
+      PF_CUDA(cudaStreamSynchronize(S.st));
+      S.rep.checks++;
+      double scale = 1.0;
+      if (tol_relative) scale = std::max(std::fabs(th.front()), std::fabs(th.back()));
+      bool ok = true;
+      for (int i = 0; i < nq; ++i) ok = ok && (res[i] <= tol * scale);
+      if (ok || last) {
+        out.blocks = k;
+        out.converged = ok || full;
+        out.theta = th;
+        out.idx = idx;
+        out.resid = res;
+        break;
+      }
+    }
+    if (last) {
+      out.blocks = k;
+      out.converged = false;
+      break;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return PF_OK;
+}
+
+static pf_status spectral_bounds_impl(Ham* H, double tol, cudaStream_t st) {
+  if (tol <= 0) tol = 1e-10;
+  int s = 4;
+  while (s > 1 && 2 * s > H->D) s >>= 1;
+  int max_blocks = (int)std::min<int64_t>(H->D / s, 600 / s);
+  if (max_blocks < 1) max_blocks = 1;
+  Solver S;
+  PF_TRY(solver_init(S, H, s, max_blocks, 2, false, st));
+  PF_TRY(start_block_raw(H->D, s, 0x5eedb0d5ull, blockp(S, 0), st));
+  PF_TRY(chol_qr3(S, blockp(S, 0), blockp(S, 0)));
+  LanczosResult R;
+  PF_TRY(block_lanczos(S, OP_H, nullptr, 0, 0, 2, 2, tol, true, 5, 5, R));
+  if (!R.converged) return PF_ENOTCONV;
+  H->emin = R.theta.front();
+  H->emax = R.theta.back();
+  H->rmin = R.resid.front();
+  H->rmax = R.resid.back();
+  H->hnorm = std::max(std::fabs(H->emin), std::fabs(H->emax));
+  H->has_bounds = 1;
+  // padded interval (Lanczos extremes lie inside the spectrum)
+  const double de0 = 0.5 * (H->emax - H->emin);
+  const double lo = H->emin - H->rmin - 1e-3 * de0;
+  const double hi = H->emax + H->rmax + 1e-3 * de0;
+  return set_rescale(H, 0.5 * (hi + lo), 0.5 * (hi - lo), st);
+}
+
+static int expected_krylov_dim(int nev, int s, double eta) {
+  return (int)std::ceil((20.427 * s + 1.696 * nev) * eta);
+}
+
+// H-space Rayleigh-Ritz on the blocked set U (nb blocks): U <- U Z, E = eig(U^T H U), residual norms.
+static pf_status rayleigh_ritz_H(Solver& S, DevBuf& U, DevBuf& HU, int nb, std::vector<double>& E,
+                                 std::vector<double>& res) {
+  const int s = S.s;
+  const int64_t D = S.D;
+  const int q = nb * s;
+  const Ham* H = S.H;
+  for (int b = 0; b < nb; ++b) {
+    const double* Ub = U.as<double>() + (int64_t)b * D * s;
+    double* HUb = HU.as<double>() + (int64_t)b * D * s;
+    PF_TRY(clenshaw_step_raw(D, H->row_ptr, H->col, H->val, PF_F64, s, Ub, Ub, nullptr, HUb, 0.0, 1.0, 0.0, S.st));
+  }
+  DevBuf G;
+  PF_TRY(G.alloc((size_t)q * q * 8, S.st));
+  PF_TRY(gram(D, s, U.as<double>(), nb, HU.as<double>(), nb, G.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
+  std::vector<int> idx(q);
+  std::iota(idx.begin(), idx.end(), 0);
+  E.assign(q, 0.0);
+  DevBuf Zr, Cr, E_dev;
+  PF_TRY(Zr.alloc((size_t)q * q * 8, S.st));
+  PF_TRY(Cr.alloc((size_t)q * q * 8, S.st));
+  size_t wb = eig_workspace_bytes(q, q);
+  DevBuf ew;
+  PF_TRY(ew.alloc(wb, S.st));
+  PF_TRY(sym_eig_select(G.as<double>(), q, q, idx.data(), q, E.data(), Zr.as<double>(), q, ew.p, wb, S.st));
+  // C row-major q x q from Zr (column-major)
+  DevBuf perm;
+  PF_TRY(perm.alloc(q * sizeof(int), S.st));
+  PF_CUDA(cudaMemcpyAsync(perm.p, idx.data(), q * sizeof(int), cudaMemcpyHostToDevice, S.st));
+  z_to_rowmajor_kernel<<<(unsigned)ceil_div((int64_t)q * q, 256), 256, 0, S.st>>>(Zr.as<double>(), q, q, q,
+                                                                                   perm.as<int>(), Cr.as<double>(), q);
+  PF_LAUNCH_CHECK("z_to_rowmajor_kernel");
+  // U2 = U C into HU's storage, then copy back; HU recomputed from U2
+  for (int b = 0; b < nb; ++b)
+    PF_TRY(tsgemm(D, s, U.as<double>(), nb, Cr.as<double>() + b * s, q, HU.as<double>() + (int64_t)b * D * s, 1,
+                  1.0, 0.0, S.st));
+  PF_CUDA(cudaMemcpyAsync(U.p, HU.p, (size_t)nb * D * s * 8, cudaMemcpyDeviceToDevice, S.st));
+  for (int b = 0; b < nb; ++b) {
+    const double* Ub = U.as<double>() + (int64_t)b * D * s;
+    double* HUb = HU.as<double>() + (int64_t)b * D * s;
+    PF_TRY(clenshaw_step_raw(D, H->row_ptr, H->col, H->val, PF_F64, s, Ub, Ub, nullptr, HUb, 0.0, 1.0, 0.0, S.st));
+  }
+  PF_TRY(E_dev.alloc(q * 8, S.st));
+  PF_CUDA(cudaMemcpyAsync(E_dev.p, E.data(), q * 8, cudaMemcpyHostToDevice, S.st));
+  DevBuf rn;
+  PF_TRY(rn.alloc(q * 8, S.st));
+  PF_TRY(colnorms(D, s, HU.as<double>(), U.as<double>(), E_dev.as<double>(), nb, rn.as<double>(), S.gscr.as<double>(),
+                  S.gscr_elems, S.st));
+  res.assign(q, 0.0);
+  PF_CUDA(cudaMemcpyAsync(res.data(), rn.p, q * 8, cudaMemcpyDeviceToHost, S.st));
+  PF_CUDA(cudaStreamSynchronize(S.st));
+  return PF_OK;
+}
+
+// Orthonormalise a blocked set (nb blocks) with two Cholesky-QR passes on the whole set.
+static pf_status orthonormalise_set(Solver& S, DevBuf& U, DevBuf& T, int nb) {
+  const int s = S.s;
+  const int q = nb * s;
+  const int64_t D = S.D;
+  DevBuf G, R, Ri, st;
+  PF_TRY(G.alloc((size_t)q * q * 8, S.st));
+  PF_TRY(R.alloc((size_t)q * q * 8, S.st));
+  PF_TRY(Ri.alloc((size_t)q * q * 8, S.st));
+  PF_TRY(st.alloc(16, S.st));
+  const double u = 1.1102230246251565e-16;
+  for (int pass = 0; pass < 2; ++pass) {
+    PF_TRY(gram(D, s, U.as<double>(), nb, U.as<double>(), nb, G.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
+    const double shift = pass == 0 ? 11.0 * ((double)D * q + (double)q * (q + 1)) * u : 0.0;
+    PF_TRY(small_chol_inv(G.as<double>(), q, shift, R.as<double>(), Ri.as<double>(), st.as<int>(), S.st));
+    for (int b = 0; b < nb; ++b)
+      PF_TRY(tsgemm(D, s, U.as<double>(), nb, Ri.as<double>() + b * s, q, T.as<double>() + (int64_t)b * D * s, 1, 1.0,
+                    0.0, S.st));
+    PF_CUDA(cudaMemcpyAsync(U.p, T.p, (size_t)nb * D * s * 8, cudaMemcpyDeviceToDevice, S.st));
+    int bad = 0;
+    PF_CUDA(cudaMemcpyAsync(&bad, st.p, sizeof(int), cudaMemcpyDeviceToHost, S.st));
+    PF_CUDA(cudaStreamSynchronize(S.st));
+    if (bad) return PF_EBREAKDOWN;
+  }
+  return PF_OK;
+}
+
+static std::vector<int> nearest_sel(const std::vector<double>& E, double lam, int nev) {
+  std::vector<int> o(E.size());
+  std::iota(o.begin(), o.end(), 0);
+  std::sort(o.begin(), o.end(), [&](int a, int b) {
+    double da = std::fabs(E[a] - lam), db = std::fabs(E[b] - lam);
+    if (da != db) return da < db;
+    return E[a] < E[b];
+  });
+  o.resize(std::min<size_t>(nev, o.size()));
+  std::sort(o.begin(), o.end(), [&](int a, int b) { return E[a] < E[b]; });
+  return o;
+}
+
+static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, const pf_solve_opts* o_in,
+                                   double* evals, double* evecs, double* resid, pf_report* rep, cudaStream_t st) {
+  pf_solve_opts o;
+  pf_default_opts(&o);
+  if (o_in) o = *o_in;
+  if (!H || !evals || !resid) return PF_EINVAL;
+  if (!H->has_rescale) return PF_ESTATE;
+  if (!o.use_abs_target && !H->has_bounds) return PF_ESTATE;
+  if (nev < 1 || nev > H->D || K < 1) return PF_EINVAL;
+  if (!o.use_abs_target && !(target_eps >= 0.0 && target_eps <= 1.0)) return PF_EINVAL;
+  int s = o.block > 0 ? o.block : 32;
+  if (!(s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32 || s == 64)) return PF_EINVAL;
+  if (o.precision != PF_F64 && o.precision != PF_F32) return PF_EINVAL;
+  const bool f32 = o.precision == PF_F32;
+  const double eta = o.eta > 0 ? o.eta : 1.5;
+  const double tol = f32 ? (o.tol_f32 > 0 ? o.tol_f32 : 1e-7) : (o.tol > 0 ? o.tol : 1e-10);
+  const double res_tol = o.res_tol > 0 ? o.res_tol : 1e-9;
+  int nev_g = o.nev_guard > 0 ? o.nev_guard : (int)std::ceil(1.2 * nev);
+  nev_g = std::max(nev_g, nev);
+  if (nev_g > H->D) nev_g = (int)H->D;
+  int Mmax = std::min<int64_t>(expected_krylov_dim(nev_g, s, eta), H->D);
+  int max_blocks = o.max_blocks > 0 ? o.max_blocks : std::max(2, Mmax / s);
+  if ((int64_t)max_blocks * s > H->D) max_blocks = (int)(H->D / s);
+  if (max_blocks < 1 || (int64_t)max_blocks * s < (int64_t)((nev_g + s - 1) / s) * s) return PF_EINVAL;
+  const int m_est = std::max(1, (int)std::ceil(expected_krylov_dim(nev_g, s, 1.0) / (double)s));
+  const int check_first = o.check_first > 0 ? o.check_first : std::max(1, (int)std::ceil(0.5 * m_est));
+  const int check_every = o.check_every > 0 ? o.check_every : std::max(1, (int)std::ceil(0.1 * m_est));
+  const int qb = (nev_g + s - 1) / s;     // Ritz blocks extracted
+  const int qpad = qb * s;
+
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  cudaEventRecord(t0, st);
+
+  Solver S;
+  PF_TRY(solver_init(S, H, s, max_blocks, std::max(qpad, nev_g), f32, st));
+  const double lam = o.use_abs_target ? o.target_abs : H->emin + target_eps * (H->emax - H->emin);
+  const double lam_t = (lam - H->Ec) / H->dE;
+  if (!(lam_t > -1.0 && lam_t < 1.0)) return PF_EINVAL;
+  std::vector<double> coeffs(K + 1);
+  PF_TRY(filter_coefficients_dev(lam_t, K, coeffs.data(), st));
+  S.rep.K = K;
+  S.rep.nev_guard = nev_g;
+  S.rep.lambda = lam;
+  S.rep.lambda_t = lam_t;
+  S.rep.emin = H->emin;
+  S.rep.emax = H->emax;
+  S.rep.Ec = H->Ec;
+  S.rep.dE = H->dE;
+  const double hnorm = H->has_bounds ? H->hnorm : std::max(std::fabs(H->Ec - H->dE), std::fabs(H->Ec + H->dE));
+  S.rep.hnorm = hnorm;
+
+  PF_TRY(start_block_raw(H->D, s, o.seed, blockp(S, 0), st));
+  PF_TRY(chol_qr3(S, blockp(S, 0), blockp(S, 0)));
+  LanczosResult R;
+  PF_TRY(block_lanczos(S, f32 ? OP_FILTER32 : OP_FILTER64, coeffs.data(), K, 1, nev_g, qpad, tol, false,
+                       check_first, check_every, R));
+  S.rep.blocks = R.blocks;
+  S.rep.krylov_dim = R.blocks * s;
+  const int M = R.blocks * s;
+  if ((int)R.idx.size() < nev_g) return PF_ENOTCONV;
+  // Ritz vectors for the qpad largest theta (the nev_g checked plus padding to whole blocks)
+  std::vector<int> idx;
+  const int qsel = std::min(qpad, M);
+  for (int i = M - qsel; i < M; ++i) idx.push_back(i);
+  std::vector<double> th(qsel);
+  PF_TRY(sym_eig_select(S.HL.as<double>(), S.Mcap, M, idx.data(), qsel, th.data(), S.Z.as<double>(), M, S.eigw.p,
+                        S.eig_bytes, st));
+  // C (M x qpad row-major): columns are the Ritz coefficient vectors, largest theta first; zero padding
+  DevBuf perm, U, HU;
+  std::vector<int> pv(qpad);
+  for (int c = 0; c < qpad; ++c) pv[c] = c < qsel ? qsel - 1 - c : 0;
+  PF_TRY(perm.alloc(qpad * sizeof(int), st));
+  PF_CUDA(cudaMemcpyAsync(perm.p, pv.data(), qpad * sizeof(int), cudaMemcpyHostToDevice, st));
+  PF_CUDA(cudaMemsetAsync(S.Cg.p, 0, (size_t)M * qpad * 8, st));
+  z_to_rowmajor_kernel<<<(unsigned)ceil_div((int64_t)M * qsel, 256), 256, 0, st>>>(S.Z.as<double>(), M, M, qsel,
+                                                                                   perm.as<int>(), S.Cg.as<double>(),
+                                                                                   qpad);
+  PF_LAUNCH_CHECK("z_to_rowmajor_kernel");
+  PF_TRY(U.alloc((size_t)qb * H->D * s * 8, st));
+  PF_TRY(HU.alloc((size_t)qb * H->D * s * 8, st));
+  for (int b = 0; b < qb; ++b)
+    PF_TRY(tsgemm(H->D, s, S.V.as<double>(), R.blocks, S.Cg.as<double>() + b * s, qpad,
+                  U.as<double>() + (int64_t)b * H->D * s, 1, 1.0, 0.0, st));
+  std::vector<double> E, res;
+  PF_TRY(rayleigh_ritz_H(S, U, HU, qb, E, res));
+  std::vector<int> sel = nearest_sel(E, lam, nev);
+  auto max_res = [&]() {
+    double m = 0;
+    for (int j : sel) m = std::max(m, res[j]);
+    return m;
+  };
+  // FP64 refinement for the FP32 filter
+  int passes = 0;
+  const int max_pass = o.refine_passes < 0 ? 0 : (o.refine_passes == 0 ? 3 : o.refine_passes);
+  const int Kr = o.refine_K > 0 ? o.refine_K : K;
+  std::vector<double> coeffs_r;
+  if (f32 && max_res() > res_tol * hnorm && max_pass > 0) {
+    coeffs_r.resize(Kr + 1);
+    PF_TRY(filter_coefficients_dev(lam_t, Kr, coeffs_r.data(), st));
+    DevBuf aux64a, aux64b;
+    PF_TRY(aux64a.alloc((size_t)H->D * s * 8, st));
+    PF_TRY(aux64b.alloc((size_t)H->D * s * 8, st));
+    while (passes < max_pass && max_res() > res_tol * hnorm) {
+      for (int b = 0; b < qb; ++b) {
+        PF_TRY(filter_apply_raw(H, PF_F64, s, U.as<double>() + (int64_t)b * H->D * s,
+                                HU.as<double>() + (int64_t)b * H->D * s, coeffs_r.data(), nullptr, Kr, aux64a.p,
+                                aux64b.p, st));
+        S.rep.filter_steps += Kr + 1;
+        S.rep.filter_steps_f64 += Kr + 1;
+      }
+      PF_CUDA(cudaMemcpyAsync(U.p, HU.p, (size_t)qb * H->D * s * 8, cudaMemcpyDeviceToDevice, st));
+      PF_TRY(orthonormalise_set(S, U, HU, qb));
+      PF_TRY(rayleigh_ritz_H(S, U, HU, qb, E, res));
+      sel = nearest_sel(E, lam, nev);
+      ++passes;
+    }
+  }
+  S.rep.refine_passes = passes;
+  // outputs
+  const double mr = max_res();
+  for (int j = 0; j < nev; ++j) {
+    evals[j] = E[sel[j]];
+    resid[j] = res[sel[j]];
+  }
+  if (evecs) {
+    DevBuf sd;
+    PF_TRY(sd.alloc(nev * sizeof(int), st));
+    PF_CUDA(cudaMemcpyAsync(sd.p, sel.data(), nev * sizeof(int), cudaMemcpyHostToDevice, st));
+    gather_cols_kernel<<<(unsigned)ceil_div(H->D * nev, 256), 256, 0, st>>>(H->D, s, U.as<double>(), sd.as<int>(),
+                                                                            nev, evecs);
+    PF_LAUNCH_CHECK("gather_cols_kernel");
+  }
+  cudaEventRecord(t1, st);
+  PF_CUDA(cudaStreamSynchronize(st));
+  float tot = 0;
+  cudaEventElapsedTime(&tot, t0, t1);
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  S.rep.ms_total = tot;
+  S.rep.max_residual = mr;
+  S.rep.converged = 0;
+  for (int j = 0; j < nev; ++j) S.rep.converged += resid[j] <= res_tol * hnorm;
+  const bool ok = S.rep.converged == nev;
+  S.rep.status = ok ? PF_OK : PF_ENOTCONV;
+  if (rep) *rep = S.rep;
+  return ok ? PF_OK : PF_ENOTCONV;
+}
+
+}  // namespace pf
+
+using namespace pf;
+
+extern "C" {
+
+void pf_default_opts(pf_solve_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->block = 32;
+  o->precision = PF_F64;
+  o->eta = 1.5;
+  o->tol = 1e-10;
+  o->tol_f32 = 1e-7;
+  o->res_tol = 1e-9;
+  o->seed = 2024;
+}
+
+pf_status pf_spectral_bounds(pf_ham* hh, double tol, double* emin, double* emax, double* rmin, double* rmax,
+                             pf_stream_t stream) {
+  Ham* H = reinterpret_cast<Ham*>(hh);
+  if (!H || !emin || !emax) return PF_EINVAL;
+  PF_TRY(spectral_bounds_impl(H, tol, (cudaStream_t)stream));
+  *emin = H->emin;
+  *emax = H->emax;
+  if (rmin) *rmin = H->rmin;
+  if (rmax) *rmax = H->rmax;
+  return PF_OK;
+}
+
+pf_status pf_filter_coefficients(double lam_t, int32_t K, double* coeffs, pf_stream_t stream) {
+  if (K < 1 || !coeffs || !(lam_t >= -1.0 && lam_t <= 1.0)) return PF_EINVAL;
+  return filter_coefficients_dev(lam_t, K, coeffs, (cudaStream_t)stream);
+}
+
+pf_status pf_choose_K(pf_ham* hh, double target_eps, int32_t nev, int32_t* K, pf_stream_t stream) {
+  Ham* H = reinterpret_cast<Ham*>(hh);
+  if (!H || !K || nev < 1) return PF_EINVAL;
+  if (!H->has_bounds || !H->has_rescale) return PF_ESTATE;
+  if (!(target_eps >= 0.0 && target_eps <= 1.0)) return PF_EINVAL;
+  double mu = 0, G = 0;
+  PF_TRY(ham_moments(H, &mu, &G, (cudaStream_t)stream));
+  const double lam = H->emin + target_eps * (H->emax - H->emin);
+  const double lt = (lam - H->Ec) / H->dE;
+  const int nev_g = (int)std::ceil(1.2 * nev);
+  const double rho = (double)H->D / (std::sqrt(2.0 * M_PI) * G) * std::exp(-(lt - mu) * (lt - mu) / (2.0 * G * G));
+  const double delta = nev_g / (2.0 * rho);
+  const double k = 2.655 * std::sqrt(std::max(1.0 - lt * lt, 0.0)) / delta;
+  *K = std::max(1, (int)std::ceil(k));
+  return PF_OK;
+}
+
+pf_status pf_polfed_solve(pf_ham* hh, double target_eps, int32_t nev, int32_t K, const pf_solve_opts* o,
+                          double* evals, double* evecs, double* resid, pf_report* rep, pf_stream_t stream) {
+  return polfed_solve_impl(reinterpret_cast<Ham*>(hh), target_eps, nev, K, o, evals, evecs, resid, rep,
+                           (cudaStream_t)stream);
+}
+
+pf_status pf_start_block(int64_t D, int32_t s, uint64_t seed, double* out, pf_stream_t stream) {
+  if (D < 1 || s < 1 || !out) return PF_EINVAL;
+  return start_block_raw(D, s, seed, out, (cudaStream_t)stream);
+}
+
+}  // extern "C"
