@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the POLFED hot path on B300: eigenpairs/s at residual <= 1e-9 ||H||.
+
+Workload (N=1): disordered XXZ chain, L=20 periodic, J=1, Delta=1, S^z_tot=0 sector
+(D=184756, nnz=2,129,556), 100 eigenpairs nearest eps=0.5, block width 32, FP32
+Chebyshev filter with FP64 Lanczos, Rayleigh-Ritz and refinement.  Step i solves
+realisation r = (rank + i*world) mod 3 with W = (1, 3, 5)[r], seed 2000 + r.  A step is
+the whole path: basis and CSR build, spectral bounds, K, coefficients, block Lanczos,
+Ritz extraction, refinement.  The Krylov basis (~1.9 GB) is far larger than L2, so no
+explicit L2 flush is needed between steps.
+
+`value` is device time (CUDA events on the solve's stream) with outputs left on the
+device; `e2e` adds the host->device copy of the disorder parameters (inside the build)
+and the device->host copy of the eigenvectors into pinned memory.  Multi-GPU (torchrun):
+replicas only, each rank solves its own realisations, time = max over ranks.
+
+`--impl reference` times the oracle (plain FP64 CPU code) on a bounded sample of the
+same workload: a fixed number of Clenshaw steps, extrapolated to one solve.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_SITES, NEV, BLOCK, EPS = 20, 100, 32, 0.5
+W_LIST = (1.0, 3.0, 5.0)
+SEED0 = 2000
+RES_TOL = 1e-9
+WORKLOAD = "xxz_L20_D184756_nev100_s32_eps0.5"
+METRIC = "eigenpairs_per_s_at_residual_1e-9"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only time the fused Clenshaw step at the workload shape (profiling)")
+    ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=40)
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+def step_bytes(D, nnz, s, w):
+    """Algorithmic bytes of one fused Clenshaw step: matrix (value + int32 column per
+    nonzero, int64 row pointers) plus V, b_{i+1}, b_{i+2} read once and b_i written."""
+    return nnz * (w + 4) + 8 * (D + 1) + 4 * D * s * w
+
+
+def ncu_traffic(kernel_tag):
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches the current source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
+    src = os.path.join(ROOT, "paper_2605_10191_b300", "csrc", "clenshaw.cu")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.strip()
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if fields.get("source_sha256") != h or "traffic_bytes_per_launch" not in fields:
+        return None
+    return float(fields["traffic_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = [l.strip().split(",") for l in open(self.f.name) if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_sample(nsteps):
+    """Seconds per FP64 Clenshaw step of the oracle at the workload shape, the oracle's K,
+    and the number of filter steps of one solve (expected Krylov blocks x (K+1))."""
+    import pf_inputs as pi
+    from oracle import hamiltonian as oh, chebyshev as oc, dos as od, lanczos as ol
+    p = pi.xxz_params(L_SITES, W=W_LIST[0], seed=SEED0)
+    H = oh.xxz_hamiltonian(p)
+    b = ol.lanczos_extrema(H, tol=1e-8)
+    Ec, dE = ol.padded_interval(b["emin"], b["emax"], b["rmin"], b["rmax"])
+    Ht = oc.rescale(H, Ec, dE)
+    mu, G = od.exact_moments(Ht)
+    lam_t = ((b["emin"] + EPS * (b["emax"] - b["emin"])) - Ec) / dE
+    nev_g = od.guard_count(NEV)
+    K = od.choose_K(lam_t, nev_g, H.D, mu, G)
+    V = ol.start_block(H.D, BLOCK, 2024)
+    a = oc.filter_coefficients(lam_t, nsteps)
+    t0 = time.perf_counter()
+    oc.clenshaw_apply(Ht, V, a)            # nsteps SpMM steps + the closing line
+    dt = (time.perf_counter() - t0) / (nsteps + 1)
+    blocks = math.ceil(od.expected_krylov_dim(nev_g, BLOCK, 1.0) / BLOCK)
+    return dt, K, blocks * (K + 1)
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    per_step = max(5, args.cpu_sample_steps // 2)
+    for _ in range(args.warmup):
+        oracle_sample(per_step)
+    secs, Ks, nsteps = [], [], []
+    for _ in range(args.steps):
+        dt, K, n = oracle_sample(per_step)
+        secs.append(dt)
+        Ks.append(K)
+        nsteps.append(n)
+    t_solve = statistics.mean(secs) * statistics.mean(nsteps)
+    value = NEV / t_solve
+    sample = (f"{per_step} oracle Clenshaw steps per bench step (scipy CSR x {BLOCK}-column FP64 block, XXZ L=20, "
+              f"W={W_LIST[0]}), extrapolated to one solve of {int(statistics.mean(nsteps))} filter steps "
+              f"(expected Krylov blocks x (K+1)); orthogonalisation not counted")
+    out = {"impl": "reference", "metric": METRIC, "value": value,
+           "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_solve, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "oracle": "plain FP64 numpy/scipy", "K": int(statistics.mean(Ks))},
+           "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_kernel_only(args):
+    import torch
+    import pf_inputs as pi
+    import paper_2605_10191_b300 as pf
+    torch.cuda.set_device(0)
+    p = pi.xxz_params(L_SITES, W=W_LIST[0], seed=SEED0)
+    H = pf.Hamiltonian.from_params(p)
+    H.spectral_bounds()
+    D, s = H.D, BLOCK
+    dt = torch.float32 if args.kernel_precision == "f32" else torch.float64
+    g = torch.Generator(device="cuda").manual_seed(1)
+    V, B1, B2 = (torch.rand(D, s, device="cuda", generator=g, dtype=dt) - 0.5 for _ in range(3))
+    for _ in range(args.warmup):
+        H.clenshaw_step(V, B1, B2, B2, 0.01, 2.0, 1.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        if i % 2 == 0:
+            H.clenshaw_step(V, B1, B2, B2, 0.01, 2.0, 1.0)
+        else:
+            H.clenshaw_step(V, B2, B1, B1, 0.01, 2.0, 1.0)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    w = 4 if dt == torch.float32 else 8
+    byt = step_bytes(D, H.nnz, s, w)
+    print(json.dumps({"kernel": f"clenshaw_step_{args.kernel_precision}_s32", "us_per_launch": 1e3 * ms,
+                      "alg_bytes": byt, "GBps": byt / ms / 1e6, "launches": args.steps}))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import pf_inputs as pi
+    import paper_2605_10191_b300 as pf
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib = pf.lib()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    pinned = torch.empty((NEV, math.comb(L_SITES, L_SITES // 2)), dtype=torch.float64, pin_memory=True)
+
+    def one_step(i, record):
+        r = (rank + i * world) % len(W_LIST)
+        p = pi.xxz_params(L_SITES, W=W_LIST[r], seed=SEED0 + r)
+        st = torch.cuda.current_stream()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(st)
+        H = pf.Hamiltonian.from_params(p)
+        H.spectral_bounds()
+        K = H.choose_K(EPS, NEV)
+        res = H.solve(EPS, NEV, K, block=BLOCK, precision=args.precision, raise_on_notconv=False)
+        ev[1].record(st)
+        pinned.copy_(res.evecs.t(), non_blocking=True)     # D x nev (column-major) -> host
+        ev[2].record(st)
+        ev[2].synchronize()
+        hn = res.report["hnorm"]
+        good = int(np.sum(res.resid <= RES_TOL * hn))
+        if record is not None:
+            record.append(dict(dev_ms=ev[0].elapsed_time(ev[1]), e2e_ms=ev[0].elapsed_time(ev[2]), good=good,
+                               rep=res.report, D=H.D, nnz=H.nnz, W=W_LIST[r], K=K,
+                               h2d=8 * L_SITES, d2h=pinned.numel() * 8 + 2 * NEV * 8))
+        del res, H
+
+    for i in range(args.warmup):
+        one_step(i, None)
+    barrier()
+    n0 = lib.pf_kernel_launches()
+    rec = []
+    with ClockSampler(local) as clocks:
+        for i in range(args.steps):
+            one_step(args.warmup + i, rec)
+        barrier()
+    launches = lib.pf_kernel_launches() - n0
+    clk = clocks.summary()
+    dev_s = sum(x["dev_ms"] for x in rec) / 1e3
+    e2e_s = sum(x["e2e_ms"] for x in rec) / 1e3
+    good = sum(x["good"] for x in rec)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_s, e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        g = torch.tensor([good, launches], device="cuda", dtype=torch.float64)
+        dist.all_reduce(g, op=dist.ReduceOp.SUM)
+        dev_s, e2e_s = float(t[0]), float(t[1])
+        good, launches = int(g[0]), int(g[1])
+    if rank != 0:
+        return
+    D, nnz = rec[0]["D"], rec[0]["nnz"]
+    # dominant kernel: the fused FP32 Clenshaw step (s=32).  Its average device duration per
+    # launch comes from the library's CUDA events around the filter applications, recorded on
+    # the solve's stream inside this timed region.
+    f32_ms = sum(x["rep"]["ms_filter_f32"] for x in rec)
+    f32_n = sum(x["rep"]["filter_steps_f32"] for x in rec)
+    f64_ms = sum(x["rep"]["ms_filter_f64"] for x in rec)
+    f64_n = sum(x["rep"]["filter_steps_f64"] for x in rec)
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if f32_n:
+        per = f32_ms / f32_n
+        byt = step_bytes(D, nnz, BLOCK, 4)
+        ach = byt / per / 1e6
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": ncu_traffic("clenshaw_f32_xxz_L20_s32"), "kernel": "clenshaw_step_kernel<float,32>",
+                "us_per_launch": 1e3 * per, "alg_bytes_per_launch": byt, "peak_source": peak_kind}
+    roof64 = None
+    if f64_n:
+        per = f64_ms / f64_n
+        flops = 2.0 * nnz * BLOCK + 3.0 * D * BLOCK
+        fp64_peak = 148 * 4 * 2.032e9 / 1e12        # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
+        roof64 = {"bound": "alu", "achieved": flops / per / 1e9, "peak": fp64_peak, "unit": "TFLOP/s",
+                  "frac": flops / per / 1e9 / fp64_peak, "kernel": "clenshaw_step_kernel<double,32>",
+                  "us_per_launch": 1e3 * per}
+    cpu = None
+    if not args.no_cpu_baseline:
+        dt, K0, n = oracle_sample(args.cpu_sample_steps)
+        v = NEV / (dt * n)
+        cpu = {"value": v, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_sample_steps} oracle FP64 Clenshaw steps (scipy CSR x 32-column block, XXZ L=20) "
+                         f"extrapolated to one solve of {n} filter steps (expected Krylov blocks x (K+1), K={K0}); "
+                         f"orthogonalisation not counted"}
+    out = {
+        "metric": METRIC, "value": good / dev_s, "unit": "eigenpairs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / len(rec),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "f32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "model": "XXZ L=20 periodic, J=1, Delta=1, h_i~U[-W,W], W in (1,3,5)",
+                   "D": D, "nnz": nnz, "nev": NEV, "block": BLOCK, "target_eps": EPS,
+                   "precision": ("FP32 filter + FP64 Lanczos/Rayleigh-Ritz/refinement" if args.precision == "f32"
+                                 else "FP64 throughout"),
+                   "K": [x["K"] for x in rec], "realisation_W": [x["W"] for x in rec],
+                   "l2": "inputs larger than L2 (Krylov basis ~1.9 GB per solve)", "parallelism": f"replicas{world}",
+                   "eigenpairs_at_tol": good, "solves": len(rec) * world},
+        "e2e": {"value": good / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": rec[0]["h2d"],
+                "d2h_bytes_per_step": rec[0]["d2h"]},
+        "gpu_launches": int(launches),
+        "roofline": roof, "roofline_fp64_refine": roof64, "cpu_baseline": cpu, "clocks": clk,
+        "phases_ms": {k: statistics.mean(x["rep"][k] for x in rec)
+                      for k in ("ms_filter_f32", "ms_filter_f64", "ms_orth", "ms_qr", "ms_check", "ms_extract",
+                                "ms_refine", "ms_total")},
+        "residual_max_over_hnorm": max(x["rep"]["max_residual"] / x["rep"]["hnorm"] for x in rec),
+        "residual_unrefined_max_over_hnorm": max(x["rep"]["max_residual_unrefined"] / x["rep"]["hnorm"]
+                                                 for x in rec),
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.kernel_only:
+        run_kernel_only(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -91,6 +91,8 @@ pf_status pf_set_allocator(pf_alloc_fn alloc, pf_free_fn release, void* ctx);
 
 const char* pf_status_str(pf_status s);
 const char* pf_last_cuda_error(void);   /* thread-local text of the last CUDA failure */
+/* Cumulative number of kernels this library has launched in the process (diagnostic). */
+long long pf_kernel_launches(void);
 
 /* ---------------------------------------------------------------------------
  * (a1) Basis enumeration.  Sec. 2 intro / App. A.2: the S^z sector of L spins with
@@ -201,11 +203,19 @@ typedef struct {
 
 typedef struct {
   int32_t status, K, blocks, krylov_dim, nev_guard, converged, checks, refine_passes;
-  int64_t filter_steps;        /* Clenshaw steps executed (all precisions)           */
-  int64_t filter_steps_f64;    /* of which FP64                                        */
+  int64_t filter_steps_f32;    /* FP32 Clenshaw steps (one launch each)                */
+  int64_t filter_steps_f64;    /* FP64 Clenshaw steps, Lanczos stage and refinement    */
   double emin, emax, Ec, dE, lambda, lambda_t, hnorm;
   double max_residual;         /* max ||Hu - Eu|| over the returned pairs              */
-  double ms_filter, ms_orth, ms_qr, ms_check, ms_extract, ms_refine, ms_total;
+  double ms_filter_f32;        /* device time of the FP32 filter applications          */
+  double ms_filter_f64;        /* device time of the FP64 filter applications          */
+  double ms_orth;              /* A_k and the two Gram-Schmidt passes                  */
+  double ms_qr;                /* Cholesky QR                                          */
+  double ms_check;             /* eigensolves of H_L at the convergence checks         */
+  double ms_extract;           /* Ritz vectors, Rayleigh-Ritz in H, residuals          */
+  double ms_refine;            /* refinement passes (includes their FP64 filter time)  */
+  double ms_total;
+  double max_residual_unrefined; /* max ||Hu - Eu|| before any refinement pass         */
 } pf_report;
 
 /* Fill o with the defaults listed in pf_solve_opts.                                */

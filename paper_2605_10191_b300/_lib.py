@@ -36,12 +36,13 @@ class pf_solve_opts(C.Structure):
 class pf_report(C.Structure):
     _fields_ = [("status", C.c_int32), ("K", C.c_int32), ("blocks", C.c_int32), ("krylov_dim", C.c_int32),
                 ("nev_guard", C.c_int32), ("converged", C.c_int32), ("checks", C.c_int32),
-                ("refine_passes", C.c_int32), ("filter_steps", C.c_int64), ("filter_steps_f64", C.c_int64),
+                ("refine_passes", C.c_int32), ("filter_steps_f32", C.c_int64), ("filter_steps_f64", C.c_int64),
                 ("emin", C.c_double), ("emax", C.c_double), ("Ec", C.c_double), ("dE", C.c_double),
                 ("lambda_", C.c_double), ("lambda_t", C.c_double), ("hnorm", C.c_double),
-                ("max_residual", C.c_double), ("ms_filter", C.c_double), ("ms_orth", C.c_double),
-                ("ms_qr", C.c_double), ("ms_check", C.c_double), ("ms_extract", C.c_double),
-                ("ms_refine", C.c_double), ("ms_total", C.c_double)]
+                ("max_residual", C.c_double), ("ms_filter_f32", C.c_double), ("ms_filter_f64", C.c_double),
+                ("ms_orth", C.c_double), ("ms_qr", C.c_double), ("ms_check", C.c_double),
+                ("ms_extract", C.c_double), ("ms_refine", C.c_double), ("ms_total", C.c_double),
+                ("max_residual_unrefined", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -58,6 +59,7 @@ PROTOTYPES = {
     "pf_set_allocator": (i32, [ALLOC_FN, FREE_FN, vp]),
     "pf_status_str": (C.c_char_p, [i32]),
     "pf_last_cuda_error": (C.c_char_p, []),
+    "pf_kernel_launches": (C.c_longlong, []),
     "pf_build_basis": (i32, [P(pf_model), P(vp), vp]),
     "pf_basis_info": (i32, [vp, P(i64), P(i64), P(i64)]),
     "pf_basis_states": (i32, [vp, P(vp)]),

@@ -16,6 +16,7 @@
 
 namespace pf {
 
+std::atomic<long long> g_kernel_launches{0};
 static thread_local char g_cuda_err[256] = {0};
 void set_cuda_error(cudaError_t e, const char* where) {
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s", where, cudaGetErrorString(e));
@@ -140,6 +141,7 @@ static pf_status build_basis_impl(const pf_model* m, Basis** out, cudaStream_t s
       unrank_kernel<<<(unsigned)ceil_div(b->D_dn, 256), 256, 0, st>>>(b->states + b->D_up, b->D_dn, L, m->N_dn,
                                                                        b->binom);
     }
+    PF_COUNT(m->kind == PF_MODEL_XXZ ? 1 : 2);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
       set_cuda_error(e, "unrank_kernel");
@@ -338,6 +340,7 @@ static pf_status exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cuda
   scan_block_sums<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(in, n, bs.as<int64_t>());
   scan_offsets<<<1, 32, 0, st>>>(bs.as<int64_t>(), nb);
   scan_apply<<<(unsigned)nb, SCAN_BLOCK, 0, st>>>(in, n, bs.as<int64_t>(), out);
+  PF_COUNT(2);
   PF_LAUNCH_CHECK("exclusive_scan");
   return PF_OK;
 }
@@ -426,6 +429,7 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
   if (!H->row_ptr) { delete H; return PF_ENOMEM; }
   unsigned grid = (unsigned)ceil_div(D, 128);
   count_kernel<<<grid, 128, 0, st>>>(M, D, counts.as<int64_t>());
+  PF_COUNT(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_cuda_error(e, "count_kernel"); dev_free(H->row_ptr, st); delete H; return PF_ECUDA; }
   s = exclusive_scan(counts.as<int64_t>(), D, H->row_ptr, st);
@@ -446,6 +450,7 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
     return PF_ENOMEM;
   }
   fill_kernel<<<grid, 128, 0, st>>>(M, D, H->row_ptr, H->col, H->val);
+  PF_COUNT(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_cuda_error(e, "fill_kernel");
@@ -521,6 +526,7 @@ pf_status ham_moments(Ham* H, double* mu_t, double* G_t, cudaStream_t st) {
   PF_TRY(part.alloc((2 * nb + 2) * sizeof(double), st));
   moments_partial<<<nb, 256, 0, st>>>(H->D, H->row_ptr, H->col, H->val_t, part.as<double>());
   moments_final<<<1, 256, 0, st>>>(part.as<double>(), nb, part.as<double>() + 2 * nb);
+  PF_COUNT(1);
   PF_LAUNCH_CHECK("moments");
   double h[2];
   PF_CUDA(cudaMemcpyAsync(h, part.as<double>() + 2 * nb, sizeof(h), cudaMemcpyDeviceToHost, st));
@@ -548,6 +554,8 @@ pf_status pf_set_allocator(pf_alloc_fn alloc, pf_free_fn release, void* ctx) {
 }
 
 const char* pf_last_cuda_error(void) { return g_cuda_err; }
+
+long long pf_kernel_launches(void) { return g_kernel_launches.load(); }
 
 const char* pf_status_str(pf_status s) {
   switch (s) {

@@ -5,6 +5,7 @@
 #include <string.h>
 #include <stdio.h>
 #include <vector>
+#include <atomic>
 #include "../../include/polfed.h"
 
 #define PF_MAX_S 64
@@ -14,7 +15,11 @@ namespace pf {
 // ---------------------------------------------------------------- errors
 void set_cuda_error(cudaError_t e, const char* where);
 
-#define PF_CUDA(call)                                   \
+// Number of kernels this library has launched (every launch site counts itself).
+extern std::atomic<long long> g_kernel_launches;
+#define PF_COUNT(n) (::pf::g_kernel_launches.fetch_add((n), std::memory_order_relaxed))
+
+#define PF_CUDA(call)                                  \
   do {                                                  \
     cudaError_t _e = (call);                            \
     if (_e != cudaSuccess) {                            \
@@ -25,6 +30,7 @@ void set_cuda_error(cudaError_t e, const char* where);
 
 #define PF_LAUNCH_CHECK(name)                           \
   do {                                                  \
+    PF_COUNT(1);                                        \
     cudaError_t _e = cudaGetLastError();                \
     if (_e != cudaSuccess) {                            \
       ::pf::set_cuda_error(_e, name);                   \

@@ -29,8 +29,11 @@ static int gram_chunks(int64_t D, int nbX, int nbY) {
   return (int)c;
 }
 
+// Upper bound of the partial-tile scratch for every nbX' <= nbX, nbY' <= nbY:
+// chunks * pairs <= ceil(1184 / pairs) * pairs < 1184 + pairs.
 size_t gram_scratch_elems(int64_t D, int s, int nbX, int nbY) {
-  return (size_t)gram_chunks(D, nbX, nbY) * nbX * nbY * s * s;
+  (void)D;
+  return ((size_t)148 * 8 + (size_t)nbX * nbY) * s * s;
 }
 
 // partial[chunk][bx][by][a][b]

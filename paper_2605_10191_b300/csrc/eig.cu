@@ -306,6 +306,7 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
     symv_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Aw, n, j, tau, p);
     wvec_kernel<<<1, 256, 0, st>>>(Aw, n, j, tau, p);
     rank2_kernel<<<(unsigned)ceil_div((int64_t)m * m, 256), 256, 0, st>>>(Aw, n, j, p);
+    PF_COUNT(4);
   }
   tri_finish_kernel<<<1, 32, 0, st>>>(Aw, n, d, e, tau);
   PF_LAUNCH_CHECK("tridiagonalisation");

@@ -70,6 +70,7 @@ static pf_status filter_coefficients_dev(double lam_t, int K, double* host, cuda
   PF_TRY(b.alloc((size_t)2 * (K + 1) * sizeof(double), st));
   coeff_kernel<<<1, 1024, 0, st>>>(lam_t, K, b.as<double>(), b.as<double>() + K + 1);
   coeff_norm_kernel<<<1, 1024, 0, st>>>(K, b.as<double>(), b.as<double>() + K + 1);
+  PF_COUNT(1);
   PF_LAUNCH_CHECK("coeff_kernel");
   PF_CUDA(cudaMemcpyAsync(host, b.p, (K + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
   PF_CUDA(cudaStreamSynchronize(st));
@@ -218,16 +219,35 @@ static pf_status apply_op(Solver& S, OpKind op, const double* Vk, double* Wk, co
     return clenshaw_step_raw(S.D, H->row_ptr, H->col, H->val, PF_F64, S.s, Vk, Vk, nullptr, Wk, 0.0, 1.0, 0.0, S.st);
   }
   if (op == OP_FILTER64) {
-    S.rep.filter_steps += K + 1;
     S.rep.filter_steps_f64 += K + 1;
     return filter_apply_raw(H, PF_F64, S.s, Vk, Wk, coeffs, nullptr, K, S.aux0.p, S.aux1.p, S.st);
   }
-  S.rep.filter_steps += K + 1;
+  S.rep.filter_steps_f32 += K + 1;
   const int64_t n = S.D * S.s;
   PF_TRY(convert_d2f(Vk, S.V32.as<float>(), n, S.st));
   PF_TRY(filter_apply_raw(H, PF_F32, S.s, S.V32.p, S.W32.p, coeffs, nullptr, K, S.aux0.p, S.aux1.p, S.st));
   return convert_f2d(S.W32.as<float>(), Wk, n, S.st);
 }
+
+// Device-time accounting of the solve's phases: events recorded on the solve's stream,
+// read back when the phase's last event has completed.
+struct PhaseClock {
+  cudaEvent_t ev[8];
+  cudaStream_t st;
+  explicit PhaseClock(cudaStream_t s) : st(s) {
+    for (auto& e : ev) cudaEventCreate(&e);
+  }
+  ~PhaseClock() {
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+  void mark(int i) { cudaEventRecord(ev[i], st); }
+  double ms(int a, int b) {
+    float t = 0;
+    cudaEventSynchronize(ev[b]);
+    cudaEventElapsedTime(&t, ev[a], ev[b]);
+    return t;
+  }
+};
 
 struct LanczosResult {
   int blocks = 0;      // number of Krylov blocks in the basis (M = blocks * s)
@@ -242,17 +262,14 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
                                double tol, bool tol_relative, int check_first, int check_every, LanczosResult& out) {
   const int s = S.s;
   const int64_t D = S.D;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  float ms = 0;
+  PhaseClock clk(S.st);
   int k = 0;
   for (;;) {
     double* Vk = blockp(S, k);
     double* W = S.W.as<double>();
-    cudaEventRecord(e0, S.st);
+    clk.mark(0);
     PF_TRY(apply_op(S, op, Vk, W, coeffs, K));
-    cudaEventRecord(e1, S.st);
+    clk.mark(1);
     // A_k = V_k^T W
     PF_TRY(gram(D, s, Vk, 1, W, 1, S.Ab, S.gscr.as<double>(), S.gscr_elems, S.st));
     hl_store_kernel<<<1, 256, 0, S.st>>>(S.HL.as<double>(), S.Mcap, k, s, S.Ab, nullptr);
@@ -262,6 +279,7 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
       PF_TRY(gram(D, s, S.V.as<double>(), k + 1, W, 1, S.Cg.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
       PF_TRY(tsgemm(D, s, S.V.as<double>(), k + 1, S.Cg.as<double>(), s, W, 1, -1.0, 1.0, S.st));
     }
+    clk.mark(2);
     // full: the basis spans the whole space, so B_{k+1} = 0 exactly.  cap: no room for
     // another block; B_{k+1} comes from the Cholesky factor of W^T W alone (enough for
     // ||B tau||), and the iteration stops.
@@ -280,9 +298,10 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
     }
     hl_store_kernel<<<1, 256, 0, S.st>>>(S.HL.as<double>(), S.Mcap, k, s, nullptr, S.Bb);
     PF_LAUNCH_CHECK("hl_store_kernel");
-    cudaEventSynchronize(e1);
-    cudaEventElapsedTime(&ms, e0, e1);
-    S.rep.ms_filter += ms;
+    clk.mark(3);
+    (op == OP_FILTER32 ? S.rep.ms_filter_f32 : S.rep.ms_filter_f64) += clk.ms(0, 1);
+    S.rep.ms_orth += clk.ms(1, 2);
+    S.rep.ms_qr += clk.ms(2, 3);
     ++k;
     const int M = k * s;
     const bool last = (k + 1 > S.max_blocks) || exhausted;
@@ -298,12 +317,15 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
       }
       const int nq = (int)idx.size();
       std::vector<double> th(nq), res(nq);
+      clk.mark(4);
       PF_TRY(sym_eig_select(S.HL.as<double>(), S.Mcap, M, idx.data(), nq, th.data(), S.Z.as<double>(), M,
                             S.eigw.p, S.eig_bytes, S.st));
       block_resid_kernel<<<(unsigned)ceil_div(nq, 64), 64, 0, S.st>>>(S.Bb, s, S.Z.as<double>(), M, M, nq, S.res);
       PF_LAUNCH_CHECK("block_resid_kernel");
       PF_CUDA(cudaMemcpyAsync(res.data(), S.res, nq * 8, cudaMemcpyDeviceToHost, S.st));
+      clk.mark(5);
       PF_CUDA(cudaStreamSynchronize(S.st));
+      S.rep.ms_check += clk.ms(4, 5);
       S.rep.checks++;
       double scale = 1.0;
       if (tol_relative) scale = std::max(std::fabs(th.front()), std::fabs(th.back()));
@@ -324,8 +346,6 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
       break;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   return PF_OK;
 }
 
@@ -515,6 +535,8 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
   S.rep.krylov_dim = R.blocks * s;
   const int M = R.blocks * s;
   if ((int)R.idx.size() < nev_g) return PF_ENOTCONV;
+  PhaseClock clk(st);
+  clk.mark(0);
   // Ritz vectors for the qpad largest theta (the nev_g checked plus padding to whole blocks)
   std::vector<int> idx;
   const int qsel = std::min(qpad, M);
@@ -546,6 +568,9 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
     for (int j : sel) m = std::max(m, res[j]);
     return m;
   };
+  clk.mark(1);
+  S.rep.ms_extract = clk.ms(0, 1);
+  S.rep.max_residual_unrefined = max_res();
   // FP64 refinement for the FP32 filter
   int passes = 0;
   const int max_pass = o.refine_passes < 0 ? 0 : (o.refine_passes == 0 ? 3 : o.refine_passes);
@@ -558,17 +583,21 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
     PF_TRY(aux64a.alloc((size_t)H->D * s * 8, st));
     PF_TRY(aux64b.alloc((size_t)H->D * s * 8, st));
     while (passes < max_pass && max_res() > res_tol * hnorm) {
+      clk.mark(2);
       for (int b = 0; b < qb; ++b) {
         PF_TRY(filter_apply_raw(H, PF_F64, s, U.as<double>() + (int64_t)b * H->D * s,
                                 HU.as<double>() + (int64_t)b * H->D * s, coeffs_r.data(), nullptr, Kr, aux64a.p,
                                 aux64b.p, st));
-        S.rep.filter_steps += Kr + 1;
         S.rep.filter_steps_f64 += Kr + 1;
       }
+      clk.mark(3);
       PF_CUDA(cudaMemcpyAsync(U.p, HU.p, (size_t)qb * H->D * s * 8, cudaMemcpyDeviceToDevice, st));
       PF_TRY(orthonormalise_set(S, U, HU, qb));
       PF_TRY(rayleigh_ritz_H(S, U, HU, qb, E, res));
       sel = nearest_sel(E, lam, nev);
+      clk.mark(4);
+      S.rep.ms_filter_f64 += clk.ms(2, 3);
+      S.rep.ms_refine += clk.ms(2, 4);
       ++passes;
     }
   }
