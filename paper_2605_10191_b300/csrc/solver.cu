@@ -502,6 +502,7 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
   const int check_every = o.check_every > 0 ? o.check_every : std::max(1, (int)std::ceil(0.1 * m_est));
   const int qb = (nev_g + s - 1) / s;     // Ritz blocks extracted
   const int qpad = qb * s;
+  const int q_reserve = f32 ? 2 * s : 0;  // extra Ritz vectors kept for the refinement set
 
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
@@ -509,7 +510,7 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
   cudaEventRecord(t0, st);
 
   Solver S;
-  PF_TRY(solver_init(S, H, s, max_blocks, std::max(qpad, nev_g), f32, st));
+  PF_TRY(solver_init(S, H, s, max_blocks, std::max(qpad + q_reserve, nev_g), f32, st));
   const double lam = o.use_abs_target ? o.target_abs : H->emin + target_eps * (H->emax - H->emin);
   const double lam_t = (lam - H->Ec) / H->dE;
   if (!(lam_t > -1.0 && lam_t < 1.0)) return PF_EINVAL;
@@ -537,29 +538,32 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
   if ((int)R.idx.size() < nev_g) return PF_ENOTCONV;
   PhaseClock clk(st);
   clk.mark(0);
-  // Ritz vectors for the qpad largest theta (the nev_g checked plus padding to whole blocks)
+  // Ritz vectors for the largest theta: qb blocks (the nev_g checked, padded to whole blocks)
+  // and, for the FP32 filter, up to two reserve blocks that join the refinement set when it
+  // stalls.  M >= qpad (the checks wait for it) and M is a multiple of s.
+  const int nb_total = std::min(qb + q_reserve / s, M / s);
+  const int qtot = nb_total * s;
   std::vector<int> idx;
-  const int qsel = std::min(qpad, M);
-  for (int i = M - qsel; i < M; ++i) idx.push_back(i);
-  std::vector<double> th(qsel);
-  PF_TRY(sym_eig_select(S.HL.as<double>(), S.Mcap, M, idx.data(), qsel, th.data(), S.Z.as<double>(), M, S.eigw.p,
+  for (int i = M - qtot; i < M; ++i) idx.push_back(i);
+  std::vector<double> th(qtot);
+  PF_TRY(sym_eig_select(S.HL.as<double>(), S.Mcap, M, idx.data(), qtot, th.data(), S.Z.as<double>(), M, S.eigw.p,
                         S.eig_bytes, st));
-  // C (M x qpad row-major): columns are the Ritz coefficient vectors, largest theta first; zero padding
+  // C (M x qtot row-major): columns are the Ritz coefficient vectors, largest theta first
   DevBuf perm, U, HU;
-  std::vector<int> pv(qpad);
-  for (int c = 0; c < qpad; ++c) pv[c] = c < qsel ? qsel - 1 - c : 0;
-  PF_TRY(perm.alloc(qpad * sizeof(int), st));
-  PF_CUDA(cudaMemcpyAsync(perm.p, pv.data(), qpad * sizeof(int), cudaMemcpyHostToDevice, st));
-  PF_CUDA(cudaMemsetAsync(S.Cg.p, 0, (size_t)M * qpad * 8, st));
-  z_to_rowmajor_kernel<<<(unsigned)ceil_div((int64_t)M * qsel, 256), 256, 0, st>>>(S.Z.as<double>(), M, M, qsel,
+  std::vector<int> pv(qtot);
+  for (int c = 0; c < qtot; ++c) pv[c] = qtot - 1 - c;
+  PF_TRY(perm.alloc(qtot * sizeof(int), st));
+  PF_CUDA(cudaMemcpyAsync(perm.p, pv.data(), qtot * sizeof(int), cudaMemcpyHostToDevice, st));
+  z_to_rowmajor_kernel<<<(unsigned)ceil_div((int64_t)M * qtot, 256), 256, 0, st>>>(S.Z.as<double>(), M, M, qtot,
                                                                                    perm.as<int>(), S.Cg.as<double>(),
-                                                                                   qpad);
+                                                                                   qtot);
   PF_LAUNCH_CHECK("z_to_rowmajor_kernel");
-  PF_TRY(U.alloc((size_t)qb * H->D * s * 8, st));
-  PF_TRY(HU.alloc((size_t)qb * H->D * s * 8, st));
-  for (int b = 0; b < qb; ++b)
-    PF_TRY(tsgemm(H->D, s, S.V.as<double>(), R.blocks, S.Cg.as<double>() + b * s, qpad,
+  PF_TRY(U.alloc((size_t)nb_total * H->D * s * 8, st));
+  PF_TRY(HU.alloc((size_t)nb_total * H->D * s * 8, st));
+  for (int b = 0; b < nb_total; ++b)
+    PF_TRY(tsgemm(H->D, s, S.V.as<double>(), R.blocks, S.Cg.as<double>() + b * s, qtot,
                   U.as<double>() + (int64_t)b * H->D * s, 1, 1.0, 0.0, st));
+  int nb = qb;   // active Ritz blocks; blocks nb..nb_total-1 of U hold the reserve
   std::vector<double> E, res;
   PF_TRY(rayleigh_ritz_H(S, U, HU, qb, E, res));
   std::vector<int> sel = nearest_sel(E, lam, nev);
@@ -571,34 +575,51 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
   clk.mark(1);
   S.rep.ms_extract = clk.ms(0, 1);
   S.rep.max_residual_unrefined = max_res();
-  // FP64 refinement for the FP32 filter
+  // FP64 refinement for the FP32 filter: subspace iteration U <- (P(H~) + c I) U on the active
+  // blocks, Cholesky QR, Rayleigh-Ritz in H.  An error component on eigenvalue k shrinks by
+  // |P_k + c| / (P_j + c) per pass for wanted pair j.  The first pass is unshifted (c = 0),
+  // which removes the far bulk (P ~ 0) fastest.  If a pass reduces the residual less than
+  // 10x, the remaining error sits where |P| is comparable to the edge pairs' P (~0.2): the
+  // filter's negative sidelobe (minimum ~ -0.22) or positive values just outside the set.
+  // Then one reserve block joins the set and later passes use c = 0.06, which halves the
+  // contraction factor on the negative sidelobe at the cost of the far bulk.
   int passes = 0;
-  const int max_pass = o.refine_passes < 0 ? 0 : (o.refine_passes == 0 ? 3 : o.refine_passes);
+  const int max_pass = o.refine_passes < 0 ? 0 : (o.refine_passes == 0 ? 8 : o.refine_passes);
   const int Kr = o.refine_K > 0 ? o.refine_K : K;
   std::vector<double> coeffs_r;
   if (f32 && max_res() > res_tol * hnorm && max_pass > 0) {
     coeffs_r.resize(Kr + 1);
     PF_TRY(filter_coefficients_dev(lam_t, Kr, coeffs_r.data(), st));
+    const double a0 = coeffs_r[0];
     DevBuf aux64a, aux64b;
     PF_TRY(aux64a.alloc((size_t)H->D * s * 8, st));
     PF_TRY(aux64b.alloc((size_t)H->D * s * 8, st));
+    double prev = max_res();
+    bool shifted = false;
     while (passes < max_pass && max_res() > res_tol * hnorm) {
+      coeffs_r[0] = shifted ? a0 + 0.06 : a0;
       clk.mark(2);
-      for (int b = 0; b < qb; ++b) {
+      for (int b = 0; b < nb; ++b) {
         PF_TRY(filter_apply_raw(H, PF_F64, s, U.as<double>() + (int64_t)b * H->D * s,
                                 HU.as<double>() + (int64_t)b * H->D * s, coeffs_r.data(), nullptr, Kr, aux64a.p,
                                 aux64b.p, st));
         S.rep.filter_steps_f64 += Kr + 1;
       }
       clk.mark(3);
-      PF_CUDA(cudaMemcpyAsync(U.p, HU.p, (size_t)qb * H->D * s * 8, cudaMemcpyDeviceToDevice, st));
-      PF_TRY(orthonormalise_set(S, U, HU, qb));
-      PF_TRY(rayleigh_ritz_H(S, U, HU, qb, E, res));
+      PF_CUDA(cudaMemcpyAsync(U.p, HU.p, (size_t)nb * H->D * s * 8, cudaMemcpyDeviceToDevice, st));
+      PF_TRY(orthonormalise_set(S, U, HU, nb));
+      PF_TRY(rayleigh_ritz_H(S, U, HU, nb, E, res));
       sel = nearest_sel(E, lam, nev);
       clk.mark(4);
       S.rep.ms_filter_f64 += clk.ms(2, 3);
       S.rep.ms_refine += clk.ms(2, 4);
       ++passes;
+      const double cur = max_res();
+      if (cur > res_tol * hnorm && cur > 0.1 * prev) {
+        shifted = true;
+        if (nb < nb_total) ++nb;
+      }
+      prev = cur;
     }
   }
   S.rep.refine_passes = passes;
