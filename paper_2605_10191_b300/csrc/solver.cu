@@ -351,8 +351,13 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
 
 static pf_status spectral_bounds_impl(Ham* H, double tol, cudaStream_t st) {
   if (tol <= 0) tol = 1e-10;
+  // Block width 4 (resolves extremal multiplicities up to 4).  When the whole space fits in
+  // the Krylov budget (D <= 600), the width is a power of two dividing D, so the last block
+  // completes the space and the extremes are then exact.
   int s = 4;
   while (s > 1 && 2 * s > H->D) s >>= 1;
+  if (H->D <= 600)
+    while (s > 1 && H->D % s != 0) s >>= 1;
   int max_blocks = (int)std::min<int64_t>(H->D / s, 600 / s);
   if (max_blocks < 1) max_blocks = 1;
   Solver S;
