@@ -199,6 +199,8 @@ typedef struct {
   uint64_t seed;          /* start block: v[r,c] = SplitMix64(seed, r*s+c) - 1/2     */
   int32_t use_abs_target; /* nonzero: target is target_abs (absolute energy)         */
   double target_abs;
+  double refine_shift;    /* shift c of P + cI in refinement passes after a stall;
+                             0 = 0.06, < 0 = never shift                              */
 } pf_solve_opts;
 
 typedef struct {

@@ -602,7 +602,8 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
     double prev = max_res();
     bool shifted = false;
     while (passes < max_pass && max_res() > res_tol * hnorm) {
-      coeffs_r[0] = shifted ? a0 + 0.06 : a0;
+      const double c_shift = o.refine_shift == 0.0 ? 0.06 : (o.refine_shift < 0.0 ? 0.0 : o.refine_shift);
+      coeffs_r[0] = shifted ? a0 + c_shift : a0;
       clk.mark(2);
       for (int b = 0; b < nb; ++b) {
         PF_TRY(filter_apply_raw(H, PF_F64, s, U.as<double>() + (int64_t)b * H->D * s,
