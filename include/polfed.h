@@ -152,7 +152,7 @@ pf_status pf_filter_coefficients(double lam_t, int32_t K, double* coeffs, pf_str
 
 /* Degree K from the Gaussian DOS with exact moments (Eq. dos_gaussian, Eq. Nev,
  * Eq. K_approx): K = ceil(2.655 sqrt(1 - lam~^2) * 2 rho(lam~) / nev_g),
- * nev_g = ceil(1.2 nev).  target_eps: lambda = Emin + eps (Emax - Emin).  Synchronises. */
+ * nev_g = ceil(1.5 nev).  target_eps: lambda = Emin + eps (Emax - Emin).  Synchronises. */
 pf_status pf_choose_K(pf_ham* H, double target_eps, int32_t nev, int32_t* K, pf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
@@ -186,7 +186,7 @@ pf_status pf_filter_apply(const pf_ham* H, int32_t prec, int32_t s, const void* 
 typedef struct {
   int32_t block;          /* s: 1..64, power of two; 0 = 32                          */
   int32_t precision;      /* pf_precision of the filter recurrence                   */
-  int32_t nev_guard;      /* Ritz pairs converged; 0 = ceil(1.2 nev)                  */
+  int32_t nev_guard;      /* Ritz pairs converged; 0 = ceil(1.5 nev)                  */
   int32_t check_first;    /* first check at this block step; 0 = rule (see DESIGN)   */
   int32_t check_every;    /* check interval in block steps; 0 = rule                 */
   int32_t max_blocks;     /* Krylov budget in blocks; 0 = from eta                    */

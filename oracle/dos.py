@@ -46,8 +46,15 @@ def k_approx(lam_t, delta):
 
 
 def guard_count(nev):
-    """nev_g = ceil(1.2 nev): the Ritz pairs converged so that the nev nearest lambda are safe."""
-    return int(math.ceil(1.2 * nev))
+    """nev_g = ceil(1.5 nev): Ritz pairs converged (and eigenvalues put above the cutoff by K).
+
+    The paper does not fix the margin.  Reading: the nev pairs nearest lambda must have filter
+    values well above the magnitude of the filter's negative sidelobe (the sinc minimum,
+    ~ -0.217, under the reading of Eq. K_approx used for OMEGA), since that ratio bounds how
+    fast an FP64 refinement pass removes errors there; with nev/nev_g = 2/3 the returned
+    edge sits at P ~ sin(2.655/1.5)/(2.655/1.5) ~ 0.55.
+    """
+    return int(math.ceil(1.5 * nev))
 
 
 def choose_K(lam_t, nev_g, D, mu_t, G_t):

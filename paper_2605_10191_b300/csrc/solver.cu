@@ -380,6 +380,13 @@ static pf_status spectral_bounds_impl(Ham* H, double tol, cudaStream_t st) {
   return set_rescale(H, 0.5 * (hi + lo), 0.5 * (hi - lo), st);
 }
 
+// Guard factor: nev_g = ceil(1.5 nev) Ritz pairs of P are converged and the degree K is
+// chosen so that about nev_g eigenvalues lie above the cutoff.  The nev returned (nearest
+// lambda) then have filter values P >~ sinc(2.655 / 1.5) ~ 0.55, well above the magnitude
+// of the filter's negative sidelobe (~0.22), which is what the FP64 refinement must
+// contract relative to them.
+static const double kGuard = 1.5;
+
 static int expected_krylov_dim(int nev, int s, double eta) {
   return (int)std::ceil((20.427 * s + 1.696 * nev) * eta);
 }
@@ -495,7 +502,7 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
   const double eta = o.eta > 0 ? o.eta : 1.5;
   const double tol = f32 ? (o.tol_f32 > 0 ? o.tol_f32 : 1e-7) : (o.tol > 0 ? o.tol : 1e-10);
   const double res_tol = o.res_tol > 0 ? o.res_tol : 1e-9;
-  int nev_g = o.nev_guard > 0 ? o.nev_guard : (int)std::ceil(1.2 * nev);
+  int nev_g = o.nev_guard > 0 ? o.nev_guard : (int)std::ceil(kGuard * nev);
   nev_g = std::max(nev_g, nev);
   if (nev_g > H->D) nev_g = (int)H->D;
   int Mmax = std::min<int64_t>(expected_krylov_dim(nev_g, s, eta), H->D);
@@ -703,7 +710,7 @@ pf_status pf_choose_K(pf_ham* hh, double target_eps, int32_t nev, int32_t* K, pf
   PF_TRY(ham_moments(H, &mu, &G, (cudaStream_t)stream));
   const double lam = H->emin + target_eps * (H->emax - H->emin);
   const double lt = (lam - H->Ec) / H->dE;
-  const int nev_g = (int)std::ceil(1.2 * nev);
+  const int nev_g = (int)std::ceil(kGuard * nev);
   const double rho = (double)H->D / (std::sqrt(2.0 * M_PI) * G) * std::exp(-(lt - mu) * (lt - mu) / (2.0 * G * G));
   const double delta = nev_g / (2.0 * rho);
   const double k = 2.655 * std::sqrt(std::max(1.0 - lt * lt, 0.0)) / delta;
