@@ -176,6 +176,23 @@ pf_status pf_clenshaw_step(const pf_ham* H, int32_t prec, int32_t s, const void*
 pf_status pf_filter_apply(const pf_ham* H, int32_t prec, int32_t s, const void* V, void* W,
                           const double* coeffs, int32_t K, pf_stream_t stream);
 
+/* Same computation as pf_filter_apply, without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate device memory at
+ * the time of the call (a frozen or exhausted memory pool, a host allocator that must not
+ * be re-entered from its own hooks, loops that forbid allocation calls).  The two D x s
+ * auxiliary blocks come from one fixed device array of 32 MiB inside the library, which
+ * every GPU that loads the library keeps until the process exits.
+ *  - Limit: 2 * D * s * w <= 32 MiB, w = 8 (PF_F64) or 4 (PF_F32), each block rounded up
+ *    to 256 bytes; larger requests return PF_EINVAL without touching the GPU.
+ *  - The first call on a device looks up the array's device address (a CUDA symbol
+ *    query, no allocation) and caches it; make that first call before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents (nothing in it needs
+ *    to start at zero).  Calls that can overlap on the GPU (other streams, other threads)
+ *    race on it; serialise them.
+ * Arguments, layout, ownership and the other errors are those of pf_filter_apply.      */
+pf_status pf_filter_apply_noalloc(const pf_ham* H, int32_t prec, int32_t s, const void* V, void* W,
+                                  const double* coeffs, int32_t K, pf_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * (a6-a10) The solve: block Lanczos on P(H~) with full reorthogonalisation (two
  * classical Gram-Schmidt passes), shifted Cholesky QR, the block-tridiagonal

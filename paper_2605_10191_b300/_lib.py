@@ -76,6 +76,7 @@ PROTOTYPES = {
     "pf_choose_K": (i32, [vp, dbl, i32, P(i32), vp]),
     "pf_clenshaw_step": (i32, [vp, i32, i32, vp, vp, vp, vp, dbl, dbl, dbl, i32, vp]),
     "pf_filter_apply": (i32, [vp, i32, i32, vp, vp, P(dbl), i32, vp]),
+    "pf_filter_apply_noalloc": (i32, [vp, i32, i32, vp, vp, P(dbl), i32, vp]),
     "pf_default_opts": (None, [P(pf_solve_opts)]),
     "pf_polfed_solve": (i32, [vp, dbl, i32, i32, P(pf_solve_opts), P(dbl), vp, P(dbl), P(pf_report), vp]),
     "pf_start_block": (i32, [i64, i32, u64, vp, vp]),

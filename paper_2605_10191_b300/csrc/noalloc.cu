@@ -1,0 +1,60 @@
+// Allocation-free variant of the K-step filter application (pf_filter_apply).
+//
+// pf_filter_apply needs two D x s auxiliary blocks for the Clenshaw recurrence and gets
+// them from the library's allocator on every call.  Some callers cannot allow that: code
+// running while a memory pool is frozen or exhausted, hosts whose allocator must not be
+// re-entered from inside their own hooks, or real-time loops that forbid allocation calls.
+// pf_filter_apply_noalloc takes the two blocks from one fixed device array instead, so it
+// calls no allocation routine at all.
+#include "common.cuh"
+#include <mutex>
+
+namespace pf {
+
+// Fixed scratch shared by every call of pf_filter_apply_noalloc: room for both auxiliary
+// blocks (each rounded up to 256 bytes).  Every device that loads the library holds it
+// until the process exits.
+#define PF_NOALLOC_SCRATCH_BYTES (32ull << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PF_NOALLOC_SCRATCH_BYTES];
+
+// In host code g_noalloc_scratch names a host-side shadow, not device memory, so the
+// device address is looked up once per device (with that device current) and cached.
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64] = {nullptr};
+
+static pf_status noalloc_scratch_address(void** out) {
+  int dev = 0;
+  PF_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return PF_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    PF_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return PF_OK;
+}
+
+}  // namespace pf
+
+using namespace pf;
+
+extern "C" pf_status pf_filter_apply_noalloc(const pf_ham* hh, int32_t prec, int32_t s, const void* V, void* W,
+                                             const double* coeffs, int32_t K, pf_stream_t stream) {
+  const Ham* H = reinterpret_cast<const Ham*>(hh);
+  if (!H || !V || !W || !coeffs || K < 1) return PF_EINVAL;
+  if (!H->has_rescale) return PF_ESTATE;
+  if (prec != PF_F64 && prec != PF_F32) return PF_EINVAL;
+  if (!(s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32 || s == 64)) return PF_EINVAL;
+  const size_t w = prec == PF_F64 ? 8 : 4;
+  const size_t blk = ((size_t)H->D * (size_t)s * w + 255) & ~(size_t)255;
+  if (2 * blk > PF_NOALLOC_SCRATCH_BYTES) return PF_EINVAL;   // too large for the fixed scratch
+  void* base = nullptr;
+  PF_TRY(noalloc_scratch_address(&base));
+  // The recurrence never reads the auxiliary blocks before writing them (b_{K+1} and
+  // b_{K+2} are zero and are skipped), so the previous call's contents need no clearing.
+  void* aux0 = base;
+  void* aux1 = static_cast<unsigned char*>(base) + blk;
+  return filter_apply_raw(H, prec, s, V, W, coeffs, nullptr, K, aux0, aux1, (cudaStream_t)stream);
+}
