@@ -175,11 +175,16 @@ __device__ __forceinline__ double hash_unit(uint64_t a) {
   return (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
 }
 
-// One thread per cluster [cs[c], cs[c+1]) of selected eigenvalues.
+// One CTA per cluster [cs[c], cs[c+1]) of selected eigenvalues.  Thread 0 factors
+// T - lambda I (tridiagonal LU with partial pivoting) and runs the two triangular solves,
+// which are sequential; the whole CTA does the Gram-Schmidt against the cluster's earlier
+// members and the normalisation.
 __global__ void inviter_kernel(const double* d, const double* e, int n, const double* w, const int* cs, int ncl,
                                double* Y, double* lu, double tnorm) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double sh[32];
+  const int c = blockIdx.x;
   if (c >= ncl) return;
+  const int t = threadIdx.x;
   double* dl = lu + (int64_t)c * 6 * n;
   double* dd = dl + n;
   double* du = dd + n;
@@ -193,68 +198,77 @@ __global__ void inviter_kernel(const double* d, const double* e, int n, const do
     double lam = w[p];
     if (p > cs[c] && lam - lam_prev < pertol) lam = lam_prev + pertol;
     lam_prev = lam;
-    // factor T - lam I with partial pivoting
-    for (int i = 0; i < n; ++i) {
-      dd[i] = d[i] - lam;
-      if (i < n - 1) {
-        dl[i] = e[i];
-        du[i] = e[i];
-      }
-      du2[i] = 0.0;
-      piv[i] = 0.0;
-    }
-    for (int i = 0; i < n - 1; ++i) {
-      if (fabs(dd[i]) >= fabs(dl[i])) {
-        double f = dd[i] != 0.0 ? dl[i] / dd[i] : 0.0;
-        dl[i] = f;
-        dd[i + 1] -= f * du[i];
-      } else {
-        double f = dd[i] / dl[i];
-        dd[i] = dl[i];
-        dl[i] = f;
-        double tmp = du[i];
-        du[i] = dd[i + 1];
-        dd[i + 1] = tmp - f * dd[i + 1];
-        if (i < n - 2) {
-          du2[i] = du[i + 1];
-          du[i + 1] = -f * du[i + 1];
-        }
-        piv[i] = 1.0;
-      }
-    }
-    for (int i = 0; i < n; ++i)
-      if (dd[i] == 0.0) dd[i] = pertol > 0 ? pertol : 1e-300;
     double* y = Y + (int64_t)p * n;
-    for (int i = 0; i < n; ++i) y[i] = hash_unit(((uint64_t)p << 32) ^ (uint64_t)i);
-    for (int it = 0; it < 4; ++it) {
-      for (int i = 0; i < n; ++i) b[i] = y[i];
-      // L solve with the row interchanges
+    for (int i = t; i < n; i += blockDim.x) y[i] = hash_unit(((uint64_t)p << 32) ^ (uint64_t)i);
+    if (t == 0) {
+      for (int i = 0; i < n; ++i) {
+        dd[i] = d[i] - lam;
+        if (i < n - 1) {
+          dl[i] = e[i];
+          du[i] = e[i];
+        }
+        du2[i] = 0.0;
+        piv[i] = 0.0;
+      }
       for (int i = 0; i < n - 1; ++i) {
-        if (piv[i] != 0.0) {
-          double tmp = b[i];
-          b[i] = b[i + 1];
-          b[i + 1] = tmp - dl[i] * b[i];
+        if (fabs(dd[i]) >= fabs(dl[i])) {
+          double f = dd[i] != 0.0 ? dl[i] / dd[i] : 0.0;
+          dl[i] = f;
+          dd[i + 1] -= f * du[i];
         } else {
-          b[i + 1] -= dl[i] * b[i];
+          double f = dd[i] / dl[i];
+          dd[i] = dl[i];
+          dl[i] = f;
+          double tmp = du[i];
+          du[i] = dd[i + 1];
+          dd[i + 1] = tmp - f * dd[i + 1];
+          if (i < n - 2) {
+            du2[i] = du[i + 1];
+            du[i + 1] = -f * du[i + 1];
+          }
+          piv[i] = 1.0;
         }
       }
-      // U solve
-      b[n - 1] /= dd[n - 1];
-      if (n > 1) b[n - 2] = (b[n - 2] - du[n - 2] * b[n - 1]) / dd[n - 2];
-      for (int i = n - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
+      for (int i = 0; i < n; ++i)
+        if (dd[i] == 0.0) dd[i] = pertol > 0 ? pertol : 1e-300;
+    }
+    __syncthreads();
+    for (int it = 0; it < 4; ++it) {
+      for (int i = t; i < n; i += blockDim.x) b[i] = y[i];
+      __syncthreads();
+      if (t == 0) {
+        // L solve with the row interchanges
+        for (int i = 0; i < n - 1; ++i) {
+          if (piv[i] != 0.0) {
+            double tmp = b[i];
+            b[i] = b[i + 1];
+            b[i + 1] = tmp - dl[i] * b[i];
+          } else {
+            b[i + 1] -= dl[i] * b[i];
+          }
+        }
+        // U solve
+        b[n - 1] /= dd[n - 1];
+        if (n > 1) b[n - 2] = (b[n - 2] - du[n - 2] * b[n - 1]) / dd[n - 2];
+        for (int i = n - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
+      }
+      __syncthreads();
       // orthogonalise against earlier members of the cluster (twice)
       for (int pass = 0; pass < 2; ++pass)
         for (int q = cs[c]; q < p; ++q) {
           const double* z = Y + (int64_t)q * n;
           double g = 0.0;
-          for (int i = 0; i < n; ++i) g = fma(z[i], b[i], g);
-          for (int i = 0; i < n; ++i) b[i] -= g * z[i];
+          for (int i = t; i < n; i += blockDim.x) g = fma(z[i], b[i], g);
+          g = block_sum(g, sh);
+          for (int i = t; i < n; i += blockDim.x) b[i] -= g * z[i];
+          __syncthreads();
         }
       double nrm = 0.0;
-      for (int i = 0; i < n; ++i) nrm = fma(b[i], b[i], nrm);
-      nrm = sqrt(nrm);
+      for (int i = t; i < n; i += blockDim.x) nrm = fma(b[i], b[i], nrm);
+      nrm = sqrt(block_sum(nrm, sh));
       if (!(nrm > 0.0)) nrm = 1.0;
-      for (int i = 0; i < n; ++i) y[i] = b[i] / nrm;
+      for (int i = t; i < n; i += blockDim.x) y[i] = b[i] / nrm;
+      __syncthreads();
     }
   }
 }
@@ -333,7 +347,7 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
   cs.push_back(q);
   const int ncl = (int)cs.size() - 1;
   PF_CUDA(cudaMemcpyAsync(cl, cs.data(), cs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  inviter_kernel<<<(unsigned)ceil_div(ncl, 32), 32, 0, st>>>(d, e, n, w, cl, ncl, Y, lu, tnorm);
+  inviter_kernel<<<(unsigned)ncl, 256, 0, st>>>(d, e, n, w, cl, ncl, Y, lu, tnorm);
   PF_LAUNCH_CHECK("inviter_kernel");
   const size_t smem = (size_t)n * sizeof(double);
   if (smem > 48 * 1024) {

@@ -111,6 +111,16 @@ __global__ void z_to_rowmajor_kernel(const double* Z, int ldz, int n, int q, con
   C[(int64_t)r * ldc + c] = Z[(int64_t)perm[c] * ldz + r];
 }
 
+// out column c = in column perm[c], both blocked D x s storage, q columns
+__global__ void permute_cols_kernel(int64_t D, int s, const double* in, const int* perm, int q, double* out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= D * q) return;
+  int c = (int)(i % q);
+  int64_t r = i / q;
+  int p = perm[c];
+  out[(int64_t)(c / s) * D * s + r * s + (c % s)] = in[(int64_t)(p / s) * D * s + r * s + (p % s)];
+}
+
 // evecs[:, j] (column-major D x nev) = U column sel[j] (blocked D x s storage)
 __global__ void gather_cols_kernel(int64_t D, int s, const double* U, const int* sel, int nev, double* out) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -392,20 +402,20 @@ static int expected_krylov_dim(int nev, int s, double eta) {
 }
 
 // H-space Rayleigh-Ritz on the blocked set U (nb blocks): U <- U Z, E = eig(U^T H U), residual norms.
-static pf_status rayleigh_ritz_H(Solver& S, DevBuf& U, DevBuf& HU, int nb, std::vector<double>& E,
+static pf_status rayleigh_ritz_H(Solver& S, double* U, double* HU, int nb, std::vector<double>& E,
                                  std::vector<double>& res) {
   const int s = S.s;
   const int64_t D = S.D;
   const int q = nb * s;
   const Ham* H = S.H;
   for (int b = 0; b < nb; ++b) {
-    const double* Ub = U.as<double>() + (int64_t)b * D * s;
-    double* HUb = HU.as<double>() + (int64_t)b * D * s;
+    const double* Ub = U + (int64_t)b * D * s;
+    double* HUb = HU + (int64_t)b * D * s;
     PF_TRY(clenshaw_step_raw(D, H->row_ptr, H->col, H->val, PF_F64, s, Ub, Ub, nullptr, HUb, 0.0, 1.0, 0.0, S.st));
   }
   DevBuf G;
   PF_TRY(G.alloc((size_t)q * q * 8, S.st));
-  PF_TRY(gram(D, s, U.as<double>(), nb, HU.as<double>(), nb, G.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
+  PF_TRY(gram(D, s, U, nb, HU, nb, G.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
   std::vector<int> idx(q);
   std::iota(idx.begin(), idx.end(), 0);
   E.assign(q, 0.0);
@@ -425,19 +435,19 @@ static pf_status rayleigh_ritz_H(Solver& S, DevBuf& U, DevBuf& HU, int nb, std::
   PF_LAUNCH_CHECK("z_to_rowmajor_kernel");
   // U2 = U C into HU's storage, then copy back; HU recomputed from U2
   for (int b = 0; b < nb; ++b)
-    PF_TRY(tsgemm(D, s, U.as<double>(), nb, Cr.as<double>() + b * s, q, HU.as<double>() + (int64_t)b * D * s, 1,
+    PF_TRY(tsgemm(D, s, U, nb, Cr.as<double>() + b * s, q, HU + (int64_t)b * D * s, 1,
                   1.0, 0.0, S.st));
-  PF_CUDA(cudaMemcpyAsync(U.p, HU.p, (size_t)nb * D * s * 8, cudaMemcpyDeviceToDevice, S.st));
+  PF_CUDA(cudaMemcpyAsync(U, HU, (size_t)nb * D * s * 8, cudaMemcpyDeviceToDevice, S.st));
   for (int b = 0; b < nb; ++b) {
-    const double* Ub = U.as<double>() + (int64_t)b * D * s;
-    double* HUb = HU.as<double>() + (int64_t)b * D * s;
+    const double* Ub = U + (int64_t)b * D * s;
+    double* HUb = HU + (int64_t)b * D * s;
     PF_TRY(clenshaw_step_raw(D, H->row_ptr, H->col, H->val, PF_F64, s, Ub, Ub, nullptr, HUb, 0.0, 1.0, 0.0, S.st));
   }
   PF_TRY(E_dev.alloc(q * 8, S.st));
   PF_CUDA(cudaMemcpyAsync(E_dev.p, E.data(), q * 8, cudaMemcpyHostToDevice, S.st));
   DevBuf rn;
   PF_TRY(rn.alloc(q * 8, S.st));
-  PF_TRY(colnorms(D, s, HU.as<double>(), U.as<double>(), E_dev.as<double>(), nb, rn.as<double>(), S.gscr.as<double>(),
+  PF_TRY(colnorms(D, s, HU, U, E_dev.as<double>(), nb, rn.as<double>(), S.gscr.as<double>(),
                   S.gscr_elems, S.st));
   res.assign(q, 0.0);
   PF_CUDA(cudaMemcpyAsync(res.data(), rn.p, q * 8, cudaMemcpyDeviceToHost, S.st));
@@ -446,7 +456,7 @@ static pf_status rayleigh_ritz_H(Solver& S, DevBuf& U, DevBuf& HU, int nb, std::
 }
 
 // Orthonormalise a blocked set (nb blocks) with two Cholesky-QR passes on the whole set.
-static pf_status orthonormalise_set(Solver& S, DevBuf& U, DevBuf& T, int nb) {
+static pf_status orthonormalise_set(Solver& S, double* U, double* T, int nb) {
   const int s = S.s;
   const int q = nb * s;
   const int64_t D = S.D;
@@ -457,13 +467,13 @@ static pf_status orthonormalise_set(Solver& S, DevBuf& U, DevBuf& T, int nb) {
   PF_TRY(st.alloc(16, S.st));
   const double u = 1.1102230246251565e-16;
   for (int pass = 0; pass < 2; ++pass) {
-    PF_TRY(gram(D, s, U.as<double>(), nb, U.as<double>(), nb, G.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
+    PF_TRY(gram(D, s, U, nb, U, nb, G.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
     const double shift = pass == 0 ? 11.0 * ((double)D * q + (double)q * (q + 1)) * u : 0.0;
     PF_TRY(small_chol_inv(G.as<double>(), q, shift, R.as<double>(), Ri.as<double>(), st.as<int>(), S.st));
     for (int b = 0; b < nb; ++b)
-      PF_TRY(tsgemm(D, s, U.as<double>(), nb, Ri.as<double>() + b * s, q, T.as<double>() + (int64_t)b * D * s, 1, 1.0,
+      PF_TRY(tsgemm(D, s, U, nb, Ri.as<double>() + b * s, q, T + (int64_t)b * D * s, 1, 1.0,
                     0.0, S.st));
-    PF_CUDA(cudaMemcpyAsync(U.p, T.p, (size_t)nb * D * s * 8, cudaMemcpyDeviceToDevice, S.st));
+    PF_CUDA(cudaMemcpyAsync(U, T, (size_t)nb * D * s * 8, cudaMemcpyDeviceToDevice, S.st));
     int bad = 0;
     PF_CUDA(cudaMemcpyAsync(&bad, st.p, sizeof(int), cudaMemcpyDeviceToHost, S.st));
     PF_CUDA(cudaStreamSynchronize(S.st));
@@ -577,7 +587,7 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
                   U.as<double>() + (int64_t)b * H->D * s, 1, 1.0, 0.0, st));
   int nb = qb;   // active Ritz blocks; blocks nb..nb_total-1 of U hold the reserve
   std::vector<double> E, res;
-  PF_TRY(rayleigh_ritz_H(S, U, HU, qb, E, res));
+  PF_TRY(rayleigh_ritz_H(S, U.as<double>(), HU.as<double>(), qb, E, res));
   std::vector<int> sel = nearest_sel(E, lam, nev);
   auto max_res = [&]() {
     double m = 0;
@@ -608,20 +618,62 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
     PF_TRY(aux64b.alloc((size_t)H->D * s * 8, st));
     double prev = max_res();
     bool shifted = false;
+    const int64_t DS = H->D * s;
+    double* Ud = U.as<double>();
+    double* HUd = HU.as<double>();
     while (passes < max_pass && max_res() > res_tol * hnorm) {
       const double c_shift = o.refine_shift == 0.0 ? 0.06 : (o.refine_shift < 0.0 ? 0.0 : o.refine_shift);
       coeffs_r[0] = shifted ? a0 + c_shift : a0;
+      // Locking: returned pairs already within half the tolerance stay in the set but are
+      // not filtered; they move to the leading blocks (rounded down to whole blocks by
+      // keeping the worst of them active).  Columns without a residual yet (a reserve block
+      // just added) are active.
+      const int q = nb * s;
+      std::vector<char> is_sel(q, 0);
+      for (int j : sel) is_sel[j] = 1;
+      std::vector<int> locked, active;
+      for (int c = 0; c < q; ++c) {
+        if (c < (int)res.size() && is_sel[c] && res[c] <= 0.5 * res_tol * hnorm) locked.push_back(c);
+        else active.push_back(c);
+      }
+      std::sort(locked.begin(), locked.end(), [&](int x, int y) { return res[x] < res[y]; });
+      while (active.size() % s != 0) {
+        active.push_back(locked.back());
+        locked.pop_back();
+      }
+      const int Lb = (int)locked.size() / s;
+      const int na = nb - Lb;
+      if (Lb > 0) {
+        std::vector<int> order(locked);
+        order.insert(order.end(), active.begin(), active.end());
+        DevBuf pd;
+        PF_TRY(pd.alloc(q * sizeof(int), st));
+        PF_CUDA(cudaMemcpyAsync(pd.p, order.data(), q * sizeof(int), cudaMemcpyHostToDevice, st));
+        permute_cols_kernel<<<(unsigned)ceil_div(H->D * q, 256), 256, 0, st>>>(H->D, s, Ud, pd.as<int>(), q, HUd);
+        PF_LAUNCH_CHECK("permute_cols_kernel");
+        PF_CUDA(cudaMemcpyAsync(Ud, HUd, (size_t)q * H->D * 8, cudaMemcpyDeviceToDevice, st));
+        PF_CUDA(cudaStreamSynchronize(st));
+      }
       clk.mark(2);
-      for (int b = 0; b < nb; ++b) {
-        PF_TRY(filter_apply_raw(H, PF_F64, s, U.as<double>() + (int64_t)b * H->D * s,
-                                HU.as<double>() + (int64_t)b * H->D * s, coeffs_r.data(), nullptr, Kr, aux64a.p,
-                                aux64b.p, st));
+      for (int b = Lb; b < nb; ++b) {
+        PF_TRY(filter_apply_raw(H, PF_F64, s, Ud + (int64_t)b * DS, HUd + (int64_t)b * DS, coeffs_r.data(), nullptr,
+                                Kr, aux64a.p, aux64b.p, st));
         S.rep.filter_steps_f64 += Kr + 1;
       }
       clk.mark(3);
-      PF_CUDA(cudaMemcpyAsync(U.p, HU.p, (size_t)nb * H->D * s * 8, cudaMemcpyDeviceToDevice, st));
-      PF_TRY(orthonormalise_set(S, U, HU, nb));
-      PF_TRY(rayleigh_ritz_H(S, U, HU, nb, E, res));
+      double* Wd = HUd + (int64_t)Lb * DS;
+      if (Lb > 0) {   // the filtered blocks against the locked ones, two Gram-Schmidt passes
+        DevBuf Cl;
+        PF_TRY(Cl.alloc((size_t)Lb * s * na * s * 8, st));
+        for (int pass = 0; pass < 2; ++pass) {
+          PF_TRY(gram(H->D, s, Ud, Lb, Wd, na, Cl.as<double>(), S.gscr.as<double>(), S.gscr_elems, st));
+          for (int b = 0; b < na; ++b)
+            PF_TRY(tsgemm(H->D, s, Ud, Lb, Cl.as<double>() + b * s, na * s, Wd + (int64_t)b * DS, 1, -1.0, 1.0, st));
+        }
+      }
+      PF_TRY(orthonormalise_set(S, Wd, Ud + (int64_t)Lb * DS, na));
+      PF_CUDA(cudaMemcpyAsync(Ud + (int64_t)Lb * DS, Wd, (size_t)na * DS * 8, cudaMemcpyDeviceToDevice, st));
+      PF_TRY(rayleigh_ritz_H(S, Ud, HUd, nb, E, res));
       sel = nearest_sel(E, lam, nev);
       clk.mark(4);
       S.rep.ms_filter_f64 += clk.ms(2, 3);
