@@ -176,6 +176,27 @@ pf_status pf_clenshaw_step(const pf_ham* H, int32_t prec, int32_t s, const void*
 pf_status pf_filter_apply(const pf_ham* H, int32_t prec, int32_t s, const void* V, void* W,
                           const double* coeffs, int32_t K, pf_stream_t stream);
 
+/* W_j = P_j(H~_j) V_j for n independent items of one precision and block width (each
+ * item its own Hamiltonian, size, coefficients and degree K_j), advanced together: a sweep
+ * of max_j(K_j) + 1 launches, each one Clenshaw step of every item over the concatenation
+ * of all items' rows.  Item j joins at launch max(K) - K_j, so all items end together.
+ * Every row is computed with the operation order of pf_filter_apply, so each W_j is
+ * bit-identical to pf_filter_apply on the same item.  The paper applies the filter to one
+ * problem at a time; this is the library's batching of many small problems.
+ *   items[j].H      : handle with H~ set;  V, W: device blocks (D_j x s) of the precision.
+ *   items[j].coeffs : host [K_j + 1];      K: >= 1.
+ * Allocates two auxiliary blocks per item, the coefficients and a table of n entries.
+ * Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ENOMEM, PF_ECUDA.                    */
+typedef struct {
+  const pf_ham* H;
+  const void* V;
+  void* W;
+  const double* coeffs;
+  int32_t K;
+} pf_filter_item;
+pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t prec, int32_t s,
+                                pf_stream_t stream);
+
 /* Same computation as pf_filter_apply, without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device memory at
  * the time of the call (a frozen or exhausted memory pool, a host allocator that must not
@@ -211,7 +232,7 @@ typedef struct {
   double tol;             /* P-space tolerance on ||B tau|| (FP64 filter); 0 = 1e-10 */
   double tol_f32;         /* same for the FP32 filter stage; 0 = 1e-7                */
   double res_tol;         /* final acceptance ||Hu - Eu|| <= res_tol ||H||; 0 = 1e-9 */
-  int32_t refine_passes;  /* FP32 path: max FP64 filter passes; <0 = none, 0 = 3     */
+  int32_t refine_passes;  /* FP32 path: max FP64 filter passes; <0 = none, 0 = 8     */
   int32_t refine_K;       /* degree of the refinement filter; 0 = K                  */
   uint64_t seed;          /* start block: v[r,c] = SplitMix64(seed, r*s+c) - 1/2     */
   int32_t use_abs_target; /* nonzero: target is target_abs (absolute energy)         */
@@ -252,6 +273,88 @@ void pf_default_opts(pf_solve_opts* o);
 pf_status pf_polfed_solve(pf_ham* H, double target_eps, int32_t nev, int32_t K,
                           const pf_solve_opts* o, double* evals, double* evecs, double* resid,
                           pf_report* rep, pf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * (a11) Batched solves: n independent problems (disorder realisations, sizes, targets)
+ * solved together.  Every problem is a resumable solve holding its Lanczos state in device
+ * memory.  Each round runs the pending filter applications of all unfinished problems
+ * (those with the same precision and block width share one sweep, as in
+ * pf_filter_apply_batch; the refinement of one problem contributes one item per active
+ * block), then each problem's orthogonalisation, QR, checks, extraction or refinement.
+ * Each problem's outputs are bit-identical to pf_polfed_solve on the same inputs.  Not in
+ * the paper, which solves one problem at a time.                                     */
+typedef struct {
+  pf_ham* H;                  /* in: handle with bounds set                               */
+  double target_eps;          /* in: as pf_polfed_solve                                   */
+  int32_t nev, K;             /* in: as pf_polfed_solve                                   */
+  const pf_solve_opts* opts;  /* in: NULL = defaults                                      */
+  double* evals;              /* out: host [nev], ascending                               */
+  double* evecs;              /* out: device D x nev column-major, may be NULL            */
+  double* resid;              /* out: host [nev]                                          */
+  pf_report* rep;             /* out: host, may be NULL                                   */
+  int32_t status;             /* out: this problem's pf_status                            */
+} pf_solve_item;
+/* Returns PF_OK when every item succeeded, else the first failing item's status; a failed
+ * shared launch (PF_ECUDA, PF_ENOMEM) is reported in every item that was running.
+ * Synchronises.                                                                    */
+pf_status pf_polfed_solve_batch(pf_solve_item* items, int32_t n, pf_stream_t stream);
+
+/* Device bytes one solve holds at its peak: the Hamiltonian (CSR, FP64 and FP32 H~ copies,
+ * basis table) for the given nnz, the resident Lanczos state (basis of the expected Krylov
+ * size with eta = 1.5, H_L, work blocks), the Ritz set and, for PF_F32, the refinement
+ * blocks.  Used by the server's admission.  Errors: PF_EINVAL.                         */
+pf_status pf_solve_footprint(int64_t D, int64_t nnz, int32_t nev, int32_t block, int32_t precision,
+                             int64_t* bytes);
+
+/* ---------------------------------------------------------------------------
+ * (a12) Serving: continuous batching of solve requests (not in the paper).  Requests are
+ * queued on submit.  Each pf_server_step (1) admits queued requests in arrival order while
+ * the sum of the admitted footprints (pf_solve_footprint with the model's nnz bound) stays
+ * within the budget and fewer than max_active are resident; a request larger than the
+ * budget is admitted alone into an empty server; admission builds the basis, Hamiltonian,
+ * spectral bounds and K (pf_choose_K) on the server's stream; (2) runs one round of all
+ * resident solves as in pf_polfed_solve_batch; (3) retires finished solves, releasing
+ * their device memory.  A request's results equal those of the one-problem calls on the
+ * same model and options, whatever else is resident.  Not thread-safe: one host thread
+ * drives a server.  Latencies are measured on the host's steady clock.               */
+typedef struct pf_server pf_server;
+typedef struct {
+  int32_t block;            /* s of every solve; 0 = 32                                    */
+  int32_t precision;        /* pf_precision of the filter                                  */
+  int32_t max_active;       /* most resident solves; 0 = 64                                */
+  int64_t mem_budget_bytes; /* admission budget; 0 = 80% of free device memory at create  */
+  double res_tol;           /* acceptance ||Hu - Eu|| <= res_tol ||H||; 0 = 1e-9           */
+  double bounds_tol;        /* spectral-bounds tolerance; 0 = 1e-10                         */
+  uint64_t seed;            /* start-block seed; 0 = 2024                                   */
+} pf_server_config;
+typedef struct {
+  int64_t id;
+  int32_t status;           /* the request's pf_status                                     */
+  int32_t nev;
+  int64_t footprint_bytes;  /* admission footprint                                         */
+  double queue_ms;          /* submit to admission                                         */
+  double latency_ms;        /* submit to completion                                        */
+} pf_request_info;
+/* cfg may be NULL (defaults).  stream: every call of the server enqueues work there.
+ * Errors: PF_EINVAL, PF_ECUDA.                                                      */
+pf_status pf_server_create(const pf_server_config* cfg, pf_stream_t stream, pf_server** out);
+/* Queue one request; m and p are copied (host).  id: host output.
+ * Errors: PF_EINVAL (model, arrays, eps outside [0,1], nev outside [1, D]).          */
+pf_status pf_server_submit(pf_server* sv, const pf_model* m, const pf_params* p, double target_eps,
+                           int32_t nev, int64_t* id);
+/* One step as above.  queued / active / finished: host outputs (may be NULL): requests
+ * waiting, resident, finished and not yet taken.  Synchronises.  A request that fails
+ * (build, bounds, solve) finishes with its status; the call itself returns PF_ECUDA only
+ * for a failure of a launch shared by all resident solves.                           */
+pf_status pf_server_step(pf_server* sv, int32_t* queued, int32_t* active, int32_t* finished);
+/* Results of a finished request, then its record is released.  evals, resid: host [nev]
+ * (may be NULL); rep, info: host (may be NULL).  Errors: PF_ESTATE (still queued or
+ * resident), PF_EINVAL (unknown or already taken id).                               */
+pf_status pf_server_take(pf_server* sv, int64_t id, double* evals, double* resid, pf_report* rep,
+                         pf_request_info* info);
+/* Sum of the footprints of the resident requests, and the budget.                   */
+pf_status pf_server_memory(const pf_server* sv, int64_t* in_use, int64_t* budget);
+void pf_server_destroy(pf_server* sv);
 
 /* Start block as the solve draws it: v[r,c] = uniform(SplitMix64(seed, r*s+c)) - 1/2,
  * uniform = top 53 bits * 2^-53 (Steele, Lea & Flood 2014).  out: device double [D*s]. */

@@ -48,6 +48,28 @@ class pf_report(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pf_filter_item(C.Structure):
+    _fields_ = [("H", C.c_void_p), ("V", C.c_void_p), ("W", C.c_void_p), ("coeffs", C.POINTER(C.c_double)),
+                ("K", C.c_int32)]
+
+
+class pf_solve_item(C.Structure):
+    _fields_ = [("H", C.c_void_p), ("target_eps", C.c_double), ("nev", C.c_int32), ("K", C.c_int32),
+                ("opts", C.POINTER(pf_solve_opts)), ("evals", C.POINTER(C.c_double)), ("evecs", C.c_void_p),
+                ("resid", C.POINTER(C.c_double)), ("rep", C.POINTER(pf_report)), ("status", C.c_int32)]
+
+
+class pf_server_config(C.Structure):
+    _fields_ = [("block", C.c_int32), ("precision", C.c_int32), ("max_active", C.c_int32),
+                ("mem_budget_bytes", C.c_int64), ("res_tol", C.c_double), ("bounds_tol", C.c_double),
+                ("seed", C.c_uint64)]
+
+
+class pf_request_info(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("nev", C.c_int32), ("footprint_bytes", C.c_int64),
+                ("queue_ms", C.c_double), ("latency_ms", C.c_double)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -80,6 +102,15 @@ PROTOTYPES = {
     "pf_default_opts": (None, [P(pf_solve_opts)]),
     "pf_polfed_solve": (i32, [vp, dbl, i32, i32, P(pf_solve_opts), P(dbl), vp, P(dbl), P(pf_report), vp]),
     "pf_start_block": (i32, [i64, i32, u64, vp, vp]),
+    "pf_filter_apply_batch": (i32, [P(pf_filter_item), i32, i32, i32, vp]),
+    "pf_polfed_solve_batch": (i32, [P(pf_solve_item), i32, vp]),
+    "pf_solve_footprint": (i32, [i64, i64, i32, i32, i32, P(i64)]),
+    "pf_server_create": (i32, [P(pf_server_config), vp, P(vp)]),
+    "pf_server_submit": (i32, [vp, P(pf_model), P(pf_params), dbl, i32, P(i64)]),
+    "pf_server_step": (i32, [vp, P(i32), P(i32), P(i32)]),
+    "pf_server_take": (i32, [vp, i64, P(dbl), P(dbl), P(pf_report), P(pf_request_info)]),
+    "pf_server_memory": (i32, [vp, P(i64), P(i64)]),
+    "pf_server_destroy": (None, [vp]),
 }
 
 _lib = None

@@ -244,17 +244,7 @@ class Hamiltonian:
     # ---- the solve
     def solve(self, eps, nev, K, block=32, precision="f64", return_vectors=True, target_abs=None, stream=None,
               raise_on_notconv=True, **opts):
-        o = L.pf_solve_opts()
-        lib().pf_default_opts(C.byref(o))
-        o.block = block
-        o.precision = L.PF_F64 if precision == "f64" else L.PF_F32
-        for k, v in opts.items():
-            if not hasattr(o, k):
-                raise TypeError(f"unknown option {k}")
-            setattr(o, k, v)
-        if target_abs is not None:
-            o.use_abs_target = 1
-            o.target_abs = float(target_abs)
+        o = _make_opts(block, precision, target_abs, opts)
         evals = np.zeros(nev)
         resid = np.zeros(nev)
         evecs = torch.empty((nev, self.D), dtype=torch.float64, device="cuda") if return_vectors else None
@@ -267,6 +257,161 @@ class Hamiltonian:
         # evecs buffer is D x nev column-major == (nev, D) row-major; expose as (D, nev)
         return SolveResult(evals=evals, resid=resid, evecs=evecs.t() if evecs is not None else None,
                            report=rep.as_dict(), status=st)
+
+
+def _make_opts(block, precision, target_abs, opts):
+    o = L.pf_solve_opts()
+    lib().pf_default_opts(C.byref(o))
+    o.block = block
+    o.precision = L.PF_F64 if precision == "f64" else L.PF_F32
+    for k, v in opts.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    if target_abs is not None:
+        o.use_abs_target = 1
+        o.target_abs = float(target_abs)
+    return o
+
+
+def filter_apply_batch(items, stream=None):
+    """W_j = P_j(H~_j) V_j for items (H, V, coeffs) of one dtype and block width, in one sweep."""
+    _install_torch_allocator()
+    n = len(items)
+    if n == 0:
+        return []
+    V0 = items[0][1]
+    prec = L.PF_F64 if V0.dtype == torch.float64 else L.PF_F32
+    arr = (L.pf_filter_item * n)()
+    keep, outs = [], []
+    for j, (H, V, coeffs) in enumerate(items):
+        c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+        W = torch.empty_like(V)
+        keep.append(c)
+        outs.append(W)
+        arr[j].H = H.handle.value if isinstance(H.handle, C.c_void_p) else H.handle
+        arr[j].V = V.data_ptr()
+        arr[j].W = W.data_ptr()
+        arr[j].coeffs = c.ctypes.data_as(C.POINTER(C.c_double))
+        arr[j].K = len(c) - 1
+    check(lib().pf_filter_apply_batch(arr, n, prec, V0.shape[1], _stream(stream)), "pf_filter_apply_batch")
+    return outs
+
+
+def solve_batch(problems, block=32, precision="f64", return_vectors=False, stream=None, **opts):
+    """Solve independent problems together.  problems: dicts with keys H, eps, nev, K and
+    optionally target_abs, block, precision (overriding the call's).  Returns one
+    SolveResult per problem (status per problem)."""
+    n = len(problems)
+    arr = (L.pf_solve_item * n)()
+    keep = []
+    for j, pb in enumerate(problems):
+        H, nev = pb["H"], int(pb["nev"])
+        o = _make_opts(pb.get("block", block), pb.get("precision", precision), pb.get("target_abs"), opts)
+        ev, rs, rep = np.zeros(nev), np.zeros(nev), L.pf_report()
+        vec = torch.empty((nev, H.D), dtype=torch.float64, device="cuda") if return_vectors else None
+        keep.append((o, ev, rs, rep, vec))
+        arr[j].H = H.handle.value if isinstance(H.handle, C.c_void_p) else H.handle
+        arr[j].target_eps = float(pb.get("eps", 0.5))
+        arr[j].nev = nev
+        arr[j].K = int(pb["K"])
+        arr[j].opts = C.pointer(o)
+        arr[j].evals = ev.ctypes.data_as(C.POINTER(C.c_double))
+        arr[j].evecs = vec.data_ptr() if vec is not None else None
+        arr[j].resid = rs.ctypes.data_as(C.POINTER(C.c_double))
+        arr[j].rep = C.pointer(rep)
+    st = lib().pf_polfed_solve_batch(arr, n, _stream(stream))
+    if st not in (L.PF_OK, L.PF_ENOTCONV, L.PF_EINVAL, L.PF_ESTATE, L.PF_EBREAKDOWN):
+        check(st, "pf_polfed_solve_batch")
+    out = []
+    for j, (o, ev, rs, rep, vec) in enumerate(keep):
+        out.append(SolveResult(evals=ev, resid=rs, evecs=vec.t() if vec is not None else None,
+                               report=rep.as_dict(), status=arr[j].status))
+    return out
+
+
+def solve_footprint(D, nnz, nev, block=32, precision="f64"):
+    """Device bytes one solve holds at its peak (the server's admission measure)."""
+    b = C.c_int64()
+    check(lib().pf_solve_footprint(int(D), int(nnz), int(nev), int(block),
+                                   L.PF_F64 if precision == "f64" else L.PF_F32, C.byref(b)), "pf_solve_footprint")
+    return b.value
+
+
+@dataclass
+class RequestResult:
+    id: int
+    status: int
+    evals: np.ndarray
+    resid: np.ndarray
+    report: dict
+    latency_ms: float
+    queue_ms: float
+    footprint_bytes: int
+
+
+class Server:
+    """Continuous-batching solve server (pf_server_*): submit requests, step, take results."""
+
+    def __init__(self, block=32, precision="f32", max_active=64, mem_budget_bytes=0, res_tol=0.0, bounds_tol=0.0,
+                 seed=0, stream=None):
+        _install_torch_allocator()
+        cfg = L.pf_server_config(block=block, precision=L.PF_F64 if precision == "f64" else L.PF_F32,
+                                 max_active=max_active, mem_budget_bytes=int(mem_budget_bytes), res_tol=res_tol,
+                                 bounds_tol=bounds_tol, seed=seed)
+        self._stream = stream
+        h = C.c_void_p()
+        check(lib().pf_server_create(C.byref(cfg), _stream(stream), C.byref(h)), "pf_server_create")
+        self.handle = h
+        self._nev = {}
+
+    def submit(self, model, eps, nev):
+        arrays = [_dbl_arr(model.h), _dbl_arr(model.mu), _dbl_arr(model.A), _dbl_arr(model.u_noise)]
+        nj = None
+        if model.n_of_j is not None:
+            nj = np.ascontiguousarray(np.asarray(model.n_of_j, dtype=np.int32))
+        prm = L.pf_params(h=arrays[0][1], mu=arrays[1][1], A=arrays[2][1], u_noise=arrays[3][1],
+                          n_of_j=nj.ctypes.data_as(C.POINTER(C.c_int32)) if nj is not None else None)
+        rid = C.c_int64()
+        check(lib().pf_server_submit(self.handle, C.byref(model.c_model()), C.byref(prm), float(eps), int(nev),
+                                     C.byref(rid)), "pf_server_submit")
+        self._nev[rid.value] = int(nev)
+        return rid.value
+
+    def step(self):
+        q, a, f = C.c_int32(), C.c_int32(), C.c_int32()
+        check(lib().pf_server_step(self.handle, C.byref(q), C.byref(a), C.byref(f)), "pf_server_step")
+        return q.value, a.value, f.value
+
+    def take(self, rid):
+        """The finished request's result, or None while it is queued or resident."""
+        nev = self._nev[rid]
+        ev, rs, rep, info = np.zeros(nev), np.zeros(nev), L.pf_report(), L.pf_request_info()
+        st = lib().pf_server_take(self.handle, int(rid), ev.ctypes.data_as(C.POINTER(C.c_double)),
+                                  rs.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep), C.byref(info))
+        if st == L.PF_ESTATE:
+            return None
+        check(st, "pf_server_take")
+        del self._nev[rid]
+        return RequestResult(id=rid, status=info.status, evals=ev, resid=rs, report=rep.as_dict(),
+                             latency_ms=info.latency_ms, queue_ms=info.queue_ms,
+                             footprint_bytes=info.footprint_bytes)
+
+    def memory(self):
+        u, b = C.c_int64(), C.c_int64()
+        check(lib().pf_server_memory(self.handle, C.byref(u), C.byref(b)), "pf_server_memory")
+        return u.value, b.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pf_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def filter_coefficients(lam_t, K, stream=None):

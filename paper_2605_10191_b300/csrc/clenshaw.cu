@@ -14,6 +14,7 @@
 // the next step (V and the matrix every step, out becomes the next B1, B2's lines are
 // rewritten in place), so whatever of the step's working set fits in L2 stays there.
 #include "common.cuh"
+#include <algorithm>
 
 namespace pf {
 
@@ -219,6 +220,175 @@ pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W
   return PF_OK;
 }
 
+// ------------------------------------------------------------------ batched sweep
+// Several filter applications W_j = P_j(H~_j) V_j (different matrices, sizes, degrees) advance
+// together: launch t of a sweep performs one Clenshaw step of every item at once, over the
+// concatenation of the items' rows.  Item j (degree K_j) joins at t0_j = T - (K_j + 1) so that
+// all items finish at the last launch; at sweep step t it runs recurrence index
+// i = K_j - (t - t0_j) with the same operands as filter_apply_raw.
+struct BatchItemDev {
+  int64_t D, row0;
+  const int64_t* rp;
+  const int32_t* col;
+  const void* val;
+  const void* V;
+  void* W;
+  void* aux0;
+  void* aux1;
+  const double* coeffs;
+  int K, t0;
+};
+
+template <typename T, int S>
+__global__ void __launch_bounds__(256) clenshaw_batch_kernel(const BatchItemDev* __restrict__ items, int n, int t,
+                                                             int64_t total_rows) {
+  using Sh = Shape<T, S>;
+  constexpr int E = Sh::E, G = Sh::G;
+  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t grow = gtid / G;
+  const int lane = (int)(gtid % G);
+  if (grow >= total_rows) return;
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].row0 <= grow) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchItemDev& it = items[lo];
+  if (t < it.t0) return;
+  const int K = it.K;
+  const int i = K - (t - it.t0);
+  const int64_t row = grow - it.row0;
+  T* aux[2] = {(T*)it.aux0, (T*)it.aux1};
+  const T* B1 = nullptr;
+  const T* B2 = nullptr;
+  T* out;
+  T alpha, beta;
+  if (i == K) {
+    alpha = T(0); beta = T(0); out = aux[i & 1];
+  } else if (i >= 1) {
+    alpha = T(2); beta = (i == K - 1) ? T(0) : T(1);
+    B1 = aux[(i + 1) & 1]; B2 = aux[i & 1]; out = aux[i & 1];
+  } else {
+    alpha = T(1); beta = (K >= 2) ? T(1) : T(0);
+    B1 = aux[1]; B2 = aux[0]; out = (T*)it.W;
+  }
+  const T a = (T)it.coeffs[i];
+  const T* __restrict__ V = (const T*)it.V;
+  const T* __restrict__ val = (const T*)it.val;
+  const int32_t* __restrict__ col = it.col;
+  const int64_t off = row * S + lane * E;
+  T acc[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) acc[e] = T(0);
+  if (alpha != T(0)) {
+    int64_t j = it.rp[row];
+    const int64_t end = it.rp[row + 1];
+    for (; j + 4 <= end; j += 4) {
+      int c0 = __ldg(col + j), c1 = __ldg(col + j + 1), c2 = __ldg(col + j + 2), c3 = __ldg(col + j + 3);
+      T h0 = __ldg(val + j), h1 = __ldg(val + j + 1), h2 = __ldg(val + j + 2), h3 = __ldg(val + j + 3);
+      Vec<T, E> b0 = ld_default<T, E>(B1 + (int64_t)c0 * S + lane * E);
+      Vec<T, E> b1 = ld_default<T, E>(B1 + (int64_t)c1 * S + lane * E);
+      Vec<T, E> b2 = ld_default<T, E>(B1 + (int64_t)c2 * S + lane * E);
+      Vec<T, E> b3 = ld_default<T, E>(B1 + (int64_t)c3 * S + lane * E);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        acc[e] = fma(h0, b0.x[e], acc[e]);
+        acc[e] = fma(h1, b1.x[e], acc[e]);
+        acc[e] = fma(h2, b2.x[e], acc[e]);
+        acc[e] = fma(h3, b3.x[e], acc[e]);
+      }
+    }
+    for (; j < end; ++j) {
+      int c0 = __ldg(col + j);
+      T h0 = __ldg(val + j);
+      Vec<T, E> b0 = ld_default<T, E>(B1 + (int64_t)c0 * S + lane * E);
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc[e] = fma(h0, b0.x[e], acc[e]);
+    }
+  }
+  Vec<T, E> v = ld_default<T, E>(V + off);
+  Vec<T, E> r;
+  if (beta != T(0)) {
+    Vec<T, E> q = ld_plain<T, E>(B2 + off);
+#pragma unroll
+    for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], a * v.x[e] - beta * q.x[e]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], a * v.x[e]);
+  }
+  st_default<T, E>(out + off, r);
+}
+
+template <typename T, int S>
+static pf_status launch_batch_s(const BatchItemDev* items, int n, int T_steps, int64_t total_rows, cudaStream_t st) {
+  using Sh = Shape<T, S>;
+  const unsigned grid = (unsigned)ceil_div(total_rows * Sh::G, 256);
+  for (int t = 0; t < T_steps; ++t) {
+    clenshaw_batch_kernel<T, S><<<grid, 256, 0, st>>>(items, n, t, total_rows);
+    PF_LAUNCH_CHECK("clenshaw_batch_kernel");
+  }
+  return PF_OK;
+}
+
+pf_status filter_sweep(const std::vector<FilterItem>& items, void* table_dev, size_t table_bytes, void* table_host,
+                       cudaStream_t st) {
+  const int n = (int)items.size();
+  if (n == 0) return PF_OK;
+  if ((size_t)n * sizeof(BatchItemDev) > table_bytes) return PF_EINVAL;
+  const int prec = items[0].prec, s = items[0].s;
+  int T = 0;
+  for (const auto& it : items) {
+    if (it.prec != prec || it.s != s || it.K < 1) return PF_EINVAL;
+    T = std::max(T, it.K + 1);
+  }
+  BatchItemDev* tab = static_cast<BatchItemDev*>(table_host);
+  int64_t row0 = 0;
+  for (int j = 0; j < n; ++j) {
+    const FilterItem& it = items[j];
+    BatchItemDev& b = tab[j];
+    b.D = it.H->D;
+    b.row0 = row0;
+    b.rp = it.H->row_ptr;
+    b.col = it.H->col;
+    b.val = prec == PF_F64 ? (const void*)it.H->val_t : (const void*)it.H->val32;
+    b.V = it.V;
+    b.W = it.W;
+    b.aux0 = it.aux0;
+    b.aux1 = it.aux1;
+    b.coeffs = it.coeffs_dev;
+    b.K = it.K;
+    b.t0 = T - (it.K + 1);
+    row0 += it.H->D;
+  }
+  PF_CUDA(cudaMemcpyAsync(table_dev, tab, n * sizeof(BatchItemDev), cudaMemcpyHostToDevice, st));
+  const BatchItemDev* d = static_cast<const BatchItemDev*>(table_dev);
+  if (prec == PF_F64) {
+    switch (s) {
+      case 1: return launch_batch_s<double, 1>(d, n, T, row0, st);
+      case 2: return launch_batch_s<double, 2>(d, n, T, row0, st);
+      case 4: return launch_batch_s<double, 4>(d, n, T, row0, st);
+      case 8: return launch_batch_s<double, 8>(d, n, T, row0, st);
+      case 16: return launch_batch_s<double, 16>(d, n, T, row0, st);
+      case 32: return launch_batch_s<double, 32>(d, n, T, row0, st);
+      case 64: return launch_batch_s<double, 64>(d, n, T, row0, st);
+    }
+  } else {
+    switch (s) {
+      case 1: return launch_batch_s<float, 1>(d, n, T, row0, st);
+      case 2: return launch_batch_s<float, 2>(d, n, T, row0, st);
+      case 4: return launch_batch_s<float, 4>(d, n, T, row0, st);
+      case 8: return launch_batch_s<float, 8>(d, n, T, row0, st);
+      case 16: return launch_batch_s<float, 16>(d, n, T, row0, st);
+      case 32: return launch_batch_s<float, 32>(d, n, T, row0, st);
+      case 64: return launch_batch_s<float, 64>(d, n, T, row0, st);
+    }
+  }
+  return PF_EINVAL;
+}
+
+size_t filter_sweep_table_bytes(int n) { return (size_t)n * sizeof(BatchItemDev); }
+
 }  // namespace pf
 
 using namespace pf;
@@ -254,6 +424,52 @@ pf_status pf_filter_apply(const pf_ham* hh, int32_t prec, int32_t s, const void*
   PF_TRY(a0.alloc(H->D * s * w, st));
   PF_TRY(a1.alloc(H->D * s * w, st));
   return filter_apply_raw(H, prec, s, V, W, coeffs, nullptr, K, a0.p, a1.p, st);
+}
+
+pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t prec, int32_t s,
+                                pf_stream_t stream) {
+  if (n < 0 || (n > 0 && !items)) return PF_EINVAL;
+  if (prec != PF_F64 && prec != PF_F32) return PF_EINVAL;
+  if (!valid_s(s)) return PF_EINVAL;
+  if (n == 0) return PF_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t w = prec == PF_F64 ? 8 : 4;
+  // one device blob: per item its K+1 coefficients and two auxiliary blocks (256-B aligned)
+  std::vector<size_t> coff(n), aoff(n);
+  size_t total = 0;
+  for (int j = 0; j < n; ++j) {
+    const Ham* H = reinterpret_cast<const Ham*>(items[j].H);
+    if (!H || !items[j].V || !items[j].W || !items[j].coeffs || items[j].K < 1) return PF_EINVAL;
+    if (!H->has_rescale) return PF_ESTATE;
+    coff[j] = total;
+    total += ((size_t)(items[j].K + 1) * 8 + 255) & ~(size_t)255;
+    aoff[j] = total;
+    total += 2 * (((size_t)H->D * s * w + 255) & ~(size_t)255);
+  }
+  DevBuf blob, table;
+  PF_TRY(blob.alloc(total, st));
+  PF_TRY(table.alloc(filter_sweep_table_bytes(n), st));
+  std::vector<double> ch;
+  std::vector<FilterItem> v(n);
+  for (int j = 0; j < n; ++j) {
+    const Ham* H = reinterpret_cast<const Ham*>(items[j].H);
+    unsigned char* base = blob.as<unsigned char>();
+    PF_CUDA(cudaMemcpyAsync(base + coff[j], items[j].coeffs, (size_t)(items[j].K + 1) * 8, cudaMemcpyHostToDevice,
+                            st));
+    FilterItem& it = v[j];
+    it.H = H;
+    it.prec = prec;
+    it.s = s;
+    it.V = items[j].V;
+    it.W = items[j].W;
+    it.coeffs_host = items[j].coeffs;
+    it.coeffs_dev = reinterpret_cast<const double*>(base + coff[j]);
+    it.K = items[j].K;
+    it.aux0 = base + aoff[j];
+    it.aux1 = base + aoff[j] + (((size_t)H->D * s * w + 255) & ~(size_t)255);
+  }
+  std::vector<unsigned char> th(filter_sweep_table_bytes(n));
+  return filter_sweep(v, table.p, table.bytes, th.data(), st);
 }
 
 }  // extern "C"

@@ -131,6 +131,23 @@ __device__ T block_sum(T v, T* sh /* >= 32 */) {
 pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* col, const void* val,
                             int prec, int s, const void* V, const void* B1, const void* B2, void* out,
                             double a, double alpha, double beta, cudaStream_t st);
+// One filter application W = P(H~) V (K steps) with its own two auxiliary blocks.
+struct FilterItem {
+  const Ham* H = nullptr;
+  int prec = 0, s = 0;
+  const void* V = nullptr;
+  void* W = nullptr;
+  const double* coeffs_host = nullptr;  // host, K+1 (single-item path)
+  const double* coeffs_dev = nullptr;   // device, K+1 (sweeps)
+  int K = 0;
+  void* aux0 = nullptr;
+  void* aux1 = nullptr;
+};
+// All items advance together, one launch per Clenshaw step over the concatenated rows.
+// Items share prec and s.  table_host/table_dev: room for filter_sweep_table_bytes(n).
+pf_status filter_sweep(const std::vector<FilterItem>& items, void* table_dev, size_t table_bytes, void* table_host,
+                       cudaStream_t st);
+size_t filter_sweep_table_bytes(int n);
 // W = P V for a D x s block (K steps); aux buffers are two D x s blocks of the filter type.
 pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs_host,
                            const void* coeffs_dev, int K, void* aux0, void* aux1, cudaStream_t st);

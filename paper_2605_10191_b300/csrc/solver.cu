@@ -19,6 +19,8 @@
 #include <cmath>
 #include <algorithm>
 #include <numeric>
+#include <chrono>
+#include <memory>
 
 namespace pf {
 
@@ -495,232 +497,682 @@ static std::vector<int> nearest_sel(const std::vector<double>& E, double lam, in
   return o;
 }
 
-static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, const pf_solve_opts* o_in,
-                                   double* evals, double* evecs, double* resid, pf_report* rep, cudaStream_t st) {
+// ------------------------------------------------------------------ resumable solve
+// One POLFED solve as a resumable task.  The filter applications the task needs next are
+// listed in `pending`; an executor runs the pending applications of all active tasks
+// (items with the same precision and block width share one sweep) and then calls
+// after_filter(), which does the task's orthogonalisation, QR, checks, extraction or
+// refinement work and lists the next applications.  pf_polfed_solve runs one task,
+// pf_polfed_solve_batch and the server run many.  The filter kernels compute every row with
+// the same operation order in all three paths, so a task's results do not depend on
+// which other tasks share its sweeps.
+struct Task {
+  enum Phase { LANCZOS = 0, REFINE = 1, DONE = 2 };
+  Ham* H = nullptr;
+  cudaStream_t st = 0;
   pf_solve_opts o;
-  pf_default_opts(&o);
-  if (o_in) o = *o_in;
-  if (!H || !evals || !resid) return PF_EINVAL;
-  if (!H->has_rescale) return PF_ESTATE;
-  if (!o.use_abs_target && !H->has_bounds) return PF_ESTATE;
-  if (nev < 1 || nev > H->D || K < 1) return PF_EINVAL;
-  if (!o.use_abs_target && !(target_eps >= 0.0 && target_eps <= 1.0)) return PF_EINVAL;
-  int s = o.block > 0 ? o.block : 32;
-  if (!(s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32 || s == 64)) return PF_EINVAL;
-  if (o.precision != PF_F64 && o.precision != PF_F32) return PF_EINVAL;
-  const bool f32 = o.precision == PF_F32;
-  const double eta = o.eta > 0 ? o.eta : 1.5;
-  const double tol = f32 ? (o.tol_f32 > 0 ? o.tol_f32 : 1e-7) : (o.tol > 0 ? o.tol : 1e-10);
-  const double res_tol = o.res_tol > 0 ? o.res_tol : 1e-9;
-  int nev_g = o.nev_guard > 0 ? o.nev_guard : (int)std::ceil(kGuard * nev);
-  nev_g = std::max(nev_g, nev);
-  if (nev_g > H->D) nev_g = (int)H->D;
-  int Mmax = std::min<int64_t>(expected_krylov_dim(nev_g, s, eta), H->D);
-  int max_blocks = o.max_blocks > 0 ? o.max_blocks : std::max(2, Mmax / s);
-  if ((int64_t)max_blocks * s > H->D) max_blocks = (int)(H->D / s);
-  if (max_blocks < 1 || (int64_t)max_blocks * s < (int64_t)((nev_g + s - 1) / s) * s) return PF_EINVAL;
-  const int m_est = std::max(1, (int)std::ceil(expected_krylov_dim(nev_g, s, 1.0) / (double)s));
-  const int check_first = o.check_first > 0 ? o.check_first : std::max(1, (int)std::ceil(0.5 * m_est));
-  const int check_every = o.check_every > 0 ? o.check_every : std::max(1, (int)std::ceil(0.1 * m_est));
-  const int qb = (nev_g + s - 1) / s;     // Ritz blocks extracted
-  const int qpad = qb * s;
-  const int q_reserve = f32 ? 2 * s : 0;  // extra Ritz vectors kept for the refinement set
-
-  cudaEvent_t t0, t1;
-  cudaEventCreate(&t0);
-  cudaEventCreate(&t1);
-  cudaEventRecord(t0, st);
-
+  int nev = 0, K = 0, s = 0, nev_g = 0, max_blocks = 0, check_first = 0, check_every = 0;
+  int qb = 0, qpad = 0, q_reserve = 0;
+  bool f32 = false;
+  double tol = 0, res_tol = 0, lam = 0, lam_t = 0, hnorm = 0;
   Solver S;
-  PF_TRY(solver_init(S, H, s, max_blocks, std::max(qpad + q_reserve, nev_g), f32, st));
-  const double lam = o.use_abs_target ? o.target_abs : H->emin + target_eps * (H->emax - H->emin);
-  const double lam_t = (lam - H->Ec) / H->dE;
-  if (!(lam_t > -1.0 && lam_t < 1.0)) return PF_EINVAL;
-  std::vector<double> coeffs(K + 1);
-  PF_TRY(filter_coefficients_dev(lam_t, K, coeffs.data(), st));
-  S.rep.K = K;
-  S.rep.nev_guard = nev_g;
-  S.rep.lambda = lam;
-  S.rep.lambda_t = lam_t;
-  S.rep.emin = H->emin;
-  S.rep.emax = H->emax;
-  S.rep.Ec = H->Ec;
-  S.rep.dE = H->dE;
-  const double hnorm = H->has_bounds ? H->hnorm : std::max(std::fabs(H->Ec - H->dE), std::fabs(H->Ec + H->dE));
-  S.rep.hnorm = hnorm;
-
-  PF_TRY(start_block_raw(H->D, s, o.seed, blockp(S, 0), st));
-  PF_TRY(chol_qr3(S, blockp(S, 0), blockp(S, 0)));
+  DevBuf coeff_dev, coeffr_dev;
+  std::vector<double> coeffs, coeffs_r;
+  Phase phase = LANCZOS;
+  int k = 0;                      // Krylov blocks completed
   LanczosResult R;
-  PF_TRY(block_lanczos(S, f32 ? OP_FILTER32 : OP_FILTER64, coeffs.data(), K, 1, nev_g, qpad, tol, false,
-                       check_first, check_every, R));
-  S.rep.blocks = R.blocks;
-  S.rep.krylov_dim = R.blocks * s;
-  const int M = R.blocks * s;
-  if ((int)R.idx.size() < nev_g) return PF_ENOTCONV;
-  PhaseClock clk(st);
-  clk.mark(0);
-  // Ritz vectors for the largest theta: qb blocks (the nev_g checked, padded to whole blocks)
-  // and, for the FP32 filter, up to two reserve blocks that join the refinement set when it
-  // stalls.  M >= qpad (the checks wait for it) and M is a multiple of s.
-  const int nb_total = std::min(qb + q_reserve / s, M / s);
-  const int qtot = nb_total * s;
-  std::vector<int> idx;
-  for (int i = M - qtot; i < M; ++i) idx.push_back(i);
-  std::vector<double> th(qtot);
-  PF_TRY(sym_eig_select(S.HL.as<double>(), S.Mcap, M, idx.data(), qtot, th.data(), S.Z.as<double>(), M, S.eigw.p,
-                        S.eig_bytes, st));
-  // C (M x qtot row-major): columns are the Ritz coefficient vectors, largest theta first
-  DevBuf perm, U, HU;
-  std::vector<int> pv(qtot);
-  for (int c = 0; c < qtot; ++c) pv[c] = qtot - 1 - c;
-  PF_TRY(perm.alloc(qtot * sizeof(int), st));
-  PF_CUDA(cudaMemcpyAsync(perm.p, pv.data(), qtot * sizeof(int), cudaMemcpyHostToDevice, st));
-  z_to_rowmajor_kernel<<<(unsigned)ceil_div((int64_t)M * qtot, 256), 256, 0, st>>>(S.Z.as<double>(), M, M, qtot,
-                                                                                   perm.as<int>(), S.Cg.as<double>(),
-                                                                                   qtot);
-  PF_LAUNCH_CHECK("z_to_rowmajor_kernel");
-  PF_TRY(U.alloc((size_t)nb_total * H->D * s * 8, st));
-  PF_TRY(HU.alloc((size_t)nb_total * H->D * s * 8, st));
-  for (int b = 0; b < nb_total; ++b)
-    PF_TRY(tsgemm(H->D, s, S.V.as<double>(), R.blocks, S.Cg.as<double>() + b * s, qtot,
-                  U.as<double>() + (int64_t)b * H->D * s, 1, 1.0, 0.0, st));
-  int nb = qb;   // active Ritz blocks; blocks nb..nb_total-1 of U hold the reserve
+  int nb = 0, nb_total = 0, passes = 0, max_pass = 0, Kr = 0, Lb = 0, na = 0;
+  double prev = 0, a0 = 0;
+  bool shifted = false;
+  DevBuf U, HU, aux64;
   std::vector<double> E, res;
-  PF_TRY(rayleigh_ritz_H(S, U.as<double>(), HU.as<double>(), qb, E, res));
-  std::vector<int> sel = nearest_sel(E, lam, nev);
-  auto max_res = [&]() {
+  std::vector<int> sel;
+  std::vector<FilterItem> pending;
+  pf_status status = PF_OK;
+  PhaseClock* clk = nullptr;
+  cudaEvent_t t_begin = nullptr, t_end = nullptr;
+
+  Task() { memset(&o, 0, sizeof(o)); }
+  Task(const Task&) = delete;
+  Task& operator=(const Task&) = delete;
+  ~Task() {
+    delete clk;
+    if (t_begin) cudaEventDestroy(t_begin);
+    if (t_end) cudaEventDestroy(t_end);
+  }
+
+  double max_res() const {
     double m = 0;
     for (int j : sel) m = std::max(m, res[j]);
     return m;
-  };
-  clk.mark(1);
-  S.rep.ms_extract = clk.ms(0, 1);
-  S.rep.max_residual_unrefined = max_res();
-  // FP64 refinement for the FP32 filter: subspace iteration U <- (P(H~) + c I) U on the active
-  // blocks, Cholesky QR, Rayleigh-Ritz in H.  An error component on eigenvalue k shrinks by
-  // |P_k + c| / (P_j + c) per pass for wanted pair j.  The first pass is unshifted (c = 0),
-  // which removes the far bulk (P ~ 0) fastest.  If a pass reduces the residual less than
-  // 10x, the remaining error sits where |P| is comparable to the edge pairs' P (~0.2): the
-  // filter's negative sidelobe (minimum ~ -0.22) or positive values just outside the set.
-  // Then one reserve block joins the set and later passes use c = 0.06, which halves the
-  // contraction factor on the negative sidelobe at the cost of the far bulk.
-  int passes = 0;
-  const int max_pass = o.refine_passes < 0 ? 0 : (o.refine_passes == 0 ? 8 : o.refine_passes);
-  const int Kr = o.refine_K > 0 ? o.refine_K : K;
-  std::vector<double> coeffs_r;
-  if (f32 && max_res() > res_tol * hnorm && max_pass > 0) {
-    coeffs_r.resize(Kr + 1);
-    PF_TRY(filter_coefficients_dev(lam_t, Kr, coeffs_r.data(), st));
-    const double a0 = coeffs_r[0];
-    DevBuf aux64a, aux64b;
-    PF_TRY(aux64a.alloc((size_t)H->D * s * 8, st));
-    PF_TRY(aux64b.alloc((size_t)H->D * s * 8, st));
-    double prev = max_res();
-    bool shifted = false;
+  }
+
+  // Validates the request, allocates the resident state, draws and orthonormalises the
+  // start block and lists the first filter application.
+  pf_status init(Ham* Hh, double target_eps, int nev_, int K_, const pf_solve_opts* o_in, cudaStream_t stream) {
+    pf_default_opts(&o);
+    if (o_in) o = *o_in;
+    H = Hh;
+    st = stream;
+    nev = nev_;
+    K = K_;
+    if (!H) return PF_EINVAL;
+    if (!H->has_rescale) return PF_ESTATE;
+    if (!o.use_abs_target && !H->has_bounds) return PF_ESTATE;
+    if (nev < 1 || nev > H->D || K < 1) return PF_EINVAL;
+    if (!o.use_abs_target && !(target_eps >= 0.0 && target_eps <= 1.0)) return PF_EINVAL;
+    s = o.block > 0 ? o.block : 32;
+    if (!(s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32 || s == 64)) return PF_EINVAL;
+    if (o.precision != PF_F64 && o.precision != PF_F32) return PF_EINVAL;
+    f32 = o.precision == PF_F32;
+    const double eta = o.eta > 0 ? o.eta : 1.5;
+    tol = f32 ? (o.tol_f32 > 0 ? o.tol_f32 : 1e-7) : (o.tol > 0 ? o.tol : 1e-10);
+    res_tol = o.res_tol > 0 ? o.res_tol : 1e-9;
+    nev_g = o.nev_guard > 0 ? o.nev_guard : (int)std::ceil(kGuard * nev);
+    nev_g = std::max(nev_g, nev);
+    if (nev_g > H->D) nev_g = (int)H->D;
+    const int Mmax = (int)std::min<int64_t>(expected_krylov_dim(nev_g, s, eta), H->D);
+    max_blocks = o.max_blocks > 0 ? o.max_blocks : std::max(2, Mmax / s);
+    if ((int64_t)max_blocks * s > H->D) max_blocks = (int)(H->D / s);
+    if (max_blocks < 1 || (int64_t)max_blocks * s < (int64_t)((nev_g + s - 1) / s) * s) return PF_EINVAL;
+    const int m_est = std::max(1, (int)std::ceil(expected_krylov_dim(nev_g, s, 1.0) / (double)s));
+    check_first = o.check_first > 0 ? o.check_first : std::max(1, (int)std::ceil(0.5 * m_est));
+    check_every = o.check_every > 0 ? o.check_every : std::max(1, (int)std::ceil(0.1 * m_est));
+    qb = (nev_g + s - 1) / s;      // Ritz blocks extracted
+    qpad = qb * s;
+    q_reserve = f32 ? 2 * s : 0;   // extra Ritz vectors kept for the refinement set
+    lam = o.use_abs_target ? o.target_abs : H->emin + target_eps * (H->emax - H->emin);
+    lam_t = (lam - H->Ec) / H->dE;
+    if (!(lam_t > -1.0 && lam_t < 1.0)) return PF_EINVAL;
+    PF_CUDA(cudaEventCreate(&t_begin));
+    PF_CUDA(cudaEventCreate(&t_end));
+    PF_CUDA(cudaEventRecord(t_begin, st));
+    clk = new PhaseClock(st);
+    PF_TRY(solver_init(S, H, s, max_blocks, std::max(qpad + q_reserve, nev_g), f32, st));
+    coeffs.resize(K + 1);
+    PF_TRY(filter_coefficients_dev(lam_t, K, coeffs.data(), st));
+    PF_TRY(coeff_dev.alloc((size_t)(K + 1) * 8, st));
+    PF_CUDA(cudaMemcpyAsync(coeff_dev.p, coeffs.data(), (size_t)(K + 1) * 8, cudaMemcpyHostToDevice, st));
+    S.rep.K = K;
+    S.rep.nev_guard = nev_g;
+    S.rep.lambda = lam;
+    S.rep.lambda_t = lam_t;
+    S.rep.emin = H->emin;
+    S.rep.emax = H->emax;
+    S.rep.Ec = H->Ec;
+    S.rep.dE = H->dE;
+    hnorm = H->has_bounds ? H->hnorm : std::max(std::fabs(H->Ec - H->dE), std::fabs(H->Ec + H->dE));
+    S.rep.hnorm = hnorm;
+    PF_TRY(start_block_raw(H->D, s, o.seed, blockp(S, 0), st));
+    PF_TRY(chol_qr3(S, blockp(S, 0), blockp(S, 0)));
+    return issue_lanczos_filter();
+  }
+
+  // W = P(H~) V_k: FP64 directly on the basis block, or FP32 on a converted copy.
+  pf_status issue_lanczos_filter() {
+    double* Vk = blockp(S, k);
+    FilterItem it;
+    it.H = H;
+    it.s = s;
+    it.coeffs_host = coeffs.data();
+    it.coeffs_dev = coeff_dev.as<double>();
+    it.K = K;
+    it.aux0 = S.aux0.p;
+    it.aux1 = S.aux1.p;
+    if (f32) {
+      PF_TRY(convert_d2f(Vk, S.V32.as<float>(), S.D * s, st));
+      it.prec = PF_F32;
+      it.V = S.V32.p;
+      it.W = S.W32.p;
+      S.rep.filter_steps_f32 += K + 1;
+    } else {
+      it.prec = PF_F64;
+      it.V = Vk;
+      it.W = S.W.p;
+      S.rep.filter_steps_f64 += K + 1;
+    }
+    clk->mark(0);
+    pending.assign(1, it);
+    return PF_OK;
+  }
+
+  pf_status after_filter() {
+    pending.clear();
+    if (phase == LANCZOS) return lanczos_post();
+    if (phase == REFINE) return refine_post();
+    return PF_OK;
+  }
+
+  // The rest of block step k after W = P V_k: A_k, two Gram-Schmidt passes against the whole
+  // basis, shifted Cholesky QR, H_L, and the periodic convergence check.
+  pf_status lanczos_post() {
+    const int64_t D = S.D;
+    double* W = S.W.as<double>();
+    double* Vk = blockp(S, k);
+    clk->mark(1);
+    if (f32) PF_TRY(convert_f2d(S.W32.as<float>(), W, D * s, st));
+    PF_TRY(gram(D, s, Vk, 1, W, 1, S.Ab, S.gscr.as<double>(), S.gscr_elems, st));
+    hl_store_kernel<<<1, 256, 0, st>>>(S.HL.as<double>(), S.Mcap, k, s, S.Ab, nullptr);
+    PF_LAUNCH_CHECK("hl_store_kernel");
+    for (int pass = 0; pass < 2; ++pass) {
+      PF_TRY(gram(D, s, S.V.as<double>(), k + 1, W, 1, S.Cg.as<double>(), S.gscr.as<double>(), S.gscr_elems, st));
+      PF_TRY(tsgemm(D, s, S.V.as<double>(), k + 1, S.Cg.as<double>(), s, W, 1, -1.0, 1.0, st));
+    }
+    clk->mark(2);
+    // full: the basis spans the whole space, so B_{k+1} = 0 exactly.  cap: no room for
+    // another block; B_{k+1} comes from the Cholesky factor of W^T W alone (enough for
+    // ||B tau||), and the iteration stops.
+    const bool full = (int64_t)(k + 1) * s >= D;
+    const bool cap = (int64_t)(k + 2) * s > D;
+    if (full) {
+      PF_CUDA(cudaMemsetAsync(S.Bb, 0, (size_t)s * s * 8, st));
+    } else if (cap) {
+      const double u = 1.1102230246251565e-16;
+      PF_TRY(gram(D, s, W, 1, W, 1, S.Gb, S.gscr.as<double>(), S.gscr_elems, st));
+      PF_TRY(small_chol_inv(S.Gb, s, 11.0 * ((double)D * s + (double)s * (s + 1)) * u, S.Bb, S.Rib, S.stat, st));
+    } else {
+      PF_TRY(chol_qr3(S, W, blockp(S, k + 1)));
+    }
+    hl_store_kernel<<<1, 256, 0, st>>>(S.HL.as<double>(), S.Mcap, k, s, nullptr, S.Bb);
+    PF_LAUNCH_CHECK("hl_store_kernel");
+    clk->mark(3);
+    (f32 ? S.rep.ms_filter_f32 : S.rep.ms_filter_f64) += clk->ms(0, 1);
+    S.rep.ms_orth += clk->ms(1, 2);
+    S.rep.ms_qr += clk->ms(2, 3);
+    ++k;
+    const int M = k * s;
+    const bool last = (k + 1 > S.max_blocks) || full || cap;
+    const bool enough = M >= nev_g && M >= qpad;
+    const bool at_check = (k >= check_first && ((k - check_first) % check_every == 0)) || last;
+    if (enough && at_check) {
+      std::vector<int> idx;
+      for (int i = M - nev_g; i < M; ++i) idx.push_back(i);
+      const int nq = (int)idx.size();
+      std::vector<double> th(nq), rr(nq);
+      clk->mark(4);
+      PF_TRY(sym_eig_select(S.HL.as<double>(), S.Mcap, M, idx.data(), nq, th.data(), S.Z.as<double>(), M, S.eigw.p,
+                            S.eig_bytes, st));
+      block_resid_kernel<<<(unsigned)ceil_div(nq, 64), 64, 0, st>>>(S.Bb, s, S.Z.as<double>(), M, M, nq, S.res);
+      PF_LAUNCH_CHECK("block_resid_kernel");
+      PF_CUDA(cudaMemcpyAsync(rr.data(), S.res, nq * 8, cudaMemcpyDeviceToHost, st));
+      clk->mark(5);
+      PF_CUDA(cudaStreamSynchronize(st));
+      S.rep.ms_check += clk->ms(4, 5);
+      S.rep.checks++;
+      bool ok = true;
+      for (int i = 0; i < nq; ++i) ok = ok && (rr[i] <= tol);
+      if (ok || last) {
+        R.blocks = k;
+        R.converged = ok || full;
+        R.theta = th;
+        R.idx = idx;
+        R.resid = rr;
+        return extract();
+      }
+    }
+    if (last) {
+      R.blocks = k;
+      R.converged = false;
+      return PF_ENOTCONV;
+    }
+    return issue_lanczos_filter();
+  }
+
+  // Ritz vectors for the largest theta: qb blocks (the nev_g checked, padded to whole blocks)
+  // and, for the FP32 filter, up to two reserve blocks that join the refinement set when it
+  // stalls; Rayleigh-Ritz in H; then refinement or done.
+  pf_status extract() {
+    const int M = R.blocks * s;
+    S.rep.blocks = R.blocks;
+    S.rep.krylov_dim = M;
+    clk->mark(0);
+    nb_total = std::min(qb + q_reserve / s, M / s);
+    const int qtot = nb_total * s;
+    std::vector<int> idx;
+    for (int i = M - qtot; i < M; ++i) idx.push_back(i);
+    std::vector<double> th(qtot);
+    PF_TRY(sym_eig_select(S.HL.as<double>(), S.Mcap, M, idx.data(), qtot, th.data(), S.Z.as<double>(), M, S.eigw.p,
+                          S.eig_bytes, st));
+    // C (M x qtot row-major): columns are the Ritz coefficient vectors, largest theta first
+    DevBuf perm;
+    std::vector<int> pv(qtot);
+    for (int c = 0; c < qtot; ++c) pv[c] = qtot - 1 - c;
+    PF_TRY(perm.alloc(qtot * sizeof(int), st));
+    PF_CUDA(cudaMemcpyAsync(perm.p, pv.data(), qtot * sizeof(int), cudaMemcpyHostToDevice, st));
+    z_to_rowmajor_kernel<<<(unsigned)ceil_div((int64_t)M * qtot, 256), 256, 0, st>>>(
+        S.Z.as<double>(), M, M, qtot, perm.as<int>(), S.Cg.as<double>(), qtot);
+    PF_LAUNCH_CHECK("z_to_rowmajor_kernel");
+    PF_TRY(U.alloc((size_t)nb_total * H->D * s * 8, st));
+    PF_TRY(HU.alloc((size_t)nb_total * H->D * s * 8, st));
+    for (int b = 0; b < nb_total; ++b)
+      PF_TRY(tsgemm(H->D, s, S.V.as<double>(), R.blocks, S.Cg.as<double>() + b * s, qtot,
+                    U.as<double>() + (int64_t)b * H->D * s, 1, 1.0, 0.0, st));
+    nb = qb;   // active Ritz blocks; blocks nb..nb_total-1 of U hold the reserve
+    PF_TRY(rayleigh_ritz_H(S, U.as<double>(), HU.as<double>(), qb, E, res));
+    sel = nearest_sel(E, lam, nev);
+    clk->mark(1);
+    S.rep.ms_extract = clk->ms(0, 1);
+    S.rep.max_residual_unrefined = max_res();
+    // FP64 refinement for the FP32 filter: subspace iteration U <- (P(H~) + c I) U on the
+    // active blocks, Cholesky QR, Rayleigh-Ritz in H.  An error component on eigenvalue k
+    // shrinks by |P_k + c| / (P_j + c) per pass for wanted pair j.  The first pass is
+    // unshifted (c = 0), which removes the far bulk (P ~ 0) fastest.  If a pass reduces the
+    // residual less than 10x, the remaining error sits where |P| is comparable to the edge
+    // pairs' P: the filter's negative sidelobe (minimum ~ -0.22) or positive values just
+    // outside the set.  Then one reserve block joins the set and later passes use c = 0.06
+    // (option refine_shift), which halves the contraction factor on the negative sidelobe
+    // at the cost of the far bulk.
+    max_pass = o.refine_passes < 0 ? 0 : (o.refine_passes == 0 ? 8 : o.refine_passes);
+    Kr = o.refine_K > 0 ? o.refine_K : K;
+    if (f32 && max_res() > res_tol * hnorm && max_pass > 0) {
+      coeffs_r.resize(Kr + 1);
+      PF_TRY(filter_coefficients_dev(lam_t, Kr, coeffs_r.data(), st));
+      a0 = coeffs_r[0];
+      PF_TRY(coeffr_dev.alloc((size_t)(Kr + 1) * 8, st));
+      PF_TRY(aux64.alloc((size_t)2 * nb_total * H->D * s * 8, st));
+      prev = max_res();
+      phase = REFINE;
+      return issue_refine_filter();
+    }
+    return finish();
+  }
+
+  // Locking: returned pairs already within half the tolerance stay in the set but are not
+  // filtered; they move to the leading blocks (rounded down to whole blocks by keeping the
+  // worst of them active).  Columns without a residual yet (a reserve block just added) are
+  // active.  Each active block is one filter item with its own auxiliary pair.
+  pf_status issue_refine_filter() {
+    const double c_shift = o.refine_shift == 0.0 ? 0.06 : (o.refine_shift < 0.0 ? 0.0 : o.refine_shift);
+    coeffs_r[0] = shifted ? a0 + c_shift : a0;
+    PF_CUDA(cudaMemcpyAsync(coeffr_dev.p, coeffs_r.data(), (size_t)(Kr + 1) * 8, cudaMemcpyHostToDevice, st));
+    const int q = nb * s;
     const int64_t DS = H->D * s;
     double* Ud = U.as<double>();
     double* HUd = HU.as<double>();
-    while (passes < max_pass && max_res() > res_tol * hnorm) {
-      const double c_shift = o.refine_shift == 0.0 ? 0.06 : (o.refine_shift < 0.0 ? 0.0 : o.refine_shift);
-      coeffs_r[0] = shifted ? a0 + c_shift : a0;
-      // Locking: returned pairs already within half the tolerance stay in the set but are
-      // not filtered; they move to the leading blocks (rounded down to whole blocks by
-      // keeping the worst of them active).  Columns without a residual yet (a reserve block
-      // just added) are active.
-      const int q = nb * s;
-      std::vector<char> is_sel(q, 0);
-      for (int j : sel) is_sel[j] = 1;
-      std::vector<int> locked, active;
-      for (int c = 0; c < q; ++c) {
-        if (c < (int)res.size() && is_sel[c] && res[c] <= 0.5 * res_tol * hnorm) locked.push_back(c);
-        else active.push_back(c);
+    std::vector<char> is_sel(q, 0);
+    for (int j : sel) is_sel[j] = 1;
+    std::vector<int> locked, active;
+    for (int c = 0; c < q; ++c) {
+      if (c < (int)res.size() && is_sel[c] && res[c] <= 0.5 * res_tol * hnorm) locked.push_back(c);
+      else active.push_back(c);
+    }
+    std::sort(locked.begin(), locked.end(), [&](int x, int y) { return res[x] < res[y]; });
+    while (active.size() % s != 0) {
+      active.push_back(locked.back());
+      locked.pop_back();
+    }
+    Lb = (int)locked.size() / s;
+    na = nb - Lb;
+    if (Lb > 0) {
+      std::vector<int> order(locked);
+      order.insert(order.end(), active.begin(), active.end());
+      DevBuf pd;
+      PF_TRY(pd.alloc(q * sizeof(int), st));
+      PF_CUDA(cudaMemcpyAsync(pd.p, order.data(), q * sizeof(int), cudaMemcpyHostToDevice, st));
+      permute_cols_kernel<<<(unsigned)ceil_div(H->D * q, 256), 256, 0, st>>>(H->D, s, Ud, pd.as<int>(), q, HUd);
+      PF_LAUNCH_CHECK("permute_cols_kernel");
+      PF_CUDA(cudaMemcpyAsync(Ud, HUd, (size_t)q * H->D * 8, cudaMemcpyDeviceToDevice, st));
+      PF_CUDA(cudaStreamSynchronize(st));
+    }
+    clk->mark(2);
+    pending.clear();
+    for (int b = Lb; b < nb; ++b) {
+      FilterItem it;
+      it.H = H;
+      it.prec = PF_F64;
+      it.s = s;
+      it.V = Ud + (int64_t)b * DS;
+      it.W = HUd + (int64_t)b * DS;
+      it.coeffs_host = coeffs_r.data();
+      it.coeffs_dev = coeffr_dev.as<double>();
+      it.K = Kr;
+      it.aux0 = aux64.as<double>() + (int64_t)(2 * b) * DS;
+      it.aux1 = aux64.as<double>() + (int64_t)(2 * b + 1) * DS;
+      pending.push_back(it);
+      S.rep.filter_steps_f64 += Kr + 1;
+    }
+    return PF_OK;
+  }
+
+  pf_status refine_post() {
+    clk->mark(3);
+    const int64_t DS = H->D * s;
+    double* Ud = U.as<double>();
+    double* HUd = HU.as<double>();
+    double* Wd = HUd + (int64_t)Lb * DS;
+    if (Lb > 0) {   // the filtered blocks against the locked ones, two Gram-Schmidt passes
+      DevBuf Cl;
+      PF_TRY(Cl.alloc((size_t)Lb * s * na * s * 8, st));
+      for (int pass = 0; pass < 2; ++pass) {
+        PF_TRY(gram(H->D, s, Ud, Lb, Wd, na, Cl.as<double>(), S.gscr.as<double>(), S.gscr_elems, st));
+        for (int b = 0; b < na; ++b)
+          PF_TRY(tsgemm(H->D, s, Ud, Lb, Cl.as<double>() + b * s, na * s, Wd + (int64_t)b * DS, 1, -1.0, 1.0, st));
       }
-      std::sort(locked.begin(), locked.end(), [&](int x, int y) { return res[x] < res[y]; });
-      while (active.size() % s != 0) {
-        active.push_back(locked.back());
-        locked.pop_back();
-      }
-      const int Lb = (int)locked.size() / s;
-      const int na = nb - Lb;
-      if (Lb > 0) {
-        std::vector<int> order(locked);
-        order.insert(order.end(), active.begin(), active.end());
-        DevBuf pd;
-        PF_TRY(pd.alloc(q * sizeof(int), st));
-        PF_CUDA(cudaMemcpyAsync(pd.p, order.data(), q * sizeof(int), cudaMemcpyHostToDevice, st));
-        permute_cols_kernel<<<(unsigned)ceil_div(H->D * q, 256), 256, 0, st>>>(H->D, s, Ud, pd.as<int>(), q, HUd);
-        PF_LAUNCH_CHECK("permute_cols_kernel");
-        PF_CUDA(cudaMemcpyAsync(Ud, HUd, (size_t)q * H->D * 8, cudaMemcpyDeviceToDevice, st));
-        PF_CUDA(cudaStreamSynchronize(st));
-      }
-      clk.mark(2);
-      for (int b = Lb; b < nb; ++b) {
-        PF_TRY(filter_apply_raw(H, PF_F64, s, Ud + (int64_t)b * DS, HUd + (int64_t)b * DS, coeffs_r.data(), nullptr,
-                                Kr, aux64a.p, aux64b.p, st));
-        S.rep.filter_steps_f64 += Kr + 1;
-      }
-      clk.mark(3);
-      double* Wd = HUd + (int64_t)Lb * DS;
-      if (Lb > 0) {   // the filtered blocks against the locked ones, two Gram-Schmidt passes
-        DevBuf Cl;
-        PF_TRY(Cl.alloc((size_t)Lb * s * na * s * 8, st));
-        for (int pass = 0; pass < 2; ++pass) {
-          PF_TRY(gram(H->D, s, Ud, Lb, Wd, na, Cl.as<double>(), S.gscr.as<double>(), S.gscr_elems, st));
-          for (int b = 0; b < na; ++b)
-            PF_TRY(tsgemm(H->D, s, Ud, Lb, Cl.as<double>() + b * s, na * s, Wd + (int64_t)b * DS, 1, -1.0, 1.0, st));
+    }
+    PF_TRY(orthonormalise_set(S, Wd, Ud + (int64_t)Lb * DS, na));
+    PF_CUDA(cudaMemcpyAsync(Ud + (int64_t)Lb * DS, Wd, (size_t)na * DS * 8, cudaMemcpyDeviceToDevice, st));
+    PF_TRY(rayleigh_ritz_H(S, Ud, HUd, nb, E, res));
+    sel = nearest_sel(E, lam, nev);
+    clk->mark(4);
+    S.rep.ms_filter_f64 += clk->ms(2, 3);
+    S.rep.ms_refine += clk->ms(2, 4);
+    ++passes;
+    const double cur = max_res();
+    if (cur <= res_tol * hnorm || passes >= max_pass) return finish();
+    if (cur > 0.1 * prev) {
+      shifted = true;
+      if (nb < nb_total) ++nb;   // the reserve block is already in place in U
+    }
+    prev = cur;
+    return issue_refine_filter();
+  }
+
+  pf_status finish() {
+    phase = DONE;
+    S.rep.refine_passes = passes;
+    PF_CUDA(cudaEventRecord(t_end, st));
+    PF_CUDA(cudaEventSynchronize(t_end));
+    float tot = 0;
+    cudaEventElapsedTime(&tot, t_begin, t_end);
+    S.rep.ms_total = tot;
+    S.rep.max_residual = max_res();
+    S.rep.converged = 0;
+    for (int j : sel) S.rep.converged += res[j] <= res_tol * hnorm;
+    status = S.rep.converged == nev ? PF_OK : PF_ENOTCONV;
+    S.rep.status = status;
+    return PF_OK;
+  }
+
+  // evals/resid host [nev] (may be NULL), evecs device D x nev column-major (may be NULL).
+  pf_status outputs(double* evals, double* evecs, double* resid, pf_report* rep) {
+    if (phase != DONE || sel.size() != (size_t)nev) return status != PF_OK ? status : PF_ESTATE;
+    for (int j = 0; j < nev; ++j) {
+      if (evals) evals[j] = E[sel[j]];
+      if (resid) resid[j] = res[sel[j]];
+    }
+    if (evecs) {
+      DevBuf sd;
+      PF_TRY(sd.alloc(nev * sizeof(int), st));
+      PF_CUDA(cudaMemcpyAsync(sd.p, sel.data(), nev * sizeof(int), cudaMemcpyHostToDevice, st));
+      gather_cols_kernel<<<(unsigned)ceil_div(H->D * nev, 256), 256, 0, st>>>(H->D, s, U.as<double>(), sd.as<int>(),
+                                                                              nev, evecs);
+      PF_LAUNCH_CHECK("gather_cols_kernel");
+      PF_CUDA(cudaStreamSynchronize(st));
+    }
+    if (rep) *rep = S.rep;
+    return status;
+  }
+};
+
+// Device bytes a solve holds at its peak besides the Hamiltonian: the resident Lanczos
+// state of solver_init, the Ritz set with H times it, and the FP32 path's refinement
+// auxiliaries, plus the transient Rayleigh-Ritz matrices.  Mirrors the allocations above.
+static size_t solve_state_bytes(int64_t D, int s, int nev, bool f32) {
+  int nev_g = std::max(nev, (int)std::ceil(kGuard * nev));
+  if (nev_g > D) nev_g = (int)D;
+  const int Mmax = (int)std::min<int64_t>(expected_krylov_dim(nev_g, s, 1.5), D);
+  int mb = std::max(2, Mmax / s);
+  if ((int64_t)mb * s > D) mb = (int)(D / s);
+  const int64_t Mcap = (int64_t)(mb + 1) * s;
+  const int qb = (nev_g + s - 1) / s;
+  const int qmax = std::max(qb * s + (f32 ? 2 * s : 0), nev_g);
+  const int nbt = (qmax + s - 1) / s;
+  const int64_t blk = D * s;
+  size_t b = (size_t)(mb + 1) * blk * 8;                    // Krylov basis
+  b += (size_t)Mcap * Mcap * 8;                             // H_L
+  b += (size_t)blk * 8 * 2;                                 // W, tmp
+  b += f32 ? (size_t)blk * 4 * 4 : (size_t)blk * 8 * 2;     // aux pair (+ V32, W32)
+  b += std::max(gram_scratch_elems(D, s, mb + 1, 1), gram_scratch_elems(D, s, nbt, nbt)) * 8;
+  b += eig_workspace_bytes((int)Mcap, std::max(qmax, 2)) + (size_t)Mcap * std::max(qmax, 2) * 8 * 2;
+  b += (size_t)nbt * blk * 8 * 2;                           // U, H U
+  if (f32) b += (size_t)2 * nbt * blk * 8;                  // refinement auxiliaries
+  b += (size_t)qmax * qmax * 8 * 5 + eig_workspace_bytes(qmax, qmax);   // Rayleigh-Ritz
+  return b + ((size_t)16 << 20);
+}
+
+// Runs the pending filter applications of a set of tasks and then each task's follow-up.
+// Items with equal (precision, block width) form one group: a group of one item runs the
+// plain K-step recurrence, larger groups run one sweep (one launch per Clenshaw step over
+// all their rows).  A task whose follow-up fails is marked done with that status; the others
+// continue.
+struct Executor {
+  DevBuf table;
+  std::vector<unsigned char> table_host;
+  cudaStream_t st = 0;
+
+  pf_status run_round(std::vector<Task*>& tasks) {
+    std::vector<std::pair<std::pair<int, int>, std::vector<FilterItem>>> groups;
+    for (Task* t : tasks) {
+      if (t->phase == Task::DONE) continue;
+      for (const FilterItem& it : t->pending) {
+        const auto key = std::make_pair(it.prec, it.s);
+        auto g = std::find_if(groups.begin(), groups.end(), [&](const auto& x) { return x.first == key; });
+        if (g == groups.end()) {
+          groups.push_back({key, {}});
+          g = groups.end() - 1;
         }
+        g->second.push_back(it);
       }
-      PF_TRY(orthonormalise_set(S, Wd, Ud + (int64_t)Lb * DS, na));
-      PF_CUDA(cudaMemcpyAsync(Ud + (int64_t)Lb * DS, Wd, (size_t)na * DS * 8, cudaMemcpyDeviceToDevice, st));
-      PF_TRY(rayleigh_ritz_H(S, Ud, HUd, nb, E, res));
-      sel = nearest_sel(E, lam, nev);
-      clk.mark(4);
-      S.rep.ms_filter_f64 += clk.ms(2, 3);
-      S.rep.ms_refine += clk.ms(2, 4);
-      ++passes;
-      const double cur = max_res();
-      if (cur > res_tol * hnorm && cur > 0.1 * prev) {
-        shifted = true;
-        if (nb < nb_total) ++nb;
+    }
+    for (auto& g : groups) {
+      const auto& items = g.second;
+      if (items.size() == 1) {
+        const FilterItem& it = items[0];
+        PF_TRY(filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, st));
+      } else {
+        const size_t need = filter_sweep_table_bytes((int)items.size());
+        if (table.bytes < need) PF_TRY(table.alloc(need * 2, st));
+        if (table_host.size() < need) table_host.resize(need * 2);
+        // table_host is pageable: the copy inside has consumed it when the call returns.
+        PF_TRY(filter_sweep(items, table.p, table.bytes, table_host.data(), st));
       }
-      prev = cur;
+    }
+    for (Task* t : tasks) {
+      if (t->phase == Task::DONE || t->pending.empty()) continue;
+      const pf_status s = t->after_filter();
+      if (s != PF_OK) {
+        t->status = s;
+        t->phase = Task::DONE;
+        t->pending.clear();
+      }
+    }
+    return PF_OK;
+  }
+
+  pf_status run(std::vector<Task*>& tasks) {
+    for (;;) {
+      bool any = false;
+      for (Task* t : tasks) any = any || (t->phase != Task::DONE && !t->pending.empty());
+      if (!any) return PF_OK;
+      PF_TRY(run_round(tasks));
     }
   }
-  S.rep.refine_passes = passes;
-  // outputs
-  const double mr = max_res();
-  for (int j = 0; j < nev; ++j) {
-    evals[j] = E[sel[j]];
-    resid[j] = res[sel[j]];
+};
+
+static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, const pf_solve_opts* o_in,
+                                   double* evals, double* evecs, double* resid, pf_report* rep, cudaStream_t st) {
+  if (!H || !evals || !resid) return PF_EINVAL;
+  Task t;
+  PF_TRY(t.init(H, target_eps, nev, K, o_in, st));
+  Executor ex;
+  ex.st = st;
+  std::vector<Task*> v{&t};
+  PF_TRY(ex.run(v));
+  if (t.phase != Task::DONE || t.sel.empty()) return t.status != PF_OK ? t.status : PF_ENOTCONV;
+  return t.outputs(evals, evecs, resid, rep);
+}
+
+// ------------------------------------------------------------------ serving
+// Continuous batching.  Requests queue on submit.  Each step admits queued requests in
+// arrival order while the sum of the admitted footprints stays within the budget (the
+// first request is admitted into an empty server whatever its size), builds their basis,
+// Hamiltonian, bounds and K, runs one executor round over all resident solves (their
+// filter applications share sweeps) and retires the finished ones, releasing their memory.
+struct Request {
+  int64_t id = 0;
+  pf_model m;
+  std::vector<double> h, mu, A, un;
+  std::vector<int32_t> nj;
+  double eps = 0.5;
+  int nev = 1;
+  int state = 0;   // 0 queued, 1 active, 2 finished
+  pf_status status = PF_OK;
+  size_t foot = 0;
+  pf_basis* basis = nullptr;
+  pf_ham* ham = nullptr;
+  Task* task = nullptr;
+  std::vector<double> evals, resid;
+  pf_report rep;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+static double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static int64_t model_dim(const pf_model& m) {
+  auto C = [](int n, int k) -> double {
+    if (k < 0 || k > n) return 0;
+    double r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return std::floor(r + 0.5);
+  };
+  if (m.kind == PF_MODEL_XXZ) return (int64_t)C(m.L, m.N);
+  if (m.kind == PF_MODEL_HUBBARD) return (int64_t)(C(m.L, m.N_up) * C(m.L, m.N_dn));
+  if (m.kind == PF_MODEL_QSUN) return (int64_t)1 << (m.N + m.L);
+  return 0;
+}
+
+// Stored entries per row, an upper bound: the diagonal plus one per bond (XXZ), two per bond
+// (Hubbard), the dot block plus one per outer spin (quantum sun).
+static int64_t model_nnz_bound(const pf_model& m, int64_t D) {
+  if (m.kind == PF_MODEL_XXZ) return D * (1 + m.L);
+  if (m.kind == PF_MODEL_HUBBARD) return D * (1 + 2 * m.L);
+  return D * (((int64_t)1 << m.N) + m.L);
+}
+
+static size_t ham_bytes(int64_t D, int64_t nnz) { return (size_t)(D + 1) * 8 + (size_t)nnz * 24 + (size_t)D * 4; }
+
+struct Server {
+  pf_server_config cfg;
+  cudaStream_t st = 0;
+  int64_t next_id = 1;
+  std::vector<Request*> queue, active, finished;
+  size_t in_use = 0;
+  Executor ex;
+
+  ~Server() {
+    for (auto* v : {&queue, &active, &finished})
+      for (Request* r : *v) {
+        release(r);
+        delete r;
+      }
   }
-  if (evecs) {
-    DevBuf sd;
-    PF_TRY(sd.alloc(nev * sizeof(int), st));
-    PF_CUDA(cudaMemcpyAsync(sd.p, sel.data(), nev * sizeof(int), cudaMemcpyHostToDevice, st));
-    gather_cols_kernel<<<(unsigned)ceil_div(H->D * nev, 256), 256, 0, st>>>(H->D, s, U.as<double>(), sd.as<int>(),
-                                                                            nev, evecs);
-    PF_LAUNCH_CHECK("gather_cols_kernel");
+  void release(Request* r) {
+    delete r->task;
+    r->task = nullptr;
+    if (r->ham) pf_free_ham(r->ham);
+    if (r->basis) pf_free_basis(r->basis);
+    r->ham = nullptr;
+    r->basis = nullptr;
   }
-  cudaEventRecord(t1, st);
-  PF_CUDA(cudaStreamSynchronize(st));
-  float tot = 0;
-  cudaEventElapsedTime(&tot, t0, t1);
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
-  S.rep.ms_total = tot;
-  S.rep.max_residual = mr;
-  S.rep.converged = 0;
-  for (int j = 0; j < nev; ++j) S.rep.converged += resid[j] <= res_tol * hnorm;
-  const bool ok = S.rep.converged == nev;
-  S.rep.status = ok ? PF_OK : PF_ENOTCONV;
-  if (rep) *rep = S.rep;
-  return ok ? PF_OK : PF_ENOTCONV;
+  pf_status admit(Request* r) {
+    pf_params p;
+    memset(&p, 0, sizeof(p));
+    p.h = r->h.empty() ? nullptr : r->h.data();
+    p.mu = r->mu.empty() ? nullptr : r->mu.data();
+    p.A = r->A.empty() ? nullptr : r->A.data();
+    p.u_noise = r->un.empty() ? nullptr : r->un.data();
+    p.n_of_j = r->nj.empty() ? nullptr : r->nj.data();
+    PF_TRY(pf_build_basis(&r->m, &r->basis, st));
+    PF_TRY(pf_build_hamiltonian(r->basis, &r->m, &p, &r->ham, st));
+    double emin, emax;
+    PF_TRY(pf_spectral_bounds(r->ham, cfg.bounds_tol, &emin, &emax, nullptr, nullptr, st));
+    int32_t K = 0;
+    PF_TRY(pf_choose_K(r->ham, r->eps, r->nev, &K, st));
+    pf_solve_opts o;
+    pf_default_opts(&o);
+    o.block = cfg.block;
+    o.precision = cfg.precision;
+    if (cfg.res_tol > 0) o.res_tol = cfg.res_tol;
+    if (cfg.seed) o.seed = cfg.seed;
+    r->task = new Task();
+    return r->task->init(reinterpret_cast<Ham*>(r->ham), r->eps, r->nev, K, &o, st);
+  }
+  void retire(Request* r, pf_status s) {
+    r->status = s;
+    r->state = 2;
+    r->t_done = now_ms();
+    in_use -= r->foot;
+    release(r);
+    finished.push_back(r);
+  }
+  pf_status step(int32_t* nq, int32_t* na, int32_t* nf) {
+    while (!queue.empty() && (int)active.size() < cfg.max_active) {
+      Request* r = queue.front();
+      if (!active.empty() && in_use + r->foot > (size_t)cfg.mem_budget_bytes) break;
+      queue.erase(queue.begin());
+      r->state = 1;
+      r->t_admit = now_ms();
+      in_use += r->foot;
+      const pf_status s = admit(r);
+      if (s != PF_OK) {
+        retire(r, s);
+        continue;
+      }
+      active.push_back(r);
+    }
+    std::vector<Task*> ts;
+    for (Request* r : active) ts.push_back(r->task);
+    if (!ts.empty()) PF_TRY(ex.run_round(ts));
+    for (size_t i = 0; i < active.size();) {
+      Request* r = active[i];
+      if (r->task->phase == Task::DONE) {
+        r->evals.assign(r->nev, 0.0);
+        r->resid.assign(r->nev, 0.0);
+        memset(&r->rep, 0, sizeof(r->rep));
+        const pf_status s = r->task->outputs(r->evals.data(), nullptr, r->resid.data(), &r->rep);
+        active.erase(active.begin() + i);
+        retire(r, s);
+      } else {
+        ++i;
+      }
+    }
+    if (nq) *nq = (int32_t)queue.size();
+    if (na) *na = (int32_t)active.size();
+    if (nf) *nf = (int32_t)finished.size();
+    return PF_OK;
+  }
+};
+
+static pf_status copy_request(const pf_model* m, const pf_params* p, Request* r) {
+  r->m = *m;
+  const int L = m->L;
+  if (L < 1 || L > 32) return PF_EINVAL;
+  if (m->kind == PF_MODEL_XXZ) {
+    if (!p->h) return PF_EINVAL;
+    r->h.assign(p->h, p->h + L);
+  } else if (m->kind == PF_MODEL_HUBBARD) {
+    if (!p->mu) return PF_EINVAL;
+    r->mu.assign(p->mu, p->mu + L);
+  } else if (m->kind == PF_MODEL_QSUN) {
+    if (!p->h || !p->A || !p->u_noise || !p->n_of_j || m->N < 1 || m->N > 10) return PF_EINVAL;
+    const int nd = 1 << m->N;
+    r->h.assign(p->h, p->h + L);
+    r->A.assign(p->A, p->A + (size_t)nd * nd);
+    r->un.assign(p->u_noise, p->u_noise + L);
+    r->nj.assign(p->n_of_j, p->n_of_j + L);
+  } else {
+    return PF_EINVAL;
+  }
+  return PF_OK;
 }
 
 }  // namespace pf
 
 using namespace pf;
+
+struct pf_server : pf::Server {};
 
 extern "C" {
 
@@ -775,6 +1227,140 @@ pf_status pf_polfed_solve(pf_ham* hh, double target_eps, int32_t nev, int32_t K,
   return polfed_solve_impl(reinterpret_cast<Ham*>(hh), target_eps, nev, K, o, evals, evecs, resid, rep,
                            (cudaStream_t)stream);
 }
+
+pf_status pf_polfed_solve_batch(pf_solve_item* items, int32_t n, pf_stream_t stream) {
+  if (n < 0 || (n > 0 && !items)) return PF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<std::unique_ptr<Task>> tasks;
+  std::vector<Task*> run;
+  std::vector<int> slot;
+  for (int i = 0; i < n; ++i) {
+    pf_solve_item& it = items[i];
+    tasks.emplace_back(new Task());
+    if (!it.H || !it.evals || !it.resid) {
+      it.status = PF_EINVAL;
+      continue;
+    }
+    const pf_status s = tasks.back()->init(reinterpret_cast<Ham*>(it.H), it.target_eps, it.nev, it.K, it.opts, st);
+    it.status = s;
+    if (s == PF_OK) {
+      run.push_back(tasks.back().get());
+      slot.push_back(i);
+    }
+  }
+  Executor ex;
+  ex.st = st;
+  const pf_status rs = ex.run(run);
+  if (rs != PF_OK) {   // a shared launch failed: every problem that was running reports it
+    for (size_t j = 0; j < run.size(); ++j) items[slot[j]].status = rs;
+    return rs;
+  }
+  pf_status first_bad = PF_OK;
+  for (size_t j = 0; j < run.size(); ++j) {
+    pf_solve_item& it = items[slot[j]];
+    Task* t = run[j];
+    it.status = (t->phase == Task::DONE && !t->sel.empty()) ? t->outputs(it.evals, it.evecs, it.resid, it.rep)
+                                                            : (t->status != PF_OK ? t->status : PF_ENOTCONV);
+  }
+  for (int i = 0; i < n; ++i)
+    if (items[i].status != PF_OK && first_bad == PF_OK) first_bad = (pf_status)items[i].status;
+  return first_bad;
+}
+
+pf_status pf_solve_footprint(int64_t D, int64_t nnz, int32_t nev, int32_t block, int32_t precision,
+                             int64_t* bytes) {
+  if (D < 1 || nnz < 0 || nev < 1 || nev > D || !bytes) return PF_EINVAL;
+  const int s = block > 0 ? block : 32;
+  if (!(s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32 || s == 64)) return PF_EINVAL;
+  if (precision != PF_F64 && precision != PF_F32) return PF_EINVAL;
+  *bytes = (int64_t)(ham_bytes(D, nnz) + solve_state_bytes(D, s, nev, precision == PF_F32));
+  return PF_OK;
+}
+
+pf_status pf_server_create(const pf_server_config* cfg, pf_stream_t stream, pf_server** out) {
+  if (!out) return PF_EINVAL;
+  *out = nullptr;
+  pf_server_config c;
+  memset(&c, 0, sizeof(c));
+  if (cfg) c = *cfg;
+  if (c.block == 0) c.block = 32;
+  if (!(c.block == 1 || c.block == 2 || c.block == 4 || c.block == 8 || c.block == 16 || c.block == 32 ||
+        c.block == 64))
+    return PF_EINVAL;
+  if (c.precision != PF_F64 && c.precision != PF_F32) return PF_EINVAL;
+  if (c.max_active <= 0) c.max_active = 64;
+  if (c.mem_budget_bytes < 0) return PF_EINVAL;
+  if (c.mem_budget_bytes == 0) {
+    size_t fr = 0, tot = 0;
+    PF_CUDA(cudaMemGetInfo(&fr, &tot));
+    c.mem_budget_bytes = (int64_t)(0.8 * (double)fr);
+  }
+  pf_server* sv = new pf_server();
+  sv->cfg = c;
+  sv->st = (cudaStream_t)stream;
+  sv->ex.st = sv->st;
+  *out = sv;
+  return PF_OK;
+}
+
+pf_status pf_server_submit(pf_server* sv, const pf_model* m, const pf_params* p, double target_eps, int32_t nev,
+                           int64_t* id) {
+  if (!sv || !m || !p || !id) return PF_EINVAL;
+  if (!(target_eps >= 0.0 && target_eps <= 1.0) || nev < 1) return PF_EINVAL;
+  std::unique_ptr<Request> r(new Request());
+  PF_TRY(copy_request(m, p, r.get()));
+  const int64_t D = model_dim(*m);
+  if (D < 1 || nev > D) return PF_EINVAL;
+  r->eps = target_eps;
+  r->nev = nev;
+  r->foot = ham_bytes(D, model_nnz_bound(*m, D)) + solve_state_bytes(D, sv->cfg.block, nev, sv->cfg.precision == PF_F32);
+  r->id = sv->next_id++;
+  r->t_submit = now_ms();
+  *id = r->id;
+  sv->queue.push_back(r.release());
+  return PF_OK;
+}
+
+pf_status pf_server_step(pf_server* sv, int32_t* queued, int32_t* active, int32_t* finished) {
+  if (!sv) return PF_EINVAL;
+  return sv->step(queued, active, finished);
+}
+
+pf_status pf_server_take(pf_server* sv, int64_t id, double* evals, double* resid, pf_report* rep,
+                         pf_request_info* info) {
+  if (!sv) return PF_EINVAL;
+  for (size_t i = 0; i < sv->finished.size(); ++i) {
+    Request* r = sv->finished[i];
+    if (r->id != id) continue;
+    if (evals && !r->evals.empty()) memcpy(evals, r->evals.data(), r->nev * sizeof(double));
+    if (resid && !r->resid.empty()) memcpy(resid, r->resid.data(), r->nev * sizeof(double));
+    if (rep) *rep = r->rep;
+    if (info) {
+      info->id = r->id;
+      info->status = r->status;
+      info->nev = r->nev;
+      info->footprint_bytes = (int64_t)r->foot;
+      info->queue_ms = r->t_admit - r->t_submit;
+      info->latency_ms = r->t_done - r->t_submit;
+    }
+    sv->finished.erase(sv->finished.begin() + i);
+    delete r;
+    return PF_OK;
+  }
+  for (auto* v : {&sv->queue, &sv->active})
+    for (Request* r : *v)
+      if (r->id == id) return PF_ESTATE;
+  return PF_EINVAL;
+}
+
+pf_status pf_server_memory(const pf_server* sv, int64_t* in_use, int64_t* budget) {
+  if (!sv) return PF_EINVAL;
+  if (in_use) *in_use = (int64_t)sv->in_use;
+  if (budget) *budget = sv->cfg.mem_budget_bytes;
+  return PF_OK;
+}
+
+void pf_server_destroy(pf_server* sv) { delete sv; }
 
 pf_status pf_start_block(int64_t D, int32_t s, uint64_t seed, double* out, pf_stream_t stream) {
   if (D < 1 || s < 1 || !out) return PF_EINVAL;
