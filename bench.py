@@ -49,6 +49,20 @@ def parse():
                     help="only time the fused Clenshaw step at the workload shape (profiling)")
     ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--L", type=int, default=L_SITES, help="solve mode: chain length (default: the L=20 workload)")
+    ap.add_argument("--nev", type=int, default=NEV, help="solve mode: eigenpairs per solve")
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serving"],
+                    help="solve: the L=20 workload; batch: many small solves together vs one at a time; "
+                         "serving: a Poisson request stream through the continuous-batching server")
+    ap.add_argument("--batch-n", type=int, default=32)
+    ap.add_argument("--batch-L", type=int, default=14)
+    ap.add_argument("--batch-nev", type=int, default=20)
+    ap.add_argument("--batch-block", type=int, default=16)
+    ap.add_argument("--serve-n", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=2.0)
+    ap.add_argument("--serve-L", default="14,16,18")
+    ap.add_argument("--serve-nev", default="20,50,200")
+    ap.add_argument("--serve-block", type=int, default=16)
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
     return ap.parse_args()
 
@@ -310,7 +324,7 @@ def run_ours(args):
         fp64_peak = 148 * 4 * 2.032e9 / 1e12        # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
         roof64 = {"bound": "alu", "achieved": flops / per / 1e9, "peak": fp64_peak, "unit": "TFLOP/s",
                   "frac": flops / per / 1e9 / fp64_peak, "kernel": "clenshaw_step_kernel<double,32>",
-                  "us_per_launch": 1e3 * per}
+                  "us_per_block_step": 1e3 * per}
     cpu = None
     if not args.no_cpu_baseline:
         dt, K0, n = oracle_sample(args.cpu_sample_steps)
@@ -324,7 +338,7 @@ def run_ours(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / len(rec),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "f32" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "model": "XXZ L=20 periodic, J=1, Delta=1, h_i~U[-W,W], W in (1,3,5)",
+        "config": {"workload": WORKLOAD, "model": f"XXZ L={L_SITES} periodic, J=1, Delta=1, h_i~U[-W,W], W in (1,3,5)",
                    "D": D, "nnz": nnz, "nev": NEV, "block": BLOCK, "target_eps": EPS,
                    "precision": ("FP32 filter + FP64 Lanczos/Rayleigh-Ritz/refinement" if args.precision == "f32"
                                  else "FP64 throughout"),
@@ -345,12 +359,140 @@ def run_ours(args):
     print(json.dumps(out))
 
 
+def _solve_one(pf, p, eps, nev, block, precision):
+    H = pf.Hamiltonian.from_params(p)
+    H.spectral_bounds()
+    K = H.choose_K(eps, nev)
+    r = H.solve(eps, nev, K, block=block, precision=precision, return_vectors=False, raise_on_notconv=False)
+    return H, K, r
+
+
+def run_batch(args):
+    """Many small solves (one disorder realisation each) together vs one at a time."""
+    import numpy as np
+    import torch
+    import pf_inputs as pi
+    import paper_2605_10191_b300 as pf
+    torch.cuda.set_device(0)
+    n, L, nev, s = args.batch_n, args.batch_L, args.batch_nev, args.batch_block
+    u = pi.uniform01(5100, np.arange(n))
+    params = [pi.xxz_params(L, W=0.5 + 7.5 * u[k], seed=5101 + k) for k in range(n)]
+    Hs, probs = [], []
+    for p in params:
+        H = pf.Hamiltonian.from_params(p)
+        H.spectral_bounds()
+        Hs.append(H)
+        probs.append(dict(H=H, eps=0.5, nev=nev, K=H.choose_K(0.5, nev)))
+
+    def good_of(res):
+        return sum(int(np.sum(r.resid <= RES_TOL * r.report["hnorm"])) for r in res)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, out
+
+    for _ in range(max(1, args.warmup)):
+        pf.solve_batch(probs[: min(4, n)], block=s, precision=args.precision)
+    lib = pf.lib()
+    n0 = lib.pf_kernel_launches()
+    tb, res_b = [], None
+    for _ in range(args.steps):
+        dt, res_b = timed(lambda: pf.solve_batch(probs, block=s, precision=args.precision))
+        tb.append(dt)
+    launches_b = (lib.pf_kernel_launches() - n0) // max(1, args.steps)
+    n0 = lib.pf_kernel_launches()
+    ts, res_s = [], None
+    for _ in range(args.steps):
+        dt, res_s = timed(lambda: [pb["H"].solve(pb["eps"], pb["nev"], pb["K"], block=s, precision=args.precision,
+                                                 return_vectors=False, raise_on_notconv=False) for pb in probs])
+        ts.append(dt)
+    launches_s = (lib.pf_kernel_launches() - n0) // max(1, args.steps)
+    same = all(np.array_equal(a.evals, b.evals) for a, b in zip(res_b, res_s))
+    gb, gs = good_of(res_b), good_of(res_s)
+    out = {"metric": "eigenpairs_per_s_at_residual_1e-9", "mode": "batch",
+           "value": gb / statistics.median(tb), "unit": "eigenpairs/s", "higher_is_better": True,
+           "one_at_a_time": gs / statistics.median(ts), "speedup": statistics.median(ts) / statistics.median(tb),
+           "results_identical": bool(same), "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "dtype": "f32+f64" if args.precision == "f32" else "f64", "data": "synthetic",
+           "config": {"workload": f"xxz_L{L}_batch{n}_nev{nev}_s{s}_eps0.5", "D": Hs[0].D, "nnz": Hs[0].nnz,
+                      "K": [pb["K"] for pb in probs][:8], "W": "U[0.5, 8] per realisation"},
+           "gpu_launches_batched": int(launches_b), "gpu_launches_one_at_a_time": int(launches_s),
+           "s_batched": statistics.median(tb), "s_one_at_a_time": statistics.median(ts)}
+    print(json.dumps(out))
+
+
+def run_serving(args):
+    """Poisson request stream through the server vs plain FP64 solves one at a time."""
+    import numpy as np
+    import torch
+    import pf_inputs as pi
+    import paper_2605_10191_b300 as pf
+    from paper_2605_10191_b300.serving import run_stream
+    torch.cuda.set_device(0)
+    Ls = tuple(int(x) for x in args.serve_L.split(","))
+    nevs = tuple(int(x) for x in args.serve_nev.split(","))
+    reqs = pi.serving_stream(args.serve_n, args.serve_rate, Ls=Ls, nevs=nevs)
+    s = args.serve_block
+    # warm-up: a short stream of the smallest sector
+    warm = pi.serving_stream(3, 100.0, Ls=(min(Ls),), nevs=(min(nevs),), seed=5900)
+    sv = pf.Server(block=s, precision="f32")
+    run_stream(sv, warm)
+    lib = pf.lib()
+    n0 = lib.pf_kernel_launches()
+    with ClockSampler(0) as clocks:
+        r = run_stream(sv, reqs)
+    launches = lib.pf_kernel_launches() - n0
+    sv.close()
+    summ = r.summary()
+    # plain FP64 path, one request at a time in arrival order; FIFO latencies from the measured
+    # service times and the same arrivals
+    svc, good64 = [], 0
+    for rq in reqs:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        H, K, res = _solve_one(pf, rq["params"], rq["eps"], rq["nev"], s, "f64")
+        torch.cuda.synchronize()
+        svc.append(time.perf_counter() - t)
+        good64 += int(np.sum(res.resid <= RES_TOL * res.report["hnorm"]))
+        del H, res
+    fin, lat = 0.0, []
+    for rq, dt in zip(reqs, svc):
+        start = max(rq["t_arrival"], fin)
+        fin = start + dt
+        lat.append(1e3 * (fin - rq["t_arrival"]))
+    span64 = fin - reqs[0]["t_arrival"]
+    out = {"metric": "eigenpairs_per_s_at_residual_1e-9", "mode": "serving", "value": summ["eigenpairs_per_s"],
+           "unit": "eigenpairs/s", "higher_is_better": True, "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
+           "serving": summ,
+           "fp64_one_at_a_time": {"eigenpairs_per_s": good64 / span64, "p50_ms": float(np.percentile(lat, 50)),
+                                  "p99_ms": float(np.percentile(lat, 99)), "service_s_total": sum(svc),
+                                  "latency": "FIFO queue simulated from measured service times, same arrivals"},
+           "n_gpus": 1, "dtype": "f32+f64", "data": "synthetic", "gpu_launches": int(launches),
+           "clocks": clocks.summary(),
+           "config": {"workload": f"serving_xxz_L{'-'.join(map(str, Ls))}_n{args.serve_n}_rate{args.serve_rate}",
+                      "requests": args.serve_n, "rate_per_s": args.serve_rate, "L": Ls, "nev": nevs,
+                      "W": "U[0.5, 8]", "eps": "U[0.2, 0.8]", "block": s,
+                      "timing": "host wall clock, arrival to completion"}}
+    print(json.dumps(out))
+
+
 def main():
+    global L_SITES, NEV, WORKLOAD
     args = parse()
+    if (args.L, args.nev) != (L_SITES, NEV):
+        L_SITES, NEV = args.L, args.nev
+        WORKLOAD = f"xxz_L{L_SITES}_D{math.comb(L_SITES, L_SITES // 2)}_nev{NEV}_s{BLOCK}_eps{EPS}"
     if args.impl == "reference":
         run_reference(args)
     elif args.kernel_only:
         run_kernel_only(args)
+    elif args.mode == "batch":
+        run_batch(args)
+    elif args.mode == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

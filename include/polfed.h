@@ -186,7 +186,8 @@ pf_status pf_filter_apply(const pf_ham* H, int32_t prec, int32_t s, const void* 
  *   items[j].H      : handle with H~ set;  V, W: device blocks (D_j x s) of the precision.
  *   items[j].coeffs : host [K_j + 1];      K: >= 1.
  * Allocates two auxiliary blocks per item, the coefficients and a table of n entries.
- * Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ENOMEM, PF_ECUDA.                    */
+ * Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ENOMEM, PF_ECUDA (including a cluster
+ * shape the device cannot schedule).                                                */
 typedef struct {
   const pf_ham* H;
   const void* V;
@@ -194,8 +195,29 @@ typedef struct {
   const double* coeffs;
   int32_t K;
 } pf_filter_item;
+/* Execution form of a batch (form argument):
+ *   PF_FORM_AUTO  (-1) each item shape's form chosen by the autotuner (pf_filter_tune);
+ *   PF_FORM_STEPS  (0) one launch per Clenshaw step over all items' rows;
+ *   PF_FORM_GRAPH (-2) the same launches as one CUDA graph (a chain of kernel nodes);
+ *   c in {1, 2, 4, 8, 16}: one persistent launch, a thread-block cluster of c CTAs per item
+ *      running the item's whole recurrence with a hardware cluster barrier between steps.
+ * Every form gives the same bits.                                                    */
+#define PF_FORM_AUTO (-1)
+#define PF_FORM_STEPS 0
+#define PF_FORM_GRAPH (-2)
 pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t prec, int32_t s,
-                                pf_stream_t stream);
+                                int32_t form, pf_stream_t stream);
+/* The autotuner's choice for items shaped like H at (prec, s), degree K: form = 0 (per-step
+ * sweep) or a cluster size c >= 1 (persistent).  The choice minimises SM-time per item step
+ * measured on the device: c SMs x the persistent step time, against all SMs x the sweep's
+ * step time over enough copies of the item to fill the GPU, divided by the copies.  Items
+ * with more than 64 rows per thread of a 16-CTA cluster always take the sweep.  Cached per
+ * (device, D, nnz, prec, s); the first call per shape runs the measurements (scratch blocks
+ * only).  sm_us (may be NULL): host [6], measured SM-microseconds per item step of the
+ * sweep and of clusters of 1, 2, 4, 8, 16 CTAs (0 = not measured).
+ * Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ENOMEM, PF_ECUDA.                    */
+pf_status pf_filter_tune(const pf_ham* H, int32_t prec, int32_t s, int32_t K, int32_t* form, double* sm_us,
+                         pf_stream_t stream);
 
 /* Same computation as pf_filter_apply, without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device memory at

@@ -11,6 +11,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpolfed.so")
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ENOTCONV, PF_ETIMEOUT, PF_ECUDA, PF_ESTATE, PF_EBREAKDOWN = range(8)
 PF_MODEL_XXZ, PF_MODEL_QSUN, PF_MODEL_HUBBARD = 0, 1, 2
 PF_F64, PF_F32 = 0, 1
+PF_FORM_AUTO, PF_FORM_STEPS, PF_FORM_GRAPH = -1, 0, -2
 
 
 class pf_model(C.Structure):
@@ -102,7 +103,8 @@ PROTOTYPES = {
     "pf_default_opts": (None, [P(pf_solve_opts)]),
     "pf_polfed_solve": (i32, [vp, dbl, i32, i32, P(pf_solve_opts), P(dbl), vp, P(dbl), P(pf_report), vp]),
     "pf_start_block": (i32, [i64, i32, u64, vp, vp]),
-    "pf_filter_apply_batch": (i32, [P(pf_filter_item), i32, i32, i32, vp]),
+    "pf_filter_apply_batch": (i32, [P(pf_filter_item), i32, i32, i32, i32, vp]),
+    "pf_filter_tune": (i32, [vp, i32, i32, i32, P(i32), P(dbl), vp]),
     "pf_polfed_solve_batch": (i32, [P(pf_solve_item), i32, vp]),
     "pf_solve_footprint": (i32, [i64, i64, i32, i32, i32, P(i64)]),
     "pf_server_create": (i32, [P(pf_server_config), vp, P(vp)]),

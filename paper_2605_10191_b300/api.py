@@ -274,8 +274,11 @@ def _make_opts(block, precision, target_abs, opts):
     return o
 
 
-def filter_apply_batch(items, stream=None):
-    """W_j = P_j(H~_j) V_j for items (H, V, coeffs) of one dtype and block width, in one sweep."""
+def filter_apply_batch(items, form="auto", stream=None):
+    """W_j = P_j(H~_j) V_j for items (H, V, coeffs) of one dtype and block width, together.
+
+    form: "auto" (autotuner), "steps" (one launch per step), "graph" (the steps as a CUDA
+    graph) or a cluster size 1/2/4/8/16 (one persistent launch)."""
     _install_torch_allocator()
     n = len(items)
     if n == 0:
@@ -294,8 +297,20 @@ def filter_apply_batch(items, stream=None):
         arr[j].W = W.data_ptr()
         arr[j].coeffs = c.ctypes.data_as(C.POINTER(C.c_double))
         arr[j].K = len(c) - 1
-    check(lib().pf_filter_apply_batch(arr, n, prec, V0.shape[1], _stream(stream)), "pf_filter_apply_batch")
+    f = {"auto": L.PF_FORM_AUTO, "steps": L.PF_FORM_STEPS, "graph": L.PF_FORM_GRAPH}.get(form, form)
+    check(lib().pf_filter_apply_batch(arr, n, prec, V0.shape[1], int(f), _stream(stream)), "pf_filter_apply_batch")
     return outs
+
+
+def filter_tune(H, K, s=32, precision="f32", stream=None):
+    """The autotuner's form for items shaped like H: (form, {candidate: SM-us per item step})."""
+    _install_torch_allocator()
+    f = C.c_int32()
+    us = (C.c_double * 6)()
+    check(lib().pf_filter_tune(H.handle, L.PF_F64 if precision == "f64" else L.PF_F32, int(s), int(K), C.byref(f),
+                               us, _stream(stream)), "pf_filter_tune")
+    names = ["sweep", "c1", "c2", "c4", "c8", "c16"]
+    return f.value, {k: us[i] for i, k in enumerate(names) if us[i] > 0}
 
 
 def solve_batch(problems, block=32, precision="f64", return_vectors=False, stream=None, **opts):

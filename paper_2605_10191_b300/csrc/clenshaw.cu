@@ -15,6 +15,10 @@
 // rewritten in place), so whatever of the step's working set fits in L2 stays there.
 #include "common.cuh"
 #include <algorithm>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace pf {
 
@@ -90,33 +94,62 @@ template <typename T, int S> struct Shape {
   static constexpr int ROWS_PER_WARP = 32 / G;
 };
 
-// out[row, :] = a V[row, :] + alpha * sum_j val[j] B1[col[j], :] - beta B2[row, :]
-template <typename T, int S, bool SPMM, bool HAS_B2>
-__global__ void __launch_bounds__(256) clenshaw_step_kernel(int64_t D, const int64_t* __restrict__ rp,
-                                                            const int32_t* __restrict__ col,
-                                                            const T* __restrict__ val, const T* __restrict__ V,
-                                                            const T* __restrict__ B1, const T* B2, T* out, T a,
-                                                            T alpha, T beta) {
+// L2-only loads (ld.global.cg) for blocks the same launch rewrites between its steps.
+template <typename T, int E>
+__device__ __forceinline__ Vec<T, E> ld_l2(const T* p) {
+  Vec<T, E> r;
+  if constexpr (sizeof(T) * E == 16) {
+    if constexpr (sizeof(T) == 4) {
+      float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+      r.x[0] = v.x; r.x[1] = v.y; r.x[2] = v.z; r.x[3] = v.w;
+    } else {
+      double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+      r.x[0] = v.x; r.x[1] = v.y;
+    }
+  } else if constexpr (sizeof(T) * E == 8 && sizeof(T) == 4) {
+    float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    r.x[0] = v.x; r.x[1] = v.y;
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) r.x[e] = __ldcg(p + e);
+  }
+  return r;
+}
+
+// One row segment (lane's E entries) of one step:
+//     out[row, :] = a V[row, :] + alpha * sum_j val[j] B1[col[j], :] - beta B2[row, :]
+// SP / B2M: 1 = the SpMM / the B2 term is present, 0 = absent, -1 = decided at run time by
+// alpha != 0 / beta != 0.  Every kernel of this file computes a row through this function, so
+// all execution forms produce the same bits: the SpMM accumulates in column order, four
+// entries per round, and the epilogue is fma(alpha, acc, fma(a, v, -beta q)) (or
+// fma(alpha, acc, a v) without B2).  L2ONLY selects ld.global.cg for B1 and B2.
+template <typename T, int S, bool L2ONLY, int SP, int B2M>
+__device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_t* __restrict__ rp,
+                                             const int32_t* __restrict__ col, const T* __restrict__ val,
+                                             const T* __restrict__ V, const T* B1, const T* B2, T* out, T a,
+                                             T alpha, T beta) {
   using Sh = Shape<T, S>;
-  constexpr int E = Sh::E, G = Sh::G;
-  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = gtid / G;
-  const int lane = (int)(gtid % G);
-  if (row >= D) return;
+  constexpr int E = Sh::E;
   const int64_t off = row * S + lane * E;
   T acc[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) acc[e] = T(0);
-  if constexpr (SPMM) {
+  const bool spmm = SP < 0 ? (alpha != T(0)) : (SP > 0);
+  const bool hb2 = B2M < 0 ? (beta != T(0)) : (B2M > 0);
+  auto ldb = [](const T* p) {
+    if constexpr (L2ONLY) return ld_l2<T, E>(p);
+    else return ld_default<T, E>(p);
+  };
+  if (spmm) {
     int64_t j = rp[row];
     const int64_t end = rp[row + 1];
     for (; j + 4 <= end; j += 4) {
       int c0 = __ldg(col + j), c1 = __ldg(col + j + 1), c2 = __ldg(col + j + 2), c3 = __ldg(col + j + 3);
       T h0 = __ldg(val + j), h1 = __ldg(val + j + 1), h2 = __ldg(val + j + 2), h3 = __ldg(val + j + 3);
-      Vec<T, E> b0 = ld_default<T, E>(B1 + (int64_t)c0 * S + lane * E);
-      Vec<T, E> b1 = ld_default<T, E>(B1 + (int64_t)c1 * S + lane * E);
-      Vec<T, E> b2 = ld_default<T, E>(B1 + (int64_t)c2 * S + lane * E);
-      Vec<T, E> b3 = ld_default<T, E>(B1 + (int64_t)c3 * S + lane * E);
+      Vec<T, E> b0 = ldb(B1 + (int64_t)c0 * S + lane * E);
+      Vec<T, E> b1 = ldb(B1 + (int64_t)c1 * S + lane * E);
+      Vec<T, E> b2 = ldb(B1 + (int64_t)c2 * S + lane * E);
+      Vec<T, E> b3 = ldb(B1 + (int64_t)c3 * S + lane * E);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         acc[e] = fma(h0, b0.x[e], acc[e]);
@@ -128,17 +161,19 @@ __global__ void __launch_bounds__(256) clenshaw_step_kernel(int64_t D, const int
     for (; j < end; ++j) {
       int c0 = __ldg(col + j);
       T h0 = __ldg(val + j);
-      Vec<T, E> b0 = ld_default<T, E>(B1 + (int64_t)c0 * S + lane * E);
+      Vec<T, E> b0 = ldb(B1 + (int64_t)c0 * S + lane * E);
 #pragma unroll
       for (int e = 0; e < E; ++e) acc[e] = fma(h0, b0.x[e], acc[e]);
     }
   }
   Vec<T, E> v = ld_default<T, E>(V + off);
   Vec<T, E> r;
-  if constexpr (HAS_B2) {
-    Vec<T, E> q = ld_plain<T, E>(B2 + off);
+  if (hb2) {
+    Vec<T, E> q;
+    if constexpr (L2ONLY) q = ld_l2<T, E>(B2 + off);
+    else q = ld_plain<T, E>(B2 + off);
 #pragma unroll
-    for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], a * v.x[e] - beta * q.x[e]);
+    for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], fma(a, v.x[e], -(beta * q.x[e])));
   } else {
 #pragma unroll
     for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], a * v.x[e]);
@@ -146,22 +181,72 @@ __global__ void __launch_bounds__(256) clenshaw_step_kernel(int64_t D, const int
   st_default<T, E>(out + off, r);
 }
 
+// One Clenshaw step over a D x s block.  rows_per_cta = 0: thread group g owns row g (one
+// row per G lanes).  rows_per_cta = R > 0: CTA b owns the contiguous rows [bR, (b+1)R) and
+// walks them in chunks of 256/G rows; the grid is one wave (SMs x resident CTAs), so each
+// SM's L1 serves the neighbour rows that fall inside its CTAs' ranges (for the XXZ chain in
+// rank order about half of all neighbours lie within +-200 rows).
+template <typename T, int S, int SP, int B2M>
+__global__ void __launch_bounds__(256, 6) clenshaw_step_kernel(int64_t D, const int64_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ col,
+                                                            const T* __restrict__ val, const T* __restrict__ V,
+                                                            const T* __restrict__ B1, const T* B2, T* out, T a,
+                                                            T alpha, T beta, int64_t rows_per_cta) {
+  using Sh = Shape<T, S>;
+  constexpr int G = Sh::G;
+  const int lane = (int)(threadIdx.x % G);
+  if (rows_per_cta > 0) {
+    const int64_t r0 = blockIdx.x * rows_per_cta;
+    const int64_t r1 = r0 + rows_per_cta < D ? r0 + rows_per_cta : D;
+    for (int64_t row = r0 + threadIdx.x / G; row < r1; row += 256 / G)
+      clenshaw_row<T, S, false, SP, B2M>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta);
+  } else {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    if (row < D) clenshaw_row<T, S, false, SP, B2M>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta);
+  }
+}
+
+// Launch shape of a step over `rows` rows: FP32 steps use one wave of contiguous row ranges
+// (the FP32 step is bound by its neighbour gathers, which the ranges keep in L1); FP64 steps
+// are bound by the FP64 pipe and keep one row per thread group.
+struct StepShape {
+  unsigned grid;
+  int64_t rows_per_cta;
+};
+template <typename T, int S, int SP, int B2M>
+static StepShape step_shape(int64_t rows) {
+  using Sh = Shape<T, S>;
+  if constexpr (sizeof(T) == 4) {
+    static int waves = [] {
+      int dev = 0, nsm = 148, occ = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, clenshaw_step_kernel<T, S, SP, B2M>, 256, 0);
+      return nsm * (occ > 0 ? occ : 1);
+    }();
+    const int64_t R = ceil_div(rows, waves);
+    if (R > 256 / Sh::G) return StepShape{(unsigned)ceil_div(rows, R), R};
+  }
+  return StepShape{(unsigned)ceil_div(rows * Sh::G, 256), 0};
+}
+
+template <typename T, int S, int SP, int B2M>
+static void launch_step_form(int64_t D, const int64_t* rp, const int32_t* col, const T* val, const T* V, const T* B1,
+                             const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st) {
+  const StepShape sh = step_shape<T, S, SP, B2M>(D);
+  clenshaw_step_kernel<T, S, SP, B2M><<<sh.grid, 256, 0, st>>>(D, rp, col, val, V, B1, B2, out, a, alpha, beta,
+                                                              sh.rows_per_cta);
+}
+
 template <typename T, int S>
 static pf_status launch_step_s(int64_t D, const int64_t* rp, const int32_t* col, const T* val, const T* V, const T* B1,
                                const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st) {
-  using Sh = Shape<T, S>;
-  const int64_t threads = D * Sh::G;
-  const unsigned grid = (unsigned)ceil_div(threads, 256);
   const bool spmm = alpha != T(0);
   const bool hb2 = beta != T(0);
-  if (spmm && hb2)
-    clenshaw_step_kernel<T, S, true, true><<<grid, 256, 0, st>>>(D, rp, col, val, V, B1, B2, out, a, alpha, beta);
-  else if (spmm)
-    clenshaw_step_kernel<T, S, true, false><<<grid, 256, 0, st>>>(D, rp, col, val, V, B1, B2, out, a, alpha, beta);
-  else if (hb2)
-    clenshaw_step_kernel<T, S, false, true><<<grid, 256, 0, st>>>(D, rp, col, val, V, B1, B2, out, a, alpha, beta);
-  else
-    clenshaw_step_kernel<T, S, false, false><<<grid, 256, 0, st>>>(D, rp, col, val, V, B1, B2, out, a, alpha, beta);
+  if (spmm && hb2) launch_step_form<T, S, 1, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
+  else if (spmm) launch_step_form<T, S, 1, 0>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
+  else if (hb2) launch_step_form<T, S, 0, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
+  else launch_step_form<T, S, 0, 0>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
   PF_LAUNCH_CHECK("clenshaw_step_kernel");
   return PF_OK;
 }
@@ -239,108 +324,268 @@ struct BatchItemDev {
   int K, t0;
 };
 
-template <typename T, int S>
-__global__ void __launch_bounds__(256) clenshaw_batch_kernel(const BatchItemDev* __restrict__ items, int n, int t,
-                                                             int64_t total_rows) {
-  using Sh = Shape<T, S>;
-  constexpr int E = Sh::E, G = Sh::G;
-  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t grow = gtid / G;
-  const int lane = (int)(gtid % G);
-  if (grow >= total_rows) return;
+// Operands of recurrence index i of one item, as in filter_apply_raw: b_i lives in aux[i & 1].
+template <typename T>
+__device__ __forceinline__ void step_operands(const BatchItemDev& it, int i, const T*& B1, const T*& B2, T*& out,
+                                              T& alpha, T& beta) {
+  T* const a0 = (T*)it.aux0;
+  T* const a1 = (T*)it.aux1;
+  T* const cur = (i & 1) ? a1 : a0;    // aux[i & 1]
+  T* const nxt = (i & 1) ? a0 : a1;    // aux[(i + 1) & 1]
+  const int K = it.K;
+  if (i == K) {
+    alpha = T(0); beta = T(0); B1 = nullptr; B2 = nullptr; out = cur;
+  } else if (i >= 1) {
+    alpha = T(2); beta = (i == K - 1) ? T(0) : T(1);
+    B1 = nxt; B2 = cur; out = cur;
+  } else {
+    alpha = T(1); beta = (K >= 2) ? T(1) : T(0);
+    B1 = a1; B2 = a0; out = (T*)it.W;
+  }
+}
+
+__device__ __forceinline__ int find_item(const BatchItemDev* __restrict__ items, int n, int64_t grow) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (items[mid].row0 <= grow) lo = mid;
     else hi = mid - 1;
   }
-  const BatchItemDev& it = items[lo];
-  if (t < it.t0) return;
-  const int K = it.K;
-  const int i = K - (t - it.t0);
-  const int64_t row = grow - it.row0;
-  T* aux[2] = {(T*)it.aux0, (T*)it.aux1};
-  const T* B1 = nullptr;
-  const T* B2 = nullptr;
-  T* out;
-  T alpha, beta;
-  if (i == K) {
-    alpha = T(0); beta = T(0); out = aux[i & 1];
-  } else if (i >= 1) {
-    alpha = T(2); beta = (i == K - 1) ? T(0) : T(1);
-    B1 = aux[(i + 1) & 1]; B2 = aux[i & 1]; out = aux[i & 1];
+  return lo;
+}
+
+// Sweep step t over all items' rows (items may differ in K).  UNI = 1: every item has the
+// same K (all t0 = 0), so the step's form (SP, B2M) is the same for all and fixed at compile
+// time, as in clenshaw_step_kernel.  rows_per_cta as in clenshaw_step_kernel.
+template <typename T, int S, int SP, int B2M>
+__global__ void __launch_bounds__(256, 4) clenshaw_batch_kernel(const BatchItemDev* __restrict__ items, int n, int t,
+                                                             int64_t total_rows, int64_t rows_per_cta) {
+  using Sh = Shape<T, S>;
+  constexpr int G = Sh::G;
+  const int lane = (int)(threadIdx.x % G);
+  int64_t r0, r1, stride;
+  if (rows_per_cta > 0) {
+    r0 = blockIdx.x * rows_per_cta + threadIdx.x / G;
+    r1 = (blockIdx.x + 1) * rows_per_cta < total_rows ? (blockIdx.x + 1) * rows_per_cta : total_rows;
+    stride = 256 / G;
   } else {
-    alpha = T(1); beta = (K >= 2) ? T(1) : T(0);
-    B1 = aux[1]; B2 = aux[0]; out = (T*)it.W;
+    r0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    r1 = r0 + 1 < total_rows ? r0 + 1 : total_rows;
+    stride = 1;
   }
-  const T a = (T)it.coeffs[i];
-  const T* __restrict__ V = (const T*)it.V;
+  for (int64_t grow = r0; grow < r1; grow += stride) {
+    const BatchItemDev& it = items[find_item(items, n, grow)];
+    if (t < it.t0) continue;
+    const int i = it.K - (t - it.t0);
+    const T* B1;
+    const T* B2;
+    T* out;
+    T alpha, beta;
+    step_operands<T>(it, i, B1, B2, out, alpha, beta);
+    clenshaw_row<T, S, false, SP, B2M>(grow - it.row0, lane, it.rp, it.col, (const T*)it.val, (const T*)it.V, B1,
+                                       B2, out, (T)__ldg(it.coeffs + i), alpha, beta);
+  }
+}
+
+// Persistent form for small items: one thread-block cluster per item (csize CTAs, its rows
+// split evenly) runs the item's whole recurrence, K+1 steps, in one launch.  Between steps
+// the cluster meets at the hardware cluster barrier (arrive.release / wait.acquire), which
+// orders the step's global stores before the next step's loads; b blocks are read with
+// L2-only loads so no SM reuses a line it cached before the rewrite.  With csize = 1 the
+// barrier is __syncthreads().  No spin-waits: both barriers are hardware barriers.
+#define PF_PERSIST_NT 512
+template <typename T, int S, bool CLUSTER>
+__global__ void __launch_bounds__(PF_PERSIST_NT) clenshaw_persistent_kernel(const BatchItemDev* __restrict__ items,
+                                                                           int n) {
+  using Sh = Shape<T, S>;
+  constexpr int G = Sh::G, ROWS = PF_PERSIST_NT / G;
+  unsigned csize = 1, crank = 0, cid = blockIdx.x;
+  if constexpr (CLUSTER) {
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(csize));
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(crank));
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(cid));
+  }
+  if ((int)cid >= n) return;   // uniform over the cluster
+  const BatchItemDev& it = items[cid];
+  const int64_t per = (it.D + csize - 1) / csize;
+  const int64_t r0 = crank * per;
+  const int64_t r1 = r0 + per < it.D ? r0 + per : it.D;
+  const int lane = threadIdx.x % G;
   const T* __restrict__ val = (const T*)it.val;
-  const int32_t* __restrict__ col = it.col;
-  const int64_t off = row * S + lane * E;
-  T acc[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) acc[e] = T(0);
-  if (alpha != T(0)) {
-    int64_t j = it.rp[row];
-    const int64_t end = it.rp[row + 1];
-    for (; j + 4 <= end; j += 4) {
-      int c0 = __ldg(col + j), c1 = __ldg(col + j + 1), c2 = __ldg(col + j + 2), c3 = __ldg(col + j + 3);
-      T h0 = __ldg(val + j), h1 = __ldg(val + j + 1), h2 = __ldg(val + j + 2), h3 = __ldg(val + j + 3);
-      Vec<T, E> b0 = ld_default<T, E>(B1 + (int64_t)c0 * S + lane * E);
-      Vec<T, E> b1 = ld_default<T, E>(B1 + (int64_t)c1 * S + lane * E);
-      Vec<T, E> b2 = ld_default<T, E>(B1 + (int64_t)c2 * S + lane * E);
-      Vec<T, E> b3 = ld_default<T, E>(B1 + (int64_t)c3 * S + lane * E);
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        acc[e] = fma(h0, b0.x[e], acc[e]);
-        acc[e] = fma(h1, b1.x[e], acc[e]);
-        acc[e] = fma(h2, b2.x[e], acc[e]);
-        acc[e] = fma(h3, b3.x[e], acc[e]);
-      }
-    }
-    for (; j < end; ++j) {
-      int c0 = __ldg(col + j);
-      T h0 = __ldg(val + j);
-      Vec<T, E> b0 = ld_default<T, E>(B1 + (int64_t)c0 * S + lane * E);
-#pragma unroll
-      for (int e = 0; e < E; ++e) acc[e] = fma(h0, b0.x[e], acc[e]);
+  const T* __restrict__ V = (const T*)it.V;
+  for (int i = it.K; i >= 0; --i) {
+    const T* B1;
+    const T* B2;
+    T* out;
+    T alpha, beta;
+    step_operands<T>(it, i, B1, B2, out, alpha, beta);
+    const T a = (T)__ldg(it.coeffs + i);
+    for (int64_t row = r0 + threadIdx.x / G; row < r1; row += ROWS)
+      clenshaw_row<T, S, true, -1, -1>(row, lane, it.rp, it.col, val, V, B1, B2, out, a, alpha, beta);
+    if constexpr (CLUSTER) {
+      asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    } else {
+      __syncthreads();
     }
   }
-  Vec<T, E> v = ld_default<T, E>(V + off);
-  Vec<T, E> r;
-  if (beta != T(0)) {
-    Vec<T, E> q = ld_plain<T, E>(B2 + off);
-#pragma unroll
-    for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], a * v.x[e] - beta * q.x[e]);
-  } else {
-#pragma unroll
-    for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], a * v.x[e]);
-  }
-  st_default<T, E>(out + off, r);
 }
 
 template <typename T, int S>
-static pf_status launch_batch_s(const BatchItemDev* items, int n, int T_steps, int64_t total_rows, cudaStream_t st) {
-  using Sh = Shape<T, S>;
-  const unsigned grid = (unsigned)ceil_div(total_rows * Sh::G, 256);
+static pf_status launch_persistent_s(const BatchItemDev* items, int n, int csize, cudaStream_t st) {
+  if (csize <= 1) {
+    clenshaw_persistent_kernel<T, S, false><<<n, PF_PERSIST_NT, 0, st>>>(items, n);
+    PF_LAUNCH_CHECK("clenshaw_persistent_kernel");
+    return PF_OK;
+  }
+  auto kern = clenshaw_persistent_kernel<T, S, true>;
+  if (csize > 8) PF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n * csize), 1, 1);
+  cfg.blockDim = dim3(PF_PERSIST_NT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  PF_COUNT(1);
+  PF_CUDA(cudaLaunchKernelEx(&cfg, kern, items, n));
+  return PF_OK;
+}
+
+// Step t of a sweep: its kernel entry and launch shape.  uniform: all items share K, so the
+// step's (SP, B2M) is known: t = 0 is b_K (no SpMM, no B2), t = 1 has no B2 (b_{K+1} = 0),
+// the last step (i = 0) has B2 when K >= 2; the generic form decides per item at run time.
+template <typename T, int S>
+static void* sweep_fn(bool uniform, int t, int K) {
+  if (!uniform) return (void*)clenshaw_batch_kernel<T, S, -1, -1>;
+  const int i = K - t;
+  if (i == K) return (void*)clenshaw_batch_kernel<T, S, 0, 0>;
+  if (i == K - 1 || (i == 0 && K < 2)) return (void*)clenshaw_batch_kernel<T, S, 1, 0>;
+  return (void*)clenshaw_batch_kernel<T, S, 1, 1>;
+}
+
+template <typename T, int S>
+static StepShape sweep_shape(int64_t rows) { return step_shape<T, S, 1, 1>(rows); }
+
+template <typename T, int S>
+static pf_status launch_batch_s(const BatchItemDev* items, int n, int T_steps, int64_t total_rows, bool uniform,
+                                cudaStream_t st) {
+  const StepShape sh = sweep_shape<T, S>(total_rows);
   for (int t = 0; t < T_steps; ++t) {
-    clenshaw_batch_kernel<T, S><<<grid, 256, 0, st>>>(items, n, t, total_rows);
-    PF_LAUNCH_CHECK("clenshaw_batch_kernel");
+    void* fn = sweep_fn<T, S>(uniform, t, T_steps - 1);
+    int nn = n, tt = t;
+    int64_t rr = total_rows, rpc = sh.rows_per_cta;
+    void* args[] = {(void*)&items, (void*)&nn, (void*)&tt, (void*)&rr, (void*)&rpc};
+    PF_CUDA(cudaLaunchKernel(fn, dim3(sh.grid), dim3(256), args, 0, st));
+    PF_COUNT(1);
   }
   return PF_OK;
 }
 
+template <typename T>
+static void* sweep_fn_s(int s, bool uniform, int t, int K) {
+  switch (s) {
+    case 1: return sweep_fn<T, 1>(uniform, t, K);
+    case 2: return sweep_fn<T, 2>(uniform, t, K);
+    case 4: return sweep_fn<T, 4>(uniform, t, K);
+    case 8: return sweep_fn<T, 8>(uniform, t, K);
+    case 16: return sweep_fn<T, 16>(uniform, t, K);
+    case 32: return sweep_fn<T, 32>(uniform, t, K);
+    case 64: return sweep_fn<T, 64>(uniform, t, K);
+  }
+  return nullptr;
+}
+
+template <typename T>
+static StepShape sweep_shape_s(int s, int64_t rows) {
+  switch (s) {
+    case 1: return sweep_shape<T, 1>(rows);
+    case 2: return sweep_shape<T, 2>(rows);
+    case 4: return sweep_shape<T, 4>(rows);
+    case 8: return sweep_shape<T, 8>(rows);
+    case 16: return sweep_shape<T, 16>(rows);
+    case 32: return sweep_shape<T, 32>(rows);
+    case 64: return sweep_shape<T, 64>(rows);
+  }
+  return StepShape{0, 0};
+}
+
+static int lanes_per_row(int prec, int s) {
+  const int w = prec == PF_F64 ? 8 : 4;
+  const int E = s * w >= 16 ? 16 / w : s;
+  return s / E;
+}
+
+SweepGraph::~SweepGraph() { reset(); }
+void SweepGraph::reset() {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  exec = nullptr;
+  graph = nullptr;
+  T = 0;
+}
+
+// The T launches of one sweep as a chain of kernel nodes.  The nodes read the item table from
+// device memory at run time, so one instantiated graph serves every sweep with the same
+// table address, item count, step count, row total and uniformity; only the table contents
+// change between launches.
+static pf_status sweep_graph_launch(SweepGraph& g, int prec, int s, const void* table, int n, int T, int64_t rows,
+                                    bool uniform, cudaStream_t st) {
+  if (!(g.exec && g.prec == prec && g.s == s && g.table == table && g.n == n && g.T == T && g.rows == rows &&
+        g.uniform == uniform)) {
+    g.reset();
+    PF_CUDA(cudaGraphCreate(&g.graph, 0));
+    const StepShape sh = prec == PF_F64 ? sweep_shape_s<double>(s, rows) : sweep_shape_s<float>(s, rows);
+    cudaGraphNode_t prev = nullptr;
+    for (int t = 0; t < T; ++t) {
+      void* fn = prec == PF_F64 ? sweep_fn_s<double>(s, uniform, t, T - 1) : sweep_fn_s<float>(s, uniform, t, T - 1);
+      if (!fn || sh.grid == 0) return PF_EINVAL;
+      const BatchItemDev* items = static_cast<const BatchItemDev*>(table);
+      int nn = n, tt = t;
+      int64_t rr = rows, rpc = sh.rows_per_cta;
+      void* args[] = {(void*)&items, (void*)&nn, (void*)&tt, (void*)&rr, (void*)&rpc};
+      cudaKernelNodeParams kp = {};
+      kp.func = fn;
+      kp.gridDim = dim3(sh.grid, 1, 1);
+      kp.blockDim = dim3(256, 1, 1);
+      kp.sharedMemBytes = 0;
+      kp.kernelParams = args;
+      kp.extra = nullptr;
+      cudaGraphNode_t node;
+      PF_CUDA(cudaGraphAddKernelNode(&node, g.graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+      prev = node;
+    }
+    PF_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+    g.prec = prec;
+    g.s = s;
+    g.table = table;
+    g.n = n;
+    g.T = T;
+    g.rows = rows;
+    g.uniform = uniform;
+  }
+  PF_COUNT(T);
+  PF_CUDA(cudaGraphLaunch(g.exec, st));
+  return PF_OK;
+}
+
 pf_status filter_sweep(const std::vector<FilterItem>& items, void* table_dev, size_t table_bytes, void* table_host,
-                       cudaStream_t st) {
+                       cudaStream_t st, int csize, SweepGraph* graph) {
   const int n = (int)items.size();
   if (n == 0) return PF_OK;
   if ((size_t)n * sizeof(BatchItemDev) > table_bytes) return PF_EINVAL;
   const int prec = items[0].prec, s = items[0].s;
+  if (!valid_s(s) || (prec != PF_F64 && prec != PF_F32) || csize < 0 || csize > 16) return PF_EINVAL;
   int T = 0;
+  bool uniform = true;
   for (const auto& it : items) {
-    if (it.prec != prec || it.s != s || it.K < 1) return PF_EINVAL;
+    if (it.prec != prec || it.s != s || it.K < 1 || !it.coeffs_dev) return PF_EINVAL;
     T = std::max(T, it.K + 1);
+    uniform = uniform && it.K == items[0].K;
   }
   BatchItemDev* tab = static_cast<BatchItemDev*>(table_host);
   int64_t row0 = 0;
@@ -363,28 +608,152 @@ pf_status filter_sweep(const std::vector<FilterItem>& items, void* table_dev, si
   }
   PF_CUDA(cudaMemcpyAsync(table_dev, tab, n * sizeof(BatchItemDev), cudaMemcpyHostToDevice, st));
   const BatchItemDev* d = static_cast<const BatchItemDev*>(table_dev);
+  if (csize >= 1) {
+#define PF_PERSIST_CASE(TT, SS) \
+  case SS: return launch_persistent_s<TT, SS>(d, n, csize, st);
+    if (prec == PF_F64) {
+      switch (s) { PF_PERSIST_CASE(double, 1) PF_PERSIST_CASE(double, 2) PF_PERSIST_CASE(double, 4)
+                   PF_PERSIST_CASE(double, 8) PF_PERSIST_CASE(double, 16) PF_PERSIST_CASE(double, 32)
+                   PF_PERSIST_CASE(double, 64) }
+    } else {
+      switch (s) { PF_PERSIST_CASE(float, 1) PF_PERSIST_CASE(float, 2) PF_PERSIST_CASE(float, 4)
+                   PF_PERSIST_CASE(float, 8) PF_PERSIST_CASE(float, 16) PF_PERSIST_CASE(float, 32)
+                   PF_PERSIST_CASE(float, 64) }
+    }
+#undef PF_PERSIST_CASE
+    return PF_EINVAL;
+  }
+  if (graph) return sweep_graph_launch(*graph, prec, s, table_dev, n, T, row0, uniform, st);
   if (prec == PF_F64) {
     switch (s) {
-      case 1: return launch_batch_s<double, 1>(d, n, T, row0, st);
-      case 2: return launch_batch_s<double, 2>(d, n, T, row0, st);
-      case 4: return launch_batch_s<double, 4>(d, n, T, row0, st);
-      case 8: return launch_batch_s<double, 8>(d, n, T, row0, st);
-      case 16: return launch_batch_s<double, 16>(d, n, T, row0, st);
-      case 32: return launch_batch_s<double, 32>(d, n, T, row0, st);
-      case 64: return launch_batch_s<double, 64>(d, n, T, row0, st);
+      case 1: return launch_batch_s<double, 1>(d, n, T, row0, uniform, st);
+      case 2: return launch_batch_s<double, 2>(d, n, T, row0, uniform, st);
+      case 4: return launch_batch_s<double, 4>(d, n, T, row0, uniform, st);
+      case 8: return launch_batch_s<double, 8>(d, n, T, row0, uniform, st);
+      case 16: return launch_batch_s<double, 16>(d, n, T, row0, uniform, st);
+      case 32: return launch_batch_s<double, 32>(d, n, T, row0, uniform, st);
+      case 64: return launch_batch_s<double, 64>(d, n, T, row0, uniform, st);
     }
   } else {
     switch (s) {
-      case 1: return launch_batch_s<float, 1>(d, n, T, row0, st);
-      case 2: return launch_batch_s<float, 2>(d, n, T, row0, st);
-      case 4: return launch_batch_s<float, 4>(d, n, T, row0, st);
-      case 8: return launch_batch_s<float, 8>(d, n, T, row0, st);
-      case 16: return launch_batch_s<float, 16>(d, n, T, row0, st);
-      case 32: return launch_batch_s<float, 32>(d, n, T, row0, st);
-      case 64: return launch_batch_s<float, 64>(d, n, T, row0, st);
+      case 1: return launch_batch_s<float, 1>(d, n, T, row0, uniform, st);
+      case 2: return launch_batch_s<float, 2>(d, n, T, row0, uniform, st);
+      case 4: return launch_batch_s<float, 4>(d, n, T, row0, uniform, st);
+      case 8: return launch_batch_s<float, 8>(d, n, T, row0, uniform, st);
+      case 16: return launch_batch_s<float, 16>(d, n, T, row0, uniform, st);
+      case 32: return launch_batch_s<float, 32>(d, n, T, row0, uniform, st);
+      case 64: return launch_batch_s<float, 64>(d, n, T, row0, uniform, st);
     }
   }
   return PF_EINVAL;
+}
+
+// ------------------------------------------------------------------ autotuner
+// How an item of a given shape runs inside a multi-item group: 0 = the per-step sweep over
+// all items' rows, c >= 1 = the persistent kernel with clusters of c CTAs.  Measured once per
+// (device, D, nnz, precision, s) on the device: the candidates run min(K, 48) + 1 steps of
+// the item on scratch blocks (so the caller's data is untouched), and the choice minimises
+// SM-time per item step, the cost that matters when many items share the GPU:
+//   persistent c: c SMs x its step time;
+//   sweep: all SMs x its step time over r copies of the item (r fills the GPU) / r.
+// Items with more than 64 rows per thread of a 16-CTA cluster always take the sweep.
+namespace {
+struct TuneKey {
+  int dev, prec, s;
+  int64_t D, nnz;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, prec, s, D, nnz) < std::tie(o.dev, o.prec, o.s, o.D, o.nnz);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneResult> g_tune;
+}  // namespace
+
+static pf_status time_ms(cudaStream_t st, const std::function<pf_status()>& f, int reps, double* ms) {
+  cudaEvent_t a, b;
+  PF_CUDA(cudaEventCreate(&a));
+  PF_CUDA(cudaEventCreate(&b));
+  pf_status rc = f();   // warm-up
+  if (rc == PF_OK) {
+    cudaEventRecord(a, st);
+    for (int r = 0; r < reps && rc == PF_OK; ++r) rc = f();
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float t = 0;
+    cudaEventElapsedTime(&t, a, b);
+    *ms = t / reps;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
+}
+
+pf_status tune_item(const FilterItem& it, cudaStream_t st, TuneResult* out) {
+  int dev = 0;
+  PF_CUDA(cudaGetDevice(&dev));
+  const TuneKey key{dev, it.prec, it.s, it.H->D, it.H->nnz};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto f = g_tune.find(key);
+    if (f != g_tune.end()) {
+      *out = f->second;
+      return PF_OK;
+    }
+  }
+  TuneResult res;
+  const int G = lanes_per_row(it.prec, it.s);
+  const int64_t D = it.H->D;
+  int nsm = 148;
+  PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const bool small = D * G <= (int64_t)16 * PF_PERSIST_NT * 64;
+  if (small) {
+    const size_t w = it.prec == PF_F64 ? 8 : 4;
+    const size_t blk = (((size_t)D * it.s * w) + 255) & ~(size_t)255;
+    const int Kt = std::min(it.K, 48);
+    // r copies fill the GPU in the sweep (about 8 resident 256-thread CTAs per SM)
+    const int r = (int)std::max<int64_t>(1, std::min<int64_t>(64, ceil_div((int64_t)nsm * 8 * 256, D * G)));
+    DevBuf scratch, table;
+    PF_TRY(scratch.alloc(blk * 3 * r, st));
+    PF_TRY(table.alloc(filter_sweep_table_bytes(r), st));
+    std::vector<FilterItem> one(1, it), many(r, it);
+    for (int j = 0; j < r; ++j) {
+      unsigned char* b = scratch.as<unsigned char>() + blk * 3 * j;
+      many[j].aux0 = b;
+      many[j].aux1 = b + blk;
+      many[j].W = b + 2 * blk;
+      many[j].K = Kt;
+    }
+    one[0] = many[0];
+    std::vector<unsigned char> th(filter_sweep_table_bytes(r));
+    double ms = 0;
+    PF_TRY(time_ms(st, [&] { return filter_sweep(many, table.p, table.bytes, th.data(), st, 0, nullptr); }, 3, &ms));
+    res.sweep_sm_us = 1e3 * ms * nsm / r / (Kt + 1);
+    double best = res.sweep_sm_us;
+    res.csize = 0;
+    const int cs[5] = {1, 2, 4, 8, 16};
+    for (int k = 0; k < 5; ++k) {
+      const int c = cs[k];
+      if (c > 1 && D < (int64_t)c * (PF_PERSIST_NT / G)) break;   // fewer rows than one pass of c CTAs
+      pf_status rc = time_ms(st, [&] { return filter_sweep(one, table.p, table.bytes, th.data(), st, c, nullptr); },
+                             3, &ms);
+      if (rc != PF_OK) {   // a cluster shape the device refuses: clear the error and stop growing
+        cudaGetLastError();
+        break;
+      }
+      res.persist_sm_us[k] = 1e3 * ms * c / (Kt + 1);
+      if (res.persist_sm_us[k] < best) {
+        best = res.persist_sm_us[k];
+        res.csize = c;
+      }
+    }
+    PF_CUDA(cudaStreamSynchronize(st));
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = res;
+  }
+  *out = res;
+  return PF_OK;
 }
 
 size_t filter_sweep_table_bytes(int n) { return (size_t)n * sizeof(BatchItemDev); }
@@ -426,11 +795,14 @@ pf_status pf_filter_apply(const pf_ham* hh, int32_t prec, int32_t s, const void*
   return filter_apply_raw(H, prec, s, V, W, coeffs, nullptr, K, a0.p, a1.p, st);
 }
 
-pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t prec, int32_t s,
+pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t prec, int32_t s, int32_t form,
                                 pf_stream_t stream) {
   if (n < 0 || (n > 0 && !items)) return PF_EINVAL;
   if (prec != PF_F64 && prec != PF_F32) return PF_EINVAL;
   if (!valid_s(s)) return PF_EINVAL;
+  if (!(form == PF_FORM_AUTO || form == PF_FORM_STEPS || form == PF_FORM_GRAPH || form == 1 || form == 2 ||
+        form == 4 || form == 8 || form == 16))
+    return PF_EINVAL;
   if (n == 0) return PF_OK;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t w = prec == PF_F64 ? 8 : 4;
@@ -469,7 +841,65 @@ pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t 
     it.aux1 = base + aoff[j] + (((size_t)H->D * s * w + 255) & ~(size_t)255);
   }
   std::vector<unsigned char> th(filter_sweep_table_bytes(n));
-  return filter_sweep(v, table.p, table.bytes, th.data(), st);
+  if (form == PF_FORM_STEPS) return filter_sweep(v, table.p, table.bytes, th.data(), st, 0, nullptr);
+  if (form == PF_FORM_GRAPH) {
+    SweepGraph g;
+    PF_TRY(filter_sweep(v, table.p, table.bytes, th.data(), st, 0, &g));
+    PF_CUDA(cudaStreamSynchronize(st));   // the graph is released on return
+    return PF_OK;
+  }
+  if (form >= 1) return filter_sweep(v, table.p, table.bytes, th.data(), st, form, nullptr);
+  // PF_FORM_AUTO: each item's form from the autotuner, one launch (or sweep) per form
+  std::vector<std::pair<int, std::vector<FilterItem>>> parts;
+  for (const FilterItem& it : v) {
+    TuneResult tr;
+    PF_TRY(tune_item(it, st, &tr));
+    auto p = std::find_if(parts.begin(), parts.end(), [&](const auto& x) { return x.first == tr.csize; });
+    if (p == parts.end()) {
+      parts.push_back({tr.csize, {}});
+      p = parts.end() - 1;
+    }
+    p->second.push_back(it);
+  }
+  for (auto& p : parts) {
+    std::vector<unsigned char> tp(filter_sweep_table_bytes((int)p.second.size()));
+    DevBuf tb;
+    PF_TRY(tb.alloc(tp.size(), st));
+    PF_TRY(filter_sweep(p.second, tb.p, tb.bytes, tp.data(), st, p.first, nullptr));
+  }
+  return PF_OK;
+}
+
+pf_status pf_filter_tune(const pf_ham* hh, int32_t prec, int32_t s, int32_t K, int32_t* form, double* sm_us,
+                         pf_stream_t stream) {
+  const Ham* H = reinterpret_cast<const Ham*>(hh);
+  if (!H || !form || K < 1) return PF_EINVAL;
+  if (!H->has_rescale) return PF_ESTATE;
+  if (prec != PF_F64 && prec != PF_F32) return PF_EINVAL;
+  if (!valid_s(s)) return PF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t w = prec == PF_F64 ? 8 : 4;
+  // a zero start block and zero coefficients: the timing does not depend on the values
+  DevBuf V, coeffs;
+  PF_TRY(V.alloc((size_t)H->D * s * w, st));
+  PF_CUDA(cudaMemsetAsync(V.p, 0, V.bytes, st));
+  PF_TRY(coeffs.alloc((size_t)(K + 1) * 8, st));
+  PF_CUDA(cudaMemsetAsync(coeffs.p, 0, coeffs.bytes, st));
+  FilterItem it;
+  it.H = H;
+  it.prec = prec;
+  it.s = s;
+  it.V = V.p;
+  it.coeffs_dev = coeffs.as<double>();
+  it.K = K;
+  TuneResult tr;
+  PF_TRY(tune_item(it, st, &tr));
+  *form = tr.csize;
+  if (sm_us) {
+    sm_us[0] = tr.sweep_sm_us;
+    for (int k = 0; k < 5; ++k) sm_us[1 + k] = tr.persist_sm_us[k];
+  }
+  return PF_OK;
 }
 
 }  // extern "C"

@@ -142,12 +142,37 @@ struct FilterItem {
   int K = 0;
   void* aux0 = nullptr;
   void* aux1 = nullptr;
+  const void* owner = nullptr;          // the solve the item belongs to (grouping only)
 };
-// All items advance together, one launch per Clenshaw step over the concatenated rows.
-// Items share prec and s.  table_host/table_dev: room for filter_sweep_table_bytes(n).
+// A per-step sweep captured as a CUDA graph (chain of T kernel nodes), reused while the table
+// address, item count, step count and row total stay the same.
+struct SweepGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int prec = -1, s = 0, n = 0, T = 0;
+  int64_t rows = 0;
+  bool uniform = false;
+  const void* table = nullptr;
+  SweepGraph() = default;
+  SweepGraph(const SweepGraph&) = delete;
+  SweepGraph& operator=(const SweepGraph&) = delete;
+  ~SweepGraph();
+  void reset();
+};
+// All items (same prec and s) advance together.  csize = 0: one launch per Clenshaw step over
+// the concatenated rows (through `graph` when given); csize >= 1: one persistent launch, one
+// cluster of csize CTAs per item.  table_host/table_dev: room for filter_sweep_table_bytes(n).
 pf_status filter_sweep(const std::vector<FilterItem>& items, void* table_dev, size_t table_bytes, void* table_host,
-                       cudaStream_t st);
+                       cudaStream_t st, int csize = 0, SweepGraph* graph = nullptr);
 size_t filter_sweep_table_bytes(int n);
+// Autotuner result for one item shape: csize 0 = sweep, >= 1 = persistent cluster size; the
+// measured SM-microseconds per item step of each candidate (0 = not measured).
+struct TuneResult {
+  int csize = 0;
+  double sweep_sm_us = 0;
+  double persist_sm_us[5] = {0, 0, 0, 0, 0};   // clusters of 1, 2, 4, 8, 16 CTAs
+};
+pf_status tune_item(const FilterItem& it, cudaStream_t st, TuneResult* out);
 // W = P V for a D x s block (K steps); aux buffers are two D x s blocks of the filter type.
 pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs_host,
                            const void* coeffs_dev, int K, void* aux0, void* aux1, cudaStream_t st);

@@ -613,6 +613,7 @@ struct Task {
     double* Vk = blockp(S, k);
     FilterItem it;
     it.H = H;
+    it.owner = this;
     it.s = s;
     it.coeffs_host = coeffs.data();
     it.coeffs_dev = coeff_dev.as<double>();
@@ -819,6 +820,7 @@ struct Task {
     for (int b = Lb; b < nb; ++b) {
       FilterItem it;
       it.H = H;
+      it.owner = this;
       it.prec = PF_F64;
       it.s = s;
       it.V = Ud + (int64_t)b * DS;
@@ -938,7 +940,22 @@ static size_t solve_state_bytes(int64_t D, int s, int nev, bool f32) {
 struct Executor {
   DevBuf table;
   std::vector<unsigned char> table_host;
+  SweepGraph graph;
   cudaStream_t st = 0;
+  int force_csize = -1;   // -1: the autotuner decides per item shape; >= 0: that form for every multi-item group
+
+  pf_status run_group(const std::vector<FilterItem>& items, int csize) {
+    if (items.empty()) return PF_OK;
+    if (items.size() == 1 && csize == 0) {
+      const FilterItem& it = items[0];
+      return filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, st);
+    }
+    const size_t need = filter_sweep_table_bytes((int)items.size());
+    if (table.bytes < need) PF_TRY(table.alloc(need * 2, st));
+    if (table_host.size() < need) table_host.resize(need * 2);
+    // table_host is pageable: the copy inside has consumed it when the call returns.
+    return filter_sweep(items, table.p, table.bytes, table_host.data(), st, csize, csize == 0 ? &graph : nullptr);
+  }
 
   pf_status run_round(std::vector<Task*>& tasks) {
     std::vector<std::pair<std::pair<int, int>, std::vector<FilterItem>>> groups;
@@ -956,15 +973,36 @@ struct Executor {
     }
     for (auto& g : groups) {
       const auto& items = g.second;
-      if (items.size() == 1) {
-        const FilterItem& it = items[0];
-        PF_TRY(filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, st));
-      } else {
-        const size_t need = filter_sweep_table_bytes((int)items.size());
-        if (table.bytes < need) PF_TRY(table.alloc(need * 2, st));
-        if (table_host.size() < need) table_host.resize(need * 2);
-        // table_host is pageable: the copy inside has consumed it when the call returns.
-        PF_TRY(filter_sweep(items, table.p, table.bytes, table_host.data(), st));
+      if (items.size() == 1) {   // one item: the plain K-step recurrence
+        PF_TRY(run_group(items, 0));
+        continue;
+      }
+      // split by execution form: per-step sweep (csize 0) or persistent clusters of csize CTAs
+      std::vector<std::pair<int, std::vector<FilterItem>>> parts;
+      for (const FilterItem& it : items) {
+        int c = force_csize;
+        if (c < 0) {
+          TuneResult tr;
+          PF_TRY(tune_item(it, st, &tr));
+          c = tr.csize;
+        }
+        auto p = std::find_if(parts.begin(), parts.end(), [&](const auto& x) { return x.first == c; });
+        if (p == parts.end()) {
+          parts.push_back({c, {}});
+          p = parts.end() - 1;
+        }
+        p->second.push_back(it);
+      }
+      for (auto& p : parts) {
+        bool one_owner = true;
+        for (const FilterItem& it : p.second) one_owner = one_owner && it.owner == p.second[0].owner;
+        if (p.first == 0 && one_owner) {
+          // the blocks of one solve (refinement): the plain recurrence per block keeps the
+          // step kernel's specialised form; sweeps pay off across solves
+          for (const FilterItem& it : p.second) PF_TRY(run_group(std::vector<FilterItem>(1, it), 0));
+        } else {
+          PF_TRY(run_group(p.second, p.first));
+        }
       }
     }
     for (Task* t : tasks) {

@@ -9,8 +9,8 @@ with G = 0x9E3779B97F4A7C15.
 """
 from .rng import splitmix64, uniform01, uniform_pm_half, normals
 from .workloads import (XXZParams, QSunParams, HubbardParams, xxz_params, qsun_params,
-                        hubbard_params, CONFIGS, config_seed)
+                        hubbard_params, CONFIGS, config_seed, serving_stream)
 
 __all__ = ["splitmix64", "uniform01", "uniform_pm_half", "normals", "XXZParams",
            "QSunParams", "HubbardParams", "xxz_params", "qsun_params", "hubbard_params",
-           "CONFIGS", "config_seed"]
+           "CONFIGS", "config_seed", "serving_stream"]

@@ -105,3 +105,25 @@ CONFIGS = {
     5: dict(name="serving_mix", model="xxz", L=(14, 16, 18, 20, 22), W=(0.5, 8.0),
             eps=(0.2, 0.8), nev=(20, 50, 200), requests=2000, precision="f32"),
 }
+
+
+def serving_stream(n, rate_per_s, Ls=(14, 16, 18, 20, 22), W_range=(0.5, 8.0), eps_range=(0.2, 0.8),
+                   nevs=(20, 50, 200), seed=5000):
+    """Request stream of the serving workload: n disordered XXZ solves with Poisson arrivals.
+
+    Request k draws five uniforms u = uniform01(seed, 5k + 0..4): L = Ls[floor(u0 len(Ls))],
+    W = W_lo + u1 (W_hi - W_lo), eps = eps_lo + u2 (eps_hi - eps_lo),
+    nev = nevs[floor(u3 len(nevs))], inter-arrival gap -ln(1 - u4) / rate_per_s.  Its
+    fields are those of xxz_params(L, W=W, seed=seed + 1 + k).  Returns a list of dicts
+    with keys params, eps, nev, t_arrival (seconds from the stream's start).
+    """
+    u = uniform01(seed, np.arange(5 * n)).reshape(n, 5)
+    out, t = [], 0.0
+    for k in range(n):
+        L = int(Ls[min(int(u[k, 0] * len(Ls)), len(Ls) - 1)])
+        W = W_range[0] + u[k, 1] * (W_range[1] - W_range[0])
+        eps = eps_range[0] + u[k, 2] * (eps_range[1] - eps_range[0])
+        nev = int(nevs[min(int(u[k, 3] * len(nevs)), len(nevs) - 1)])
+        t += -np.log1p(-u[k, 4]) / rate_per_s
+        out.append(dict(params=xxz_params(L, W=W, seed=seed + 1 + k), eps=float(eps), nev=nev, t_arrival=t))
+    return out

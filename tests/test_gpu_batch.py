@@ -129,3 +129,64 @@ def test_solve_batch_mixed_precision_and_bad_item(pf):
                               return_vectors=False)
         assert np.array_equal(r.evals, alone.evals)
         assert np.array_equal(r.resid, alone.resid)
+
+
+@pytest.mark.parametrize("form", ["steps", "graph", 1, 2, 4, 8, 16, "auto"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_filter_batch_forms_bitwise(pf, form, dtype):
+    """Every execution form (per-step launches, CUDA graph, persistent clusters of 1-16 CTAs,
+    autotuned) gives the bits of the one-problem filter."""
+    items, singles = [], []
+    for j, p in enumerate(_problems()):
+        H = pf.Hamiltonian.from_params(p)
+        H.spectral_bounds()
+        K = [40, 97, 13, 64, 1][j]
+        c = pf.filter_coefficients(0.1 * j - 0.2, K)
+        V = _start(H.D, 8, 200 + j, dtype)
+        items.append((H, V, c))
+        singles.append(H.filter_apply(V, c))
+    outs = pf.filter_apply_batch(items, form=form)
+    torch.cuda.synchronize()
+    for W, Ws in zip(outs, singles):
+        assert torch.equal(W, Ws)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_filter_L18_range_form_matches_oracle_and_batch(pf, dtype):
+    """At D = 48620 the FP32 step runs in the contiguous-range form; it must match the oracle
+    (FP64 bar, or the FP32 error bound) and the sweep forms bit for bit."""
+    p = pi.xxz_params(18, W=2.0, seed=1801)
+    H = pf.Hamiltonian.from_params(p)
+    H.spectral_bounds()
+    Ec, dE, _, _ = H.rescaled()
+    K = 40
+    c = pf.filter_coefficients(0.1, K)
+    V = _start(H.D, 32, 1802, dtype)
+    W = H.filter_apply(V, c)
+    Ht = oc.rescale(oh.build(p), Ec, dE)
+    ref = oc.clenshaw_apply(Ht, V.double().cpu().numpy(), c)
+    err = np.abs(W.double().cpu().numpy() - ref).max()
+    if dtype == torch.float64:
+        assert err <= K * 40 * 2.0 ** -53 * max(1.0, np.abs(ref).max()) * 8
+    else:
+        assert err < 50 * np.sqrt(K) * 2.0 ** -24 * np.abs(V.cpu().numpy()).max() * 8
+    H2 = pf.Hamiltonian.from_params(pi.xxz_params(16, W=1.0, seed=1803))
+    H2.spectral_bounds()
+    V2 = _start(H2.D, 32, 1804, dtype)
+    c2 = pf.filter_coefficients(-0.3, 25)
+    W2 = H2.filter_apply(V2, c2)
+    for form in ["steps", "graph"]:
+        outs = pf.filter_apply_batch([(H, V, c), (H2, V2, c2)], form=form)
+        assert torch.equal(outs[0], W) and torch.equal(outs[1], W2)
+
+
+def test_filter_tune_reports(pf):
+    small = pf.Hamiltonian.from_params(pi.xxz_params(10, W=1.0, seed=1901))
+    small.spectral_bounds()
+    form, us = pf.filter_tune(small, 100, s=8, precision="f32")
+    assert form in (0, 1, 2, 4, 8, 16)
+    assert us["sweep"] > 0 and us["c1"] > 0
+    best = min(us.values())
+    assert us["sweep" if form == 0 else f"c{form}"] == best
+    again, _ = pf.filter_tune(small, 100, s=8, precision="f32")
+    assert again == form                                  # cached
