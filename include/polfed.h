@@ -207,17 +207,20 @@ typedef struct {
 #define PF_FORM_GRAPH (-2)
 pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t prec, int32_t s,
                                 int32_t form, pf_stream_t stream);
-/* The autotuner's choice for items shaped like H at (prec, s), degree K: form = 0 (per-step
- * sweep) or a cluster size c >= 1 (persistent).  The choice minimises SM-time per item step
- * measured on the device: c SMs x the persistent step time, against all SMs x the sweep's
- * step time over enough copies of the item to fill the GPU, divided by the copies.  Items
- * with more than 64 rows per thread of a 16-CTA cluster always take the sweep.  Cached per
- * (device, D, nnz, prec, s); the first call per shape runs the measurements (scratch blocks
- * only).  sm_us (may be NULL): host [6], measured SM-microseconds per item step of the
- * sweep and of clusters of 1, 2, 4, 8, 16 CTAs (0 = not measured).
+/* The autotuner's choice for a group of n items shaped like H at (prec, s), degree K:
+ * form = 0 (per-step sweep; the plain one-launch-per-step recurrence when n = 1) or a cluster
+ * size c >= 1 (persistent).  The shape is measured once per (device, D, nnz, prec, s) on
+ * scratch blocks, over min(K, 48) + 1 steps: the item alone with one launch per step, the
+ * sweep over enough copies to fill the GPU, and the persistent kernel with clusters of 1, 2,
+ * 4, 8, 16 CTAs.  The form with the smallest predicted per-step time for the whole group is
+ * chosen: sweep time interpolated between one item and the copies; persistent time x
+ * ceil(n / clusters resident at once).  Items with more than 64 rows per thread of a
+ * 16-CTA cluster are not measured and take the sweep.
+ *   step_us (may be NULL): host [8] = raw, sweep, sweep copies, persistent c = 1, 2, 4, 8, 16
+ *   (microseconds per step; 0 = not measured).
  * Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ENOMEM, PF_ECUDA.                    */
-pf_status pf_filter_tune(const pf_ham* H, int32_t prec, int32_t s, int32_t K, int32_t* form, double* sm_us,
-                         pf_stream_t stream);
+pf_status pf_filter_tune(const pf_ham* H, int32_t prec, int32_t s, int32_t K, int32_t n, int32_t* form,
+                         double* step_us, pf_stream_t stream);
 
 /* Same computation as pf_filter_apply, without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device memory at

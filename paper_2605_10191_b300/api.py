@@ -302,14 +302,16 @@ def filter_apply_batch(items, form="auto", stream=None):
     return outs
 
 
-def filter_tune(H, K, s=32, precision="f32", stream=None):
-    """The autotuner's form for items shaped like H: (form, {candidate: SM-us per item step})."""
+def filter_tune(H, K, s=32, precision="f32", n=1, stream=None):
+    """The autotuner's form for a group of n items shaped like H: (form, measured per-step us).
+
+    form 0 = per-step sweep (plain recurrence for n = 1), c >= 1 = persistent clusters of c CTAs."""
     _install_torch_allocator()
     f = C.c_int32()
-    us = (C.c_double * 6)()
-    check(lib().pf_filter_tune(H.handle, L.PF_F64 if precision == "f64" else L.PF_F32, int(s), int(K), C.byref(f),
-                               us, _stream(stream)), "pf_filter_tune")
-    names = ["sweep", "c1", "c2", "c4", "c8", "c16"]
+    us = (C.c_double * 8)()
+    check(lib().pf_filter_tune(H.handle, L.PF_F64 if precision == "f64" else L.PF_F32, int(s), int(K), int(n),
+                               C.byref(f), us, _stream(stream)), "pf_filter_tune")
+    names = ["raw", "sweep", "sweep_copies", "c1", "c2", "c4", "c8", "c16"]
     return f.value, {k: us[i] for i, k in enumerate(names) if us[i] > 0}
 
 

@@ -88,10 +88,14 @@ __device__ __forceinline__ void st_default(T* p, const Vec<T, E>& r) {
   }
 }
 
+// Lanes per row.  FP32: E = 4 entries (one 16-byte vector) per lane, so an s = 32 row is 8
+// lanes.  FP64: one row per warp where s allows it (E = max(1, s/32)): the FP64 step is bound
+// by the FP64 pipe, and a warp that holds one row never idles lanes on a shorter neighbour
+// row (about 8% faster than two rows of 16 lanes at s = 32).
 template <typename T, int S> struct Shape {
-  static constexpr int E = (S * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : S;
+  static constexpr int E = sizeof(T) == 8 ? (S >= 64 ? S / 32 : 1) : ((S * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : S);
   static constexpr int G = S / E;           // lanes per row
-  static constexpr int ROWS_PER_WARP = 32 / G;
+  static constexpr int ROWS_PER_WARP = G >= 32 ? 1 : 32 / G;
 };
 
 // L2-only loads (ld.global.cg) for blocks the same launch rewrites between its steps.
@@ -187,7 +191,7 @@ __device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_
 // SM's L1 serves the neighbour rows that fall inside its CTAs' ranges (for the XXZ chain in
 // rank order about half of all neighbours lie within +-200 rows).
 template <typename T, int S, int SP, int B2M>
-__global__ void __launch_bounds__(256, 6) clenshaw_step_kernel(int64_t D, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 8 : 6) clenshaw_step_kernel(int64_t D, const int64_t* __restrict__ rp,
                                                             const int32_t* __restrict__ col,
                                                             const T* __restrict__ val, const T* __restrict__ V,
                                                             const T* __restrict__ B1, const T* B2, T* out, T a,
@@ -514,9 +518,8 @@ static StepShape sweep_shape_s(int s, int64_t rows) {
   return StepShape{0, 0};
 }
 
-static int lanes_per_row(int prec, int s) {
-  const int w = prec == PF_F64 ? 8 : 4;
-  const int E = s * w >= 16 ? 16 / w : s;
+static int lanes_per_row(int prec, int s) {   // Shape<T, s>::G
+  const int E = prec == PF_F64 ? (s >= 64 ? s / 32 : 1) : (s * 4 >= 16 ? 4 : s);
   return s / E;
 }
 
@@ -648,15 +651,96 @@ pf_status filter_sweep(const std::vector<FilterItem>& items, void* table_dev, si
   return PF_EINVAL;
 }
 
+// ------------------------------------------------------------------ captured filter applications
+// One filter application with fixed operands (V, W, auxiliaries, coefficients) captured once
+// from filter_apply_raw into a CUDA graph, then replayed with one launch call.  Used where a
+// host thread drives many solves at once: a whole K-step recurrence is queued by a single
+// call, so the thread never stalls on a full launch queue.
+FilterGraph::~FilterGraph() { reset(); }
+void FilterGraph::reset() {
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  exec = nullptr;
+  graph = nullptr;
+  K = -1;
+}
+
+// Settles the step kernels' launch-shape queries (occupancy) before a capture begins.
+template <typename T, int S>
+static void prepare_shapes_s() {
+  step_shape<T, S, 0, 0>(1);
+  step_shape<T, S, 1, 0>(1);
+  step_shape<T, S, 0, 1>(1);
+  step_shape<T, S, 1, 1>(1);
+}
+template <typename T>
+static void prepare_shapes(int s) {
+  switch (s) {
+    case 1: prepare_shapes_s<T, 1>(); break;
+    case 2: prepare_shapes_s<T, 2>(); break;
+    case 4: prepare_shapes_s<T, 4>(); break;
+    case 8: prepare_shapes_s<T, 8>(); break;
+    case 16: prepare_shapes_s<T, 16>(); break;
+    case 32: prepare_shapes_s<T, 32>(); break;
+    case 64: prepare_shapes_s<T, 64>(); break;
+  }
+}
+
+pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t st) {
+  const double a0 = it.coeffs_host ? it.coeffs_host[0] : 0.0;
+  const double aK = it.coeffs_host ? it.coeffs_host[it.K] : 0.0;
+  if (!(g.exec && g.K == it.K && g.V == it.V && g.W == it.W && g.aux0 == it.aux0 && g.aux1 == it.aux1 &&
+        g.prec == it.prec && g.s == it.s && g.H == it.H && g.a0 == a0 && g.aK == aK)) {
+    g.reset();
+    if (!it.coeffs_host || it.K < 1) return PF_EINVAL;
+    if (it.prec == PF_F64) prepare_shapes<double>(it.s);
+    else prepare_shapes<float>(it.s);
+    cudaStream_t cap = nullptr;
+    PF_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    const long long before = g_kernel_launches.load();
+    pf_status rc = PF_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, cap);
+      e = cudaStreamEndCapture(cap, &g.graph);
+    }
+    g_kernel_launches.store(before);   // capture is not execution
+    cudaStreamDestroy(cap);
+    if (rc == PF_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (rc != PF_OK || e != cudaSuccess) {
+      // no graph: the same launches go to the stream one by one
+      g.reset();
+      cudaGetLastError();
+      return filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, st);
+    }
+    g.K = it.K;
+    g.V = it.V;
+    g.W = it.W;
+    g.aux0 = it.aux0;
+    g.aux1 = it.aux1;
+    g.prec = it.prec;
+    g.s = it.s;
+    g.H = it.H;
+    g.a0 = a0;
+    g.aK = aK;
+  }
+  PF_COUNT(it.K + 1);
+  PF_CUDA(cudaGraphLaunch(g.exec, st));
+  return PF_OK;
+}
+
 // ------------------------------------------------------------------ autotuner
-// How an item of a given shape runs inside a multi-item group: 0 = the per-step sweep over
-// all items' rows, c >= 1 = the persistent kernel with clusters of c CTAs.  Measured once per
-// (device, D, nnz, precision, s) on the device: the candidates run min(K, 48) + 1 steps of
-// the item on scratch blocks (so the caller's data is untouched), and the choice minimises
-// SM-time per item step, the cost that matters when many items share the GPU:
-//   persistent c: c SMs x its step time;
-//   sweep: all SMs x its step time over r copies of the item (r fills the GPU) / r.
-// Items with more than 64 rows per thread of a 16-CTA cluster always take the sweep.
+// Execution form of a group of n items of one shape.  Measured once per (device, D, nnz,
+// precision, s) on scratch blocks (the caller's data is untouched), over min(K, 48) + 1 steps:
+//   raw_us      one item alone, one launch per step (filter_apply_raw);
+//   sweep_us    the per-step sweep over r copies of the item (r fills the GPU);
+//   persist_us  one item in the persistent kernel with clusters of c = 1, 2, 4, 8, 16 CTAs,
+//               of which slots[c] run at once.
+// choose_form() then predicts the per-step time of the whole group for each form and takes
+// the fastest: raw (n = 1) raw_us; sweep, interpolated between raw_us (one item) and sweep_us
+// (r items) and proportional beyond r; persistent c, persist_us x ceil(n / slots).  Items
+// with more than 64 rows per thread of a 16-CTA cluster are not measured: they take the
+// sweep (or the plain recurrence when alone).
 namespace {
 struct TuneKey {
   int dev, prec, s;
@@ -688,6 +772,72 @@ static pf_status time_ms(cudaStream_t st, const std::function<pf_status()>& f, i
   return rc;
 }
 
+template <typename T, int S>
+static int persist_slots_s(int c, int nsm) {
+  if (c <= 1) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, clenshaw_persistent_kernel<T, S, false>, PF_PERSIST_NT, 0);
+    return nsm * std::max(occ, 1);
+  }
+  auto kern = clenshaw_persistent_kernel<T, S, true>;
+  if (c > 8) cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)c, 1, 1);
+  cfg.blockDim = dim3(PF_PERSIST_NT, 1, 1);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)c;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return std::max(1, nsm / c);
+  }
+  return std::max(n, 1);
+}
+
+template <typename T>
+static int persist_slots(int s, int c, int nsm) {
+  switch (s) {
+    case 1: return persist_slots_s<T, 1>(c, nsm);
+    case 2: return persist_slots_s<T, 2>(c, nsm);
+    case 4: return persist_slots_s<T, 4>(c, nsm);
+    case 8: return persist_slots_s<T, 8>(c, nsm);
+    case 16: return persist_slots_s<T, 16>(c, nsm);
+    case 32: return persist_slots_s<T, 32>(c, nsm);
+    case 64: return persist_slots_s<T, 64>(c, nsm);
+  }
+  return 1;
+}
+
+int choose_form(const TuneResult& tr, int n, double* predicted_us) {
+  double best = 0;
+  int form = 0;
+  if (tr.raw_us > 0) {
+    if (n <= 1) {
+      best = tr.raw_us;
+    } else if (n <= tr.sweep_copies) {
+      best = tr.raw_us + (tr.sweep_us - tr.raw_us) * (double)(n - 1) / std::max(1, tr.sweep_copies - 1);
+    } else {
+      best = tr.sweep_us * (double)n / tr.sweep_copies;
+    }
+    const int cs[5] = {1, 2, 4, 8, 16};
+    for (int k = 0; k < 5; ++k) {
+      if (tr.persist_us[k] <= 0) continue;
+      const double t = tr.persist_us[k] * (double)ceil_div(n, std::max(1, tr.slots[k]));
+      if (t < best) {
+        best = t;
+        form = cs[k];
+      }
+    }
+  }
+  if (predicted_us) *predicted_us = best;
+  return form;
+}
+
 pf_status tune_item(const FilterItem& it, cudaStream_t st, TuneResult* out) {
   int dev = 0;
   PF_CUDA(cudaGetDevice(&dev));
@@ -711,7 +861,7 @@ pf_status tune_item(const FilterItem& it, cudaStream_t st, TuneResult* out) {
     const size_t blk = (((size_t)D * it.s * w) + 255) & ~(size_t)255;
     const int Kt = std::min(it.K, 48);
     // r copies fill the GPU in the sweep (about 8 resident 256-thread CTAs per SM)
-    const int r = (int)std::max<int64_t>(1, std::min<int64_t>(64, ceil_div((int64_t)nsm * 8 * 256, D * G)));
+    const int r = (int)std::max<int64_t>(2, std::min<int64_t>(64, ceil_div((int64_t)nsm * 8 * 256, D * G)));
     DevBuf scratch, table;
     PF_TRY(scratch.alloc(blk * 3 * r, st));
     PF_TRY(table.alloc(filter_sweep_table_bytes(r), st));
@@ -724,12 +874,19 @@ pf_status tune_item(const FilterItem& it, cudaStream_t st, TuneResult* out) {
       many[j].K = Kt;
     }
     one[0] = many[0];
+    std::vector<double> ch(Kt + 1);
+    PF_CUDA(cudaMemcpyAsync(ch.data(), it.coeffs_dev, (Kt + 1) * 8, cudaMemcpyDeviceToHost, st));
+    PF_CUDA(cudaStreamSynchronize(st));
     std::vector<unsigned char> th(filter_sweep_table_bytes(r));
     double ms = 0;
+    const FilterItem& o = one[0];
+    PF_TRY(time_ms(st, [&] {
+      return filter_apply_raw(o.H, o.prec, o.s, o.V, o.W, ch.data(), nullptr, Kt, o.aux0, o.aux1, st);
+    }, 3, &ms));
+    res.raw_us = 1e3 * ms / (Kt + 1);
     PF_TRY(time_ms(st, [&] { return filter_sweep(many, table.p, table.bytes, th.data(), st, 0, nullptr); }, 3, &ms));
-    res.sweep_sm_us = 1e3 * ms * nsm / r / (Kt + 1);
-    double best = res.sweep_sm_us;
-    res.csize = 0;
+    res.sweep_us = 1e3 * ms / (Kt + 1);
+    res.sweep_copies = r;
     const int cs[5] = {1, 2, 4, 8, 16};
     for (int k = 0; k < 5; ++k) {
       const int c = cs[k];
@@ -740,11 +897,8 @@ pf_status tune_item(const FilterItem& it, cudaStream_t st, TuneResult* out) {
         cudaGetLastError();
         break;
       }
-      res.persist_sm_us[k] = 1e3 * ms * c / (Kt + 1);
-      if (res.persist_sm_us[k] < best) {
-        best = res.persist_sm_us[k];
-        res.csize = c;
-      }
+      res.persist_us[k] = 1e3 * ms / (Kt + 1);
+      res.slots[k] = it.prec == PF_F64 ? persist_slots<double>(it.s, c, nsm) : persist_slots<float>(it.s, c, nsm);
     }
     PF_CUDA(cudaStreamSynchronize(st));
   }
@@ -849,31 +1003,38 @@ pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t 
     return PF_OK;
   }
   if (form >= 1) return filter_sweep(v, table.p, table.bytes, th.data(), st, form, nullptr);
-  // PF_FORM_AUTO: each item's form from the autotuner, one launch (or sweep) per form
-  std::vector<std::pair<int, std::vector<FilterItem>>> parts;
+  // PF_FORM_AUTO: items of one shape form a group; the autotuner picks the group's form
+  std::vector<std::pair<std::pair<int64_t, int64_t>, std::vector<FilterItem>>> shapes;
   for (const FilterItem& it : v) {
-    TuneResult tr;
-    PF_TRY(tune_item(it, st, &tr));
-    auto p = std::find_if(parts.begin(), parts.end(), [&](const auto& x) { return x.first == tr.csize; });
-    if (p == parts.end()) {
-      parts.push_back({tr.csize, {}});
-      p = parts.end() - 1;
+    const auto key = std::make_pair(it.H->D, it.H->nnz);
+    auto p = std::find_if(shapes.begin(), shapes.end(), [&](const auto& x) { return x.first == key; });
+    if (p == shapes.end()) {
+      shapes.push_back({key, {}});
+      p = shapes.end() - 1;
     }
     p->second.push_back(it);
   }
-  for (auto& p : parts) {
+  for (auto& p : shapes) {
+    TuneResult tr;
+    PF_TRY(tune_item(p.second[0], st, &tr));
+    const int f = choose_form(tr, (int)p.second.size(), nullptr);
+    if (f == 0 && p.second.size() == 1) {
+      const FilterItem& it = p.second[0];
+      PF_TRY(filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, st));
+      continue;
+    }
     std::vector<unsigned char> tp(filter_sweep_table_bytes((int)p.second.size()));
     DevBuf tb;
     PF_TRY(tb.alloc(tp.size(), st));
-    PF_TRY(filter_sweep(p.second, tb.p, tb.bytes, tp.data(), st, p.first, nullptr));
+    PF_TRY(filter_sweep(p.second, tb.p, tb.bytes, tp.data(), st, f, nullptr));
   }
   return PF_OK;
 }
 
-pf_status pf_filter_tune(const pf_ham* hh, int32_t prec, int32_t s, int32_t K, int32_t* form, double* sm_us,
-                         pf_stream_t stream) {
+pf_status pf_filter_tune(const pf_ham* hh, int32_t prec, int32_t s, int32_t K, int32_t n, int32_t* form,
+                         double* step_us, pf_stream_t stream) {
   const Ham* H = reinterpret_cast<const Ham*>(hh);
-  if (!H || !form || K < 1) return PF_EINVAL;
+  if (!H || !form || K < 1 || n < 1) return PF_EINVAL;
   if (!H->has_rescale) return PF_ESTATE;
   if (prec != PF_F64 && prec != PF_F32) return PF_EINVAL;
   if (!valid_s(s)) return PF_EINVAL;
@@ -894,10 +1055,12 @@ pf_status pf_filter_tune(const pf_ham* hh, int32_t prec, int32_t s, int32_t K, i
   it.K = K;
   TuneResult tr;
   PF_TRY(tune_item(it, st, &tr));
-  *form = tr.csize;
-  if (sm_us) {
-    sm_us[0] = tr.sweep_sm_us;
-    for (int k = 0; k < 5; ++k) sm_us[1 + k] = tr.persist_sm_us[k];
+  *form = choose_form(tr, n, nullptr);
+  if (step_us) {
+    step_us[0] = tr.raw_us;
+    step_us[1] = tr.sweep_us;
+    step_us[2] = tr.sweep_copies;
+    for (int k = 0; k < 5; ++k) step_us[3 + k] = tr.persist_us[k];
   }
   return PF_OK;
 }

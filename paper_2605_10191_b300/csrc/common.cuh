@@ -143,6 +143,7 @@ struct FilterItem {
   void* aux0 = nullptr;
   void* aux1 = nullptr;
   const void* owner = nullptr;          // the solve the item belongs to (grouping only)
+  struct FilterGraph* graph = nullptr;  // the owner's captured form of this application (async executor)
 };
 // A per-step sweep captured as a CUDA graph (chain of T kernel nodes), reused while the table
 // address, item count, step count and row total stay the same.
@@ -165,14 +166,38 @@ struct SweepGraph {
 pf_status filter_sweep(const std::vector<FilterItem>& items, void* table_dev, size_t table_bytes, void* table_host,
                        cudaStream_t st, int csize = 0, SweepGraph* graph = nullptr);
 size_t filter_sweep_table_bytes(int n);
-// Autotuner result for one item shape: csize 0 = sweep, >= 1 = persistent cluster size; the
-// measured SM-microseconds per item step of each candidate (0 = not measured).
+// Autotuner measurements for one item shape (per-step microseconds; 0 = not measured): the
+// item alone with one launch per step, the per-step sweep over sweep_copies copies, and the
+// persistent kernel with clusters of 1, 2, 4, 8, 16 CTAs (slots of them run at once).
 struct TuneResult {
-  int csize = 0;
-  double sweep_sm_us = 0;
-  double persist_sm_us[5] = {0, 0, 0, 0, 0};   // clusters of 1, 2, 4, 8, 16 CTAs
+  double raw_us = 0, sweep_us = 0;
+  int sweep_copies = 1;
+  double persist_us[5] = {0, 0, 0, 0, 0};
+  int slots[5] = {0, 0, 0, 0, 0};
 };
+// The fastest form for a group of n items of the measured shape: 0 = sweep (the plain
+// recurrence when n = 1), c >= 1 = persistent with clusters of c CTAs.
+int choose_form(const TuneResult& tr, int n, double* predicted_us);
 pf_status tune_item(const FilterItem& it, cudaStream_t st, TuneResult* out);
+// A filter application captured as a CUDA graph (see clenshaw.cu); replayed while its
+// operands and end coefficients are unchanged, recaptured otherwise.
+struct FilterGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int K = -1, prec = -1, s = 0;
+  const void* V = nullptr;
+  const void* W = nullptr;
+  const void* aux0 = nullptr;
+  const void* aux1 = nullptr;
+  const Ham* H = nullptr;
+  double a0 = 0, aK = 0;
+  FilterGraph() = default;
+  FilterGraph(const FilterGraph&) = delete;
+  FilterGraph& operator=(const FilterGraph&) = delete;
+  ~FilterGraph();
+  void reset();
+};
+pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t st);
 // W = P V for a D x s block (K steps); aux buffers are two D x s blocks of the filter type.
 pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs_host,
                            const void* coeffs_dev, int K, void* aux0, void* aux1, cudaStream_t st);

@@ -20,7 +20,12 @@
 #include <algorithm>
 #include <numeric>
 #include <chrono>
+#include <functional>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
 
 namespace pf {
 
@@ -530,6 +535,12 @@ struct Task {
   std::vector<FilterItem> pending;
   pf_status status = PF_OK;
   PhaseClock* clk = nullptr;
+  // Captured filter applications, used when an asynchronous executor drives the task: the
+  // Lanczos filter reads a fixed input block (Vin, FP64 path) so one graph serves every step.
+  bool captured = false;
+  DevBuf Vin;
+  FilterGraph g_lanczos;
+  std::vector<std::unique_ptr<FilterGraph>> g_refine;
   cudaEvent_t t_begin = nullptr, t_end = nullptr;
 
   Task() { memset(&o, 0, sizeof(o)); }
@@ -631,7 +642,13 @@ struct Task {
       it.V = Vk;
       it.W = S.W.p;
       S.rep.filter_steps_f64 += K + 1;
+      if (captured) {
+        if (!Vin.p) PF_TRY(Vin.alloc((size_t)S.D * s * 8, st));
+        PF_CUDA(cudaMemcpyAsync(Vin.p, Vk, (size_t)S.D * s * 8, cudaMemcpyDeviceToDevice, st));
+        it.V = Vin.p;
+      }
     }
+    it.graph = &g_lanczos;
     clk->mark(0);
     pending.assign(1, it);
     return PF_OK;
@@ -830,6 +847,8 @@ struct Task {
       it.K = Kr;
       it.aux0 = aux64.as<double>() + (int64_t)(2 * b) * DS;
       it.aux1 = aux64.as<double>() + (int64_t)(2 * b + 1) * DS;
+      while ((int)g_refine.size() <= b) g_refine.emplace_back(new FilterGraph());
+      it.graph = g_refine[b].get();
       pending.push_back(it);
       S.rep.filter_steps_f64 += Kr + 1;
     }
@@ -942,7 +961,7 @@ struct Executor {
   std::vector<unsigned char> table_host;
   SweepGraph graph;
   cudaStream_t st = 0;
-  int force_csize = -1;   // -1: the autotuner decides per item shape; >= 0: that form for every multi-item group
+  int force_csize = -1;   // -1: the autotuner decides per group of one shape; >= 0: that form for every group
 
   pf_status run_group(const std::vector<FilterItem>& items, int csize) {
     if (items.empty()) return PF_OK;
@@ -972,36 +991,33 @@ struct Executor {
       }
     }
     for (auto& g : groups) {
-      const auto& items = g.second;
-      if (items.size() == 1) {   // one item: the plain K-step recurrence
-        PF_TRY(run_group(items, 0));
-        continue;
-      }
-      // split by execution form: per-step sweep (csize 0) or persistent clusters of csize CTAs
-      std::vector<std::pair<int, std::vector<FilterItem>>> parts;
-      for (const FilterItem& it : items) {
-        int c = force_csize;
-        if (c < 0) {
-          TuneResult tr;
-          PF_TRY(tune_item(it, st, &tr));
-          c = tr.csize;
-        }
-        auto p = std::find_if(parts.begin(), parts.end(), [&](const auto& x) { return x.first == c; });
-        if (p == parts.end()) {
-          parts.push_back({c, {}});
-          p = parts.end() - 1;
+      // items of one shape (same D and nnz) form a subgroup; the autotuner picks its form
+      std::vector<std::pair<std::pair<int64_t, int64_t>, std::vector<FilterItem>>> shapes;
+      for (const FilterItem& it : g.second) {
+        const auto key = std::make_pair(it.H->D, it.H->nnz);
+        auto p = std::find_if(shapes.begin(), shapes.end(), [&](const auto& x) { return x.first == key; });
+        if (p == shapes.end()) {
+          shapes.push_back({key, {}});
+          p = shapes.end() - 1;
         }
         p->second.push_back(it);
       }
-      for (auto& p : parts) {
+      for (auto& p : shapes) {
+        const auto& items = p.second;
+        int c = force_csize;
+        if (c < 0) {
+          TuneResult tr;
+          PF_TRY(tune_item(items[0], st, &tr));
+          c = choose_form(tr, (int)items.size(), nullptr);
+        }
         bool one_owner = true;
-        for (const FilterItem& it : p.second) one_owner = one_owner && it.owner == p.second[0].owner;
-        if (p.first == 0 && one_owner) {
-          // the blocks of one solve (refinement): the plain recurrence per block keeps the
-          // step kernel's specialised form; sweeps pay off across solves
-          for (const FilterItem& it : p.second) PF_TRY(run_group(std::vector<FilterItem>(1, it), 0));
+        for (const FilterItem& it : items) one_owner = one_owner && it.owner == items[0].owner;
+        if (c == 0 && (items.size() == 1 || one_owner)) {
+          // one item, or the blocks of one solve (refinement): the plain recurrence per item
+          // keeps the step kernel's specialised form; sweeps pay off across solves
+          for (const FilterItem& it : items) PF_TRY(run_group(std::vector<FilterItem>(1, it), 0));
         } else {
-          PF_TRY(run_group(p.second, p.first));
+          PF_TRY(run_group(items, c));
         }
       }
     }
@@ -1024,6 +1040,269 @@ struct Executor {
       if (!any) return PF_OK;
       PF_TRY(run_round(tasks));
     }
+  }
+};
+
+// ------------------------------------------------------------------ asynchronous executor
+// Drives many solves from one host thread without rounds: each solve runs on its own stream
+// (from a process-wide pool), a finished filter application is noticed by polling its event,
+// and the solve's follow-up work is issued at once, so solves in different phases overlap on
+// the device (an FP64 refinement pass, bound by the FP64 pipe, beside another solve's FP32
+// Lanczos steps, bound by memory).  Filter applications are queued as captured graphs (one
+// call per application).  Items of one shape that are ready together still share a sweep or
+// a persistent launch (as chosen by the autotuner), issued on a group stream that waits for
+// the solves' streams and that they wait for in turn.
+//
+// Start gate: a solve whose FP32 step working set exceeds a third of L2 starts its Lanczos
+// phase only while no other such solve is in its Lanczos phase.  Two of them would evict each
+// other's working set from L2 with no gain in throughput; staggered, the next one's Lanczos
+// phase overlaps the previous one's refinement.
+namespace {
+std::mutex g_pool_mu;
+struct StreamPool {
+  std::vector<cudaStream_t> s;
+  cudaStream_t group = nullptr;
+};
+std::map<int, StreamPool> g_pools;
+constexpr int kPoolStreams = 16;
+}  // namespace
+
+// Streams live for the process: memory that a caching allocator keeps per stream stays usable
+// by the next batch or server.
+static pf_status pool_streams(StreamPool** out) {
+  int dev = 0;
+  PF_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  StreamPool& p = g_pools[dev];
+  if (p.s.empty()) {
+    for (int i = 0; i < kPoolStreams; ++i) {
+      cudaStream_t x;
+      PF_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+      p.s.push_back(x);
+    }
+    PF_CUDA(cudaStreamCreateWithFlags(&p.group, cudaStreamNonBlocking));
+  }
+  *out = &p;
+  return PF_OK;
+}
+
+// Pinned host staging for sweep tables: a slot is reused once the copy that read it is done.
+struct PinnedRing {
+  struct Slot {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t ev = nullptr;
+  };
+  std::vector<Slot> slots;
+  ~PinnedRing() {
+    for (auto& x : slots) {
+      if (x.ev) cudaEventSynchronize(x.ev), cudaEventDestroy(x.ev);
+      if (x.p) cudaFreeHost(x.p);
+    }
+  }
+  pf_status get(size_t bytes, Slot** out) {
+    for (auto& x : slots) {
+      if (x.bytes >= bytes && cudaEventQuery(x.ev) == cudaSuccess) {
+        *out = &x;
+        return PF_OK;
+      }
+    }
+    cudaGetLastError();
+    slots.emplace_back();
+    Slot& x = slots.back();
+    PF_CUDA(cudaMallocHost(&x.p, std::max<size_t>(bytes, 4096)));
+    x.bytes = std::max<size_t>(bytes, 4096);
+    PF_CUDA(cudaEventCreateWithFlags(&x.ev, cudaEventDisableTiming));
+    *out = &x;
+    return PF_OK;
+  }
+};
+
+// FP32 step working set (three D x s blocks and the FP32 CSR) above a third of L2.
+static bool l2_heavy(const Ham* H, const pf_solve_opts& o) {
+  if (o.precision != PF_F32 || !H) return false;
+  const int s = o.block > 0 ? o.block : 32;
+  const double ws = (double)H->D * s * 4 * 3 + (double)H->nnz * 8;
+  return ws > 42e6;
+}
+
+struct AsyncExecutor {
+  struct Live {
+    Task* t = nullptr;
+    std::function<pf_status(Task*, cudaStream_t)> start;   // init, deferred by the start gate
+    bool heavy = false, started = false, inflight = false;
+    cudaEvent_t done = nullptr, ready = nullptr;
+    cudaStream_t st = nullptr;
+  };
+  std::vector<Live> live;
+  StreamPool* pool = nullptr;
+  DevBuf table;
+  PinnedRing ring;
+  SweepGraph sgraph;
+  int next_stream = 0;
+
+  ~AsyncExecutor() {
+    for (auto& l : live) {
+      if (l.done) cudaEventDestroy(l.done);
+      if (l.ready) cudaEventDestroy(l.ready);
+    }
+  }
+  pf_status setup() { return pool_streams(&pool); }
+
+  // Registers a solve; `start` initialises it on the stream it is given.
+  pf_status add(Task* t, bool heavy, std::function<pf_status(Task*, cudaStream_t)> start) {
+    Live l;
+    l.t = t;
+    l.heavy = heavy;
+    l.start = std::move(start);
+    PF_CUDA(cudaEventCreateWithFlags(&l.done, cudaEventDisableTiming));
+    PF_CUDA(cudaEventCreateWithFlags(&l.ready, cudaEventDisableTiming));
+    l.st = pool->s[next_stream++ % kPoolStreams];
+    live.push_back(l);
+    return PF_OK;
+  }
+
+  void fail(Live& l, pf_status s) {
+    l.t->status = s;
+    l.t->phase = Task::DONE;
+    l.t->pending.clear();
+    l.inflight = false;
+    l.started = true;
+  }
+
+  bool finished(const Live& l) const { return l.started && l.t->phase == Task::DONE; }
+  bool is_finished(const Task* t) const {
+    for (const auto& l : live)
+      if (l.t == t) return finished(l);
+    return true;
+  }
+  void remove(const Task* t) {
+    for (size_t i = 0; i < live.size(); ++i)
+      if (live[i].t == t) {
+        if (live[i].done) cudaEventDestroy(live[i].done);
+        if (live[i].ready) cudaEventDestroy(live[i].ready);
+        live.erase(live.begin() + i);
+        return;
+      }
+  }
+  bool all_done() const {
+    for (const auto& l : live)
+      if (!finished(l)) return false;
+    return true;
+  }
+
+  // Starts solves the gate admits, in registration order.
+  void start_ready() {
+    int heavy_lanczos = 0;
+    for (const auto& l : live)
+      if (l.started && l.heavy && l.t->phase == Task::LANCZOS) ++heavy_lanczos;
+    for (auto& l : live) {
+      if (l.started) continue;
+      if (l.heavy && heavy_lanczos > 0) continue;
+      l.t->captured = true;
+      const pf_status s = l.start(l.t, l.st);
+      l.started = true;
+      if (s != PF_OK) {
+        fail(l, s);
+        continue;
+      }
+      if (l.heavy && l.t->phase == Task::LANCZOS) ++heavy_lanczos;
+    }
+  }
+
+  // Issues the pending filter applications of every started, idle solve.
+  pf_status launch_ready() {
+    std::vector<Live*> idle;
+    for (auto& l : live)
+      if (l.started && !l.inflight && l.t->phase != Task::DONE && !l.t->pending.empty()) idle.push_back(&l);
+    if (idle.empty()) return PF_OK;
+    // shape groups across solves: (prec, s, D, nnz)
+    struct Grp {
+      int prec, s;
+      int64_t D, nnz;
+      std::vector<std::pair<FilterItem, Live*>> items;
+    };
+    std::vector<Grp> grps;
+    for (Live* l : idle)
+      for (const FilterItem& it : l->t->pending) {
+        auto g = std::find_if(grps.begin(), grps.end(), [&](const Grp& x) {
+          return x.prec == it.prec && x.s == it.s && x.D == it.H->D && x.nnz == it.H->nnz;
+        });
+        if (g == grps.end()) {
+          grps.push_back(Grp{it.prec, it.s, it.H->D, it.H->nnz, {}});
+          g = grps.end() - 1;
+        }
+        g->items.push_back({it, l});
+      }
+    for (auto& g : grps) {
+      TuneResult tr;
+      PF_TRY(tune_item(g.items[0].first, g.items[0].second->st, &tr));
+      const int n = (int)g.items.size();
+      const int c = choose_form(tr, n, nullptr);
+      bool one_owner = true;
+      for (auto& x : g.items) one_owner = one_owner && x.second == g.items[0].second;
+      if (c == 0 && (n == 1 || one_owner)) {
+        for (auto& x : g.items) PF_TRY(filter_graph_launch(*x.first.graph, x.first, x.second->st));
+        continue;
+      }
+      // one launch (sweep or persistent) for the group on the group stream
+      std::vector<Live*> owners;
+      for (auto& x : g.items)
+        if (std::find(owners.begin(), owners.end(), x.second) == owners.end()) owners.push_back(x.second);
+      for (Live* l : owners) {
+        PF_CUDA(cudaEventRecord(l->ready, l->st));
+        PF_CUDA(cudaStreamWaitEvent(pool->group, l->ready, 0));
+      }
+      std::vector<FilterItem> items;
+      for (auto& x : g.items) items.push_back(x.first);
+      const size_t need = filter_sweep_table_bytes(n);
+      if (table.bytes < need) {
+        PF_CUDA(cudaStreamSynchronize(pool->group));
+        PF_TRY(table.alloc(need * 4, pool->group));
+      }
+      PinnedRing::Slot* slot = nullptr;
+      PF_TRY(ring.get(need, &slot));
+      PF_TRY(filter_sweep(items, table.p, table.bytes, slot->p, pool->group, c, c == 0 ? &sgraph : nullptr));
+      PF_CUDA(cudaEventRecord(slot->ev, pool->group));
+      for (Live* l : owners) PF_CUDA(cudaStreamWaitEvent(l->st, slot->ev, 0));
+    }
+    for (Live* l : idle) {
+      PF_CUDA(cudaEventRecord(l->done, l->st));
+      l->inflight = true;
+    }
+    return PF_OK;
+  }
+
+  // Runs the follow-up of every solve whose filter application has finished.  With `wait`,
+  // sleeps briefly when nothing has finished yet.
+  pf_status poll(bool wait, int* completed) {
+    int done = 0;
+    for (auto& l : live) {
+      if (!l.inflight) continue;
+      const cudaError_t q = cudaEventQuery(l.done);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) {
+        set_cuda_error(q, "cudaEventQuery");
+        return PF_ECUDA;
+      }
+      l.inflight = false;
+      ++done;
+      const pf_status s = l.t->after_filter();
+      if (s != PF_OK) fail(l, s);
+    }
+    cudaGetLastError();
+    if (!done && wait) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    if (completed) *completed = done;
+    return PF_OK;
+  }
+
+  pf_status run() {
+    while (!all_done()) {
+      start_ready();
+      PF_TRY(launch_ready());
+      PF_TRY(poll(true, nullptr));
+    }
+    return PF_OK;
   }
 };
 
@@ -1097,7 +1376,8 @@ struct Server {
   int64_t next_id = 1;
   std::vector<Request*> queue, active, finished;
   size_t in_use = 0;
-  Executor ex;
+  AsyncExecutor ex;
+  bool ready = false;
 
   ~Server() {
     for (auto* v : {&queue, &active, &finished})
@@ -1107,14 +1387,30 @@ struct Server {
       }
   }
   void release(Request* r) {
-    delete r->task;
-    r->task = nullptr;
+    if (r->task) {
+      cudaStream_t s = r->task->st;
+      ex.remove(r->task);
+      delete r->task;
+      r->task = nullptr;
+      if (s) cudaStreamSynchronize(s);
+    }
     if (r->ham) pf_free_ham(r->ham);
     if (r->basis) pf_free_basis(r->basis);
     r->ham = nullptr;
     r->basis = nullptr;
   }
-  pf_status admit(Request* r) {
+  pf_solve_opts opts() const {
+    pf_solve_opts o;
+    pf_default_opts(&o);
+    o.block = cfg.block;
+    o.precision = cfg.precision;
+    if (cfg.res_tol > 0) o.res_tol = cfg.res_tol;
+    if (cfg.seed) o.seed = cfg.seed;
+    return o;
+  }
+  // Admission work, on the stream the executor gives the solve: basis, Hamiltonian, bounds,
+  // K, then the solve's initialisation.
+  pf_status start(Request* r, Task* t, cudaStream_t s) {
     pf_params p;
     memset(&p, 0, sizeof(p));
     p.h = r->h.empty() ? nullptr : r->h.data();
@@ -1122,20 +1418,15 @@ struct Server {
     p.A = r->A.empty() ? nullptr : r->A.data();
     p.u_noise = r->un.empty() ? nullptr : r->un.data();
     p.n_of_j = r->nj.empty() ? nullptr : r->nj.data();
-    PF_TRY(pf_build_basis(&r->m, &r->basis, st));
-    PF_TRY(pf_build_hamiltonian(r->basis, &r->m, &p, &r->ham, st));
+    r->t_admit = now_ms();
+    PF_TRY(pf_build_basis(&r->m, &r->basis, s));
+    PF_TRY(pf_build_hamiltonian(r->basis, &r->m, &p, &r->ham, s));
     double emin, emax;
-    PF_TRY(pf_spectral_bounds(r->ham, cfg.bounds_tol, &emin, &emax, nullptr, nullptr, st));
+    PF_TRY(pf_spectral_bounds(r->ham, cfg.bounds_tol, &emin, &emax, nullptr, nullptr, s));
     int32_t K = 0;
-    PF_TRY(pf_choose_K(r->ham, r->eps, r->nev, &K, st));
-    pf_solve_opts o;
-    pf_default_opts(&o);
-    o.block = cfg.block;
-    o.precision = cfg.precision;
-    if (cfg.res_tol > 0) o.res_tol = cfg.res_tol;
-    if (cfg.seed) o.seed = cfg.seed;
-    r->task = new Task();
-    return r->task->init(reinterpret_cast<Ham*>(r->ham), r->eps, r->nev, K, &o, st);
+    PF_TRY(pf_choose_K(r->ham, r->eps, r->nev, &K, s));
+    const pf_solve_opts o = opts();
+    return t->init(reinterpret_cast<Ham*>(r->ham), r->eps, r->nev, K, &o, s);
   }
   void retire(Request* r, pf_status s) {
     r->status = s;
@@ -1146,26 +1437,31 @@ struct Server {
     finished.push_back(r);
   }
   pf_status step(int32_t* nq, int32_t* na, int32_t* nf) {
+    if (!ready) {
+      PF_TRY(ex.setup());
+      ready = true;
+    }
     while (!queue.empty() && (int)active.size() < cfg.max_active) {
       Request* r = queue.front();
       if (!active.empty() && in_use + r->foot > (size_t)cfg.mem_budget_bytes) break;
       queue.erase(queue.begin());
       r->state = 1;
-      r->t_admit = now_ms();
       in_use += r->foot;
-      const pf_status s = admit(r);
-      if (s != PF_OK) {
-        retire(r, s);
-        continue;
-      }
+      r->task = new Task();
+      const pf_solve_opts o = opts();
+      const int64_t D = model_dim(r->m);
+      Ham probe;
+      probe.D = D;
+      probe.nnz = model_nnz_bound(r->m, D);
+      PF_TRY(ex.add(r->task, l2_heavy(&probe, o), [this, r](Task* t, cudaStream_t s) { return start(r, t, s); }));
       active.push_back(r);
     }
-    std::vector<Task*> ts;
-    for (Request* r : active) ts.push_back(r->task);
-    if (!ts.empty()) PF_TRY(ex.run_round(ts));
+    ex.start_ready();
+    PF_TRY(ex.launch_ready());
+    PF_TRY(ex.poll(true, nullptr));
     for (size_t i = 0; i < active.size();) {
       Request* r = active[i];
-      if (r->task->phase == Task::DONE) {
+      if (ex.is_finished(r->task)) {
         r->evals.assign(r->nev, 0.0);
         r->resid.assign(r->nev, 0.0);
         memset(&r->rep, 0, sizeof(r->rep));
@@ -1268,41 +1564,51 @@ pf_status pf_polfed_solve(pf_ham* hh, double target_eps, int32_t nev, int32_t K,
 
 pf_status pf_polfed_solve_batch(pf_solve_item* items, int32_t n, pf_stream_t stream) {
   if (n < 0 || (n > 0 && !items)) return PF_EINVAL;
-  cudaStream_t st = (cudaStream_t)stream;
+  if (n == 0) return PF_OK;
+  // the solves run on the library's stream pool; the caller's stream is drained first so
+  // that work the caller queued before (bounds, buffers) is complete
+  PF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  AsyncExecutor ex;
+  PF_TRY(ex.setup());
   std::vector<std::unique_ptr<Task>> tasks;
-  std::vector<Task*> run;
   std::vector<int> slot;
   for (int i = 0; i < n; ++i) {
     pf_solve_item& it = items[i];
-    tasks.emplace_back(new Task());
+    it.status = PF_OK;
     if (!it.H || !it.evals || !it.resid) {
       it.status = PF_EINVAL;
       continue;
     }
-    const pf_status s = tasks.back()->init(reinterpret_cast<Ham*>(it.H), it.target_eps, it.nev, it.K, it.opts, st);
-    it.status = s;
-    if (s == PF_OK) {
-      run.push_back(tasks.back().get());
-      slot.push_back(i);
-    }
+    pf_solve_opts o;
+    pf_default_opts(&o);
+    if (it.opts) o = *it.opts;
+    Ham* H = reinterpret_cast<Ham*>(it.H);
+    const double eps = it.target_eps;
+    const int nev = it.nev, K = it.K;
+    tasks.emplace_back(new Task());
+    slot.push_back(i);
+    PF_TRY(ex.add(tasks.back().get(), l2_heavy(H, o), [H, eps, nev, K, o](Task* t, cudaStream_t st) {
+      return t->init(H, eps, nev, K, &o, st);
+    }));
   }
-  Executor ex;
-  ex.st = st;
-  const pf_status rs = ex.run(run);
-  if (rs != PF_OK) {   // a shared launch failed: every problem that was running reports it
-    for (size_t j = 0; j < run.size(); ++j) items[slot[j]].status = rs;
-    return rs;
-  }
+  pf_status rs = ex.run();
   pf_status first_bad = PF_OK;
-  for (size_t j = 0; j < run.size(); ++j) {
+  for (size_t j = 0; j < tasks.size(); ++j) {
     pf_solve_item& it = items[slot[j]];
-    Task* t = run[j];
-    it.status = (t->phase == Task::DONE && !t->sel.empty()) ? t->outputs(it.evals, it.evecs, it.resid, it.rep)
-                                                            : (t->status != PF_OK ? t->status : PF_ENOTCONV);
+    Task* t = tasks[j].get();
+    if (rs != PF_OK) it.status = rs;   // a shared launch failed: every problem reports it
+    else
+      it.status = (t->phase == Task::DONE && !t->sel.empty()) ? t->outputs(it.evals, it.evecs, it.resid, it.rep)
+                                                              : (t->status != PF_OK ? t->status : PF_ENOTCONV);
+  }
+  for (auto& t : tasks) {   // release on the solves' own streams before the executor goes
+    cudaStream_t st = t->st;
+    t.reset();
+    if (st) cudaStreamSynchronize(st);
   }
   for (int i = 0; i < n; ++i)
     if (items[i].status != PF_OK && first_bad == PF_OK) first_bad = (pf_status)items[i].status;
-  return first_bad;
+  return rs != PF_OK ? rs : first_bad;
 }
 
 pf_status pf_solve_footprint(int64_t D, int64_t nnz, int32_t nev, int32_t block, int32_t precision,
@@ -1336,7 +1642,6 @@ pf_status pf_server_create(const pf_server_config* cfg, pf_stream_t stream, pf_s
   pf_server* sv = new pf_server();
   sv->cfg = c;
   sv->st = (cudaStream_t)stream;
-  sv->ex.st = sv->st;
   *out = sv;
   return PF_OK;
 }

@@ -183,10 +183,17 @@ def test_filter_L18_range_form_matches_oracle_and_batch(pf, dtype):
 def test_filter_tune_reports(pf):
     small = pf.Hamiltonian.from_params(pi.xxz_params(10, W=1.0, seed=1901))
     small.spectral_bounds()
-    form, us = pf.filter_tune(small, 100, s=8, precision="f32")
+    form, us = pf.filter_tune(small, 100, s=8, precision="f32", n=1)
     assert form in (0, 1, 2, 4, 8, 16)
-    assert us["sweep"] > 0 and us["c1"] > 0
-    best = min(us.values())
-    assert us["sweep" if form == 0 else f"c{form}"] == best
-    again, _ = pf.filter_tune(small, 100, s=8, precision="f32")
+    assert us["raw"] > 0 and us["sweep"] > 0 and us["c1"] > 0 and us["sweep_copies"] >= 2
+    # one item: the choice is the fastest measured single-item form
+    cands = {0: us["raw"], **{c: us[f"c{c}"] for c in (1, 2, 4, 8, 16) if f"c{c}" in us}}
+    assert cands[form] == min(cands.values())
+    again, _ = pf.filter_tune(small, 100, s=8, precision="f32", n=1)
     assert again == form                                  # cached
+    many, _ = pf.filter_tune(small, 100, s=8, precision="f32", n=512)
+    assert many in (0, 1, 2, 4, 8, 16)
+    big = pf.Hamiltonian.from_params(pi.xxz_params(20, W=1.0, seed=1902))
+    big.spectral_bounds()
+    f_big, us_big = pf.filter_tune(big, 100, s=32, precision="f32", n=4)
+    assert f_big == 0 and "raw" not in us_big             # large shapes take the sweep, unmeasured
