@@ -264,6 +264,13 @@ typedef struct {
   double target_abs;
   double refine_shift;    /* shift c of P + cI in refinement passes after a stall;
                              0 = 0.06, < 0 = never shift                              */
+  int32_t refine_reserve; /* FP32 path: reserve Ritz blocks beyond the guard kept for
+                             the refinement set; 0 = 2, < 0 = none                    */
+  int32_t refine_full_set;/* nonzero: the reserve blocks are in the refinement set from
+                             the first pass (default: one joins per stalled pass)     */
+  double refine_guard_lock;/* refinement locks a pair outside the returned set (guard,
+                             reserve) once its residual is <= this x res_tol ||H||;
+                             0 = 10, < 0 = never (returned pairs lock at 0.5)          */
 } pf_solve_opts;
 
 typedef struct {

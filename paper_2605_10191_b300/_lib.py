@@ -31,7 +31,8 @@ class pf_solve_opts(C.Structure):
                 ("check_first", C.c_int32), ("check_every", C.c_int32), ("max_blocks", C.c_int32),
                 ("eta", C.c_double), ("tol", C.c_double), ("tol_f32", C.c_double), ("res_tol", C.c_double),
                 ("refine_passes", C.c_int32), ("refine_K", C.c_int32), ("seed", C.c_uint64),
-                ("use_abs_target", C.c_int32), ("target_abs", C.c_double), ("refine_shift", C.c_double)]
+                ("use_abs_target", C.c_int32), ("target_abs", C.c_double), ("refine_shift", C.c_double),
+                ("refine_reserve", C.c_int32), ("refine_full_set", C.c_int32), ("refine_guard_lock", C.c_double)]
 
 
 class pf_report(C.Structure):

@@ -591,7 +591,8 @@ struct Task {
     check_every = o.check_every > 0 ? o.check_every : std::max(1, (int)std::ceil(0.1 * m_est));
     qb = (nev_g + s - 1) / s;      // Ritz blocks extracted
     qpad = qb * s;
-    q_reserve = f32 ? 2 * s : 0;   // extra Ritz vectors kept for the refinement set
+    // extra Ritz vectors kept for the refinement set
+    q_reserve = f32 ? (o.refine_reserve < 0 ? 0 : (o.refine_reserve == 0 ? 2 : o.refine_reserve)) * s : 0;
     lam = o.use_abs_target ? o.target_abs : H->emin + target_eps * (H->emax - H->emin);
     lam_t = (lam - H->Ec) / H->dE;
     if (!(lam_t > -1.0 && lam_t < 1.0)) return PF_EINVAL;
@@ -790,15 +791,20 @@ struct Task {
       PF_TRY(aux64.alloc((size_t)2 * nb_total * H->D * s * 8, st));
       prev = max_res();
       phase = REFINE;
+      if (o.refine_full_set && nb < nb_total) {   // the reserve joins the set now
+        nb = nb_total;
+        res.resize(qb * s);                       // reserve columns have no residual yet
+      }
       return issue_refine_filter();
     }
     return finish();
   }
 
-  // Locking: returned pairs already within half the tolerance stay in the set but are not
-  // filtered; they move to the leading blocks (rounded down to whole blocks by keeping the
-  // worst of them active).  Columns without a residual yet (a reserve block just added) are
-  // active.  Each active block is one filter item with its own auxiliary pair.
+  // Locking: returned pairs already within half the tolerance (other pairs of the set within
+  // refine_guard_lock x the tolerance) stay in the set but are not filtered; they move to the
+  // leading blocks (rounded down to whole blocks by keeping the worst of them active).
+  // Columns without a residual yet (a reserve block just added) are active.  Each active block
+  // is one filter item with its own auxiliary pair.
   pf_status issue_refine_filter() {
     const double c_shift = o.refine_shift == 0.0 ? 0.06 : (o.refine_shift < 0.0 ? 0.0 : o.refine_shift);
     coeffs_r[0] = shifted ? a0 + c_shift : a0;
@@ -809,9 +815,16 @@ struct Task {
     double* HUd = HU.as<double>();
     std::vector<char> is_sel(q, 0);
     for (int j : sel) is_sel[j] = 1;
+    // Guard and reserve pairs only span the buffer the returned pairs converge against; once
+    // accurate to a few times the tolerance they stop being filtered too (a later pass unlocks
+    // any whose residual grows again).
+    const double glock = o.refine_guard_lock == 0.0 ? 10.0 : o.refine_guard_lock;
     std::vector<int> locked, active;
     for (int c = 0; c < q; ++c) {
-      if (c < (int)res.size() && is_sel[c] && res[c] <= 0.5 * res_tol * hnorm) locked.push_back(c);
+      const bool have = c < (int)res.size();
+      const bool lock_sel = have && is_sel[c] && res[c] <= 0.5 * res_tol * hnorm;
+      const bool lock_guard = have && !is_sel[c] && glock > 0 && res[c] <= glock * res_tol * hnorm;
+      if (lock_sel || lock_guard) locked.push_back(c);
       else active.push_back(c);
     }
     std::sort(locked.begin(), locked.end(), [&](int x, int y) { return res[x] < res[y]; });
