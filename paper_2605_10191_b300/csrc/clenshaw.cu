@@ -204,6 +204,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 8 : 6) clenshaw_step_ker
     const int64_t r1 = r0 + rows_per_cta < D ? r0 + rows_per_cta : D;
     for (int64_t row = r0 + threadIdx.x / G; row < r1; row += 256 / G)
       clenshaw_row<T, S, false, SP, B2M>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta);
+  } else if (rows_per_cta < 0) {   // grid-stride over row groups (a capped grid)
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+    for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; row < D; row += groups)
+      clenshaw_row<T, S, false, SP, B2M>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta);
   } else {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
     if (row < D) clenshaw_row<T, S, false, SP, B2M>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta);
@@ -212,60 +216,70 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 8 : 6) clenshaw_step_ker
 
 // Launch shape of a step over `rows` rows: FP32 steps use one wave of contiguous row ranges
 // (the FP32 step is bound by its neighbour gathers, which the ranges keep in L1); FP64 steps
-// are bound by the FP64 pipe and keep one row per thread group.
+// are bound by the FP64 pipe and keep one row per thread group.  cta_cap > 0 limits the CTAs
+// per SM (the grid is then one wave of that many per SM: ranges for FP32, a grid-stride loop
+// for FP64), leaving SM thread slots and registers to a kernel of another solve running
+// beside it.
 struct StepShape {
   unsigned grid;
   int64_t rows_per_cta;
 };
 template <typename T, int S, int SP, int B2M>
-static StepShape step_shape(int64_t rows) {
+static StepShape step_shape(int64_t rows, int cta_cap = 0) {
   using Sh = Shape<T, S>;
+  static const int nsm_occ[2] = {[] {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return nsm;
+  }(), [] {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, clenshaw_step_kernel<T, S, SP, B2M>, 256, 0);
+    return occ > 0 ? occ : 1;
+  }()};
+  const int per_sm = cta_cap > 0 ? std::min(nsm_occ[1], cta_cap) : nsm_occ[1];
+  const int64_t waves = (int64_t)nsm_occ[0] * per_sm;
   if constexpr (sizeof(T) == 4) {
-    static int waves = [] {
-      int dev = 0, nsm = 148, occ = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, clenshaw_step_kernel<T, S, SP, B2M>, 256, 0);
-      return nsm * (occ > 0 ? occ : 1);
-    }();
     const int64_t R = ceil_div(rows, waves);
     if (R > 256 / Sh::G) return StepShape{(unsigned)ceil_div(rows, R), R};
   }
-  return StepShape{(unsigned)ceil_div(rows * Sh::G, 256), 0};
+  const int64_t classic = ceil_div(rows * Sh::G, 256);
+  if (cta_cap > 0 && classic > waves) return StepShape{(unsigned)waves, -1};
+  return StepShape{(unsigned)classic, 0};
 }
 
 template <typename T, int S, int SP, int B2M>
 static void launch_step_form(int64_t D, const int64_t* rp, const int32_t* col, const T* val, const T* V, const T* B1,
-                             const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st) {
-  const StepShape sh = step_shape<T, S, SP, B2M>(D);
+                             const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st, int cta_cap) {
+  const StepShape sh = step_shape<T, S, SP, B2M>(D, cta_cap);
   clenshaw_step_kernel<T, S, SP, B2M><<<sh.grid, 256, 0, st>>>(D, rp, col, val, V, B1, B2, out, a, alpha, beta,
                                                               sh.rows_per_cta);
 }
 
 template <typename T, int S>
 static pf_status launch_step_s(int64_t D, const int64_t* rp, const int32_t* col, const T* val, const T* V, const T* B1,
-                               const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st) {
+                               const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
   const bool spmm = alpha != T(0);
   const bool hb2 = beta != T(0);
-  if (spmm && hb2) launch_step_form<T, S, 1, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
-  else if (spmm) launch_step_form<T, S, 1, 0>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
-  else if (hb2) launch_step_form<T, S, 0, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
-  else launch_step_form<T, S, 0, 0>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
+  if (spmm && hb2) launch_step_form<T, S, 1, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
+  else if (spmm) launch_step_form<T, S, 1, 0>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
+  else if (hb2) launch_step_form<T, S, 0, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
+  else launch_step_form<T, S, 0, 0>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
   PF_LAUNCH_CHECK("clenshaw_step_kernel");
   return PF_OK;
 }
 
 template <typename T>
 static pf_status launch_step(int s, int64_t D, const int64_t* rp, const int32_t* col, const T* val, const T* V,
-                             const T* B1, const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st) {
+                             const T* B1, const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
   switch (s) {
-    case 1: return launch_step_s<T, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
-    case 2: return launch_step_s<T, 2>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
-    case 4: return launch_step_s<T, 4>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
-    case 8: return launch_step_s<T, 8>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
-    case 16: return launch_step_s<T, 16>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
-    case 32: return launch_step_s<T, 32>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
-    case 64: return launch_step_s<T, 64>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st);
+    case 1: return launch_step_s<T, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 2: return launch_step_s<T, 2>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 4: return launch_step_s<T, 4>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 8: return launch_step_s<T, 8>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 16: return launch_step_s<T, 16>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 32: return launch_step_s<T, 32>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 64: return launch_step_s<T, 64>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
   }
   return PF_EINVAL;
 }
@@ -274,38 +288,38 @@ static bool valid_s(int s) { return s == 1 || s == 2 || s == 4 || s == 8 || s ==
 
 pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* col, const void* val, int prec, int s,
                             const void* V, const void* B1, const void* B2, void* out, double a, double alpha,
-                            double beta, cudaStream_t st) {
+                            double beta, cudaStream_t st, int cta_cap) {
   if (!valid_s(s) || D <= 0 || !V || !out) return PF_EINVAL;
   if (alpha != 0.0 && (!B1 || !val)) return PF_EINVAL;
   if (beta != 0.0 && !B2) return PF_EINVAL;
   if (beta != 0.0 && beta != 1.0) return PF_EINVAL;
   if (prec == PF_F64)
     return launch_step<double>(s, D, row_ptr, col, (const double*)val, (const double*)V, (const double*)B1,
-                               (const double*)B2, (double*)out, a, alpha, beta, st);
+                               (const double*)B2, (double*)out, a, alpha, beta, st, cta_cap);
   if (prec == PF_F32)
     return launch_step<float>(s, D, row_ptr, col, (const float*)val, (const float*)V, (const float*)B1,
-                              (const float*)B2, (float*)out, (float)a, (float)alpha, (float)beta, st);
+                              (const float*)B2, (float*)out, (float)a, (float)alpha, (float)beta, st, cta_cap);
   return PF_EINVAL;
 }
 
 // K-step recurrence.  b_i lives in aux[i & 1]: step i reads b_{i+1} = aux[(i+1)&1] and
 // overwrites b_{i+2} (= aux[i&1]) with b_i.
 pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs, const void*,
-                           int K, void* aux0, void* aux1, cudaStream_t st) {
+                           int K, void* aux0, void* aux1, cudaStream_t st, int cta_cap) {
   if (K < 1 || !coeffs) return PF_EINVAL;
   const void* val = prec == PF_F64 ? (const void*)H->val_t : (const void*)H->val32;
   void* aux[2] = {aux0, aux1};
   // i = K: b_K = a_K V
   PF_TRY(clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, s, V, nullptr, nullptr, aux[K & 1], coeffs[K], 0.0,
-                           0.0, st));
+                           0.0, st, cta_cap));
   for (int i = K - 1; i >= 1; --i) {
     const double beta = (i == K - 1) ? 0.0 : 1.0;
     PF_TRY(clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, s, V, aux[(i + 1) & 1], aux[i & 1], aux[i & 1],
-                             coeffs[i], 2.0, beta, st));
+                             coeffs[i], 2.0, beta, st, cta_cap));
   }
   // P V = a_0 V + H~ b_1 - b_2
   const double beta = (K >= 2) ? 1.0 : 0.0;
-  PF_TRY(clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, s, V, aux[1], aux[0], W, coeffs[0], 1.0, beta, st));
+  PF_TRY(clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, s, V, aux[1], aux[0], W, coeffs[0], 1.0, beta, st, cta_cap));
   return PF_OK;
 }
 
@@ -690,7 +704,7 @@ pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t
   const double a0 = it.coeffs_host ? it.coeffs_host[0] : 0.0;
   const double aK = it.coeffs_host ? it.coeffs_host[it.K] : 0.0;
   if (!(g.exec && g.K == it.K && g.V == it.V && g.W == it.W && g.aux0 == it.aux0 && g.aux1 == it.aux1 &&
-        g.prec == it.prec && g.s == it.s && g.H == it.H && g.a0 == a0 && g.aK == aK)) {
+        g.prec == it.prec && g.s == it.s && g.H == it.H && g.a0 == a0 && g.aK == aK && g.cap == it.cta_cap)) {
     g.reset();
     if (!it.coeffs_host || it.K < 1) return PF_EINVAL;
     if (it.prec == PF_F64) prepare_shapes<double>(it.s);
@@ -701,7 +715,8 @@ pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t
     pf_status rc = PF_OK;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      rc = filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, cap);
+      rc = filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, cap,
+                            it.cta_cap);
       e = cudaStreamEndCapture(cap, &g.graph);
     }
     g_kernel_launches.store(before);   // capture is not execution
@@ -711,7 +726,8 @@ pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t
       // no graph: the same launches go to the stream one by one
       g.reset();
       cudaGetLastError();
-      return filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, st);
+      return filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, st,
+                              it.cta_cap);
     }
     g.K = it.K;
     g.V = it.V;
@@ -723,6 +739,7 @@ pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t
     g.H = it.H;
     g.a0 = a0;
     g.aK = aK;
+    g.cap = it.cta_cap;
   }
   PF_COUNT(it.K + 1);
   PF_CUDA(cudaGraphLaunch(g.exec, st));

@@ -128,9 +128,10 @@ __device__ T block_sum(T v, T* sh /* >= 32 */) {
 
 // ---------------------------------------------------------------- cross-unit API
 // Clenshaw step on raw CSR arrays (clenshaw.cu)
+// cta_cap > 0 limits the step's CTAs per SM (room for another solve's kernels beside it).
 pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* col, const void* val,
                             int prec, int s, const void* V, const void* B1, const void* B2, void* out,
-                            double a, double alpha, double beta, cudaStream_t st);
+                            double a, double alpha, double beta, cudaStream_t st, int cta_cap = 0);
 // One filter application W = P(H~) V (K steps) with its own two auxiliary blocks.
 struct FilterItem {
   const Ham* H = nullptr;
@@ -144,6 +145,7 @@ struct FilterItem {
   void* aux1 = nullptr;
   const void* owner = nullptr;          // the solve the item belongs to (grouping only)
   struct FilterGraph* graph = nullptr;  // the owner's captured form of this application (async executor)
+  int cta_cap = 0;                      // CTAs per SM for its steps (0 = all that fit)
 };
 // A per-step sweep captured as a CUDA graph (chain of T kernel nodes), reused while the table
 // address, item count, step count and row total stay the same.
@@ -191,6 +193,7 @@ struct FilterGraph {
   const void* aux1 = nullptr;
   const Ham* H = nullptr;
   double a0 = 0, aK = 0;
+  int cap = 0;
   FilterGraph() = default;
   FilterGraph(const FilterGraph&) = delete;
   FilterGraph& operator=(const FilterGraph&) = delete;
@@ -200,7 +203,7 @@ struct FilterGraph {
 pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t st);
 // W = P V for a D x s block (K steps); aux buffers are two D x s blocks of the filter type.
 pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs_host,
-                           const void* coeffs_dev, int K, void* aux0, void* aux1, cudaStream_t st);
+                           const void* coeffs_dev, int K, void* aux0, void* aux1, cudaStream_t st, int cta_cap = 0);
 
 // Dense tall-skinny kernels (dense.cu).  Blocked storage: nb blocks, each D x s row-major,
 // block b at X + b*D*s.

@@ -1235,6 +1235,22 @@ struct AsyncExecutor {
       int64_t D, nnz;
       std::vector<std::pair<FilterItem, Live*>> items;
     };
+    // Overlap: while one solve runs its FP32 Lanczos phase and another its FP64 refinement,
+    // their large steps are capped at 3 (FP32) and 4 (FP64) CTAs per SM, which fit together
+    // in one SM's registers (3 x 256 x 40 + 4 x 256 x 32 of 65536) and thread slots, so the
+    // memory-bound and the FP64-bound steps share every SM instead of queueing for slots.
+    bool lanczos32 = false, refine64 = false;
+    for (const auto& l : live) {
+      if (!l.started || l.t->phase == Task::DONE) continue;
+      lanczos32 = lanczos32 || (l.t->phase == Task::LANCZOS && l.t->f32 && l.heavy);
+      refine64 = refine64 || (l.t->phase == Task::REFINE && l.heavy);
+    }
+    const bool overlap = lanczos32 && refine64;
+    for (Live* l : idle)
+      for (FilterItem& it : l->t->pending) {
+        const double blk = (double)it.H->D * it.s * (it.prec == PF_F64 ? 8 : 4);
+        it.cta_cap = (overlap && blk >= 16e6) ? (it.prec == PF_F64 ? 4 : 3) : 0;
+      }
     std::vector<Grp> grps;
     for (Live* l : idle)
       for (const FilterItem& it : l->t->pending) {

@@ -67,3 +67,21 @@ def test_full_size_fp32_path_equals_fp64_path(solved):
     hn = r32.report["hnorm"]
     assert r64.status == 0
     assert np.max(np.abs(np.sort(r32.evals) - np.sort(r64.evals))) <= 1e-10 * hn
+
+
+def test_full_size_overlapped_batch_equals_alone(pf, solved):
+    """Two full-size solves in one batch overlap on the device (the second's FP32 Lanczos phase
+    beside the first's FP64 refinement, with both kernels capped in CTAs per SM); each result
+    must equal the one-problem solve bit for bit."""
+    p, H, K, r32, _ = solved
+    p2 = pi.xxz_params(20, W=3.0, seed=2001)
+    H2 = pf.Hamiltonian.from_params(p2)
+    H2.spectral_bounds()
+    K2 = H2.choose_K(0.5, 100)
+    alone2 = H2.solve(0.5, 100, K2, block=32, precision="f32", return_vectors=False)
+    res = pf.solve_batch([dict(H=H, eps=0.5, nev=100, K=K), dict(H=H2, eps=0.5, nev=100, K=K2)], block=32,
+                         precision="f32", return_vectors=True)
+    assert [r.status for r in res] == [0, 0]
+    assert np.array_equal(res[0].evals, r32.evals) and np.array_equal(res[0].resid, r32.resid)
+    assert torch.equal(res[0].evecs, r32.evecs)
+    assert np.array_equal(res[1].evals, alone2.evals) and np.array_equal(res[1].resid, alone2.resid)
