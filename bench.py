@@ -49,8 +49,9 @@ def parse():
                     help="only time the fused Clenshaw step at the workload shape (profiling)")
     ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-pipeline", dest="pipeline", action="store_false",
-                    help="solve mode: one solve after another instead of the overlapped batch of all steps")
+    ap.add_argument("--pipeline", action="store_true",
+                    help="solve mode: the timed steps as one overlapped batch instead of one solve after another")
+    ap.add_argument("--no-pipeline", dest="pipeline", action="store_false")
     ap.add_argument("--L", type=int, default=L_SITES, help="solve mode: chain length (default: the L=20 workload)")
     ap.add_argument("--nev", type=int, default=NEV, help="solve mode: eigenpairs per solve")
     ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serving"],

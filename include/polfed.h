@@ -288,6 +288,8 @@ typedef struct {
   double ms_refine;            /* refinement passes (includes their FP64 filter time)  */
   double ms_total;
   double max_residual_unrefined; /* max ||Hu - Eu|| before any refinement pass         */
+  int32_t refine_active[8];    /* blocks filtered in refinement pass p (p < 8)         */
+  double refine_residual[8];   /* max ||Hu - Eu|| of the returned pairs after pass p   */
 } pf_report;
 
 /* Fill o with the defaults listed in pf_solve_opts.                                */

@@ -44,10 +44,15 @@ class pf_report(C.Structure):
                 ("max_residual", C.c_double), ("ms_filter_f32", C.c_double), ("ms_filter_f64", C.c_double),
                 ("ms_orth", C.c_double), ("ms_qr", C.c_double), ("ms_check", C.c_double),
                 ("ms_extract", C.c_double), ("ms_refine", C.c_double), ("ms_total", C.c_double),
-                ("max_residual_unrefined", C.c_double)]
+                ("max_residual_unrefined", C.c_double), ("refine_active", C.c_int32 * 8),
+                ("refine_residual", C.c_double * 8)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if not isinstance(v, (int, float)) else v
+        return out
 
 
 class pf_filter_item(C.Structure):

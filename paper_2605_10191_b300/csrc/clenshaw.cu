@@ -176,8 +176,10 @@ __device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_
     Vec<T, E> q;
     if constexpr (L2ONLY) q = ld_l2<T, E>(B2 + off);
     else q = ld_plain<T, E>(B2 + off);
+    // beta is 0 or 1; with the B2 term known present it is 1, so -beta q is -q (the same bits
+    // as the run-time form, where 1 * q is exact)
 #pragma unroll
-    for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], fma(a, v.x[e], -(beta * q.x[e])));
+    for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], fma(a, v.x[e], B2M > 0 ? -q.x[e] : -(beta * q.x[e])));
   } else {
 #pragma unroll
     for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], a * v.x[e]);

@@ -890,6 +890,10 @@ struct Task {
     clk->mark(4);
     S.rep.ms_filter_f64 += clk->ms(2, 3);
     S.rep.ms_refine += clk->ms(2, 4);
+    if (passes < 8) {
+      S.rep.refine_active[passes] = na;
+      S.rep.refine_residual[passes] = max_res();
+    }
     ++passes;
     const double cur = max_res();
     if (cur <= res_tol * hnorm || passes >= max_pass) return finish();
