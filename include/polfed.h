@@ -262,8 +262,8 @@ typedef struct {
   uint64_t seed;          /* start block: v[r,c] = SplitMix64(seed, r*s+c) - 1/2     */
   int32_t use_abs_target; /* nonzero: target is target_abs (absolute energy)         */
   double target_abs;
-  double refine_shift;    /* shift c of P + cI in refinement passes after a stall;
-                             0 = 0.06, < 0 = never shift                              */
+  double refine_shift;    /* shift c of P + cI in refinement passes after the first;
+                             0 = 0.05, < 0 = never shift                              */
   int32_t refine_reserve; /* FP32 path: reserve Ritz blocks beyond the guard kept for
                              the refinement set; 0 = 2, < 0 = none                    */
   int32_t refine_full_set;/* nonzero: the reserve blocks are in the refinement set from

@@ -528,7 +528,6 @@ struct Task {
   LanczosResult R;
   int nb = 0, nb_total = 0, passes = 0, max_pass = 0, Kr = 0, Lb = 0, na = 0;
   double prev = 0, a0 = 0;
-  bool shifted = false;
   DevBuf U, HU, aux64;
   std::vector<double> E, res;
   std::vector<int> sel;
@@ -775,12 +774,13 @@ struct Task {
     // FP64 refinement for the FP32 filter: subspace iteration U <- (P(H~) + c I) U on the
     // active blocks, Cholesky QR, Rayleigh-Ritz in H.  An error component on eigenvalue k
     // shrinks by |P_k + c| / (P_j + c) per pass for wanted pair j.  The first pass is
-    // unshifted (c = 0), which removes the far bulk (P ~ 0) fastest.  If a pass reduces the
-    // residual less than 10x, the remaining error sits where |P| is comparable to the edge
-    // pairs' P: the filter's negative sidelobe (minimum ~ -0.22) or positive values just
-    // outside the set.  Then one reserve block joins the set and later passes use c = 0.06
-    // (option refine_shift), which halves the contraction factor on the negative sidelobe
-    // at the cost of the far bulk.
+    // unshifted (c = 0), which removes the far bulk (P ~ 0) fastest.  What remains after it
+    // sits where |P| is comparable to the edge pairs' P (~0.6): the filter's negative sidelobe
+    // (minimum ~ -0.22) and the positive values just outside the set (second peak ~0.13).
+    // Later passes use c = 0.05 (option refine_shift), which makes the two contraction
+    // factors about equal, (0.22 - c)/(0.6 + c) ~ (0.13 + c)/(0.6 + c) ~ 0.27, against 0.36
+    // unshifted; the far bulk, already gone, then shrinks only by c/(0.6 + c).  A pass that
+    // gains less than 10x also adds one reserve block to the set.
     max_pass = o.refine_passes < 0 ? 0 : (o.refine_passes == 0 ? 8 : o.refine_passes);
     Kr = o.refine_K > 0 ? o.refine_K : K;
     if (f32 && max_res() > res_tol * hnorm && max_pass > 0) {
@@ -806,8 +806,8 @@ struct Task {
   // Columns without a residual yet (a reserve block just added) are active.  Each active block
   // is one filter item with its own auxiliary pair.
   pf_status issue_refine_filter() {
-    const double c_shift = o.refine_shift == 0.0 ? 0.06 : (o.refine_shift < 0.0 ? 0.0 : o.refine_shift);
-    coeffs_r[0] = shifted ? a0 + c_shift : a0;
+    const double c_shift = o.refine_shift == 0.0 ? 0.05 : (o.refine_shift < 0.0 ? 0.0 : o.refine_shift);
+    coeffs_r[0] = passes > 0 ? a0 + c_shift : a0;
     PF_CUDA(cudaMemcpyAsync(coeffr_dev.p, coeffs_r.data(), (size_t)(Kr + 1) * 8, cudaMemcpyHostToDevice, st));
     const int q = nb * s;
     const int64_t DS = H->D * s;
@@ -897,10 +897,7 @@ struct Task {
     ++passes;
     const double cur = max_res();
     if (cur <= res_tol * hnorm || passes >= max_pass) return finish();
-    if (cur > 0.1 * prev) {
-      shifted = true;
-      if (nb < nb_total) ++nb;   // the reserve block is already in place in U
-    }
+    if (cur > 0.1 * prev && nb < nb_total) ++nb;   // the reserve block is already in place in U
     prev = cur;
     return issue_refine_filter();
   }
