@@ -54,7 +54,9 @@ def parse():
     ap.add_argument("--no-pipeline", dest="pipeline", action="store_false")
     ap.add_argument("--L", type=int, default=L_SITES, help="solve mode: chain length (default: the L=20 workload)")
     ap.add_argument("--nev", type=int, default=NEV, help="solve mode: eigenpairs per solve")
-    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serving"],
+    ap.add_argument("--config", type=int, default=3, choices=[1, 3, 4],
+                    help="model mode: workload 1 (XXZ L=12), 3 (quantum sun N=3 L=15) or 4 (Hubbard L=12)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serving", "model"],
                     help="solve: the L=20 workload; batch: many small solves together vs one at a time; "
                          "serving: a Poisson request stream through the continuous-batching server")
     ap.add_argument("--batch-n", type=int, default=32)
@@ -465,6 +467,67 @@ def run_batch(args):
     print(json.dumps(out))
 
 
+def run_model(args):
+    """One of the other workloads (quantum sun, Hubbard, small XXZ): solves of seeded realisations."""
+    import numpy as np
+    import torch
+    import pf_inputs as pi
+    import paper_2605_10191_b300 as pf
+    torch.cuda.set_device(0)
+    c = pi.CONFIGS[args.config]
+    if c["model"] == "qsun":
+        mk = lambda r: pi.qsun_params(N=c["N"], L=c["L"], g0=c["g0"], alpha=c["alpha"], gamma=c["gamma"],
+                                      seed=pi.config_seed(args.config, r))
+    elif c["model"] == "hubbard":
+        mk = lambda r: pi.hubbard_params(c["L"], c["N_up"], c["N_dn"], t=c["t"], U=c["U"], W=c["W"],
+                                         seed=pi.config_seed(args.config, r))
+    else:
+        mk = lambda r: pi.xxz_params(c["L"], W=c["W"], seed=pi.config_seed(args.config, r))
+    prec = args.precision
+    nev, s, eps = c["nev"], c["block"], c["eps"]
+
+    def one(r):
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        H = pf.Hamiltonian.from_params(mk(r))
+        H.spectral_bounds()
+        K = H.choose_K(eps, nev)
+        res = H.solve(eps, nev, K, block=s, precision=prec, return_vectors=False, raise_on_notconv=False)
+        e1.record(st)
+        e1.synchronize()
+        hn = res.report["hnorm"]
+        return dict(ms=e0.elapsed_time(e1), good=int(np.sum(res.resid <= RES_TOL * hn)), rep=res.report, K=K, D=H.D,
+                    nnz=H.nnz)
+
+    for r in range(args.warmup):
+        one(r)
+    with ClockSampler(0) as clocks:
+        rec = [one(args.warmup + r) for r in range(args.steps)]
+    t = sum(x["ms"] for x in rec) / 1e3
+    good = sum(x["good"] for x in rec)
+    st32 = sum(x["rep"]["filter_steps_f32"] for x in rec)
+    st64 = sum(x["rep"]["filter_steps_f64"] for x in rec)
+    w = 4 if prec == "f32" else 8
+    D, nnz = rec[0]["D"], rec[0]["nnz"]
+    out = {"metric": METRIC, "mode": "model", "value": good / t, "unit": "eigenpairs/s", "higher_is_better": True,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(rec), "dtype": "f32+f64" if prec == "f32" else "f64",
+           "data": "synthetic", "config": {"workload": c["name"], "D": D, "nnz": nnz, "nev": nev, "block": s,
+                                           "target_eps": eps, "K": [x["K"] for x in rec]},
+           "eigenpairs_at_tol": good, "solves": len(rec), "clocks": clocks.summary(),
+           "phases_ms": {k: statistics.mean(x["rep"][k] for x in rec)
+                         for k in ("ms_filter_f32", "ms_filter_f64", "ms_orth", "ms_qr", "ms_check", "ms_extract",
+                                   "ms_refine", "ms_total")}}
+    if st32:
+        per = sum(x["rep"]["ms_filter_f32"] for x in rec) / st32
+        byt = step_bytes(D, nnz, s, 4)
+        out["step_f32"] = {"us": 1e3 * per, "GBps": byt / per / 1e6, "alg_bytes": byt}
+    if st64:
+        per = sum(x["rep"]["ms_filter_f64"] for x in rec) / st64
+        out["step_f64"] = {"us_per_block_step": 1e3 * per, "TFLOPs": (2.0 * nnz * s + 3.0 * D * s) / per / 1e9}
+    print(json.dumps(out))
+
+
 def run_serving(args):
     """Poisson request stream through the server vs plain FP64 solves one at a time."""
     import numpy as np
@@ -534,6 +597,8 @@ def main():
         run_batch(args)
     elif args.mode == "serving":
         run_serving(args)
+    elif args.mode == "model":
+        run_model(args)
     else:
         run_ours(args)
 
