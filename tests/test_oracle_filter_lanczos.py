@@ -187,3 +187,90 @@ def test_block_lanczos_invariants():
         lhs = np.linalg.norm(ch.clenshaw_apply(Ht, u[:, None], a)[:, 0] - th[j] * u)
         rhs = np.linalg.norm(B @ T[M - s:, j])
         assert abs(lhs - rhs) < 1e-12
+
+
+# ---------------------------------------------------------------- KPM density of states
+from oracle import kpm
+
+
+def test_kpm_moments_with_basis_vectors_are_exact_traces():
+    """With the D vectors sqrt(D) e_i the stochastic trace is the exact trace: mu_n = sum_k T_n(E~_k)."""
+    H, w, _ = _xxz12()
+    Ec, dE = -0.16, 6.72
+    Ht = ch.rescale(H, Ec, dE)
+    wt = (w - Ec) / dE
+    N = 40
+    mu = kpm.moments(Ht, math.sqrt(H.D) * np.eye(H.D), N)
+    exact = np.array([np.sum(np.cos(n * np.arccos(wt))) for n in range(N)])
+    assert np.max(np.abs(mu - exact)) < 1e-9 * H.D
+
+
+def test_kpm_moments_equal_spectral_form():
+    """Same random vectors: recurrence moments = (1/R) sum_r v^T U diag(T_n(E~)) U^T v."""
+    H, w, U = _xxz12()
+    Ec, dE = -0.16, 6.72
+    Ht = ch.rescale(H, Ec, dE)
+    V = kpm.random_block(H.D, 8, 77)
+    mu = kpm.moments(Ht, V, 30)
+    P = U.T @ V
+    th = np.arccos((w - Ec) / dE)
+    ref = np.array([np.sum(np.cos(n * th)[:, None] * P * P) / 8 for n in range(30)])
+    assert np.max(np.abs(mu - ref)) < 1e-9 * H.D
+
+
+def test_random_block_statistics():
+    V = kpm.random_block(20000, 4, 5)
+    assert abs(V.mean()) < 0.02 and abs(V.var() - 1.0) < 0.02
+
+
+def test_jackson_kernel_values():
+    g = kpm.jackson(64)
+    assert abs(g[0] - 1.0) < 1e-14
+    assert np.all(np.diff(g) < 0) and g[-1] > 0
+    # N = 1: g_0 = [2 cos 0 + 0]/2 = 1
+    assert abs(kpm.jackson(1)[0] - 1.0) < 1e-15
+
+
+def test_kpm_dos_integrates_to_D_and_tracks_exact_density():
+    H, w, _ = _xxz12()
+    Ec, dE = -0.16, 6.72
+    Ht = ch.rescale(H, Ec, dE)
+    wt = (w - Ec) / dE
+    mu = np.array([np.sum(np.cos(n * np.arccos(wt))) for n in range(60)])
+    # integral over [-1, 1] with x = cos(t): int rho dx = mu_0 g_0 (the T_n, n >= 1, integrate to 0)
+    t = (np.arange(20000) + 0.5) * math.pi / 20000
+    integ = np.sum(kpm.dos_kpm(np.cos(t), mu) * np.sin(t)) * math.pi / 20000
+    assert abs(integ - H.D) < 1e-6 * H.D
+    # the smoothed density near the centre within 15 % of a histogram of the exact levels
+    lo, hi = -0.05, 0.05
+    count = np.sum((wt > lo) & (wt < hi))
+    xs = np.linspace(lo, hi, 201)
+    est = np.trapezoid(kpm.dos_kpm(xs, mu), xs)
+    assert abs(est - count) < 0.15 * count
+
+
+def test_kpm_maxdos_of_symmetric_spectrum_is_centre():
+    # XX chain without fields: the spectrum is symmetric about 0 (particle-hole), so is rho_KPM
+    H = hm.xxz_hamiltonian(pi.xxz_params(12, Delta=0.0, W=0.0, seed=1))
+    w, _ = dense.eigh_dense(H)
+    dE = 1.01 * max(abs(w[0]), abs(w[-1]))
+    wt = w / dE
+    mu = np.array([np.sum(np.cos(n * np.arccos(wt))) for n in range(40)])
+    assert np.max(np.abs(mu[1::2])) < 1e-9 * H.D
+    em = kpm.maxdos(mu)
+    assert abs(em) < 1e-3
+    assert kpm.offset_target(em, 0.0) == em
+    assert abs(kpm.offset_target(0.2, 1.0) - 1.0) < 1e-15 and abs(kpm.offset_target(0.2, -1.0) + 1.0) < 1e-15
+    assert abs(kpm.offset_target(0.2, 0.5) - 0.6) < 1e-15
+
+
+def test_kpm_choose_K_satisfies_condition():
+    H, w, _ = _xxz12()
+    Ec, dE = -0.16, 6.72
+    wt = (w - Ec) / dE
+    mu = np.array([np.sum(np.cos(n * np.arccos(wt))) for n in range(80)])
+    lam_t, nev_g = 0.05, 30
+    K = kpm.choose_K(lam_t, nev_g, mu)
+    delta = dos.window_halfwidth(nev_g, float(kpm.dos_kpm(lam_t, mu)[0]))
+    edge = lambda k: float(np.max(ch.filter_value(np.array([lam_t - delta, lam_t + delta]), lam_t, k)))
+    assert edge(K) <= dos.OMEGA < edge(K - 1)
