@@ -390,6 +390,29 @@ pf_status pf_server_take(pf_server* sv, int64_t id, double* evals, double* resid
 pf_status pf_server_memory(const pf_server* sv, int64_t* in_use, int64_t* budget);
 void pf_server_destroy(pf_server* sv);
 
+/* ---------------------------------------------------------------------------
+ * Kernel polynomial method for the density of states (Sec. 3.3, Eq. dos_kpm, App. B).
+ * mu_n = Tr T_n(H~), n = 0..N-1, estimated as (1/R) sum_r <r| T_n(H~) |r> over the columns of a
+ * D x R random block with entries sqrt(12) (u - 1/2), u the start block's SplitMix64 uniforms
+ * (entry (i, r) from counter i R + r; zero mean, unit variance).  Two moments per FP64
+ * Clenshaw step (doubling: T_2n = 2 T_n^2 - 1, T_2n+1 = 2 T_n+1 T_n - T_1).
+ *   H: handle with H~ set.  R: 1, 2, 4, ..., 64.  mu: host [N].  Synchronises.
+ * Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ENOMEM, PF_ECUDA.                    */
+pf_status pf_kpm_moments(pf_ham* H, int32_t N, int32_t R, uint64_t seed, double* mu, pf_stream_t stream);
+/* rho_KPM(x) = [mu_0 g_0 + 2 sum_{n=1}^{N-1} mu_n g_n T_n(x)] / (pi sqrt(1 - x^2)) with the
+ * Jackson kernel g_n, at nx points x in (-1, 1) (host arrays).  Errors: PF_EINVAL.     */
+pf_status pf_kpm_dos(const double* mu, int32_t N, const double* x, int32_t nx, double* rho);
+/* Targets that need the density (Sec. 5.2): E~_maxdos = argmax of rho_KPM on a grid of 4001
+ * points in [-0.999, 0.999]; lam_t = E~_maxdos + eta (1 - E~_maxdos) for eta >= 0,
+ * E~_maxdos + eta (E~_maxdos + 1) for eta < 0 (eta = 0 is :maxdos, (:offset, eta) otherwise).
+ * Errors: PF_EINVAL (eta outside [-1, 1]).                                          */
+pf_status pf_kpm_target(const double* mu, int32_t N, double eta, double* lam_t);
+/* K from Eq. condition_for_K with rho(lam~) from KPM: delta = nev_g / (2 rho) (Eq. Nev,
+ * nev_g = ceil(1.5 nev)), then the smallest K in [K_approx/2, 2 K_approx] whose filter is at
+ * most Omega = sin(2.655)/2.655 at both window edges lam~ +- delta (bisection).
+ * Errors: PF_EINVAL (rho <= 0, lam_t outside (-1, 1)).                               */
+pf_status pf_choose_K_kpm(const double* mu, int32_t N, double lam_t, int32_t nev, int32_t* K);
+
 /* Start block as the solve draws it: v[r,c] = uniform(SplitMix64(seed, r*s+c)) - 1/2,
  * uniform = top 53 bits * 2^-53 (Steele, Lea & Flood 2014).  out: device double [D*s]. */
 pf_status pf_start_block(int64_t D, int32_t s, uint64_t seed, double* out, pf_stream_t stream);

@@ -119,6 +119,10 @@ PROTOTYPES = {
     "pf_server_take": (i32, [vp, i64, P(dbl), P(dbl), P(pf_report), P(pf_request_info)]),
     "pf_server_memory": (i32, [vp, P(i64), P(i64)]),
     "pf_server_destroy": (None, [vp]),
+    "pf_kpm_moments": (i32, [vp, i32, i32, u64, P(dbl), vp]),
+    "pf_kpm_dos": (i32, [P(dbl), i32, P(dbl), i32, P(dbl)]),
+    "pf_kpm_target": (i32, [P(dbl), i32, dbl, P(dbl)]),
+    "pf_choose_K_kpm": (i32, [P(dbl), i32, dbl, i32, P(i32)]),
 }
 
 _lib = None

@@ -223,6 +223,19 @@ class Hamiltonian:
         check(lib().pf_choose_K(self.handle, float(eps), int(nev), C.byref(K), _stream(stream)), "pf_choose_K")
         return K.value
 
+    # ---- density of states (kernel polynomial method)
+    def kpm_moments(self, N=128, R=32, seed=7, stream=None):
+        """mu_n = Tr T_n(H~), n < N, estimated with R random vectors (pf_kpm_moments)."""
+        mu = np.zeros(N)
+        check(lib().pf_kpm_moments(self.handle, int(N), int(R), C.c_uint64(seed),
+                                   mu.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)), "pf_kpm_moments")
+        return mu
+
+    def target_abs(self, lam_t):
+        """Absolute energy of a rescaled target E~ (for solve(target_abs=...))."""
+        Ec, dE, _, _ = self.rescaled()
+        return Ec + dE * float(lam_t)
+
     # ---- kernels
     def clenshaw_step(self, V, B1, B2, out, a, alpha, beta, use_H=False, stream=None):
         prec = L.PF_F64 if V.dtype == torch.float64 else L.PF_F32
@@ -429,6 +442,34 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def kpm_dos(mu, x):
+    """rho_KPM at the points x (Jackson kernel)."""
+    m = np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
+    xs = np.ascontiguousarray(np.atleast_1d(np.asarray(x, dtype=np.float64)))
+    out = np.zeros_like(xs)
+    check(lib().pf_kpm_dos(m.ctypes.data_as(C.POINTER(C.c_double)), len(m), xs.ctypes.data_as(C.POINTER(C.c_double)),
+                           len(xs), out.ctypes.data_as(C.POINTER(C.c_double))), "pf_kpm_dos")
+    return out
+
+
+def kpm_target(mu, eta=0.0):
+    """Rescaled target E~: :maxdos for eta = 0, (:offset, eta) otherwise."""
+    m = np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
+    t = C.c_double()
+    check(lib().pf_kpm_target(m.ctypes.data_as(C.POINTER(C.c_double)), len(m), float(eta), C.byref(t)),
+          "pf_kpm_target")
+    return t.value
+
+
+def choose_K_kpm(mu, lam_t, nev):
+    """K from Eq. condition_for_K with the KPM density at lam_t."""
+    m = np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
+    K = C.c_int32()
+    check(lib().pf_choose_K_kpm(m.ctypes.data_as(C.POINTER(C.c_double)), len(m), float(lam_t), int(nev), C.byref(K)),
+          "pf_choose_K_kpm")
+    return K.value
 
 
 def filter_coefficients(lam_t, K, stream=None):
