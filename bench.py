@@ -365,7 +365,8 @@ def run_ours(args):
         fp64_peak = 148 * 4 * 2.032e9 / 1e12        # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
         roof64 = {"bound": "alu", "achieved": flops / per / 1e9, "peak": fp64_peak, "unit": "TFLOP/s",
                   "frac": flops / per / 1e9 / fp64_peak, "kernel": "clenshaw_step_kernel<double,32>",
-                  "us_per_block_step": 1e3 * per}
+                  "us_per_block_step": 1e3 * per, "traffic": ncu_traffic("clenshaw_f64_xxz_L20_s32"),
+                  "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz"}
     cpu = None
     if not args.no_cpu_baseline:
         dt, K0, n = oracle_sample(args.cpu_sample_steps)
