@@ -330,7 +330,8 @@ typedef struct {
 } pf_solve_item;
 /* Returns PF_OK when every item succeeded, else the first failing item's status; a failed
  * shared launch (PF_ECUDA, PF_ENOMEM) is reported in every item that was running.
- * Synchronises.                                                                    */
+ * `stream` is synchronised first; the solves then run on the library's pool of streams
+ * (process-wide, 16 streams) and are complete when the call returns.                */
 pf_status pf_polfed_solve_batch(pf_solve_item* items, int32_t n, pf_stream_t stream);
 
 /* Device bytes one solve holds at its peak: the Hamiltonian (CSR, FP64 and FP32 H~ copies,
@@ -369,7 +370,8 @@ typedef struct {
   double queue_ms;          /* submit to admission                                         */
   double latency_ms;        /* submit to completion                                        */
 } pf_request_info;
-/* cfg may be NULL (defaults).  stream: every call of the server enqueues work there.
+/* cfg may be NULL (defaults).  The resident solves run on the library's pool of streams
+ * (one per solve, shared round-robin beyond 16), not on `stream`, which is reserved.
  * Errors: PF_EINVAL, PF_ECUDA.                                                      */
 pf_status pf_server_create(const pf_server_config* cfg, pf_stream_t stream, pf_server** out);
 /* Queue one request; m and p are copied (host).  id: host output.

@@ -115,6 +115,137 @@ __global__ void rank2_kernel(double* Aw, int n, int j, const double* p) {
   *a -= v[l] * w[i] + w[l] * v[i];
 }
 
+// The whole tridiagonalisation in one launch: one thread-block cluster of CS CTAs walks the
+// columns and meets at the hardware cluster barrier (arrive.release / wait.acquire) between
+// the four phases of each column: the reflector (CTA 0, as house_kernel), p = tau A22 v (warps
+// of the whole cluster, as symv_kernel), w = p - (tau/2)(p.v) v (every CTA forms the dot in the
+// same order, then writes its slice, as wvec_kernel) and the rank-2 update (as rank2_kernel).
+// Data another CTA wrote is read with L2-only loads.  For H_L up to 1024 this replaces four
+// launches per column with one launch, so small solves (and many solves at once) are no longer
+// bound by launch latency.  No spin-waits: the barriers are hardware barriers.
+#define PF_TRI_NT 512
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(PF_TRI_NT) tridiag_cluster_kernel(double* Aw, int n, double* d, double* e,
+                                                                    double* tau, double* p) {
+  __shared__ double sh[32];
+  unsigned rank, cs;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(cs));
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int gwarp = (int)rank * (PF_TRI_NT / 32) + warp, nwarps = (int)cs * (PF_TRI_NT / 32);
+  const int gtid = (int)rank * PF_TRI_NT + tid, nthr = (int)cs * PF_TRI_NT;
+  (void)nthr;
+  for (int j = 0; j + 2 < n; ++j) {
+    const int m = n - j - 1;
+    double* x = Aw + (int64_t)j * n + j + 1;
+    if (rank == 0) {   // reflector: H x = beta e1, H = I - tau v v^T, v_0 = 1
+      double sig = 0.0;
+      for (int i = 1 + tid; i < m; i += PF_TRI_NT) {
+        const double xi = ldcg(x + i);
+        sig += xi * xi;
+      }
+      sig = block_sum(sig, sh);
+      const double alpha = ldcg(x);
+      double beta, t, scale;
+      if (sig == 0.0) {
+        beta = alpha;
+        t = 0.0;
+        scale = 0.0;
+      } else {
+        const double nrm = sqrt(alpha * alpha + sig);
+        beta = alpha <= 0.0 ? nrm : -nrm;
+        t = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      __syncthreads();
+      for (int i = 1 + tid; i < m; i += PF_TRI_NT) x[i] = ldcg(x + i) * scale;
+      if (tid == 0) {
+        x[0] = 1.0;
+        d[j] = ldcg(Aw + (int64_t)j * n + j);
+        e[j] = beta;
+        tau[j] = t;
+      }
+    }
+    cluster_sync_all();
+    const double tj = ldcg(tau + j);
+    // p_i = tau_j sum_l A22[l, i] v_l
+    for (int i = gwarp; i < m; i += nwarps) {
+      const double* col = Aw + (int64_t)(j + 1 + i) * n + j + 1;
+      double sacc = 0.0;
+      for (int l = lane; l < m; l += 32) sacc = fma(ldcg(col + l), ldcg(x + l), sacc);
+      sacc = warp_sum(sacc);
+      if (lane == 0) p[i] = tj * sacc;
+    }
+    cluster_sync_all();
+    // w = p - (tau/2)(p.v) v
+    double g = 0.0;
+    for (int i = tid; i < m; i += PF_TRI_NT) g = fma(ldcg(p + i), ldcg(x + i), g);
+    g = block_sum(g, sh);
+    const double c = 0.5 * tj * g;
+    for (int i = gtid; i < m; i += nthr) p[n + i] = ldcg(p + i) - c * ldcg(x + i);
+    cluster_sync_all();
+    // A22[l, i] -= v_l w_i + w_l v_i
+    const double* w = p + n;
+    for (int i = gwarp; i < m; i += nwarps) {   // column i of A22 per warp, rows across the lanes
+      double* col = Aw + (int64_t)(j + 1 + i) * n + j + 1;
+      const double wi = ldcg(w + i), vi = ldcg(x + i);
+      for (int l = lane; l < m; l += 32) col[l] = ldcg(col + l) - (ldcg(x + l) * wi + ldcg(w + l) * vi);
+    }
+    cluster_sync_all();
+  }
+}
+
+// Largest cluster (16, else 8, 4, 2) the device can run for the fused tridiagonalisation;
+// 0 when clusters are unavailable.
+static int tridiag_cluster_size() {
+  static const int cs = [] {
+    auto kern = tridiag_cluster_kernel;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int c : {16, 8, 4, 2}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)c, 1, 1);
+      cfg.blockDim = dim3(PF_TRI_NT, 1, 1);
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)c;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters >= 1) return c;
+      cudaGetLastError();
+    }
+    return 0;
+  }();
+  return cs;
+}
+
+static pf_status tridiag_cluster(double* Aw, int n, double* d, double* e, double* tau, double* p, int cs,
+                                 cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)cs, 1, 1);
+  cfg.blockDim = dim3(PF_TRI_NT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  PF_COUNT(1);
+  PF_CUDA(cudaLaunchKernelEx(&cfg, tridiag_cluster_kernel, Aw, n, d, e, tau, p));
+  return PF_OK;
+}
+
 __global__ void tri_finish_kernel(const double* Aw, int n, double* d, double* e, double* tau) {
   if (threadIdx.x != 0) return;
   if (n == 1) {
@@ -316,13 +447,18 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
   const int64_t nn = (int64_t)n * n;
   eig_copy_kernel<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>(A, lda, n, Aw);
   PF_LAUNCH_CHECK("eig_copy_kernel");
-  for (int j = 0; j + 2 < n; ++j) {
-    const int m = n - j - 1;
-    house_kernel<<<1, 256, 0, st>>>(Aw, n, j, d, e, tau);
-    symv_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Aw, n, j, tau, p);
-    wvec_kernel<<<1, 256, 0, st>>>(Aw, n, j, tau, p);
-    rank2_kernel<<<(unsigned)ceil_div((int64_t)m * m, 256), 256, 0, st>>>(Aw, n, j, p);
-    PF_COUNT(4);
+  const int ccs = n <= 1024 ? tridiag_cluster_size() : 0;
+  if (ccs > 0) {
+    PF_TRY(tridiag_cluster(Aw, n, d, e, tau, p, ccs, st));
+  } else {
+    for (int j = 0; j + 2 < n; ++j) {
+      const int m = n - j - 1;
+      house_kernel<<<1, 256, 0, st>>>(Aw, n, j, d, e, tau);
+      symv_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Aw, n, j, tau, p);
+      wvec_kernel<<<1, 256, 0, st>>>(Aw, n, j, tau, p);
+      rank2_kernel<<<(unsigned)ceil_div((int64_t)m * m, 256), 256, 0, st>>>(Aw, n, j, p);
+      PF_COUNT(4);
+    }
   }
   tri_finish_kernel<<<1, 32, 0, st>>>(Aw, n, d, e, tau);
   PF_LAUNCH_CHECK("tridiagonalisation");
