@@ -247,7 +247,7 @@ pf_status pf_filter_apply_noalloc(const pf_ham* H, int32_t prec, int32_t s, cons
  * ||H u - E u|| (Sec. 4.3), and, for PF_F32, FP64 refinement passes.
  */
 typedef struct {
-  int32_t block;          /* s: 1..64, power of two; 0 = 32                          */
+  int32_t block;          /* s: 1..64, power of two; 0 = 32; < 0 = pf_autotune_block  */
   int32_t precision;      /* pf_precision of the filter recurrence                   */
   int32_t nev_guard;      /* Ritz pairs converged; 0 = ceil(1.5 nev)                  */
   int32_t check_first;    /* first check at this block step; 0 = rule (see DESIGN)   */
@@ -354,7 +354,7 @@ pf_status pf_solve_footprint(int64_t D, int64_t nnz, int32_t nev, int32_t block,
  * drives a server.  Latencies are measured on the host's steady clock.               */
 typedef struct pf_server pf_server;
 typedef struct {
-  int32_t block;            /* s of every solve; 0 = 32                                    */
+  int32_t block;            /* s of every solve; 0 = 32; < 0 = autotuned per request        */
   int32_t precision;        /* pf_precision of the filter                                  */
   int32_t max_active;       /* most resident solves; 0 = 64                                */
   int64_t mem_budget_bytes; /* admission budget; 0 = 80% of free device memory at create  */
@@ -414,6 +414,16 @@ pf_status pf_kpm_target(const double* mu, int32_t N, double eta, double* lam_t);
  * most Omega = sin(2.655)/2.655 at both window edges lam~ +- delta (bisection).
  * Errors: PF_EINVAL (rho <= 0, lam_t outside (-1, 1)).                               */
 pf_status pf_choose_K_kpm(const double* mu, int32_t N, double lam_t, int32_t nev, int32_t* K);
+
+/* Block width from the autotuner: the step kernel is timed (8 steps on scratch blocks) for
+ * s = 8, 16, 32, 64 and the width with the smallest predicted Lanczos filter time,
+ * ceil(expectedkrylovdim(nev_g, s, 1) / s) x t_step(s) (Sec. 5.5's Krylov-size fit, nev_g =
+ * ceil(1.5 nev)), is returned; widths above nev_g (and above D/2) are skipped.  Timings are
+ * cached per (device, D, nnz, precision).  A solve with block < 0 uses this choice.
+ *   step_us, cost: host [4] (may be NULL): measured step time and predicted cost per candidate
+ *   (0 = skipped).  Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ENOMEM, PF_ECUDA.   */
+pf_status pf_autotune_block(pf_ham* H, int32_t precision, int32_t nev, int32_t* block, double* step_us,
+                            double* cost, pf_stream_t stream);
 
 /* Start block as the solve draws it: v[r,c] = uniform(SplitMix64(seed, r*s+c)) - 1/2,
  * uniform = top 53 bits * 2^-53 (Steele, Lea & Flood 2014).  out: device double [D*s]. */

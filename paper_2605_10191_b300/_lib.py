@@ -123,6 +123,7 @@ PROTOTYPES = {
     "pf_kpm_dos": (i32, [P(dbl), i32, P(dbl), i32, P(dbl)]),
     "pf_kpm_target": (i32, [P(dbl), i32, dbl, P(dbl)]),
     "pf_choose_K_kpm": (i32, [P(dbl), i32, dbl, i32, P(i32)]),
+    "pf_autotune_block": (i32, [vp, i32, i32, P(i32), P(dbl), P(dbl), vp]),
 }
 
 _lib = None

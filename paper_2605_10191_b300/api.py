@@ -231,6 +231,15 @@ class Hamiltonian:
                                    mu.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)), "pf_kpm_moments")
         return mu
 
+    def autotune_block(self, nev, precision="f32", stream=None):
+        """(block width, {s: measured step us}, {s: predicted Lanczos filter cost}) from the autotuner."""
+        b = C.c_int32()
+        us, cost = (C.c_double * 4)(), (C.c_double * 4)()
+        check(lib().pf_autotune_block(self.handle, L.PF_F64 if precision == "f64" else L.PF_F32, int(nev),
+                                      C.byref(b), us, cost, _stream(stream)), "pf_autotune_block")
+        cands = (8, 16, 32, 64)
+        return b.value, {c: us[i] for i, c in enumerate(cands)}, {c: cost[i] for i, c in enumerate(cands) if cost[i] > 0}
+
     def target_abs(self, lam_t):
         """Absolute energy of a rescaled target E~ (for solve(target_abs=...))."""
         Ec, dE, _, _ = self.rescaled()

@@ -20,12 +20,14 @@
 #include <algorithm>
 #include <numeric>
 #include <chrono>
+#include <array>
 #include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
+#include <tuple>
 
 namespace pf {
 
@@ -502,6 +504,98 @@ static std::vector<int> nearest_sel(const std::vector<double>& E, double lam, in
   return o;
 }
 
+// ------------------------------------------------------------------ block-width autotuner
+// The block width s trades matrix reuse against Krylov size: one Clenshaw step over a D x s
+// block costs t(s) (measured here: 8 steps of the step kernel on scratch blocks, per
+// candidate), and the Krylov space needs about expectedkrylovdim(nev_g, s, 1) / s blocks of
+// K+1 steps (Sec. 5.5: (20.427 s + 1.696 nev_g) / s).  The choice minimises the predicted
+// filter time of the Lanczos stage, blocks(s) x t(s), over s in {8, 16, 32, 64} with s not above
+// the padded guard count.  Measured once per (device, D, nnz, precision).
+namespace {
+struct BlockKey {
+  int dev, prec;
+  int64_t D, nnz;
+  bool operator<(const BlockKey& o) const { return std::tie(dev, prec, D, nnz) < std::tie(o.dev, o.prec, o.D, o.nnz); }
+};
+std::mutex g_block_mu;
+std::map<BlockKey, std::array<double, 4>> g_block_us;
+}  // namespace
+
+static const int kBlockCand[4] = {8, 16, 32, 64};
+
+static pf_status measure_block_steps(const Ham* H, int prec, cudaStream_t st, std::array<double, 4>& us) {
+  int dev = 0;
+  PF_CUDA(cudaGetDevice(&dev));
+  const BlockKey key{dev, prec, H->D, H->nnz};
+  {
+    std::lock_guard<std::mutex> lock(g_block_mu);
+    auto f = g_block_us.find(key);
+    if (f != g_block_us.end()) {
+      us = f->second;
+      return PF_OK;
+    }
+  }
+  const size_t w = prec == PF_F64 ? 8 : 4;
+  const size_t blk = (size_t)H->D * 64 * w;
+  DevBuf buf;
+  PF_TRY(buf.alloc(3 * blk, st));
+  PF_CUDA(cudaMemsetAsync(buf.p, 0, 3 * blk, st));
+  unsigned char* b = buf.as<unsigned char>();
+  const void* val = prec == PF_F64 ? (const void*)H->val_t : (const void*)H->val32;
+  cudaEvent_t e0, e1;
+  PF_CUDA(cudaEventCreate(&e0));
+  PF_CUDA(cudaEventCreate(&e1));
+  pf_status rc = PF_OK;
+  for (int c = 0; c < 4 && rc == PF_OK; ++c) {
+    const int sc = kBlockCand[c];
+    auto step = [&] {
+      return clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, sc, b, b + blk, b + 2 * blk, b + 2 * blk, 0.5, 2.0,
+                               1.0, st);
+    };
+    rc = step();   // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 8 && rc == PF_OK; ++r) rc = step();
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    us[c] = 1e3 * ms / 8;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  PF_TRY(rc);
+  std::lock_guard<std::mutex> lock(g_block_mu);
+  g_block_us[key] = us;
+  return PF_OK;
+}
+
+static int expected_krylov_dim(int nev, int s, double eta);
+
+static pf_status autotune_block(const Ham* H, int prec, int nev, cudaStream_t st, int* s_out, double* us_out,
+                                double* cost_out) {
+  std::array<double, 4> us;
+  PF_TRY(measure_block_steps(H, prec, st, us));
+  const int nev_g = std::max(nev, (int)std::ceil(1.5 * nev));
+  double best = 0;
+  int bs = 0;
+  for (int c = 0; c < 4; ++c) {
+    const int sc = kBlockCand[c];
+    if (sc > 8 && sc > nev_g) break;                        // wider than the guard: no gain
+    if ((int64_t)sc * 2 > H->D) break;
+    const double blocks = std::ceil(expected_krylov_dim(nev_g, sc, 1.0) / (double)sc);
+    const double cost = blocks * us[c];
+    if (cost_out) cost_out[c] = cost;
+    if (bs == 0 || cost < best) {
+      best = cost;
+      bs = sc;
+    }
+  }
+  if (us_out)
+    for (int c = 0; c < 4; ++c) us_out[c] = us[c];
+  *s_out = bs ? bs : 8;
+  return PF_OK;
+}
+
 // ------------------------------------------------------------------ resumable solve
 // One POLFED solve as a resumable task.  The filter applications the task needs next are
 // listed in `pending`; an executor runs the pending applications of all active tasks
@@ -571,9 +665,14 @@ struct Task {
     if (!o.use_abs_target && !H->has_bounds) return PF_ESTATE;
     if (nev < 1 || nev > H->D || K < 1) return PF_EINVAL;
     if (!o.use_abs_target && !(target_eps >= 0.0 && target_eps <= 1.0)) return PF_EINVAL;
+    if (o.precision != PF_F64 && o.precision != PF_F32) return PF_EINVAL;
+    if (o.block < 0) {   // the autotuner picks the block width
+      if (!H->has_rescale) return PF_ESTATE;
+      PF_TRY(autotune_block(H, o.precision, nev, stream, &s, nullptr, nullptr));
+      o.block = s;
+    }
     s = o.block > 0 ? o.block : 32;
     if (!(s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32 || s == 64)) return PF_EINVAL;
-    if (o.precision != PF_F64 && o.precision != PF_F32) return PF_EINVAL;
     f32 = o.precision == PF_F32;
     const double eta = o.eta > 0 ? o.eta : 1.5;
     tol = f32 ? (o.tol_f32 > 0 ? o.tol_f32 : 1e-7) : (o.tol > 0 ? o.tol : 1e-10);
@@ -1658,8 +1757,8 @@ pf_status pf_server_create(const pf_server_config* cfg, pf_stream_t stream, pf_s
   memset(&c, 0, sizeof(c));
   if (cfg) c = *cfg;
   if (c.block == 0) c.block = 32;
-  if (!(c.block == 1 || c.block == 2 || c.block == 4 || c.block == 8 || c.block == 16 || c.block == 32 ||
-        c.block == 64))
+  if (!(c.block < 0 || c.block == 1 || c.block == 2 || c.block == 4 || c.block == 8 || c.block == 16 ||
+        c.block == 32 || c.block == 64))
     return PF_EINVAL;
   if (c.precision != PF_F64 && c.precision != PF_F32) return PF_EINVAL;
   if (c.max_active <= 0) c.max_active = 64;
@@ -1686,7 +1785,8 @@ pf_status pf_server_submit(pf_server* sv, const pf_model* m, const pf_params* p,
   if (D < 1 || nev > D) return PF_EINVAL;
   r->eps = target_eps;
   r->nev = nev;
-  r->foot = ham_bytes(D, model_nnz_bound(*m, D)) + solve_state_bytes(D, sv->cfg.block, nev, sv->cfg.precision == PF_F32);
+  const int sb = sv->cfg.block > 0 ? sv->cfg.block : 32;   // autotuned widths are estimated at 32
+  r->foot = ham_bytes(D, model_nnz_bound(*m, D)) + solve_state_bytes(D, sb, nev, sv->cfg.precision == PF_F32);
   r->id = sv->next_id++;
   r->t_submit = now_ms();
   *id = r->id;
@@ -1734,6 +1834,20 @@ pf_status pf_server_memory(const pf_server* sv, int64_t* in_use, int64_t* budget
 }
 
 void pf_server_destroy(pf_server* sv) { delete sv; }
+
+pf_status pf_autotune_block(pf_ham* hh, int32_t precision, int32_t nev, int32_t* block, double* step_us,
+                            double* cost, pf_stream_t stream) {
+  Ham* H = reinterpret_cast<Ham*>(hh);
+  if (!H || !block || nev < 1) return PF_EINVAL;
+  if (precision != PF_F64 && precision != PF_F32) return PF_EINVAL;
+  if (!H->has_rescale) return PF_ESTATE;
+  int s = 0;
+  if (cost)
+    for (int c = 0; c < 4; ++c) cost[c] = 0.0;
+  PF_TRY(autotune_block(H, precision, nev, (cudaStream_t)stream, &s, step_us, cost));
+  *block = s;
+  return PF_OK;
+}
 
 pf_status pf_start_block(int64_t D, int32_t s, uint64_t seed, double* out, pf_stream_t stream) {
   if (D < 1 || s < 1 || !out) return PF_EINVAL;

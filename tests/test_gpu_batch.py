@@ -197,3 +197,28 @@ def test_filter_tune_reports(pf):
     big.spectral_bounds()
     f_big, us_big = pf.filter_tune(big, 100, s=32, precision="f32", n=4)
     assert f_big == 0 and "raw" not in us_big             # large shapes take the sweep, unmeasured
+
+
+def test_block_autotuner(pf):
+    H = pf.Hamiltonian.from_params(pi.xxz_params(14, W=2.0, seed=1951))
+    H.spectral_bounds()
+    s, us, cost = H.autotune_block(20, precision="f32")
+    assert s in (8, 16, 32, 64) and all(v > 0 for v in us.values())
+    assert cost[s] == min(cost.values())                  # the predicted cheapest width
+    assert all(c <= 30 for c in cost)                     # no width above nev_g = 30
+    assert H.autotune_block(20, precision="f32")[0] == s  # cached timings, same choice
+
+
+def test_solve_with_autotuned_block_matches_dense(pf):
+    p = pi.xxz_params(12, W=2.0, seed=1001)
+    Ho = oh.build(p)
+    w, _ = dense.eigh_dense(Ho)
+    hn = max(abs(w[0]), abs(w[-1]))
+    H = pf.Hamiltonian.from_params(p)
+    H.spectral_bounds()
+    s, _, _ = H.autotune_block(10, precision="f64")
+    K = H.choose_K(0.5, 10)
+    res = H.solve(0.5, 10, K, block=-1, precision="f64")
+    assert res.status == 0 and res.report["krylov_dim"] % s == 0
+    sel = dense.nearest(w, res.report["lambda_"], 10)
+    assert np.max(np.abs(res.evals - w[sel])) <= 1e-10 * hn and np.max(res.resid) <= 1e-9 * hn
