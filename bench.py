@@ -76,6 +76,24 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def realisation(rank, world, i):
+    """Realisation solved by `rank` at step i: ranks take disjoint realisations each step (replicas)."""
+    return (rank + i * world) % len(W_LIST)
+
+
+def combine_ranks(times_max, counts_sum, world, device):
+    """Whole-job numbers: times are the max over ranks, counts the sum (no-op for one rank)."""
+    if world <= 1:
+        return list(times_max), list(counts_sum)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(times_max), device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    g = torch.tensor(list(counts_sum), device=device, dtype=torch.float64)
+    dist.all_reduce(g, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t], [int(x) for x in g]
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -260,7 +278,7 @@ def run_ours(args):
     pinned = torch.empty((NEV, math.comb(L_SITES, L_SITES // 2)), dtype=torch.float64, pin_memory=True)
 
     def one_step(i, record):
-        r = (rank + i * world) % len(W_LIST)
+        r = realisation(rank, world, i)
         p = pi.xxz_params(L_SITES, W=W_LIST[r], seed=SEED0 + r)
         st = torch.cuda.current_stream()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -289,7 +307,7 @@ def run_ours(args):
         ev[0].record(st)
         probs, meta = [], []
         for i in range(first, first + count):
-            r = (rank + i * world) % len(W_LIST)
+            r = realisation(rank, world, i)
             H = pf.Hamiltonian.from_params(pi.xxz_params(L_SITES, W=W_LIST[r], seed=SEED0 + r))
             H.spectral_bounds()
             K = H.choose_K(EPS, NEV)
@@ -331,14 +349,7 @@ def run_ours(args):
     dev_s = sum(x["dev_ms"] for x in rec) / 1e3
     e2e_s = sum(x["e2e_ms"] for x in rec) / 1e3
     good = sum(x["good"] for x in rec)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([dev_s, e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        g = torch.tensor([good, launches], device="cuda", dtype=torch.float64)
-        dist.all_reduce(g, op=dist.ReduceOp.SUM)
-        dev_s, e2e_s = float(t[0]), float(t[1])
-        good, launches = int(g[0]), int(g[1])
+    (dev_s, e2e_s), (good, launches) = combine_ranks((dev_s, e2e_s), (good, launches), world, "cuda")
     if rank != 0:
         return
     D, nnz = rec[0]["D"], rec[0]["nnz"]
