@@ -258,7 +258,7 @@ typedef struct {
   double tol_f32;         /* same for the FP32 filter stage; 0 = 1e-7                */
   double res_tol;         /* final acceptance ||Hu - Eu|| <= res_tol ||H||; 0 = 1e-9 */
   int32_t refine_passes;  /* FP32 path: max FP64 filter passes; <0 = none, 0 = 8     */
-  int32_t refine_K;       /* degree of the refinement filter; 0 = K                  */
+  int32_t refine_K;       /* degree of the refinement filter; 0 = 0.7 K              */
   uint64_t seed;          /* start block: v[r,c] = SplitMix64(seed, r*s+c) - 1/2     */
   int32_t use_abs_target; /* nonzero: target is target_abs (absolute energy)         */
   double target_abs;
@@ -416,10 +416,11 @@ pf_status pf_kpm_target(const double* mu, int32_t N, double eta, double* lam_t);
 pf_status pf_choose_K_kpm(const double* mu, int32_t N, double lam_t, int32_t nev, int32_t* K);
 
 /* Block width from the autotuner: the step kernel is timed (8 steps on scratch blocks) for
- * s = 8, 16, 32, 64 and the width with the smallest predicted Lanczos filter time,
+ * s = 8, 16, 32, 64 and the width with the smallest predicted filter time is returned:
  * ceil(expectedkrylovdim(nev_g, s, 1) / s) x t_step(s) (Sec. 5.5's Krylov-size fit, nev_g =
- * ceil(1.5 nev)), is returned; widths above nev_g (and above D/2) are skipped.  Timings are
- * cached per (device, D, nnz, precision).  A solve with block < 0 uses this choice.
+ * ceil(1.5 nev)), plus for PF_F32 the FP64 refinement, 1.3 x 0.7 x ceil(nev_g / s) x t_step64(s)
+ * (per unit degree); widths above nev_g (and above D/2) are skipped.  Timings are cached per
+ * (device, D, nnz, precision).  A solve with block < 0 uses this choice.
  *   step_us, cost: host [4] (may be NULL): measured step time and predicted cost per candidate
  *   (0 = skipped).  Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ENOMEM, PF_ECUDA.   */
 pf_status pf_autotune_block(pf_ham* H, int32_t precision, int32_t nev, int32_t* block, double* step_us,
