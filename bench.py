@@ -190,9 +190,11 @@ def oracle_sample(nsteps):
     K = od.choose_K(lam_t, nev_g, H.D, mu, G)
     V = ol.start_block(H.D, BLOCK, 2024)
     a = oc.filter_coefficients(lam_t, nsteps)
-    t0 = time.perf_counter()
-    oc.clenshaw_apply(Ht, V, a)            # nsteps SpMM steps + the closing line
-    dt = (time.perf_counter() - t0) / (nsteps + 1)
+    from threadpoolctl import threadpool_limits
+    with threadpool_limits(limits=1):      # one core: the reported `cores`
+        t0 = time.perf_counter()
+        oc.clenshaw_apply(Ht, V, a)        # nsteps SpMM steps + the closing line
+        dt = (time.perf_counter() - t0) / (nsteps + 1)
     blocks = math.ceil(od.expected_krylov_dim(nev_g, BLOCK, 1.0) / BLOCK)
     return dt, K, blocks * (K + 1)
 
