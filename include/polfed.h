@@ -258,7 +258,8 @@ typedef struct {
   double tol_f32;         /* same for the FP32 filter stage; 0 = 1e-7                */
   double res_tol;         /* final acceptance ||Hu - Eu|| <= res_tol ||H||; 0 = 1e-9 */
   int32_t refine_passes;  /* FP32 path: max FP64 filter passes; <0 = none, 0 = 8     */
-  int32_t refine_K;       /* degree of the refinement filter; 0 = 0.7 K              */
+  int32_t refine_K;       /* degree of the refinement filter; 0 = 0.7 K for K >= 1000
+                             (back to K after a stalled pass), else K                  */
   uint64_t seed;          /* start block: v[r,c] = SplitMix64(seed, r*s+c) - 1/2     */
   int32_t use_abs_target; /* nonzero: target is target_abs (absolute energy)         */
   double target_abs;

@@ -884,10 +884,12 @@ struct Task {
     // unshifted; the far bulk, already gone, then shrinks only by c/(0.6 + c).  A pass that
     // gains less than 10x also adds one reserve block to the set.
     max_pass = o.refine_passes < 0 ? 0 : (o.refine_passes == 0 ? 8 : o.refine_passes);
-    // degree of the refinement filter: 0.7 K by default (measured at L=20, W = 1, 3, 5: the
-    // passes and blocks filtered stay the same as with K, and each pass costs 30 % less;
-    // 0.55 K needs extra passes)
-    Kr = o.refine_K > 0 ? o.refine_K : std::max(1, (int)(0.7 * K));
+    // degree of the refinement filter: 0.7 K by default when K >= 1000 (measured at L=20,
+    // W = 1, 3, 5: the passes and blocks filtered stay the same as with K, and each pass costs
+    // 30 % less; 0.55 K needs extra passes).  Low-degree filters (small sectors, targets near
+    // the spectral edge) keep K: there the wider lobe let a reserve block bring in a spurious
+    // pair (XXZ L=16, nev=100, K=114 stalled at 0.06 ||H||, and converges with K).
+    Kr = o.refine_K > 0 ? o.refine_K : (K >= 1000 ? (int)(0.7 * K) : K);
     if (f32 && max_res() > res_tol * hnorm && max_pass > 0) {
       coeffs_r.resize(Kr + 1);
       PF_TRY(filter_coefficients_dev(lam_t, Kr, coeffs_r.data(), st));
@@ -1003,6 +1005,15 @@ struct Task {
     const double cur = max_res();
     if (cur <= res_tol * hnorm || passes >= max_pass) return finish();
     if (cur > 0.1 * prev && nb < nb_total) ++nb;   // the reserve block is already in place in U
+    if (cur > 0.5 * prev && Kr < K && o.refine_K <= 0) {
+      // the shorter default degree stalled (its wider lobe separates the set's edge too little
+      // for this spectrum): the remaining passes use the Lanczos degree K
+      Kr = K;
+      coeffs_r.assign(Kr + 1, 0.0);
+      PF_TRY(filter_coefficients_dev(lam_t, Kr, coeffs_r.data(), st));
+      a0 = coeffs_r[0];
+      PF_TRY(coeffr_dev.alloc((size_t)(Kr + 1) * 8, st));
+    }
     prev = cur;
     return issue_refine_filter();
   }
