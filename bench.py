@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--kernel-only", action="store_true",
                     help="only time the fused Clenshaw step at the workload shape (profiling)")
-    ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64", "df64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pipeline", action="store_true",
                     help="solve mode: the timed steps as one overlapped batch instead of one solve after another")
@@ -190,8 +190,15 @@ def oracle_sample(nsteps):
     K = od.choose_K(lam_t, nev_g, H.D, mu, G)
     V = ol.start_block(H.D, BLOCK, 2024)
     a = oc.filter_coefficients(lam_t, nsteps)
-    from threadpoolctl import threadpool_limits
-    with threadpool_limits(limits=1):      # one core: the reported `cores`
+    # one core, the reported `cores`: scipy's CSR x dense product and numpy's elementwise
+    # operations run on one thread; threadpoolctl, where installed, also holds BLAS to one
+    try:
+        from threadpoolctl import threadpool_limits
+        one_core = threadpool_limits(limits=1)
+    except ImportError:
+        import contextlib
+        one_core = contextlib.nullcontext()
+    with one_core:
         t0 = time.perf_counter()
         oc.clenshaw_apply(Ht, V, a)        # nsteps SpMM steps + the closing line
         dt = (time.perf_counter() - t0) / (nsteps + 1)
@@ -237,9 +244,13 @@ def run_kernel_only(args):
     H = pf.Hamiltonian.from_params(p)
     H.spectral_bounds()
     D, s = H.D, BLOCK
-    dt = torch.float32 if args.kernel_precision == "f32" else torch.float64
+    dt = torch.float64 if args.kernel_precision == "f64" else torch.float32
+    shape = (D, s, 2) if args.kernel_precision == "df64" else (D, s)
     g = torch.Generator(device="cuda").manual_seed(1)
-    V, B1, B2 = (torch.rand(D, s, device="cuda", generator=g, dtype=dt) - 0.5 for _ in range(3))
+    V, B1, B2 = (torch.rand(*shape, device="cuda", generator=g, dtype=dt) - 0.5 for _ in range(3))
+    if args.kernel_precision == "df64":   # (hi, lo) pairs with |lo| below an ulp of hi
+        for X in (V, B1, B2):
+            X[..., 1] *= 2.0 ** -24 * X[..., 0]
     for _ in range(args.warmup):
         H.clenshaw_step(V, B1, B2, B2, 0.01, 2.0, 1.0)
     torch.cuda.synchronize()
@@ -253,7 +264,7 @@ def run_kernel_only(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
-    w = 4 if dt == torch.float32 else 8
+    w = 4 if args.kernel_precision == "f32" else 8
     byt = step_bytes(D, H.nnz, s, w)
     print(json.dumps({"kernel": f"clenshaw_step_{args.kernel_precision}_s32", "us_per_launch": 1e3 * ms,
                       "alg_bytes": byt, "GBps": byt / ms / 1e6, "launches": args.steps}))

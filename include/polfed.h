@@ -47,7 +47,17 @@ typedef enum {
 
 typedef enum { PF_MODEL_XXZ = 0, PF_MODEL_QSUN = 1, PF_MODEL_HUBBARD = 2 } pf_model_kind;
 typedef enum { PF_BC_PERIODIC = 0, PF_BC_OPEN = 1 } pf_boundary;
-typedef enum { PF_F64 = 0, PF_F32 = 1 } pf_precision;
+/* Arithmetic of a filter (Clenshaw) step.
+ *  PF_F64   double blocks, FP64 values and arithmetic.
+ *  PF_F32   float blocks, FP32 values and arithmetic.
+ *  PF_DF64  pair-float ("double-float", Dekker 1971): every entry is a pair of floats
+ *           (hi, lo), value hi + lo, stored interleaved (8 bytes per entry, a D x s block
+ *           is D x s x 2 floats, row-major); products are split exactly with FMA and sums
+ *           carried with Knuth's two-sum, so a step's relative rounding error is about
+ *           2^-47 (FP64 gives 2^-53) while it runs on the FP32 units.  The exponent
+ *           range is FP32's (|x| < 3.4e38): a recurrence on a spectrum inside [-1, 1]
+ *           stays within (K + 1) max|a_n| times the input's size.                  */
+typedef enum { PF_F64 = 0, PF_F32 = 1, PF_DF64 = 2 } pf_precision;
 
 /* Model description (paper App. A).
  *  XXZ (Eq. xxz): L sites, N up spins (S^z_tot sector), couplings J, Delta, fields h_i.
@@ -163,7 +173,8 @@ pf_status pf_choose_K(pf_ham* H, double target_eps, int32_t nev, int32_t* K, pf_
  * (b_i overwrites b_{i+2}); out must not alias V or B1.  alpha = 0 skips the SpMM
  * (B1 may then be NULL).  If use_H is nonzero the unscaled H is used instead of H~
  * (then only precision PF_F64 is allowed).
- *   prec: PF_F64 (double blocks, FP64 values) or PF_F32 (float blocks, FP32 values).
+ *   prec: PF_F64 (double blocks, FP64 values), PF_F32 (float blocks, FP32 values) or
+ *         PF_DF64 (pair-float blocks and values; a, alpha, beta are split into pairs).
  *   s   : block width, one of 1, 2, 4, 8, 16, 32, 64.
  * Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ECUDA.                             */
 pf_status pf_clenshaw_step(const pf_ham* H, int32_t prec, int32_t s, const void* V,
@@ -171,8 +182,9 @@ pf_status pf_clenshaw_step(const pf_ham* H, int32_t prec, int32_t s, const void*
                            double beta, int32_t use_H, pf_stream_t stream);
 
 /* W = P(H~) V for a D x s block: the whole recurrence, K steps, with two internal
- * D x s auxiliary blocks.  coeffs: host [K+1].  V and W are double blocks for
- * PF_F64; for PF_F32 they are float blocks.                                        */
+ * D x s auxiliary blocks.  coeffs: host [K+1] (FP64 for every precision).  V and W
+ * are double blocks for PF_F64, float blocks for PF_F32 and pair-float blocks
+ * (D x s x 2 floats) for PF_DF64.                                                  */
 pf_status pf_filter_apply(const pf_ham* H, int32_t prec, int32_t s, const void* V, void* W,
                           const double* coeffs, int32_t K, pf_stream_t stream);
 
@@ -272,6 +284,9 @@ typedef struct {
   double refine_guard_lock;/* refinement locks a pair outside the returned set (guard,
                              reserve) once its residual is <= this x res_tol ||H||;
                              0 = 10, < 0 = never (returned pairs lock at 0.5)          */
+  int32_t refine_precision;/* arithmetic of the refinement filter: PF_DF64 (pair-float,
+                             pf_default_opts) or PF_F64; the Ritz vectors, Gram-Schmidt,
+                             Rayleigh-Ritz and residuals stay FP64 either way          */
 } pf_solve_opts;
 
 typedef struct {

@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpolfed.so")
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ENOTCONV, PF_ETIMEOUT, PF_ECUDA, PF_ESTATE, PF_EBREAKDOWN = range(8)
 PF_MODEL_XXZ, PF_MODEL_QSUN, PF_MODEL_HUBBARD = 0, 1, 2
-PF_F64, PF_F32 = 0, 1
+PF_F64, PF_F32, PF_DF64 = 0, 1, 2
 PF_FORM_AUTO, PF_FORM_STEPS, PF_FORM_GRAPH = -1, 0, -2
 
 
@@ -32,7 +32,8 @@ class pf_solve_opts(C.Structure):
                 ("eta", C.c_double), ("tol", C.c_double), ("tol_f32", C.c_double), ("res_tol", C.c_double),
                 ("refine_passes", C.c_int32), ("refine_K", C.c_int32), ("seed", C.c_uint64),
                 ("use_abs_target", C.c_int32), ("target_abs", C.c_double), ("refine_shift", C.c_double),
-                ("refine_reserve", C.c_int32), ("refine_full_set", C.c_int32), ("refine_guard_lock", C.c_double)]
+                ("refine_reserve", C.c_int32), ("refine_full_set", C.c_int32), ("refine_guard_lock", C.c_double),
+                ("refine_precision", C.c_int32)]
 
 
 class pf_report(C.Structure):

@@ -2,7 +2,8 @@
 
 PyTorch supplies device memory (through the allocator hook) and streams.  Vector
 blocks are torch tensors of shape (D, s), row-major, float64 or float32, on the
-current CUDA device.
+current CUDA device; a pair-float block (PF_DF64) is a float32 tensor of shape
+(D, s, 2) holding (hi, lo) per entry.
 """
 import ctypes as C
 from dataclasses import dataclass
@@ -44,6 +45,24 @@ def _stream(stream=None):
 
 def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _block_prec(V):
+    """Filter precision of a vector block: float64 (D, s), float32 (D, s) or pairs (D, s, 2)."""
+    if V.dtype == torch.float64:
+        return L.PF_F64
+    if V.dtype == torch.float32 and V.dim() == 3 and V.shape[2] == 2:
+        return L.PF_DF64
+    return L.PF_F32
+
+
+_PREC_NAMES = {"f64": L.PF_F64, "f32": L.PF_F32, "df64": L.PF_DF64}
+
+
+def _prec_code(name):
+    if name not in _PREC_NAMES:
+        raise ValueError(f"unknown precision {name!r}")
+    return _PREC_NAMES[name]
 
 
 def _dbl_arr(x):
@@ -247,7 +266,7 @@ class Hamiltonian:
 
     # ---- kernels
     def clenshaw_step(self, V, B1, B2, out, a, alpha, beta, use_H=False, stream=None):
-        prec = L.PF_F64 if V.dtype == torch.float64 else L.PF_F32
+        prec = _block_prec(V)
         s = V.shape[1]
         check(lib().pf_clenshaw_step(self.handle, prec, s, _ptr(V), _ptr(B1), _ptr(B2), _ptr(out), float(a),
                                      float(alpha), float(beta), int(bool(use_H)), _stream(stream)),
@@ -255,7 +274,7 @@ class Hamiltonian:
         return out
 
     def filter_apply(self, V, coeffs, W=None, stream=None):
-        prec = L.PF_F64 if V.dtype == torch.float64 else L.PF_F32
+        prec = _block_prec(V)
         W = torch.empty_like(V) if W is None else W
         c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
         check(lib().pf_filter_apply(self.handle, prec, V.shape[1], _ptr(V), _ptr(W),
@@ -289,6 +308,8 @@ def _make_opts(block, precision, target_abs, opts):
     for k, v in opts.items():
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
+        if k == "refine_precision" and isinstance(v, str):
+            v = _prec_code(v)
         setattr(o, k, v)
     if target_abs is not None:
         o.use_abs_target = 1
@@ -306,7 +327,7 @@ def filter_apply_batch(items, form="auto", stream=None):
     if n == 0:
         return []
     V0 = items[0][1]
-    prec = L.PF_F64 if V0.dtype == torch.float64 else L.PF_F32
+    prec = _block_prec(V0)
     arr = (L.pf_filter_item * n)()
     keep, outs = [], []
     for j, (H, V, coeffs) in enumerate(items):
@@ -331,7 +352,7 @@ def filter_tune(H, K, s=32, precision="f32", n=1, stream=None):
     _install_torch_allocator()
     f = C.c_int32()
     us = (C.c_double * 8)()
-    check(lib().pf_filter_tune(H.handle, L.PF_F64 if precision == "f64" else L.PF_F32, int(s), int(K), int(n),
+    check(lib().pf_filter_tune(H.handle, _prec_code(precision), int(s), int(K), int(n),
                                C.byref(f), us, _stream(stream)), "pf_filter_tune")
     names = ["raw", "sweep", "sweep_copies", "c1", "c2", "c4", "c8", "c16"]
     return f.value, {k: us[i] for i, k in enumerate(names) if us[i] > 0}

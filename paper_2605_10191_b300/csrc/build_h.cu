@@ -443,8 +443,10 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
   H->val = (double*)dev_alloc(nnz * sizeof(double), st);
   H->val_t = (double*)dev_alloc(nnz * sizeof(double), st);
   H->val32 = (float*)dev_alloc(nnz * sizeof(float), st);
-  if (!H->col || !H->val || !H->val_t || !H->val32) {
+  H->val_df = (float2*)dev_alloc(nnz * sizeof(float2), st);
+  if (!H->col || !H->val || !H->val_t || !H->val32 || !H->val_df) {
     dev_free(H->col, st); dev_free(H->val, st); dev_free(H->val_t, st); dev_free(H->val32, st);
+    dev_free(H->val_df, st);
     dev_free(H->row_ptr, st);
     delete H;
     return PF_ENOMEM;
@@ -455,6 +457,7 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
   if (e != cudaSuccess) {
     set_cuda_error(e, "fill_kernel");
     dev_free(H->col, st); dev_free(H->val, st); dev_free(H->val_t, st); dev_free(H->val32, st);
+    dev_free(H->val_df, st);
     dev_free(H->row_ptr, st);
     delete H;
     return PF_ECUDA;
@@ -465,13 +468,15 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
 
 // ------------------------------------------------------------------ rescale and moments
 __global__ void rescale_kernel(int64_t D, const int64_t* rp, const int32_t* col, const double* val, double Ec,
-                               double dE, double* vt, float* v32) {
+                               double dE, double* vt, float* v32, float2* vdf) {
   int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= D) return;
   for (int64_t j = rp[row]; j < rp[row + 1]; ++j) {
     double x = (col[j] == row) ? (val[j] - Ec) / dE : val[j] / dE;
     vt[j] = x;
-    v32[j] = (float)x;
+    const float hi = (float)x;
+    v32[j] = hi;
+    vdf[j] = make_float2(hi, (float)(x - (double)hi));   // x - hi is exact in FP64
   }
 }
 
@@ -480,7 +485,7 @@ pf_status set_rescale(Ham* H, double Ec, double dE, cudaStream_t st) {
   H->Ec = Ec;
   H->dE = dE;
   rescale_kernel<<<(unsigned)ceil_div(H->D, 256), 256, 0, st>>>(H->D, H->row_ptr, H->col, H->val, Ec, dE, H->val_t,
-                                                                 H->val32);
+                                                                 H->val32, H->val_df);
   PF_LAUNCH_CHECK("rescale_kernel");
   H->has_rescale = 1;
   return PF_OK;
@@ -630,6 +635,7 @@ void pf_free_ham(pf_ham* hh) {
   dev_free(H->val, H->st);
   dev_free(H->val_t, H->st);
   dev_free(H->val32, H->st);
+  dev_free(H->val_df, H->st);
   delete H;
 }
 

@@ -19,8 +19,101 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
+
+// Pair-float entries per lane and the step kernel's resident CTAs per SM (64 registers).
+#ifndef PF_DF_E
+#define PF_DF_E 4
+#endif
+#ifndef PF_DF_MINB
+#define PF_DF_MINB 4
+#endif
 
 namespace pf {
+
+// ------------------------------------------------------------------ pair-float arithmetic
+// A value held as the unevaluated sum hi + lo of two floats (Dekker 1971; on GPUs, Thall 2006).
+// The step needs x * y + z only, built from two error-free transformations:
+//   two_prod: x y = p + e exactly, p = rn(x y), e = fma(x, y, -p);
+//   two_sum (Knuth): a + b = s + t exactly, s = rn(a + b), w = rn(s - a),
+//                    t = rn(rn(a - rn(s - w)) + rn(b - w)).
+// x * y + z keeps hi = two_sum(z.hi, p).s and lo = z.lo + (t + e + x.hi y.lo + x.lo y.hi)
+// (x.lo y.lo, below 2^-48 of the product, is dropped), so a chain of them is the compensated
+// dot product of Ogita, Rump and Oishi (2005): error about 2^-47 relative to the sum of the
+// terms' magnitudes.  Results stay unnormalised (|lo| may exceed half an ulp of hi) until a
+// step stores them.  Every operation is an _rn intrinsic, which the compiler neither
+// contracts into an FMA nor reorders: the transformations are exact only as written.
+struct __align__(8) df2 {
+  float hi, lo;
+  df2() = default;
+  __host__ __device__ constexpr df2(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ explicit constexpr df2(int x) : hi((float)x), lo(0.0f) {}
+  __host__ __device__ explicit df2(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+};
+
+__host__ __device__ __forceinline__ df2 operator-(df2 a) { return df2(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ bool operator!=(df2 a, df2 b) { return a.hi != b.hi || a.lo != b.lo; }
+__device__ __forceinline__ df2 operator*(df2 x, df2 y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return df2(p, e);
+}
+__device__ __forceinline__ df2 df_fma(df2 x, df2 y, df2 z) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  const float s = __fadd_rn(z.hi, p);
+  const float w = __fsub_rn(s, z.hi);
+  const float t = __fadd_rn(__fsub_rn(z.hi, __fsub_rn(s, w)), __fsub_rn(p, w));
+  return df2(s, __fadd_rn(z.lo, __fadd_rn(t, e)));
+}
+// two_sum(hi, lo): the stored form, |lo| <= half an ulp of hi
+__device__ __forceinline__ df2 df_norm(df2 a) {
+  const float s = __fadd_rn(a.hi, a.lo);
+  const float w = __fsub_rn(s, a.hi);
+  return df2(s, __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, w)), __fsub_rn(a.lo, w)));
+}
+
+template <typename T> constexpr bool is_df = std::is_same_v<T, df2>;
+// x * y + z in the step's arithmetic (one rounding for FP32 / FP64)
+template <typename T> __device__ __forceinline__ T fmadd(T x, T y, T z) {
+  if constexpr (is_df<T>) return df_fma(x, y, z);
+  else return ::fma(x, y, z);
+}
+template <typename T> __device__ __forceinline__ T stored(T x) {
+  if constexpr (is_df<T>) return df_norm(x);
+  else return x;
+}
+// Coefficient i of a device table: FP64 values, or for pair-float steps pairs (hi, lo) written
+// by the host (df2(double)), so that no step kernel executes an FP64 instruction.
+template <typename T> __device__ __forceinline__ T load_coeff(const double* c) {
+  if constexpr (is_df<T>) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(c));
+    return df2(v.x, v.y);
+  } else {
+    return (T)__ldg(c);
+  }
+}
+// Host: the device coefficient table of a precision (pairs for PF_DF64, else the values).
+void coeff_table_host(int prec, const double* c, int n, double* out) {
+  for (int i = 0; i < n; ++i) {
+    if (prec == PF_DF64) {
+      const df2 d(c[i]);
+      memcpy(out + i, &d, 8);
+    } else {
+      out[i] = c[i];
+    }
+  }
+}
+static double coeff_value_host(int prec, double stored_bits) {
+  if (prec != PF_DF64) return stored_bits;
+  df2 d;
+  memcpy(&d, &stored_bits, 8);
+  return (double)d.hi + (double)d.lo;
+}
 
 template <typename T, int E> struct Vec;
 template <> struct Vec<float, 1> { float x[1]; };
@@ -28,53 +121,98 @@ template <> struct Vec<float, 2> { float x[2]; };
 template <> struct __align__(16) Vec<float, 4> { float x[4]; };
 template <> struct Vec<double, 1> { double x[1]; };
 template <> struct __align__(16) Vec<double, 2> { double x[2]; };
+template <> struct Vec<df2, 1> { df2 x[1]; };
+template <> struct __align__(16) Vec<df2, 2> { df2 x[2]; };
+template <> struct __align__(16) Vec<df2, 4> { df2 x[4]; };
+template <> struct __align__(16) Vec<df2, 8> { df2 x[8]; };
+
+// Pair-float segment loads and stores: 16-byte vectors (one 8-byte vector for E = 1).
+// MODE 0: read-only path (ld.global.nc), 1: coherent (ld.global), 2: L2 only (ld.global.cg).
+template <int MODE, int E>
+__device__ __forceinline__ Vec<df2, E> ld_df(const df2* p) {
+  Vec<df2, E> r;
+  if constexpr (E == 1) {
+    const float2* q = reinterpret_cast<const float2*>(p);
+    const float2 v = MODE == 0 ? __ldg(q) : MODE == 1 ? *q : __ldcg(q);
+    r.x[0] = df2(v.x, v.y);
+  } else {
+#pragma unroll
+    for (int k = 0; k < E; k += 2) {
+      const float4* q = reinterpret_cast<const float4*>(p + k);
+      const float4 v = MODE == 0 ? __ldg(q) : MODE == 1 ? *q : __ldcg(q);
+      r.x[k] = df2(v.x, v.y);
+      r.x[k + 1] = df2(v.z, v.w);
+    }
+  }
+  return r;
+}
+template <int E>
+__device__ __forceinline__ void st_df(df2* p, const Vec<df2, E>& r) {
+  if constexpr (E == 1) {
+    *reinterpret_cast<float2*>(p) = make_float2(r.x[0].hi, r.x[0].lo);
+  } else {
+#pragma unroll
+    for (int k = 0; k < E; k += 2)
+      *reinterpret_cast<float4*>(p + k) = make_float4(r.x[k].hi, r.x[k].lo, r.x[k + 1].hi, r.x[k + 1].lo);
+  }
+}
 
 template <typename T, int E>
 __device__ __forceinline__ Vec<T, E> ld_default(const T* p) {
-  Vec<T, E> r;
-  if constexpr (sizeof(T) * E == 16) {
-    if constexpr (sizeof(T) == 4) {
-      float4 v = __ldg(reinterpret_cast<const float4*>(p));
-      r.x[0] = v.x; r.x[1] = v.y; r.x[2] = v.z; r.x[3] = v.w;
-    } else {
-      double2 v = __ldg(reinterpret_cast<const double2*>(p));
-      r.x[0] = v.x; r.x[1] = v.y;
-    }
-  } else if constexpr (sizeof(T) * E == 8 && sizeof(T) == 4) {
-    float2 v = __ldg(reinterpret_cast<const float2*>(p));
-    r.x[0] = v.x; r.x[1] = v.y;
+  if constexpr (is_df<T>) {
+    return ld_df<0, E>(p);
   } else {
+    Vec<T, E> r;
+    if constexpr (sizeof(T) * E == 16) {
+      if constexpr (sizeof(T) == 4) {
+        float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        r.x[0] = v.x; r.x[1] = v.y; r.x[2] = v.z; r.x[3] = v.w;
+      } else {
+        double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        r.x[0] = v.x; r.x[1] = v.y;
+      }
+    } else if constexpr (sizeof(T) * E == 8 && sizeof(T) == 4) {
+      float2 v = __ldg(reinterpret_cast<const float2*>(p));
+      r.x[0] = v.x; r.x[1] = v.y;
+    } else {
 #pragma unroll
-    for (int e = 0; e < E; ++e) r.x[e] = __ldg(p + e);
+      for (int e = 0; e < E; ++e) r.x[e] = __ldg(p + e);
+    }
+    return r;
   }
-  return r;
 }
 
 // Coherent load for B2, which the same kernel overwrites (out may alias it).
 template <typename T, int E>
 __device__ __forceinline__ Vec<T, E> ld_plain(const T* p) {
-  Vec<T, E> r;
-  if constexpr (sizeof(T) * E == 16) {
-    if constexpr (sizeof(T) == 4) {
-      float4 v = *reinterpret_cast<const float4*>(p);
-      r.x[0] = v.x; r.x[1] = v.y; r.x[2] = v.z; r.x[3] = v.w;
-    } else {
-      double2 v = *reinterpret_cast<const double2*>(p);
-      r.x[0] = v.x; r.x[1] = v.y;
-    }
-  } else if constexpr (sizeof(T) * E == 8 && sizeof(T) == 4) {
-    float2 v = *reinterpret_cast<const float2*>(p);
-    r.x[0] = v.x; r.x[1] = v.y;
+  if constexpr (is_df<T>) {
+    return ld_df<1, E>(p);
   } else {
+    Vec<T, E> r;
+    if constexpr (sizeof(T) * E == 16) {
+      if constexpr (sizeof(T) == 4) {
+        float4 v = *reinterpret_cast<const float4*>(p);
+        r.x[0] = v.x; r.x[1] = v.y; r.x[2] = v.z; r.x[3] = v.w;
+      } else {
+        double2 v = *reinterpret_cast<const double2*>(p);
+        r.x[0] = v.x; r.x[1] = v.y;
+      }
+    } else if constexpr (sizeof(T) * E == 8 && sizeof(T) == 4) {
+      float2 v = *reinterpret_cast<const float2*>(p);
+      r.x[0] = v.x; r.x[1] = v.y;
+    } else {
 #pragma unroll
-    for (int e = 0; e < E; ++e) r.x[e] = p[e];
+      for (int e = 0; e < E; ++e) r.x[e] = p[e];
+    }
+    return r;
   }
-  return r;
 }
 
 template <typename T, int E>
 __device__ __forceinline__ void st_default(T* p, const Vec<T, E>& r) {
-  if constexpr (sizeof(T) * E == 16) {
+  if constexpr (is_df<T>) {
+    st_df<E>(p, r);
+  } else if constexpr (sizeof(T) * E == 16) {
     if constexpr (sizeof(T) == 4) {
       *reinterpret_cast<float4*>(p) = make_float4(r.x[0], r.x[1], r.x[2], r.x[3]);
     } else {
@@ -92,8 +230,13 @@ __device__ __forceinline__ void st_default(T* p, const Vec<T, E>& r) {
 // lanes.  FP64: one row per warp where s allows it (E = max(1, s/32)): the FP64 step is bound
 // by the FP64 pipe, and a warp that holds one row never idles lanes on a shorter neighbour
 // row (about 8% faster than two rows of 16 lanes at s = 32).
+// Pair-float: E = 4 pairs (two 16-byte vectors) per lane, 8 lanes per s = 32 row as in FP32:
+// its step is bound by the neighbour gathers, not by arithmetic (12 FP32 operations per
+// product, against one FP64 FMA at 1/64 of the FP32 rate).  Measured at XXZ L = 20, s = 32:
+// 73.5 us with E = 4 against 93.3 us with E = 2 and 95.7 us with E = 8 (same bits).
 template <typename T, int S> struct Shape {
-  static constexpr int E = sizeof(T) == 8 ? (S >= 64 ? S / 32 : 1) : ((S * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : S);
+  static constexpr int E = is_df<T> ? (S >= PF_DF_E ? PF_DF_E : S)
+                         : sizeof(T) == 8 ? (S >= 64 ? S / 32 : 1) : ((S * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : S);
   static constexpr int G = S / E;           // lanes per row
   static constexpr int ROWS_PER_WARP = G >= 32 ? 1 : 32 / G;
 };
@@ -101,23 +244,37 @@ template <typename T, int S> struct Shape {
 // L2-only loads (ld.global.cg) for blocks the same launch rewrites between its steps.
 template <typename T, int E>
 __device__ __forceinline__ Vec<T, E> ld_l2(const T* p) {
-  Vec<T, E> r;
-  if constexpr (sizeof(T) * E == 16) {
-    if constexpr (sizeof(T) == 4) {
-      float4 v = __ldcg(reinterpret_cast<const float4*>(p));
-      r.x[0] = v.x; r.x[1] = v.y; r.x[2] = v.z; r.x[3] = v.w;
-    } else {
-      double2 v = __ldcg(reinterpret_cast<const double2*>(p));
-      r.x[0] = v.x; r.x[1] = v.y;
-    }
-  } else if constexpr (sizeof(T) * E == 8 && sizeof(T) == 4) {
-    float2 v = __ldcg(reinterpret_cast<const float2*>(p));
-    r.x[0] = v.x; r.x[1] = v.y;
+  if constexpr (is_df<T>) {
+    return ld_df<2, E>(p);
   } else {
+    Vec<T, E> r;
+    if constexpr (sizeof(T) * E == 16) {
+      if constexpr (sizeof(T) == 4) {
+        float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+        r.x[0] = v.x; r.x[1] = v.y; r.x[2] = v.z; r.x[3] = v.w;
+      } else {
+        double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+        r.x[0] = v.x; r.x[1] = v.y;
+      }
+    } else if constexpr (sizeof(T) * E == 8 && sizeof(T) == 4) {
+      float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+      r.x[0] = v.x; r.x[1] = v.y;
+    } else {
 #pragma unroll
-    for (int e = 0; e < E; ++e) r.x[e] = __ldcg(p + e);
+      for (int e = 0; e < E; ++e) r.x[e] = __ldcg(p + e);
+    }
+    return r;
   }
-  return r;
+}
+
+// A matrix value (read-only path).
+template <typename T> __device__ __forceinline__ T ld_val(const T* p) {
+  if constexpr (is_df<T>) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return df2(v.x, v.y);
+  } else {
+    return __ldg(p);
+  }
 }
 
 // One row segment (lane's E entries) of one step:
@@ -149,25 +306,25 @@ __device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_
     const int64_t end = rp[row + 1];
     for (; j + 4 <= end; j += 4) {
       int c0 = __ldg(col + j), c1 = __ldg(col + j + 1), c2 = __ldg(col + j + 2), c3 = __ldg(col + j + 3);
-      T h0 = __ldg(val + j), h1 = __ldg(val + j + 1), h2 = __ldg(val + j + 2), h3 = __ldg(val + j + 3);
+      T h0 = ld_val(val + j), h1 = ld_val(val + j + 1), h2 = ld_val(val + j + 2), h3 = ld_val(val + j + 3);
       Vec<T, E> b0 = ldb(B1 + (int64_t)c0 * S + lane * E);
       Vec<T, E> b1 = ldb(B1 + (int64_t)c1 * S + lane * E);
       Vec<T, E> b2 = ldb(B1 + (int64_t)c2 * S + lane * E);
       Vec<T, E> b3 = ldb(B1 + (int64_t)c3 * S + lane * E);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        acc[e] = fma(h0, b0.x[e], acc[e]);
-        acc[e] = fma(h1, b1.x[e], acc[e]);
-        acc[e] = fma(h2, b2.x[e], acc[e]);
-        acc[e] = fma(h3, b3.x[e], acc[e]);
+        acc[e] = fmadd(h0, b0.x[e], acc[e]);
+        acc[e] = fmadd(h1, b1.x[e], acc[e]);
+        acc[e] = fmadd(h2, b2.x[e], acc[e]);
+        acc[e] = fmadd(h3, b3.x[e], acc[e]);
       }
     }
     for (; j < end; ++j) {
       int c0 = __ldg(col + j);
-      T h0 = __ldg(val + j);
+      T h0 = ld_val(val + j);
       Vec<T, E> b0 = ldb(B1 + (int64_t)c0 * S + lane * E);
 #pragma unroll
-      for (int e = 0; e < E; ++e) acc[e] = fma(h0, b0.x[e], acc[e]);
+      for (int e = 0; e < E; ++e) acc[e] = fmadd(h0, b0.x[e], acc[e]);
     }
   }
   Vec<T, E> v = ld_default<T, E>(V + off);
@@ -179,10 +336,11 @@ __device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_
     // beta is 0 or 1; with the B2 term known present it is 1, so -beta q is -q (the same bits
     // as the run-time form, where 1 * q is exact)
 #pragma unroll
-    for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], fma(a, v.x[e], B2M > 0 ? -q.x[e] : -(beta * q.x[e])));
+    for (int e = 0; e < E; ++e)
+      r.x[e] = stored(fmadd(alpha, acc[e], fmadd(a, v.x[e], B2M > 0 ? -q.x[e] : -(beta * q.x[e]))));
   } else {
 #pragma unroll
-    for (int e = 0; e < E; ++e) r.x[e] = fma(alpha, acc[e], a * v.x[e]);
+    for (int e = 0; e < E; ++e) r.x[e] = stored(fmadd(alpha, acc[e], a * v.x[e]));
   }
   st_default<T, E>(out + off, r);
 }
@@ -192,8 +350,11 @@ __device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_
 // walks them in chunks of 256/G rows; the grid is one wave (SMs x resident CTAs), so each
 // SM's L1 serves the neighbour rows that fall inside its CTAs' ranges (for the XXZ chain in
 // rank order about half of all neighbours lie within +-200 rows).
+template <typename T> constexpr int step_min_blocks() {
+  return is_df<T> ? PF_DF_MINB : sizeof(T) == 8 ? 8 : 6;
+}
 template <typename T, int S, int SP, int B2M>
-__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 8 : 6) clenshaw_step_kernel(int64_t D, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(256, step_min_blocks<T>()) clenshaw_step_kernel(int64_t D, const int64_t* __restrict__ rp,
                                                             const int32_t* __restrict__ col,
                                                             const T* __restrict__ val, const T* __restrict__ V,
                                                             const T* __restrict__ B1, const T* B2, T* out, T a,
@@ -216,8 +377,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 8 : 6) clenshaw_step_ker
   }
 }
 
-// Launch shape of a step over `rows` rows: FP32 steps use one wave of contiguous row ranges
-// (the FP32 step is bound by its neighbour gathers, which the ranges keep in L1); FP64 steps
+// Launch shape of a step over `rows` rows: FP32 and pair-float steps use one wave of contiguous
+// row ranges (they are bound by their neighbour gathers, which the ranges keep in L1); FP64 steps
 // are bound by the FP64 pipe and keep one row per thread group.  cta_cap > 0 limits the CTAs
 // per SM (the grid is then one wave of that many per SM: ranges for FP32, a grid-stride loop
 // for FP64), leaving SM thread slots and registers to a kernel of another solve running
@@ -241,7 +402,7 @@ static StepShape step_shape(int64_t rows, int cta_cap = 0) {
   }()};
   const int per_sm = cta_cap > 0 ? std::min(nsm_occ[1], cta_cap) : nsm_occ[1];
   const int64_t waves = (int64_t)nsm_occ[0] * per_sm;
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (!std::is_same_v<T, double>) {
     const int64_t R = ceil_div(rows, waves);
     if (R > 256 / Sh::G) return StepShape{(unsigned)ceil_div(rows, R), R};
   }
@@ -301,6 +462,9 @@ pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* co
   if (prec == PF_F32)
     return launch_step<float>(s, D, row_ptr, col, (const float*)val, (const float*)V, (const float*)B1,
                               (const float*)B2, (float*)out, (float)a, (float)alpha, (float)beta, st, cta_cap);
+  if (prec == PF_DF64)
+    return launch_step<df2>(s, D, row_ptr, col, (const df2*)val, (const df2*)V, (const df2*)B1, (const df2*)B2,
+                            (df2*)out, df2(a), df2(alpha), df2(beta), st, cta_cap);
   return PF_EINVAL;
 }
 
@@ -309,7 +473,7 @@ pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* co
 pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs, const void*,
                            int K, void* aux0, void* aux1, cudaStream_t st, int cta_cap) {
   if (K < 1 || !coeffs) return PF_EINVAL;
-  const void* val = prec == PF_F64 ? (const void*)H->val_t : (const void*)H->val32;
+  const void* val = ham_vals(H, prec);
   void* aux[2] = {aux0, aux1};
   // i = K: b_K = a_K V
   PF_TRY(clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, s, V, nullptr, nullptr, aux[K & 1], coeffs[K], 0.0,
@@ -403,7 +567,7 @@ __global__ void __launch_bounds__(256, 4) clenshaw_batch_kernel(const BatchItemD
     T alpha, beta;
     step_operands<T>(it, i, B1, B2, out, alpha, beta);
     clenshaw_row<T, S, false, SP, B2M>(grow - it.row0, lane, it.rp, it.col, (const T*)it.val, (const T*)it.V, B1,
-                                       B2, out, (T)__ldg(it.coeffs + i), alpha, beta);
+                                       B2, out, load_coeff<T>(it.coeffs + i), alpha, beta);
   }
 }
 
@@ -439,7 +603,7 @@ __global__ void __launch_bounds__(PF_PERSIST_NT) clenshaw_persistent_kernel(cons
     T* out;
     T alpha, beta;
     step_operands<T>(it, i, B1, B2, out, alpha, beta);
-    const T a = (T)__ldg(it.coeffs + i);
+    const T a = load_coeff<T>(it.coeffs + i);
     for (int64_t row = r0 + threadIdx.x / G; row < r1; row += ROWS)
       clenshaw_row<T, S, true, -1, -1>(row, lane, it.rp, it.col, val, V, B1, B2, out, a, alpha, beta);
     if constexpr (CLUSTER) {
@@ -535,7 +699,8 @@ static StepShape sweep_shape_s(int s, int64_t rows) {
 }
 
 static int lanes_per_row(int prec, int s) {   // Shape<T, s>::G
-  const int E = prec == PF_F64 ? (s >= 64 ? s / 32 : 1) : (s * 4 >= 16 ? 4 : s);
+  const int E = prec == PF_F64 ? (s >= 64 ? s / 32 : 1) : prec == PF_DF64 ? (s >= PF_DF_E ? PF_DF_E : s)
+                                                                          : (s * 4 >= 16 ? 4 : s);
   return s / E;
 }
 
@@ -558,10 +723,13 @@ static pf_status sweep_graph_launch(SweepGraph& g, int prec, int s, const void* 
         g.uniform == uniform)) {
     g.reset();
     PF_CUDA(cudaGraphCreate(&g.graph, 0));
-    const StepShape sh = prec == PF_F64 ? sweep_shape_s<double>(s, rows) : sweep_shape_s<float>(s, rows);
+    const StepShape sh = prec == PF_F64 ? sweep_shape_s<double>(s, rows)
+                         : prec == PF_DF64 ? sweep_shape_s<df2>(s, rows) : sweep_shape_s<float>(s, rows);
     cudaGraphNode_t prev = nullptr;
     for (int t = 0; t < T; ++t) {
-      void* fn = prec == PF_F64 ? sweep_fn_s<double>(s, uniform, t, T - 1) : sweep_fn_s<float>(s, uniform, t, T - 1);
+      void* fn = prec == PF_F64    ? sweep_fn_s<double>(s, uniform, t, T - 1)
+                 : prec == PF_DF64 ? sweep_fn_s<df2>(s, uniform, t, T - 1)
+                                   : sweep_fn_s<float>(s, uniform, t, T - 1);
       if (!fn || sh.grid == 0) return PF_EINVAL;
       const BatchItemDev* items = static_cast<const BatchItemDev*>(table);
       int nn = n, tt = t;
@@ -598,7 +766,7 @@ pf_status filter_sweep(const std::vector<FilterItem>& items, void* table_dev, si
   if (n == 0) return PF_OK;
   if ((size_t)n * sizeof(BatchItemDev) > table_bytes) return PF_EINVAL;
   const int prec = items[0].prec, s = items[0].s;
-  if (!valid_s(s) || (prec != PF_F64 && prec != PF_F32) || csize < 0 || csize > 16) return PF_EINVAL;
+  if (!valid_s(s) || !valid_prec(prec) || csize < 0 || csize > 16) return PF_EINVAL;
   int T = 0;
   bool uniform = true;
   for (const auto& it : items) {
@@ -615,7 +783,7 @@ pf_status filter_sweep(const std::vector<FilterItem>& items, void* table_dev, si
     b.row0 = row0;
     b.rp = it.H->row_ptr;
     b.col = it.H->col;
-    b.val = prec == PF_F64 ? (const void*)it.H->val_t : (const void*)it.H->val32;
+    b.val = ham_vals(it.H, prec);
     b.V = it.V;
     b.W = it.W;
     b.aux0 = it.aux0;
@@ -634,6 +802,10 @@ pf_status filter_sweep(const std::vector<FilterItem>& items, void* table_dev, si
       switch (s) { PF_PERSIST_CASE(double, 1) PF_PERSIST_CASE(double, 2) PF_PERSIST_CASE(double, 4)
                    PF_PERSIST_CASE(double, 8) PF_PERSIST_CASE(double, 16) PF_PERSIST_CASE(double, 32)
                    PF_PERSIST_CASE(double, 64) }
+    } else if (prec == PF_DF64) {
+      switch (s) { PF_PERSIST_CASE(df2, 1) PF_PERSIST_CASE(df2, 2) PF_PERSIST_CASE(df2, 4)
+                   PF_PERSIST_CASE(df2, 8) PF_PERSIST_CASE(df2, 16) PF_PERSIST_CASE(df2, 32)
+                   PF_PERSIST_CASE(df2, 64) }
     } else {
       switch (s) { PF_PERSIST_CASE(float, 1) PF_PERSIST_CASE(float, 2) PF_PERSIST_CASE(float, 4)
                    PF_PERSIST_CASE(float, 8) PF_PERSIST_CASE(float, 16) PF_PERSIST_CASE(float, 32)
@@ -652,6 +824,16 @@ pf_status filter_sweep(const std::vector<FilterItem>& items, void* table_dev, si
       case 16: return launch_batch_s<double, 16>(d, n, T, row0, uniform, st);
       case 32: return launch_batch_s<double, 32>(d, n, T, row0, uniform, st);
       case 64: return launch_batch_s<double, 64>(d, n, T, row0, uniform, st);
+    }
+  } else if (prec == PF_DF64) {
+    switch (s) {
+      case 1: return launch_batch_s<df2, 1>(d, n, T, row0, uniform, st);
+      case 2: return launch_batch_s<df2, 2>(d, n, T, row0, uniform, st);
+      case 4: return launch_batch_s<df2, 4>(d, n, T, row0, uniform, st);
+      case 8: return launch_batch_s<df2, 8>(d, n, T, row0, uniform, st);
+      case 16: return launch_batch_s<df2, 16>(d, n, T, row0, uniform, st);
+      case 32: return launch_batch_s<df2, 32>(d, n, T, row0, uniform, st);
+      case 64: return launch_batch_s<df2, 64>(d, n, T, row0, uniform, st);
     }
   } else {
     switch (s) {
@@ -710,6 +892,7 @@ pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t
     g.reset();
     if (!it.coeffs_host || it.K < 1) return PF_EINVAL;
     if (it.prec == PF_F64) prepare_shapes<double>(it.s);
+    else if (it.prec == PF_DF64) prepare_shapes<df2>(it.s);
     else prepare_shapes<float>(it.s);
     cudaStream_t cap = nullptr;
     PF_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -876,7 +1059,7 @@ pf_status tune_item(const FilterItem& it, cudaStream_t st, TuneResult* out) {
   PF_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const bool small = D * G <= (int64_t)16 * PF_PERSIST_NT * 64;
   if (small) {
-    const size_t w = it.prec == PF_F64 ? 8 : 4;
+    const size_t w = prec_bytes(it.prec);
     const size_t blk = (((size_t)D * it.s * w) + 255) & ~(size_t)255;
     const int Kt = std::min(it.K, 48);
     // r copies fill the GPU in the sweep (about 8 resident 256-thread CTAs per SM)
@@ -896,6 +1079,7 @@ pf_status tune_item(const FilterItem& it, cudaStream_t st, TuneResult* out) {
     std::vector<double> ch(Kt + 1);
     PF_CUDA(cudaMemcpyAsync(ch.data(), it.coeffs_dev, (Kt + 1) * 8, cudaMemcpyDeviceToHost, st));
     PF_CUDA(cudaStreamSynchronize(st));
+    for (double& c : ch) c = coeff_value_host(it.prec, c);
     std::vector<unsigned char> th(filter_sweep_table_bytes(r));
     double ms = 0;
     const FilterItem& o = one[0];
@@ -917,7 +1101,9 @@ pf_status tune_item(const FilterItem& it, cudaStream_t st, TuneResult* out) {
         break;
       }
       res.persist_us[k] = 1e3 * ms / (Kt + 1);
-      res.slots[k] = it.prec == PF_F64 ? persist_slots<double>(it.s, c, nsm) : persist_slots<float>(it.s, c, nsm);
+      res.slots[k] = it.prec == PF_F64    ? persist_slots<double>(it.s, c, nsm)
+                     : it.prec == PF_DF64 ? persist_slots<df2>(it.s, c, nsm)
+                                          : persist_slots<float>(it.s, c, nsm);
     }
     PF_CUDA(cudaStreamSynchronize(st));
   }
@@ -947,7 +1133,7 @@ pf_status pf_clenshaw_step(const pf_ham* hh, int32_t prec, int32_t s, const void
     val = H->val;
   } else {
     if (!H->has_rescale) return PF_ESTATE;
-    val = prec == PF_F64 ? (const void*)H->val_t : (const void*)H->val32;
+    val = ham_vals(H, prec);
   }
   return clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, s, V, B1, B2, out, a, alpha, beta,
                            (cudaStream_t)stream);
@@ -958,10 +1144,10 @@ pf_status pf_filter_apply(const pf_ham* hh, int32_t prec, int32_t s, const void*
   const Ham* H = reinterpret_cast<const Ham*>(hh);
   if (!H || !V || !W || !coeffs || K < 1) return PF_EINVAL;
   if (!H->has_rescale) return PF_ESTATE;
-  if (prec != PF_F64 && prec != PF_F32) return PF_EINVAL;
+  if (!valid_prec(prec)) return PF_EINVAL;
   if (!valid_s(s)) return PF_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t w = prec == PF_F64 ? 8 : 4;
+  const size_t w = prec_bytes(prec);
   DevBuf a0, a1;
   PF_TRY(a0.alloc(H->D * s * w, st));
   PF_TRY(a1.alloc(H->D * s * w, st));
@@ -971,14 +1157,14 @@ pf_status pf_filter_apply(const pf_ham* hh, int32_t prec, int32_t s, const void*
 pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t prec, int32_t s, int32_t form,
                                 pf_stream_t stream) {
   if (n < 0 || (n > 0 && !items)) return PF_EINVAL;
-  if (prec != PF_F64 && prec != PF_F32) return PF_EINVAL;
+  if (!valid_prec(prec)) return PF_EINVAL;
   if (!valid_s(s)) return PF_EINVAL;
   if (!(form == PF_FORM_AUTO || form == PF_FORM_STEPS || form == PF_FORM_GRAPH || form == 1 || form == 2 ||
         form == 4 || form == 8 || form == 16))
     return PF_EINVAL;
   if (n == 0) return PF_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t w = prec == PF_F64 ? 8 : 4;
+  const size_t w = prec_bytes(prec);
   // one device blob: per item its K+1 coefficients and two auxiliary blocks (256-B aligned)
   std::vector<size_t> coff(n), aoff(n);
   size_t total = 0;
@@ -994,13 +1180,16 @@ pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t 
   DevBuf blob, table;
   PF_TRY(blob.alloc(total, st));
   PF_TRY(table.alloc(filter_sweep_table_bytes(n), st));
+  // the device coefficient tables (pairs for PF_DF64); a pageable source is consumed by the
+  // time cudaMemcpyAsync returns
   std::vector<double> ch;
   std::vector<FilterItem> v(n);
   for (int j = 0; j < n; ++j) {
     const Ham* H = reinterpret_cast<const Ham*>(items[j].H);
     unsigned char* base = blob.as<unsigned char>();
-    PF_CUDA(cudaMemcpyAsync(base + coff[j], items[j].coeffs, (size_t)(items[j].K + 1) * 8, cudaMemcpyHostToDevice,
-                            st));
+    ch.resize(items[j].K + 1);
+    coeff_table_host(prec, items[j].coeffs, items[j].K + 1, ch.data());
+    PF_CUDA(cudaMemcpyAsync(base + coff[j], ch.data(), (size_t)(items[j].K + 1) * 8, cudaMemcpyHostToDevice, st));
     FilterItem& it = v[j];
     it.H = H;
     it.prec = prec;
@@ -1055,10 +1244,10 @@ pf_status pf_filter_tune(const pf_ham* hh, int32_t prec, int32_t s, int32_t K, i
   const Ham* H = reinterpret_cast<const Ham*>(hh);
   if (!H || !form || K < 1 || n < 1) return PF_EINVAL;
   if (!H->has_rescale) return PF_ESTATE;
-  if (prec != PF_F64 && prec != PF_F32) return PF_EINVAL;
+  if (!valid_prec(prec)) return PF_EINVAL;
   if (!valid_s(s)) return PF_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t w = prec == PF_F64 ? 8 : 4;
+  const size_t w = prec_bytes(prec);
   // a zero start block and zero coefficients: the timing does not depend on the values
   DevBuf V, coeffs;
   PF_TRY(V.alloc((size_t)H->D * s * w, st));

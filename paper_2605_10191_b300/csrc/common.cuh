@@ -75,6 +75,10 @@ struct DevBuf {
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+inline bool valid_prec(int prec) { return prec == PF_F64 || prec == PF_F32 || prec == PF_DF64; }
+// bytes per block entry of a filter precision (a pair-float entry is two floats)
+inline size_t prec_bytes(int prec) { return prec == PF_F32 ? 4 : 8; }
+
 // ---------------------------------------------------------------- handles
 struct Basis {
   pf_model m;
@@ -92,6 +96,7 @@ struct Ham {
   double* val = nullptr;        // device [nnz], H
   double* val_t = nullptr;      // device [nnz], H~ (FP64)
   float* val32 = nullptr;       // device [nnz], H~ (FP32)
+  float2* val_df = nullptr;     // device [nnz], H~ as pair-float (hi, lo), hi = val32
   int has_rescale = 0, has_bounds = 0;
   double Ec = 0, dE = 1, emin = 0, emax = 0, rmin = 0, rmax = 0, hnorm = 0;
   cudaStream_t st = 0;
@@ -127,6 +132,11 @@ __device__ T block_sum(T v, T* sh /* >= 32 */) {
 }
 
 // ---------------------------------------------------------------- cross-unit API
+// The matrix values a step of precision prec reads: H~ in FP64, FP32 or pair-float.
+inline const void* ham_vals(const Ham* H, int prec) {
+  return prec == PF_F64 ? (const void*)H->val_t : prec == PF_F32 ? (const void*)H->val32 : (const void*)H->val_df;
+}
+
 // Clenshaw step on raw CSR arrays (clenshaw.cu)
 // cta_cap > 0 limits the step's CTAs per SM (room for another solve's kernels beside it).
 pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* col, const void* val,
@@ -201,6 +211,9 @@ struct FilterGraph {
   void reset();
 };
 pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t st);
+// Device coefficient table of a filter precision, n entries of 8 bytes: the values, or for
+// PF_DF64 their (hi, lo) float pairs (the form the sweep and persistent kernels read).
+void coeff_table_host(int prec, const double* c, int n, double* out);
 // W = P V for a D x s block (K steps); aux buffers are two D x s blocks of the filter type.
 pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs_host,
                            const void* coeffs_dev, int K, void* aux0, void* aux1, cudaStream_t st, int cta_cap = 0);
@@ -221,6 +234,10 @@ pf_status colnorms(int64_t D, int s, const double* A, const double* B, const dou
 // Conversions between double and float blocks
 pf_status convert_d2f(const double* x, float* y, int64_t n, cudaStream_t st);
 pf_status convert_f2d(const float* x, double* y, int64_t n, cudaStream_t st);
+// Between double and pair-float blocks (n entries): hi = rn(x), lo = rn(x - hi); back: hi + lo.
+// x and y may be the same buffer (both 8 bytes per entry).
+pf_status convert_d2df(const double* x, float2* y, int64_t n, cudaStream_t st);
+pf_status convert_df2d(const float2* x, double* y, int64_t n, cudaStream_t st);
 // Small dense helpers on one CTA
 // Shifted Cholesky of G (n x n, row-major), writes upper R (row-major) with G + shift*I = R^T R;
 // Rinv = R^{-1} (upper); status[0] = 0 ok, 1 = not positive definite.

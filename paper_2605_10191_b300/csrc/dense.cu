@@ -304,6 +304,34 @@ pf_status convert_f2d(const float* x, double* y, int64_t n, cudaStream_t st) {
   PF_LAUNCH_CHECK("f2d_kernel");
   return PF_OK;
 }
+// In place allowed: each thread reads its 8 bytes before writing them.
+__global__ void d2df_kernel(const double* x, float2* y, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const double v = x[i];
+    const float hi = (float)v;
+    y[i] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+__global__ void df2d_kernel(const float2* x, double* y, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float2 v = x[i];
+    y[i] = (double)v.x + (double)v.y;   // exact: the pair's sum has at most 49 significant bits
+  }
+}
+pf_status convert_d2df(const double* x, float2* y, int64_t n, cudaStream_t st) {
+  if (n <= 0) return PF_OK;
+  d2df_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(x, y, n);
+  PF_LAUNCH_CHECK("d2df_kernel");
+  return PF_OK;
+}
+pf_status convert_df2d(const float2* x, double* y, int64_t n, cudaStream_t st) {
+  if (n <= 0) return PF_OK;
+  df2d_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(x, y, n);
+  PF_LAUNCH_CHECK("df2d_kernel");
+  return PF_OK;
+}
 
 // ------------------------------------------------------------------ small dense (one CTA)
 // G row-major n x n (symmetric).  R upper with (G + shift I) = R^T R, shift = shift_rel * trace(G),

@@ -45,9 +45,9 @@ extern "C" pf_status pf_filter_apply_noalloc(const pf_ham* hh, int32_t prec, int
   const Ham* H = reinterpret_cast<const Ham*>(hh);
   if (!H || !V || !W || !coeffs || K < 1) return PF_EINVAL;
   if (!H->has_rescale) return PF_ESTATE;
-  if (prec != PF_F64 && prec != PF_F32) return PF_EINVAL;
+  if (!valid_prec(prec)) return PF_EINVAL;
   if (!(s == 1 || s == 2 || s == 4 || s == 8 || s == 16 || s == 32 || s == 64)) return PF_EINVAL;
-  const size_t w = prec == PF_F64 ? 8 : 4;
+  const size_t w = prec_bytes(prec);
   const size_t blk = ((size_t)H->D * (size_t)s * w + 255) & ~(size_t)255;
   if (2 * blk > PF_NOALLOC_SCRATCH_BYTES) return PF_EINVAL;   // too large for the fixed scratch
   void* base = nullptr;

@@ -535,13 +535,13 @@ static pf_status measure_block_steps(const Ham* H, int prec, cudaStream_t st, st
       return PF_OK;
     }
   }
-  const size_t w = prec == PF_F64 ? 8 : 4;
+  const size_t w = prec_bytes(prec);
   const size_t blk = (size_t)H->D * 64 * w;
   DevBuf buf;
   PF_TRY(buf.alloc(3 * blk, st));
   PF_CUDA(cudaMemsetAsync(buf.p, 0, 3 * blk, st));
   unsigned char* b = buf.as<unsigned char>();
-  const void* val = prec == PF_F64 ? (const void*)H->val_t : (const void*)H->val32;
+  const void* val = ham_vals(H, prec);
   cudaEvent_t e0, e1;
   PF_CUDA(cudaEventCreate(&e0));
   PF_CUDA(cudaEventCreate(&e1));
@@ -572,10 +572,10 @@ static pf_status measure_block_steps(const Ham* H, int prec, cudaStream_t st, st
 static int expected_krylov_dim(int nev, int s, double eta);
 
 static pf_status autotune_block(const Ham* H, int prec, int nev, cudaStream_t st, int* s_out, double* us_out,
-                                double* cost_out) {
+                                double* cost_out, int refine_prec = PF_DF64) {
   std::array<double, 4> us, us64;
   PF_TRY(measure_block_steps(H, prec, st, us));
-  if (prec == PF_F32) PF_TRY(measure_block_steps(H, PF_F64, st, us64));
+  if (prec == PF_F32) PF_TRY(measure_block_steps(H, refine_prec, st, us64));
   const int nev_g = std::max(nev, (int)std::ceil(1.5 * nev));
   double best = 0;
   int bs = 0;
@@ -585,7 +585,7 @@ static pf_status autotune_block(const Ham* H, int prec, int nev, cudaStream_t st
     if ((int64_t)sc * 2 > H->D) break;
     const double blocks = std::ceil(expected_krylov_dim(nev_g, sc, 1.0) / (double)sc);
     double cost = blocks * us[c];
-    // FP32 path: FP64 refinement of the guard set, ~1.3 passes at degree 0.7 K on average
+    // FP32 path: refinement of the guard set, ~1.3 passes at degree 0.7 K on average
     if (prec == PF_F32) cost += 1.3 * 0.7 * std::ceil(nev_g / (double)sc) * us64[c];
     if (cost_out) cost_out[c] = cost;
     if (bs == 0 || cost < best) {
@@ -648,6 +648,9 @@ struct Task {
     if (t_end) cudaEventDestroy(t_end);
   }
 
+  // arithmetic of the refinement filter (PF_DF64 or PF_F64)
+  int refine_prec() const { return o.refine_precision; }
+
   double max_res() const {
     double m = 0;
     for (int j : sel) m = std::max(m, res[j]);
@@ -669,9 +672,10 @@ struct Task {
     if (nev < 1 || nev > H->D || K < 1) return PF_EINVAL;
     if (!o.use_abs_target && !(target_eps >= 0.0 && target_eps <= 1.0)) return PF_EINVAL;
     if (o.precision != PF_F64 && o.precision != PF_F32) return PF_EINVAL;
+    if (o.refine_precision != PF_F64 && o.refine_precision != PF_DF64) return PF_EINVAL;
     if (o.block < 0) {   // the autotuner picks the block width
       if (!H->has_rescale) return PF_ESTATE;
-      PF_TRY(autotune_block(H, o.precision, nev, stream, &s, nullptr, nullptr));
+      PF_TRY(autotune_block(H, o.precision, nev, stream, &s, nullptr, nullptr, refine_prec()));
       o.block = s;
     }
     s = o.block > 0 ? o.block : 32;
@@ -915,7 +919,12 @@ struct Task {
   pf_status issue_refine_filter() {
     const double c_shift = o.refine_shift == 0.0 ? 0.05 : (o.refine_shift < 0.0 ? 0.0 : o.refine_shift);
     coeffs_r[0] = passes > 0 ? a0 + c_shift : a0;
-    PF_CUDA(cudaMemcpyAsync(coeffr_dev.p, coeffs_r.data(), (size_t)(Kr + 1) * 8, cudaMemcpyHostToDevice, st));
+    const int rprec = refine_prec();
+    {
+      std::vector<double> tab(Kr + 1);   // pageable: consumed when the copy call returns
+      coeff_table_host(rprec, coeffs_r.data(), Kr + 1, tab.data());
+      PF_CUDA(cudaMemcpyAsync(coeffr_dev.p, tab.data(), (size_t)(Kr + 1) * 8, cudaMemcpyHostToDevice, st));
+    }
     const int q = nb * s;
     const int64_t DS = H->D * s;
     double* Ud = U.as<double>();
@@ -954,14 +963,20 @@ struct Task {
     }
     clk->mark(2);
     pending.clear();
+    // Pair-float filter: the active blocks are converted into the HU blocks, which the filter
+    // reads as V and which hold its FP64 result after refine_post converts W back; W is
+    // written over the active U blocks, which are only scratch until the set is rebuilt.
+    const bool pair = rprec == PF_DF64;
+    if (pair && na > 0)
+      PF_TRY(convert_d2df(Ud + (int64_t)Lb * DS, reinterpret_cast<float2*>(HUd + (int64_t)Lb * DS), na * DS, st));
     for (int b = Lb; b < nb; ++b) {
       FilterItem it;
       it.H = H;
       it.owner = this;
-      it.prec = PF_F64;
+      it.prec = rprec;
       it.s = s;
-      it.V = Ud + (int64_t)b * DS;
-      it.W = HUd + (int64_t)b * DS;
+      it.V = pair ? (const void*)(HUd + (int64_t)b * DS) : (const void*)(Ud + (int64_t)b * DS);
+      it.W = pair ? (void*)(Ud + (int64_t)b * DS) : (void*)(HUd + (int64_t)b * DS);
       it.coeffs_host = coeffs_r.data();
       it.coeffs_dev = coeffr_dev.as<double>();
       it.K = Kr;
@@ -981,6 +996,8 @@ struct Task {
     double* Ud = U.as<double>();
     double* HUd = HU.as<double>();
     double* Wd = HUd + (int64_t)Lb * DS;
+    if (refine_prec() == PF_DF64 && na > 0)   // W (pairs, over the active U blocks) to FP64
+      PF_TRY(convert_df2d(reinterpret_cast<const float2*>(Ud + (int64_t)Lb * DS), Wd, na * DS, st));
     if (Lb > 0) {   // the filtered blocks against the locked ones, two Gram-Schmidt passes
       DevBuf Cl;
       PF_TRY(Cl.alloc((size_t)Lb * s * na * s * 8, st));
@@ -1352,10 +1369,10 @@ struct AsyncExecutor {
       int64_t D, nnz;
       std::vector<std::pair<FilterItem, Live*>> items;
     };
-    // Overlap: while one solve runs its FP32 Lanczos phase and another its FP64 refinement,
-    // their large steps are capped at 3 (FP32) and 4 (FP64) CTAs per SM, which fit together
-    // in one SM's registers (3 x 256 x 40 + 4 x 256 x 32 of 65536) and thread slots, so the
-    // memory-bound and the FP64-bound steps share every SM instead of queueing for slots.
+    // Overlap: while one solve runs its FP32 Lanczos phase and another its refinement, their
+    // large steps are capped at 3 (FP32) and 4 (FP64) or 2 (pair-float) CTAs per SM, which fit
+    // together in one SM's registers (3 x 256 x 40 + 4 x 256 x 32, or + 2 x 256 x 54, of 65536)
+    // and thread slots, so both kinds of step share every SM instead of queueing for slots.
     bool lanczos32 = false, refine64 = false;
     for (const auto& l : live) {
       if (!l.started || l.t->phase == Task::DONE) continue;
@@ -1365,8 +1382,8 @@ struct AsyncExecutor {
     const bool overlap = lanczos32 && refine64;
     for (Live* l : idle)
       for (FilterItem& it : l->t->pending) {
-        const double blk = (double)it.H->D * it.s * (it.prec == PF_F64 ? 8 : 4);
-        it.cta_cap = (overlap && blk >= 16e6) ? (it.prec == PF_F64 ? 4 : 3) : 0;
+        const double blk = (double)it.H->D * it.s * prec_bytes(it.prec);
+        it.cta_cap = (overlap && blk >= 16e6) ? (it.prec == PF_F64 ? 4 : it.prec == PF_DF64 ? 2 : 3) : 0;
       }
     std::vector<Grp> grps;
     for (Live* l : idle)
@@ -1666,6 +1683,7 @@ void pf_default_opts(pf_solve_opts* o) {
   o->tol_f32 = 1e-7;
   o->res_tol = 1e-9;
   o->seed = 2024;
+  o->refine_precision = PF_DF64;
 }
 
 pf_status pf_spectral_bounds(pf_ham* hh, double tol, double* emin, double* emax, double* rmin, double* rmax,
