@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--refine-precision", default="f64", choices=["f64", "df64"],
+                    help="arithmetic of the refinement filter: FP64 (the workload's definition) or pair-float")
+    ap.add_argument("--no-variant", action="store_true",
+                    help="solve mode: skip the extra timed solves with the pair-float refinement filter")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only time the fused Clenshaw step at the workload shape (profiling)")
     ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64", "df64"])
@@ -106,6 +110,37 @@ def step_bytes(D, nnz, s, w):
     """Algorithmic bytes of one fused Clenshaw step: matrix (value + int32 column per
     nonzero, int64 row pointers) plus V, b_{i+1}, b_{i+2} read once and b_i written."""
     return nnz * (w + 4) + 8 * (D + 1) + 4 * D * s * w
+
+
+def refine_roofline(rec, D, nnz, refine_precision, peak, peak_kind):
+    """Roofline of the refinement filter's step (ms_filter_f64 / filter_steps_f64 count the
+    refinement's steps).  FP64: bound by the FP64 pipe; pair-float: bound like the FP32 step
+    (HBM roofline, 8 bytes per entry and value)."""
+    f64_ms = sum(x["rep"]["ms_filter_f64"] for x in rec)
+    f64_n = sum(x["rep"]["filter_steps_f64"] for x in rec)
+    if not f64_n:
+        return None
+    per = f64_ms / f64_n
+    if refine_precision == "df64":
+        byt = step_bytes(D, nnz, BLOCK, 8)
+        ach = byt / per / 1e6
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": ncu_traffic("clenshaw_df64_xxz_L20_s32"), "kernel": "clenshaw_step_kernel<df2,32>",
+                "us_per_launch": 1e3 * per, "alg_bytes_per_launch": byt, "peak_source": peak_kind}
+    flops = 2.0 * nnz * BLOCK + 3.0 * D * BLOCK
+    fp64_peak = 148 * 4 * 2.032e9 / 1e12        # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
+    return {"bound": "alu", "achieved": flops / per / 1e9, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": flops / per / 1e9 / fp64_peak, "kernel": "clenshaw_step_kernel<double,32>",
+            "us_per_launch": 1e3 * per, "traffic": ncu_traffic("clenshaw_f64_xxz_L20_s32"),
+            "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz"}
+
+
+def dtype_name(args):
+    """Arithmetic of the path: FP32 filter, pair-float (f32x2) or FP64 refinement filter, FP64
+    Lanczos and Rayleigh-Ritz; or FP64 throughout."""
+    if getattr(args, "precision", "f32") != "f32":
+        return "f64"
+    return "f32+f32x2+f64" if getattr(args, "refine_precision", "df64") == "df64" else "f32+f64"
 
 
 def ncu_traffic(kernel_tag):
@@ -290,7 +325,7 @@ def run_ours(args):
 
     pinned = torch.empty((NEV, math.comb(L_SITES, L_SITES // 2)), dtype=torch.float64, pin_memory=True)
 
-    def one_step(i, record):
+    def one_step(i, record, refine_precision=args.refine_precision):
         r = realisation(rank, world, i)
         p = pi.xxz_params(L_SITES, W=W_LIST[r], seed=SEED0 + r)
         st = torch.cuda.current_stream()
@@ -299,7 +334,8 @@ def run_ours(args):
         H = pf.Hamiltonian.from_params(p)
         H.spectral_bounds()
         K = H.choose_K(EPS, NEV)
-        res = H.solve(EPS, NEV, K, block=BLOCK, precision=args.precision, raise_on_notconv=False)
+        res = H.solve(EPS, NEV, K, block=BLOCK, precision=args.precision, raise_on_notconv=False,
+                      refine_precision=refine_precision)
         ev[1].record(st)
         pinned.copy_(res.evecs.t(), non_blocking=True)     # D x nev (column-major) -> host
         ev[2].record(st)
@@ -326,7 +362,8 @@ def run_ours(args):
             K = H.choose_K(EPS, NEV)
             probs.append(dict(H=H, eps=EPS, nev=NEV, K=K))
             meta.append((r, K))
-        res = pf.solve_batch(probs, block=BLOCK, precision=args.precision, return_vectors=True)
+        res = pf.solve_batch(probs, block=BLOCK, precision=args.precision, return_vectors=True,
+                             refine_precision=args.refine_precision)
         ev[1].record(st)
         for x in res:
             pinned.copy_(x.evecs.t(), non_blocking=True)
@@ -371,8 +408,6 @@ def run_ours(args):
     # the solve's stream inside this timed region.
     f32_ms = sum(x["rep"]["ms_filter_f32"] for x in rec)
     f32_n = sum(x["rep"]["filter_steps_f32"] for x in rec)
-    f64_ms = sum(x["rep"]["ms_filter_f64"] for x in rec)
-    f64_n = sum(x["rep"]["filter_steps_f64"] for x in rec)
     peak, peak_kind = measured_peaks()
     roof = None
     if f32_n:
@@ -382,15 +417,29 @@ def run_ours(args):
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "traffic": ncu_traffic("clenshaw_f32_xxz_L20_s32"), "kernel": "clenshaw_step_kernel<float,32>",
                 "us_per_launch": 1e3 * per, "alg_bytes_per_launch": byt, "peak_source": peak_kind}
-    roof64 = None
-    if f64_n:
-        per = f64_ms / f64_n
-        flops = 2.0 * nnz * BLOCK + 3.0 * D * BLOCK
-        fp64_peak = 148 * 4 * 2.032e9 / 1e12        # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz
-        roof64 = {"bound": "alu", "achieved": flops / per / 1e9, "peak": fp64_peak, "unit": "TFLOP/s",
-                  "frac": flops / per / 1e9 / fp64_peak, "kernel": "clenshaw_step_kernel<double,32>",
-                  "us_per_block_step": 1e3 * per, "traffic": ncu_traffic("clenshaw_f64_xxz_L20_s32"),
-                  "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz"}
+    roof64 = refine_roofline(rec, D, nnz, args.refine_precision, peak, peak_kind)
+    phase_keys = ("ms_filter_f32", "ms_filter_f64", "ms_orth", "ms_qr", "ms_check", "ms_extract", "ms_refine",
+                  "ms_total")
+    variant = None
+    if (world == 1 and not args.pipeline and args.precision == "f32" and args.refine_precision == "f64"
+            and not args.no_variant):
+        # the same solves with the refinement filter in pair-float on the FP32 units, timed the
+        # same way after the main region (reported beside `value`, not in it)
+        vrec = []
+        with ClockSampler(local) as vclocks:
+            for i in range(args.steps):
+                one_step(args.warmup + i, vrec, "df64")
+            torch.cuda.synchronize()
+        v_dev = sum(x["dev_ms"] for x in vrec) / 1e3
+        v_good = sum(x["good"] for x in vrec)
+        variant = {"value": v_good / v_dev, "unit": "eigenpairs/s", "ms_per_step": 1e3 * v_dev / len(vrec),
+                   "dtype": "f32+f32x2+f64",
+                   "refinement_filter": "pair-float (FP32 hi + lo, about 2^-47 relative error per step); "
+                                        "refinement Rayleigh-Ritz, Gram-Schmidt and residuals FP64",
+                   "eigenpairs_at_tol": v_good, "solves": len(vrec), "clocks": vclocks.summary(),
+                   "roofline_refine": refine_roofline(vrec, D, nnz, "df64", peak, peak_kind),
+                   "phases_ms": {k: statistics.mean(x["rep"][k] for x in vrec) for k in phase_keys},
+                   "residual_max_over_hnorm": max(x["rep"]["max_residual"] / x["rep"]["hnorm"] for x in vrec)}
     cpu = None
     if not args.no_cpu_baseline:
         dt, K0, n = oracle_sample(args.cpu_sample_steps)
@@ -403,11 +452,12 @@ def run_ours(args):
         "metric": METRIC, "value": good / dev_s, "unit": "eigenpairs/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / len(rec),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if args.precision == "f32" else "f64", "data": "synthetic",
+        "dtype": dtype_name(args), "data": "synthetic",
         "config": {"workload": WORKLOAD, "model": f"XXZ L={L_SITES} periodic, J=1, Delta=1, h_i~U[-W,W], W in (1,3,5)",
                    "D": D, "nnz": nnz, "nev": NEV, "block": BLOCK, "target_eps": EPS,
-                   "precision": ("FP32 filter + FP64 Lanczos/Rayleigh-Ritz/refinement" if args.precision == "f32"
-                                 else "FP64 throughout"),
+                   "precision": (f"FP32 filter + FP64 Lanczos/Rayleigh-Ritz + "
+                                 f"{'pair-float (FP32 hi+lo)' if args.refine_precision == 'df64' else 'FP64'} "
+                                 f"refinement filter" if args.precision == "f32" else "FP64 throughout"),
                    "K": [x["K"] for x in rec], "realisation_W": [x["W"] for x in rec],
                    "l2": "inputs larger than L2 (Krylov basis ~1.9 GB per solve)", "parallelism": f"replicas{world}",
                    "execution": ("the timed steps as one overlapped batch (pf_polfed_solve_batch)" if args.pipeline
@@ -416,13 +466,12 @@ def run_ours(args):
         "e2e": {"value": good / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": rec[0]["h2d"],
                 "d2h_bytes_per_step": rec[0]["d2h"]},
         "gpu_launches": int(launches),
-        "roofline": roof, "roofline_fp64_refine": roof64, "cpu_baseline": cpu, "clocks": clk,
-        "phases_ms": {k: statistics.mean(x["rep"][k] for x in rec)
-                      for k in ("ms_filter_f32", "ms_filter_f64", "ms_orth", "ms_qr", "ms_check", "ms_extract",
-                                "ms_refine", "ms_total")},
+        "roofline": roof, "roofline_refine": roof64, "cpu_baseline": cpu, "clocks": clk,
+        "phases_ms": {k: statistics.mean(x["rep"][k] for x in rec) for k in phase_keys},
         "residual_max_over_hnorm": max(x["rep"]["max_residual"] / x["rep"]["hnorm"] for x in rec),
         "residual_unrefined_max_over_hnorm": max(x["rep"]["max_residual_unrefined"] / x["rep"]["hnorm"]
                                                  for x in rec),
+        "variant_refine_pairfloat": variant,
     }
     print(json.dumps(out))
 
@@ -484,7 +533,7 @@ def run_batch(args):
            "value": gb / statistics.median(tb), "unit": "eigenpairs/s", "higher_is_better": True,
            "one_at_a_time": gs / statistics.median(ts), "speedup": statistics.median(ts) / statistics.median(tb),
            "results_identical": bool(same), "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "dtype": "f32+f64" if args.precision == "f32" else "f64", "data": "synthetic",
+           "dtype": dtype_name(args), "data": "synthetic",
            "config": {"workload": f"xxz_L{L}_batch{n}_nev{nev}_s{s}_eps0.5", "D": Hs[0].D, "nnz": Hs[0].nnz,
                       "K": [pb["K"] for pb in probs][:8], "W": "U[0.5, 8] per realisation"},
            "gpu_launches_batched": int(launches_b), "gpu_launches_one_at_a_time": int(launches_s),
@@ -536,7 +585,7 @@ def run_model(args):
     w = 4 if prec == "f32" else 8
     D, nnz = rec[0]["D"], rec[0]["nnz"]
     out = {"metric": METRIC, "mode": "model", "value": good / t, "unit": "eigenpairs/s", "higher_is_better": True,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(rec), "dtype": "f32+f64" if prec == "f32" else "f64",
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(rec), "dtype": "f32+f32x2+f64" if prec == "f32" else "f64",
            "data": "synthetic", "config": {"workload": c["name"], "D": D, "nnz": nnz, "nev": nev, "block": s,
                                            "target_eps": eps, "K": [x["K"] for x in rec]},
            "eigenpairs_at_tol": good, "solves": len(rec), "clocks": clocks.summary(),
@@ -549,7 +598,8 @@ def run_model(args):
         out["step_f32"] = {"us": 1e3 * per, "GBps": byt / per / 1e6, "alg_bytes": byt}
     if st64:
         per = sum(x["rep"]["ms_filter_f64"] for x in rec) / st64
-        out["step_f64"] = {"us_per_block_step": 1e3 * per, "TFLOPs": (2.0 * nnz * s + 3.0 * D * s) / per / 1e9}
+        out["step_refine"] = {"us": 1e3 * per, "GBps": step_bytes(D, nnz, s, 8) / per / 1e6,
+                              "kernel": "pair-float" if prec == "f32" else "FP64"}
     print(json.dumps(out))
 
 
@@ -599,7 +649,7 @@ def run_serving(args):
            "fp64_one_at_a_time": {"eigenpairs_per_s": good64 / span64, "p50_ms": float(np.percentile(lat, 50)),
                                   "p99_ms": float(np.percentile(lat, 99)), "service_s_total": sum(svc),
                                   "latency": "FIFO queue simulated from measured service times, same arrivals"},
-           "n_gpus": 1, "dtype": "f32+f64", "data": "synthetic", "gpu_launches": int(launches),
+           "n_gpus": 1, "dtype": "f32+f32x2+f64", "data": "synthetic", "gpu_launches": int(launches),
            "clocks": clocks.summary(),
            "config": {"workload": f"serving_xxz_L{'-'.join(map(str, Ls))}_n{args.serve_n}_rate{args.serve_rate}",
                       "requests": args.serve_n, "rate_per_s": args.serve_rate, "L": Ls, "nev": nevs,

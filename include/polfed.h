@@ -284,9 +284,10 @@ typedef struct {
   double refine_guard_lock;/* refinement locks a pair outside the returned set (guard,
                              reserve) once its residual is <= this x res_tol ||H||;
                              0 = 10, < 0 = never (returned pairs lock at 0.5)          */
-  int32_t refine_precision;/* arithmetic of the refinement filter: PF_DF64 (pair-float,
-                             pf_default_opts) or PF_F64; the Ritz vectors, Gram-Schmidt,
-                             Rayleigh-Ritz and residuals stay FP64 either way          */
+  int32_t refine_precision;/* arithmetic of the refinement filter: PF_F64 (the default)
+                             or PF_DF64 (pair-float on the FP32 units, about 2x faster
+                             steps); Gram-Schmidt, Rayleigh-Ritz and the residual check
+                             stay FP64 either way                                      */
 } pf_solve_opts;
 
 typedef struct {

@@ -572,7 +572,7 @@ static pf_status measure_block_steps(const Ham* H, int prec, cudaStream_t st, st
 static int expected_krylov_dim(int nev, int s, double eta);
 
 static pf_status autotune_block(const Ham* H, int prec, int nev, cudaStream_t st, int* s_out, double* us_out,
-                                double* cost_out, int refine_prec = PF_DF64) {
+                                double* cost_out, int refine_prec = PF_F64) {
   std::array<double, 4> us, us64;
   PF_TRY(measure_block_steps(H, prec, st, us));
   if (prec == PF_F32) PF_TRY(measure_block_steps(H, refine_prec, st, us64));
@@ -1683,7 +1683,7 @@ void pf_default_opts(pf_solve_opts* o) {
   o->tol_f32 = 1e-7;
   o->res_tol = 1e-9;
   o->seed = 2024;
-  o->refine_precision = PF_DF64;
+  o->refine_precision = PF_F64;
 }
 
 pf_status pf_spectral_bounds(pf_ham* hh, double tol, double* emin, double* emax, double* rmin, double* rmax,

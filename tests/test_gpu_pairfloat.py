@@ -186,7 +186,7 @@ def test_filter_df64_L18_range_form(pf):
 @pytest.mark.parametrize("L,nev,s", [(12, 20, 8), (14, 40, 16)])
 def test_solve_refine_pairfloat_vs_fp64(pf, L, nev, s):
     """FP32 filter with the refinement in pair-float or in FP64: both reach the residual bar
-    and the dense eigenvalues; pair-float is the default."""
+    and the dense eigenvalues; FP64 is the default."""
     p = pi.xxz_params(L, W=2.5, seed=2200 + L)
     H = pf.Hamiltonian.from_params(p)
     H.spectral_bounds()
@@ -204,7 +204,7 @@ def test_solve_refine_pairfloat_vs_fp64(pf, L, nev, s):
         assert np.max(r.resid) <= 1e-9 * hn, rp
         out[rp] = r
     d = H.solve(0.5, nev, K, block=s, precision="f32", target_abs=lam)
-    assert np.array_equal(d.evals, out["df64"].evals)
+    assert np.array_equal(d.evals, out["f64"].evals)
 
 
 def test_pairfloat_rejects(pf):
