@@ -33,6 +33,11 @@ Fermi-Hubbard (not in the paper; open chain):
   strictly between i and j); element -t times that sign.
   Diagonal: for i = 0..L-1, + U*(n_up_i*n_dn_i); then for i = 0..L-1,
   + mu_i*(n_up_i + n_dn_i) (the occupations as doubles).
+
+QREM (Eq. qrem, App. A): H = sum_alpha E_alpha |alpha><alpha| - Gamma sum_i sigma^x_i on
+  the full space of L spins, row = state.  sigma^x_i flips bit i with element 1, so
+  state alpha couples to alpha ^ (1 << i) with element -Gamma for i = 0..L-1.
+  Diagonal: E_alpha.
 """
 from dataclasses import dataclass
 import numpy as np
@@ -204,6 +209,19 @@ def hubbard_hamiltonian(p):
     return H
 
 
+def qrem_hamiltonian(p):
+    """Eq. qrem on the full 2^L space: diagonal E_alpha, single spin flips with -Gamma."""
+    L = p.L
+    D = 1 << L
+    states = np.arange(D, dtype=np.int64)
+    rows, cols, vals = [states], [states], [np.asarray(p.E, dtype=np.float64).copy()]
+    for i in range(L):
+        rows.append(states)
+        cols.append(states ^ (1 << i))
+        vals.append(np.full(D, -p.Gamma))
+    return csr_from_terms(D, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+
+
 def build(p):
-    """Dispatch on the parameter record's model kind (0 XXZ, 1 quantum sun, 2 Hubbard)."""
-    return {0: xxz_hamiltonian, 1: qsun_hamiltonian, 2: hubbard_hamiltonian}[p.kind](p)
+    """Dispatch on the parameter record's model kind (0 XXZ, 1 quantum sun, 2 Hubbard, 3 QREM)."""
+    return {0: xxz_hamiltonian, 1: qsun_hamiltonian, 2: hubbard_hamiltonian, 3: qrem_hamiltonian}[p.kind](p)

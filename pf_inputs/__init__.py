@@ -8,9 +8,9 @@ the i-th output of a stream seeded with ``seed`` is ``mix64(seed + (i+1)*G)``
 with G = 0x9E3779B97F4A7C15.
 """
 from .rng import splitmix64, uniform01, uniform_pm_half, normals
-from .workloads import (XXZParams, QSunParams, HubbardParams, xxz_params, qsun_params,
-                        hubbard_params, CONFIGS, config_seed, serving_stream)
+from .workloads import (XXZParams, QSunParams, HubbardParams, QREMParams, xxz_params, qsun_params,
+                        hubbard_params, qrem_params, CONFIGS, config_seed, serving_stream)
 
 __all__ = ["splitmix64", "uniform01", "uniform_pm_half", "normals", "XXZParams",
-           "QSunParams", "HubbardParams", "xxz_params", "qsun_params", "hubbard_params",
-           "CONFIGS", "config_seed", "serving_stream"]
+           "QSunParams", "HubbardParams", "QREMParams", "xxz_params", "qsun_params", "hubbard_params",
+           "qrem_params", "CONFIGS", "config_seed", "serving_stream"]

@@ -11,7 +11,7 @@ import numpy as np
 
 from .rng import uniform01, normals
 
-XXZ, QSUN, HUBBARD = 0, 1, 2
+XXZ, QSUN, HUBBARD, QREM = 0, 1, 2, 3
 PBC, OBC = 0, 1
 
 
@@ -58,6 +58,23 @@ class HubbardParams:
     seed: int = 0
     mu: np.ndarray = field(default=None, repr=False)     # on-site potentials mu_i
     kind: int = HUBBARD
+
+
+@dataclass
+class QREMParams:
+    L: int                      # spins; the full space of 2^L states (row = state)
+    Gamma: float = 1.0          # transverse field
+    seed: int = 0
+    E: np.ndarray = field(default=None, repr=False)      # energies E_alpha, alpha = 0..2^L-1
+    kind: int = QREM
+
+
+def qrem_params(L, Gamma=1.0, seed=0):
+    """E_alpha = sqrt(L/2) g_alpha, g_alpha the Box-Muller normals(seed, 2^L) (Eq. qrem: independent
+    Gaussian energies with mean 0 and standard deviation sqrt(L/2))."""
+    D = 1 << L
+    E = np.sqrt(L / 2.0) * normals(seed, D)
+    return QREMParams(L=L, Gamma=Gamma, seed=seed, E=E)
 
 
 def xxz_params(L, N=None, J=1.0, Delta=1.0, W=0.0, bc=PBC, seed=0):

@@ -158,3 +158,49 @@ def test_hubbard_atomic_limit_and_counts():
     L, N = 6, 3
     per = (L - 1) * 2 * math.comb(L - 2, N - 1) * math.comb(L, N)
     assert H.nnz - H.D == 2 * per
+
+
+# ---------------------------------------------------------------- QREM (Eq. qrem)
+def _qrem(L, Gamma, E):
+    return pi.QREMParams(L=L, Gamma=Gamma, E=np.asarray(E, dtype=np.float64))
+
+
+@pytest.mark.parametrize("L", [1, 4, 6])
+def test_qrem_transverse_field_only_spectrum_closed_form(L):
+    # E = 0: H = -Gamma sum_i sigma^x_i, eigenvalues -Gamma (L - 2k) with multiplicity binom(L, k)
+    G = 0.7
+    w = np.linalg.eigvalsh(hm.build(_qrem(L, G, np.zeros(1 << L))).dense())
+    ref = np.sort(np.concatenate([np.full(math.comb(L, k), -G * (L - 2 * k)) for k in range(L + 1)]))
+    assert np.max(np.abs(w - ref)) < 1e-12
+
+
+def test_qrem_two_level_closed_form():
+    E0, E1, G = 0.3, -1.1, 0.45
+    w = np.linalg.eigvalsh(hm.build(_qrem(1, G, [E0, E1])).dense())
+    m, r = 0.5 * (E0 + E1), np.hypot(0.5 * (E0 - E1), G)
+    assert np.allclose(w, [m - r, m + r], atol=1e-15)
+
+
+def test_qrem_structure_diagonal_and_traces():
+    L = 7
+    p = pi.qrem_params(L, Gamma=0.8, seed=31)
+    H = hm.build(p)
+    D = 1 << L
+    assert H.D == D and H.nnz == D * (L + 1)
+    M = H.dense()
+    assert np.array_equal(M, M.T)
+    assert np.array_equal(np.diag(M), p.E)
+    for r in (0, 5, D - 1):
+        cols = H.indices[H.indptr[r]:H.indptr[r + 1]]
+        assert list(cols) == sorted([r] + [r ^ (1 << i) for i in range(L)])
+        off = H.data[H.indptr[r]:H.indptr[r + 1]][cols != r]
+        assert np.all(off == -0.8)
+    assert abs(np.trace(M) - p.E.sum()) < 1e-12
+    assert abs(np.sum(M * M) - (np.sum(p.E ** 2) + L * D * 0.8 ** 2)) < 1e-9
+
+
+def test_qrem_energies_statistics():
+    L = 14
+    E = pi.qrem_params(L, seed=7).E
+    assert abs(E.mean()) < 4 * np.sqrt(L / 2.0) / np.sqrt(E.size)
+    assert abs(E.std() / np.sqrt(L / 2.0) - 1.0) < 0.03
