@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--refine-precision", default="f64", choices=["f64", "df64"],
                     help="arithmetic of the refinement filter: FP64 (the workload's definition) or pair-float")
+    ap.add_argument("--mapping", default="structured", choices=["structured", "csr"],
+                    help="model mode, QREM: how the steps read H~ (generated bit-flip columns or the CSR)")
     ap.add_argument("--no-variant", action="store_true",
                     help="solve mode: skip the extra timed solves with the pair-float refinement filter")
     ap.add_argument("--kernel-only", action="store_true",
@@ -58,7 +60,7 @@ def parse():
     ap.add_argument("--no-pipeline", dest="pipeline", action="store_false")
     ap.add_argument("--L", type=int, default=L_SITES, help="solve mode: chain length (default: the L=20 workload)")
     ap.add_argument("--nev", type=int, default=NEV, help="solve mode: eigenpairs per solve")
-    ap.add_argument("--config", type=int, default=3, choices=[1, 3, 4],
+    ap.add_argument("--config", type=int, default=3, choices=[1, 3, 4, 6],
                     help="model mode: workload 1 (XXZ L=12), 3 (quantum sun N=3 L=15) or 4 (Hubbard L=12)")
     ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serving", "model"],
                     help="solve: the L=20 workload; batch: many small solves together vs one at a time; "
@@ -555,6 +557,8 @@ def run_model(args):
     elif c["model"] == "hubbard":
         mk = lambda r: pi.hubbard_params(c["L"], c["N_up"], c["N_dn"], t=c["t"], U=c["U"], W=c["W"],
                                          seed=pi.config_seed(args.config, r))
+    elif c["model"] == "qrem":
+        mk = lambda r: pi.qrem_params(c["L"], Gamma=c["Gamma"], seed=pi.config_seed(args.config, r))
     else:
         mk = lambda r: pi.xxz_params(c["L"], W=c["W"], seed=pi.config_seed(args.config, r))
     prec = args.precision
@@ -565,9 +569,12 @@ def run_model(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
         H = pf.Hamiltonian.from_params(mk(r))
+        if c["model"] == "qrem":
+            H.set_mapping(args.mapping)
         H.spectral_bounds()
         K = H.choose_K(eps, nev)
-        res = H.solve(eps, nev, K, block=s, precision=prec, return_vectors=False, raise_on_notconv=False)
+        res = H.solve(eps, nev, K, block=s, precision=prec, return_vectors=False, raise_on_notconv=False,
+                      refine_precision=args.refine_precision)
         e1.record(st)
         e1.synchronize()
         hn = res.report["hnorm"]
@@ -585,21 +592,29 @@ def run_model(args):
     w = 4 if prec == "f32" else 8
     D, nnz = rec[0]["D"], rec[0]["nnz"]
     out = {"metric": METRIC, "mode": "model", "value": good / t, "unit": "eigenpairs/s", "higher_is_better": True,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(rec), "dtype": "f32+f32x2+f64" if prec == "f32" else "f64",
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(rec), "dtype": dtype_name(args),
            "data": "synthetic", "config": {"workload": c["name"], "D": D, "nnz": nnz, "nev": nev, "block": s,
                                            "target_eps": eps, "K": [x["K"] for x in rec]},
            "eigenpairs_at_tol": good, "solves": len(rec), "clocks": clocks.summary(),
            "phases_ms": {k: statistics.mean(x["rep"][k] for x in rec)
                          for k in ("ms_filter_f32", "ms_filter_f64", "ms_orth", "ms_qr", "ms_check", "ms_extract",
                                    "ms_refine", "ms_total")}}
+    structured = c["model"] == "qrem" and args.mapping == "structured"
+    if structured:
+        out["config"]["mapping"] = "structured (bit-flip columns generated in registers; diagonal read)"
+
+    def alg_bytes(w):
+        # the structured mapping reads only the diagonal of the matrix
+        return D * w + 4 * D * s * w if structured else step_bytes(D, nnz, s, w)
+
     if st32:
         per = sum(x["rep"]["ms_filter_f32"] for x in rec) / st32
-        byt = step_bytes(D, nnz, s, 4)
+        byt = alg_bytes(4)
         out["step_f32"] = {"us": 1e3 * per, "GBps": byt / per / 1e6, "alg_bytes": byt}
     if st64:
         per = sum(x["rep"]["ms_filter_f64"] for x in rec) / st64
-        out["step_refine"] = {"us": 1e3 * per, "GBps": step_bytes(D, nnz, s, 8) / per / 1e6,
-                              "kernel": "pair-float" if prec == "f32" else "FP64"}
+        out["step_refine"] = {"us": 1e3 * per, "GBps": alg_bytes(8) / per / 1e6,
+                              "kernel": "pair-float" if args.refine_precision == "df64" and prec == "f32" else "FP64"}
     print(json.dumps(out))
 
 

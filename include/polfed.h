@@ -45,7 +45,7 @@ typedef enum {
   PF_EBREAKDOWN = 7 /* Cholesky-QR breakdown the recovery path could not repair       */
 } pf_status;
 
-typedef enum { PF_MODEL_XXZ = 0, PF_MODEL_QSUN = 1, PF_MODEL_HUBBARD = 2 } pf_model_kind;
+typedef enum { PF_MODEL_XXZ = 0, PF_MODEL_QSUN = 1, PF_MODEL_HUBBARD = 2, PF_MODEL_QREM = 3 } pf_model_kind;
 typedef enum { PF_BC_PERIODIC = 0, PF_BC_OPEN = 1 } pf_boundary;
 /* Arithmetic of a filter (Clenshaw) step.
  *  PF_F64   double blocks, FP64 values and arithmetic.
@@ -68,7 +68,9 @@ typedef enum { PF_F64 = 0, PF_F32 = 1, PF_DF64 = 2 } pf_precision;
  *     ray j couples dot spin n(j) and outer spin j with g0 alpha^(j + u_noise_j)/4.
  *  Fermi-Hubbard (not in the paper): L sites, N_up / N_dn fermions, hopping t,
  *     interaction U, potentials mu_i; row = rank_up * D_dn + rank_dn; Jordan-Wigner
- *     order: all up modes, then all down modes.                                     */
+ *     order: all up modes, then all down modes.
+ *  QREM (Eq. qrem): L spins, full space D = 2^L, row = state; diagonal E_alpha,
+ *     single spin flips alpha -> alpha ^ (1 << i) with element -Gamma.              */
 typedef struct {
   int32_t kind;     /* pf_model_kind                                   */
   int32_t L;        /* sites (XXZ, Hubbard) or outer spins (quantum sun) */
@@ -78,6 +80,7 @@ typedef struct {
   double J, Delta;  /* XXZ                                              */
   double t, U;      /* Hubbard                                          */
   double g0, alpha, gamma; /* quantum sun                               */
+  double Gamma;     /* QREM transverse field                            */
 } pf_model;
 
 /* Disorder and random couplings, host arrays (copied during the call).          */
@@ -87,6 +90,7 @@ typedef struct {
   const double* A;        /* quantum-sun raw normals, [2^N * 2^N] row-major         */
   const double* u_noise;  /* quantum-sun exponent noise u_j - j, [L]                */
   const int32_t* n_of_j;  /* quantum-sun dot spin coupled to outer spin j, [L]      */
+  const double* E;        /* QREM energies E_alpha, [2^L]                           */
 } pf_params;
 
 typedef struct pf_basis pf_basis;
@@ -148,6 +152,16 @@ pf_status pf_spectral_bounds(pf_ham* H, double tol, double* emin, double* emax, 
 /* Set the rescaling directly (E_c, dE) and write H~ values; for tests and for callers
  * that know their bounds.                                                          */
 pf_status pf_set_rescale(pf_ham* H, double Ec, double dE, pf_stream_t stream);
+/* How the Clenshaw steps read H~ (custom mappings, Sec. 5.7-5.8).
+ *  PF_MAP_CSR         the stored CSR arrays (every model; the default except QREM).
+ *  PF_MAP_STRUCTURED  QREM only (its default): a row's columns r ^ (1 << i) are generated
+ *                     in registers in ascending order and every off-diagonal element is the
+ *                     one value -Gamma / dE; only the diagonal is read.  The FMA sequence is
+ *                     the CSR step's, so both mappings give the same bits.
+ * Errors: PF_EINVAL (unknown mapping, or structured for another model).              */
+typedef enum { PF_MAP_CSR = 0, PF_MAP_STRUCTURED = 1 } pf_mapping;
+pf_status pf_ham_set_mapping(pf_ham* H, int32_t mapping);
+
 /* Rescaling and the device arrays of H~ values (FP64 and FP32, CSR order).         */
 pf_status pf_ham_rescaled(const pf_ham* H, double* Ec, double* dE, const double** val64,
                           const float** val32);

@@ -9,7 +9,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpolfed.so")
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ENOTCONV, PF_ETIMEOUT, PF_ECUDA, PF_ESTATE, PF_EBREAKDOWN = range(8)
-PF_MODEL_XXZ, PF_MODEL_QSUN, PF_MODEL_HUBBARD = 0, 1, 2
+PF_MODEL_XXZ, PF_MODEL_QSUN, PF_MODEL_HUBBARD, PF_MODEL_QREM = 0, 1, 2, 3
+PF_MAP_CSR, PF_MAP_STRUCTURED = 0, 1
 PF_F64, PF_F32, PF_DF64 = 0, 1, 2
 PF_FORM_AUTO, PF_FORM_STEPS, PF_FORM_GRAPH = -1, 0, -2
 
@@ -18,12 +19,13 @@ class pf_model(C.Structure):
     _fields_ = [("kind", C.c_int32), ("L", C.c_int32), ("N", C.c_int32), ("N_up", C.c_int32),
                 ("N_dn", C.c_int32), ("bc", C.c_int32), ("J", C.c_double), ("Delta", C.c_double),
                 ("t", C.c_double), ("U", C.c_double), ("g0", C.c_double), ("alpha", C.c_double),
-                ("gamma", C.c_double)]
+                ("gamma", C.c_double), ("Gamma", C.c_double)]
 
 
 class pf_params(C.Structure):
     _fields_ = [("h", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double)), ("A", C.POINTER(C.c_double)),
-                ("u_noise", C.POINTER(C.c_double)), ("n_of_j", C.POINTER(C.c_int32))]
+                ("u_noise", C.POINTER(C.c_double)), ("n_of_j", C.POINTER(C.c_int32)),
+                ("E", C.POINTER(C.c_double))]
 
 
 class pf_solve_opts(C.Structure):
@@ -101,6 +103,7 @@ PROTOTYPES = {
     "pf_spectral_bounds": (i32, [vp, dbl, P(dbl), P(dbl), P(dbl), P(dbl), vp]),
     "pf_set_rescale": (i32, [vp, dbl, dbl, vp]),
     "pf_ham_rescaled": (i32, [vp, P(dbl), P(dbl), P(vp), P(vp)]),
+    "pf_ham_set_mapping": (i32, [vp, i32]),
     "pf_ham_moments": (i32, [vp, P(dbl), P(dbl), vp]),
     "pf_filter_coefficients": (i32, [dbl, i32, P(dbl), vp]),
     "pf_choose_K": (i32, [vp, dbl, i32, P(i32), vp]),

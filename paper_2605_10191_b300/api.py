@@ -65,6 +65,17 @@ def _prec_code(name):
     return _PREC_NAMES[name]
 
 
+def _c_params(model):
+    """pf_params over the model's host arrays, and the arrays it points into (keep them alive)."""
+    arrays = [_dbl_arr(model.h), _dbl_arr(model.mu), _dbl_arr(model.A), _dbl_arr(model.u_noise), _dbl_arr(model.E)]
+    nj = None
+    if model.n_of_j is not None:
+        nj = np.ascontiguousarray(np.asarray(model.n_of_j, dtype=np.int32))
+    prm = L.pf_params(h=arrays[0][1], mu=arrays[1][1], A=arrays[2][1], u_noise=arrays[3][1],
+                      n_of_j=nj.ctypes.data_as(C.POINTER(C.c_int32)) if nj is not None else None, E=arrays[4][1])
+    return prm, (arrays, nj)
+
+
 def _dbl_arr(x):
     if x is None:
         return None, None
@@ -102,11 +113,13 @@ class Model:
     g0: float = 1.0
     alpha: float = 0.75
     gamma: float = 1.0
+    Gamma: float = 1.0
     h: object = None
     mu: object = None
     A: object = None
     u_noise: object = None
     n_of_j: object = None
+    E: object = None
 
     @staticmethod
     def from_params(p):
@@ -119,12 +132,14 @@ class Model:
                          u_noise=p.u_noise, n_of_j=p.n_of_j)
         if k == L.PF_MODEL_HUBBARD:
             return Model(kind=k, L=p.L, N_up=p.N_up, N_dn=p.N_dn, bc=p.bc, t=p.t, U=p.U, mu=p.mu)
+        if k == L.PF_MODEL_QREM:
+            return Model(kind=k, L=p.L, Gamma=p.Gamma, E=p.E)
         raise ValueError(f"unknown model kind {k}")
 
     def c_model(self):
         return L.pf_model(kind=self.kind, L=self.L, N=self.N, N_up=self.N_up, N_dn=self.N_dn, bc=self.bc,
                           J=self.J, Delta=self.Delta, t=self.t, U=self.U, g0=self.g0, alpha=self.alpha,
-                          gamma=self.gamma)
+                          gamma=self.gamma, Gamma=self.Gamma)
 
 
 class Basis:
@@ -173,13 +188,7 @@ class Hamiltonian:
         _install_torch_allocator()
         self.model = model
         self.basis = Basis(model, stream)
-        arrays = [_dbl_arr(model.h), _dbl_arr(model.mu), _dbl_arr(model.A), _dbl_arr(model.u_noise)]
-        nj = None
-        if model.n_of_j is not None:
-            nj = np.ascontiguousarray(np.asarray(model.n_of_j, dtype=np.int32))
-        self._keep = (arrays, nj)
-        prm = L.pf_params(h=arrays[0][1], mu=arrays[1][1], A=arrays[2][1], u_noise=arrays[3][1],
-                          n_of_j=nj.ctypes.data_as(C.POINTER(C.c_int32)) if nj is not None else None)
+        prm, self._keep = _c_params(model)
         h = C.c_void_p()
         check(lib().pf_build_hamiltonian(self.basis.handle, C.byref(model.c_model()), C.byref(prm), C.byref(h),
                                          _stream(stream)), "pf_build_hamiltonian")
@@ -208,6 +217,11 @@ class Hamiltonian:
         return (_copy_device(rp.value, self.D + 1, "<i8", torch.int64),
                 _copy_device(col.value, self.nnz, "<i4", torch.int32),
                 _copy_device(val.value, self.nnz, "<f8", torch.float64))
+
+    def set_mapping(self, mapping):
+        """How the steps read H~: "csr" or "structured" (QREM only, its default)."""
+        m = {"csr": L.PF_MAP_CSR, "structured": L.PF_MAP_STRUCTURED}[mapping]
+        check(lib().pf_ham_set_mapping(self.handle, m), "pf_ham_set_mapping")
 
     def rescaled(self):
         Ec, dE, v64, v32 = C.c_double(), C.c_double(), C.c_void_p(), C.c_void_p()
@@ -426,12 +440,7 @@ class Server:
         self._nev = {}
 
     def submit(self, model, eps, nev):
-        arrays = [_dbl_arr(model.h), _dbl_arr(model.mu), _dbl_arr(model.A), _dbl_arr(model.u_noise)]
-        nj = None
-        if model.n_of_j is not None:
-            nj = np.ascontiguousarray(np.asarray(model.n_of_j, dtype=np.int32))
-        prm = L.pf_params(h=arrays[0][1], mu=arrays[1][1], A=arrays[2][1], u_noise=arrays[3][1],
-                          n_of_j=nj.ctypes.data_as(C.POINTER(C.c_int32)) if nj is not None else None)
+        prm, keep = _c_params(model)
         rid = C.c_int64()
         check(lib().pf_server_submit(self.handle, C.byref(model.c_model()), C.byref(prm), float(eps), int(nev),
                                      C.byref(rid)), "pf_server_submit")

@@ -119,6 +119,9 @@ static pf_status build_basis_impl(const pf_model* m, Basis** out, cudaStream_t s
   } else if (m->kind == PF_MODEL_QSUN) {
     if (L < 1 || m->N < 1 || m->N > 5 || m->N + L > 30) { delete b; return PF_EINVAL; }
     b->D = (int64_t)1 << (m->N + L);
+  } else if (m->kind == PF_MODEL_QREM) {
+    if (L < 1 || L > 30) { delete b; return PF_EINVAL; }
+    b->D = (int64_t)1 << L;
   } else {
     delete b;
     return PF_EINVAL;
@@ -162,6 +165,8 @@ struct DevModel {
   int kind, L, N, nbonds;
   int64_t Dd;                 // Hubbard: down-table length
   double jdq, halfJ, negt, U;
+  double negG;                // QREM: -Gamma
+  const double* E;            // QREM energies [2^L]
   const double* hhalf;        // XXZ/qsun: h_i * 0.5
   const double* mu;           // Hubbard
   const double* hdot;         // qsun: 2^N x 2^N
@@ -244,6 +249,9 @@ __device__ void gen_row(const DevModel& M, int64_t row, RowTerms& T) {
       uint32_t flip = (1u << (L + M.nj[j])) | (1u << j);
       T.push((int64_t)(s ^ flip), M.coef[j]);
     }
+  } else if (M.kind == PF_MODEL_QREM) {
+    T.push(row, M.E[row]);
+    for (int i = 0; i < L; ++i) T.push((int64_t)((uint32_t)row ^ (1u << i)), M.negG);
   } else {  // Hubbard
     int64_t iu = row / M.Dd, id = row % M.Dd;
     uint32_t up = M.states[iu], dn = M.dns[id];
@@ -360,7 +368,7 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
   M.binom = b->binom;
   M.nbonds = (m->bc == PF_BC_PERIODIC) ? L : L - 1;
   // host-side parameter preprocessing (each a single correctly rounded operation)
-  std::vector<double> hh, mu, hdot, coef;
+  std::vector<double> hh, mu, hdot, coef, en;
   std::vector<int32_t> nj;
   if (m->kind == PF_MODEL_XXZ) {
     if (!p->h) return PF_EINVAL;
@@ -387,6 +395,11 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
       nj[j] = p->n_of_j[j];
       if (nj[j] < 0 || nj[j] >= m->N) return PF_EINVAL;
     }
+  } else if (m->kind == PF_MODEL_QREM) {
+    if (!p->E) return PF_EINVAL;
+    M.nbonds = 0;
+    M.negG = -m->Gamma;
+    en.assign(p->E, p->E + b->D);
   } else if (m->kind == PF_MODEL_HUBBARD) {
     if (!p->mu) return PF_EINVAL;
     M.negt = -m->t;
@@ -402,7 +415,7 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
   size_t nd_off = 0;
   std::vector<double> blob;
   auto add = [&](const std::vector<double>& v) { size_t o = blob.size(); blob.insert(blob.end(), v.begin(), v.end()); return o; };
-  size_t o_hh = add(hh), o_mu = add(mu), o_hd = add(hdot), o_cf = add(coef);
+  size_t o_hh = add(hh), o_mu = add(mu), o_hd = add(hdot), o_cf = add(coef), o_en = add(en);
   (void)nd_off;
   size_t nblob = blob.size() * sizeof(double) + nj.size() * sizeof(int32_t) + 16;
   DevBuf dblob;
@@ -415,6 +428,7 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
   M.mu = dbl + o_mu;
   M.hdot = dbl + o_hd;
   M.coef = dbl + o_cf;
+  M.E = dbl + o_en;
   M.nj = dnj;
 
   Ham* H = new Ham();
@@ -462,6 +476,7 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
     delete H;
     return PF_ECUDA;
   }
+  H->mapping = m->kind == PF_MODEL_QREM ? PF_MAP_STRUCTURED : PF_MAP_CSR;
   *out = H;
   return PF_OK;
 }
@@ -480,6 +495,19 @@ __global__ void rescale_kernel(int64_t D, const int64_t* rp, const int32_t* col,
   }
 }
 
+// The diagonal of H~ in the three value forms, copied from the CSR (structured mapping).
+__global__ void diag_copy_kernel(int64_t D, const int64_t* rp, const int32_t* col, const double* vt,
+                                 const float* v32, const float2* vdf, double* dt, float* d32, float2* ddf) {
+  int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= D) return;
+  for (int64_t j = rp[row]; j < rp[row + 1]; ++j)
+    if (col[j] == row) {
+      dt[row] = vt[j];
+      d32[row] = v32[j];
+      ddf[row] = vdf[j];
+    }
+}
+
 pf_status set_rescale(Ham* H, double Ec, double dE, cudaStream_t st) {
   if (!(dE > 0.0) || !std::isfinite(Ec) || !std::isfinite(dE)) return PF_EINVAL;
   H->Ec = Ec;
@@ -487,6 +515,20 @@ pf_status set_rescale(Ham* H, double Ec, double dE, cudaStream_t st) {
   rescale_kernel<<<(unsigned)ceil_div(H->D, 256), 256, 0, st>>>(H->D, H->row_ptr, H->col, H->val, Ec, dE, H->val_t,
                                                                  H->val32, H->val_df);
   PF_LAUNCH_CHECK("rescale_kernel");
+  if (H->m.kind == PF_MODEL_QREM) {
+    // structured mapping: every off-diagonal element of H~ is -Gamma / dE (the value the
+    // rescale kernel computes for each of them), the diagonal is kept per row
+    if (!H->diag_t) {
+      H->diag_t = (double*)dev_alloc(H->D * sizeof(double), st);
+      H->diag32 = (float*)dev_alloc(H->D * sizeof(float), st);
+      H->diag_df = (float2*)dev_alloc(H->D * sizeof(float2), st);
+      if (!H->diag_t || !H->diag32 || !H->diag_df) return PF_ENOMEM;
+    }
+    diag_copy_kernel<<<(unsigned)ceil_div(H->D, 256), 256, 0, st>>>(H->D, H->row_ptr, H->col, H->val_t, H->val32,
+                                                                    H->val_df, H->diag_t, H->diag32, H->diag_df);
+    PF_LAUNCH_CHECK("diag_copy_kernel");
+    H->off_t = (-H->m.Gamma) / dE;
+  }
   H->has_rescale = 1;
   return PF_OK;
 }
@@ -636,6 +678,9 @@ void pf_free_ham(pf_ham* hh) {
   dev_free(H->val_t, H->st);
   dev_free(H->val32, H->st);
   dev_free(H->val_df, H->st);
+  dev_free(H->diag_t, H->st);
+  dev_free(H->diag32, H->st);
+  dev_free(H->diag_df, H->st);
   delete H;
 }
 
@@ -643,6 +688,20 @@ pf_status pf_set_rescale(pf_ham* hh, double Ec, double dE, pf_stream_t stream) {
   Ham* H = reinterpret_cast<Ham*>(hh);
   if (!H) return PF_EINVAL;
   return set_rescale(H, Ec, dE, (cudaStream_t)stream);
+}
+
+pf_status pf_ham_set_mapping(pf_ham* hh, int32_t mapping) {
+  Ham* H = reinterpret_cast<Ham*>(hh);
+  if (!H) return PF_EINVAL;
+  if (mapping == PF_MAP_CSR) {
+    H->mapping = PF_MAP_CSR;
+    return PF_OK;
+  }
+  if (mapping == PF_MAP_STRUCTURED && H->m.kind == PF_MODEL_QREM) {
+    H->mapping = PF_MAP_STRUCTURED;
+    return PF_OK;
+  }
+  return PF_EINVAL;
 }
 
 pf_status pf_ham_rescaled(const pf_ham* hh, double* Ec, double* dE, const double** val64, const float** val32) {

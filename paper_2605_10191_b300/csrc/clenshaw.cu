@@ -277,6 +277,28 @@ template <typename T> __device__ __forceinline__ T ld_val(const T* p) {
   }
 }
 
+// The end of a row segment: out = fma(alpha, acc, fma(a, v, -beta q)), or fma(alpha, acc, a v)
+// without the B2 term.  beta is 0 or 1; with the B2 term known present it is 1, so -beta q is -q
+// (the same bits as the run-time form, where 1 * q is exact).
+template <typename T, int E, bool L2ONLY, int B2M>
+__device__ __forceinline__ void row_epilogue(int64_t off, const T (&acc)[E], bool hb2, const T* __restrict__ V,
+                                             const T* B2, T* out, T a, T alpha, T beta) {
+  Vec<T, E> v = ld_default<T, E>(V + off);
+  Vec<T, E> r;
+  if (hb2) {
+    Vec<T, E> q;
+    if constexpr (L2ONLY) q = ld_l2<T, E>(B2 + off);
+    else q = ld_plain<T, E>(B2 + off);
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      r.x[e] = stored(fmadd(alpha, acc[e], fmadd(a, v.x[e], B2M > 0 ? -q.x[e] : -(beta * q.x[e]))));
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) r.x[e] = stored(fmadd(alpha, acc[e], a * v.x[e]));
+  }
+  st_default<T, E>(out + off, r);
+}
+
 // One row segment (lane's E entries) of one step:
 //     out[row, :] = a V[row, :] + alpha * sum_j val[j] B1[col[j], :] - beta B2[row, :]
 // SP / B2M: 1 = the SpMM / the B2 term is present, 0 = absent, -1 = decided at run time by
@@ -327,22 +349,7 @@ __device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_
       for (int e = 0; e < E; ++e) acc[e] = fmadd(h0, b0.x[e], acc[e]);
     }
   }
-  Vec<T, E> v = ld_default<T, E>(V + off);
-  Vec<T, E> r;
-  if (hb2) {
-    Vec<T, E> q;
-    if constexpr (L2ONLY) q = ld_l2<T, E>(B2 + off);
-    else q = ld_plain<T, E>(B2 + off);
-    // beta is 0 or 1; with the B2 term known present it is 1, so -beta q is -q (the same bits
-    // as the run-time form, where 1 * q is exact)
-#pragma unroll
-    for (int e = 0; e < E; ++e)
-      r.x[e] = stored(fmadd(alpha, acc[e], fmadd(a, v.x[e], B2M > 0 ? -q.x[e] : -(beta * q.x[e]))));
-  } else {
-#pragma unroll
-    for (int e = 0; e < E; ++e) r.x[e] = stored(fmadd(alpha, acc[e], a * v.x[e]));
-  }
-  st_default<T, E>(out + off, r);
+  row_epilogue<T, E, L2ONLY, B2M>(off, acc, hb2, V, B2, out, a, alpha, beta);
 }
 
 // One Clenshaw step over a D x s block.  rows_per_cta = 0: thread group g owns row g (one
@@ -377,6 +384,106 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) clenshaw_step_kerne
   }
 }
 
+// Structured mapping of QREM (Eq. qrem; the custom GPU mapping of Sec. 5.8): row r of H~ holds
+// d_r = diag[r] at column r and the one value g = -Gamma / dE at the L columns r ^ (1 << i).  The
+// columns are generated in registers in ascending order, as the CSR stores them: r - 2^i for the
+// set bits i from the highest down, then r, then r + 2^i for the unset bits from the lowest up.
+// The FMA sequence (rounds of four, then the rest, in that order) is clenshaw_row's, so the
+// structured and the CSR mappings give the same bits.
+template <typename T, int S, int SP, int B2M>
+__device__ __forceinline__ void qrem_row(int64_t row, int lane, int L, const T* __restrict__ diag, T g,
+                                         const T* __restrict__ V, const T* B1, const T* B2, T* out, T a, T alpha,
+                                         T beta) {
+  using Sh = Shape<T, S>;
+  constexpr int E = Sh::E;
+  const int64_t off = row * S + lane * E;
+  T acc[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) acc[e] = T(0);
+  const bool spmm = SP < 0 ? (alpha != T(0)) : (SP > 0);
+  const bool hb2 = B2M < 0 ? (beta != T(0)) : (B2M > 0);
+  if (spmm) {
+    const uint32_t r = (uint32_t)row;
+    const uint32_t full = L >= 32 ? 0xffffffffu : ((1u << L) - 1u);
+    uint32_t sb = r & full;     // set bits still to visit, highest first
+    uint32_t ub = ~r & full;    // unset bits still to visit, lowest first
+    bool dpend = true;
+    const T dr = ld_val(diag + row);
+    auto next = [&](uint32_t& c, T& h) {
+      if (sb) {
+        const int i = 31 - __clz(sb);
+        sb ^= 1u << i;
+        c = r ^ (1u << i);
+        h = g;
+      } else if (dpend) {
+        dpend = false;
+        c = r;
+        h = dr;
+      } else {
+        const int i = __ffs(ub) - 1;
+        ub &= ub - 1u;
+        c = r | (1u << i);
+        h = g;
+      }
+    };
+    const int n = L + 1;
+    int j = 0;
+    for (; j + 4 <= n; j += 4) {
+      uint32_t c0, c1, c2, c3;
+      T h0, h1, h2, h3;
+      next(c0, h0);
+      next(c1, h1);
+      next(c2, h2);
+      next(c3, h3);
+      Vec<T, E> b0 = ld_default<T, E>(B1 + (int64_t)c0 * S + lane * E);
+      Vec<T, E> b1 = ld_default<T, E>(B1 + (int64_t)c1 * S + lane * E);
+      Vec<T, E> b2 = ld_default<T, E>(B1 + (int64_t)c2 * S + lane * E);
+      Vec<T, E> b3 = ld_default<T, E>(B1 + (int64_t)c3 * S + lane * E);
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        acc[e] = fmadd(h0, b0.x[e], acc[e]);
+        acc[e] = fmadd(h1, b1.x[e], acc[e]);
+        acc[e] = fmadd(h2, b2.x[e], acc[e]);
+        acc[e] = fmadd(h3, b3.x[e], acc[e]);
+      }
+    }
+    for (; j < n; ++j) {
+      uint32_t c0;
+      T h0;
+      next(c0, h0);
+      Vec<T, E> b0 = ld_default<T, E>(B1 + (int64_t)c0 * S + lane * E);
+#pragma unroll
+      for (int e = 0; e < E; ++e) acc[e] = fmadd(h0, b0.x[e], acc[e]);
+    }
+  }
+  row_epilogue<T, E, false, B2M>(off, acc, hb2, V, B2, out, a, alpha, beta);
+}
+
+template <typename T, int S, int SP, int B2M>
+__global__ void __launch_bounds__(256, step_min_blocks<T>()) qrem_step_kernel(int64_t D, int L,
+                                                                              const T* __restrict__ diag, T g,
+                                                                              const T* __restrict__ V,
+                                                                              const T* __restrict__ B1, const T* B2,
+                                                                              T* out, T a, T alpha, T beta,
+                                                                              int64_t rows_per_cta) {
+  using Sh = Shape<T, S>;
+  constexpr int G = Sh::G;
+  const int lane = (int)(threadIdx.x % G);
+  if (rows_per_cta > 0) {
+    const int64_t r0 = blockIdx.x * rows_per_cta;
+    const int64_t r1 = r0 + rows_per_cta < D ? r0 + rows_per_cta : D;
+    for (int64_t row = r0 + threadIdx.x / G; row < r1; row += 256 / G)
+      qrem_row<T, S, SP, B2M>(row, lane, L, diag, g, V, B1, B2, out, a, alpha, beta);
+  } else if (rows_per_cta < 0) {
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+    for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; row < D; row += groups)
+      qrem_row<T, S, SP, B2M>(row, lane, L, diag, g, V, B1, B2, out, a, alpha, beta);
+  } else {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    if (row < D) qrem_row<T, S, SP, B2M>(row, lane, L, diag, g, V, B1, B2, out, a, alpha, beta);
+  }
+}
+
 // Launch shape of a step over `rows` rows: FP32 and pair-float steps use one wave of contiguous
 // row ranges (they are bound by their neighbour gathers, which the ranges keep in L1); FP64 steps
 // are bound by the FP64 pipe and keep one row per thread group.  cta_cap > 0 limits the CTAs
@@ -387,21 +494,23 @@ struct StepShape {
   unsigned grid;
   int64_t rows_per_cta;
 };
-template <typename T, int S, int SP, int B2M>
-static StepShape step_shape(int64_t rows, int cta_cap = 0) {
+static int device_sms() {
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return nsm;
+}
+template <typename K>
+static int kernel_occupancy(K kern) {
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
+  return occ > 0 ? occ : 1;
+}
+template <typename T, int S>
+static StepShape shape_for(int64_t rows, int cta_cap, int nsm, int occ) {
   using Sh = Shape<T, S>;
-  static const int nsm_occ[2] = {[] {
-    int dev = 0, nsm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    return nsm;
-  }(), [] {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, clenshaw_step_kernel<T, S, SP, B2M>, 256, 0);
-    return occ > 0 ? occ : 1;
-  }()};
-  const int per_sm = cta_cap > 0 ? std::min(nsm_occ[1], cta_cap) : nsm_occ[1];
-  const int64_t waves = (int64_t)nsm_occ[0] * per_sm;
+  const int per_sm = cta_cap > 0 ? std::min(occ, cta_cap) : occ;
+  const int64_t waves = (int64_t)nsm * per_sm;
   if constexpr (!std::is_same_v<T, double>) {
     const int64_t R = ceil_div(rows, waves);
     if (R > 256 / Sh::G) return StepShape{(unsigned)ceil_div(rows, R), R};
@@ -409,6 +518,18 @@ static StepShape step_shape(int64_t rows, int cta_cap = 0) {
   const int64_t classic = ceil_div(rows * Sh::G, 256);
   if (cta_cap > 0 && classic > waves) return StepShape{(unsigned)waves, -1};
   return StepShape{(unsigned)classic, 0};
+}
+template <typename T, int S, int SP, int B2M>
+static StepShape step_shape(int64_t rows, int cta_cap = 0) {
+  static const int nsm = device_sms();
+  static const int occ = kernel_occupancy(clenshaw_step_kernel<T, S, SP, B2M>);
+  return shape_for<T, S>(rows, cta_cap, nsm, occ);
+}
+template <typename T, int S, int SP, int B2M>
+static StepShape qrem_shape(int64_t rows, int cta_cap = 0) {
+  static const int nsm = device_sms();
+  static const int occ = kernel_occupancy(qrem_step_kernel<T, S, SP, B2M>);
+  return shape_for<T, S>(rows, cta_cap, nsm, occ);
 }
 
 template <typename T, int S, int SP, int B2M>
@@ -468,24 +589,80 @@ pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* co
   return PF_EINVAL;
 }
 
+// Structured-mapping (QREM) step launches: same shapes, validation and operands as the CSR step.
+template <typename T, int S, int SP, int B2M>
+static void launch_qrem_form(int64_t D, int L, const T* diag, T g, const T* V, const T* B1, const T* B2, T* out,
+                             T a, T alpha, T beta, cudaStream_t st, int cap) {
+  const StepShape sh = qrem_shape<T, S, SP, B2M>(D, cap);
+  qrem_step_kernel<T, S, SP, B2M><<<sh.grid, 256, 0, st>>>(D, L, diag, g, V, B1, B2, out, a, alpha, beta,
+                                                          sh.rows_per_cta);
+}
+template <typename T, int S>
+static pf_status launch_qrem_s(int64_t D, int L, const T* diag, T g, const T* V, const T* B1, const T* B2, T* out,
+                               T a, T alpha, T beta, cudaStream_t st, int cap) {
+  const bool spmm = alpha != T(0);
+  const bool hb2 = beta != T(0);
+  if (spmm && hb2) launch_qrem_form<T, S, 1, 1>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+  else if (spmm) launch_qrem_form<T, S, 1, 0>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+  else if (hb2) launch_qrem_form<T, S, 0, 1>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+  else launch_qrem_form<T, S, 0, 0>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+  PF_LAUNCH_CHECK("qrem_step_kernel");
+  return PF_OK;
+}
+template <typename T>
+static pf_status launch_qrem(int s, int64_t D, int L, const T* diag, T g, const T* V, const T* B1, const T* B2,
+                             T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
+  switch (s) {
+    case 1: return launch_qrem_s<T, 1>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 2: return launch_qrem_s<T, 2>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 4: return launch_qrem_s<T, 4>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 8: return launch_qrem_s<T, 8>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 16: return launch_qrem_s<T, 16>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 32: return launch_qrem_s<T, 32>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 64: return launch_qrem_s<T, 64>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+  }
+  return PF_EINVAL;
+}
+
+// One step of H~ through the handle's mapping: the CSR arrays, or the structured QREM rows.
+pf_status ham_step(const Ham* H, int prec, int s, const void* V, const void* B1, const void* B2, void* out,
+                   double a, double alpha, double beta, cudaStream_t st, int cta_cap) {
+  if (H->mapping != PF_MAP_STRUCTURED || !H->diag_t)
+    return clenshaw_step_raw(H->D, H->row_ptr, H->col, ham_vals(H, prec), prec, s, V, B1, B2, out, a, alpha, beta,
+                             st, cta_cap);
+  if (!valid_s(s) || !V || !out) return PF_EINVAL;
+  if (alpha != 0.0 && !B1) return PF_EINVAL;
+  if (beta != 0.0 && !B2) return PF_EINVAL;
+  if (beta != 0.0 && beta != 1.0) return PF_EINVAL;
+  const int64_t D = H->D;
+  const int L = H->m.L;
+  if (prec == PF_F64)
+    return launch_qrem<double>(s, D, L, H->diag_t, H->off_t, (const double*)V, (const double*)B1,
+                               (const double*)B2, (double*)out, a, alpha, beta, st, cta_cap);
+  if (prec == PF_F32)
+    return launch_qrem<float>(s, D, L, H->diag32, (float)H->off_t, (const float*)V, (const float*)B1,
+                              (const float*)B2, (float*)out, (float)a, (float)alpha, (float)beta, st, cta_cap);
+  if (prec == PF_DF64)
+    return launch_qrem<df2>(s, D, L, reinterpret_cast<const df2*>(H->diag_df), df2(H->off_t), (const df2*)V,
+                            (const df2*)B1, (const df2*)B2, (df2*)out, df2(a), df2(alpha), df2(beta), st, cta_cap);
+  return PF_EINVAL;
+}
+
 // K-step recurrence.  b_i lives in aux[i & 1]: step i reads b_{i+1} = aux[(i+1)&1] and
 // overwrites b_{i+2} (= aux[i&1]) with b_i.
 pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs, const void*,
                            int K, void* aux0, void* aux1, cudaStream_t st, int cta_cap) {
   if (K < 1 || !coeffs) return PF_EINVAL;
-  const void* val = ham_vals(H, prec);
   void* aux[2] = {aux0, aux1};
   // i = K: b_K = a_K V
-  PF_TRY(clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, s, V, nullptr, nullptr, aux[K & 1], coeffs[K], 0.0,
-                           0.0, st, cta_cap));
+  PF_TRY(ham_step(H, prec, s, V, nullptr, nullptr, aux[K & 1], coeffs[K], 0.0, 0.0, st, cta_cap));
   for (int i = K - 1; i >= 1; --i) {
     const double beta = (i == K - 1) ? 0.0 : 1.0;
-    PF_TRY(clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, s, V, aux[(i + 1) & 1], aux[i & 1], aux[i & 1],
-                             coeffs[i], 2.0, beta, st, cta_cap));
+    PF_TRY(ham_step(H, prec, s, V, aux[(i + 1) & 1], aux[i & 1], aux[i & 1], coeffs[i], 2.0, beta, st, cta_cap));
   }
   // P V = a_0 V + H~ b_1 - b_2
   const double beta = (K >= 2) ? 1.0 : 0.0;
-  PF_TRY(clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, s, V, aux[1], aux[0], W, coeffs[0], 1.0, beta, st, cta_cap));
+  PF_TRY(ham_step(H, prec, s, V, aux[1], aux[0], W, coeffs[0], 1.0, beta, st, cta_cap));
   return PF_OK;
 }
 
@@ -870,6 +1047,10 @@ static void prepare_shapes_s() {
   step_shape<T, S, 1, 0>(1);
   step_shape<T, S, 0, 1>(1);
   step_shape<T, S, 1, 1>(1);
+  qrem_shape<T, S, 0, 0>(1);
+  qrem_shape<T, S, 1, 0>(1);
+  qrem_shape<T, S, 0, 1>(1);
+  qrem_shape<T, S, 1, 1>(1);
 }
 template <typename T>
 static void prepare_shapes(int s) {
@@ -1127,16 +1308,13 @@ pf_status pf_clenshaw_step(const pf_ham* hh, int32_t prec, int32_t s, const void
                            void* out, double a, double alpha, double beta, int32_t use_H, pf_stream_t stream) {
   const Ham* H = reinterpret_cast<const Ham*>(hh);
   if (!H) return PF_EINVAL;
-  const void* val;
   if (use_H) {
     if (prec != PF_F64) return PF_EINVAL;
-    val = H->val;
-  } else {
-    if (!H->has_rescale) return PF_ESTATE;
-    val = ham_vals(H, prec);
+    return clenshaw_step_raw(H->D, H->row_ptr, H->col, H->val, prec, s, V, B1, B2, out, a, alpha, beta,
+                             (cudaStream_t)stream);
   }
-  return clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, s, V, B1, B2, out, a, alpha, beta,
-                           (cudaStream_t)stream);
+  if (!H->has_rescale) return PF_ESTATE;
+  return ham_step(H, prec, s, V, B1, B2, out, a, alpha, beta, (cudaStream_t)stream, 0);
 }
 
 pf_status pf_filter_apply(const pf_ham* hh, int32_t prec, int32_t s, const void* V, void* W, const double* coeffs,

@@ -97,6 +97,13 @@ struct Ham {
   double* val_t = nullptr;      // device [nnz], H~ (FP64)
   float* val32 = nullptr;       // device [nnz], H~ (FP32)
   float2* val_df = nullptr;     // device [nnz], H~ as pair-float (hi, lo), hi = val32
+  // structured mapping (QREM): the diagonal of H~ per row in the three forms, and the one
+  // off-diagonal value (-Gamma / dE); the steps then read no CSR arrays
+  int mapping = PF_MAP_CSR;
+  double* diag_t = nullptr;
+  float* diag32 = nullptr;
+  float2* diag_df = nullptr;
+  double off_t = 0.0;
   int has_rescale = 0, has_bounds = 0;
   double Ec = 0, dE = 1, emin = 0, emax = 0, rmin = 0, rmax = 0, hnorm = 0;
   cudaStream_t st = 0;
@@ -142,6 +149,10 @@ inline const void* ham_vals(const Ham* H, int prec) {
 pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* col, const void* val,
                             int prec, int s, const void* V, const void* B1, const void* B2, void* out,
                             double a, double alpha, double beta, cudaStream_t st, int cta_cap = 0);
+// One step of H~ through the handle's mapping (CSR arrays or the structured QREM rows); the
+// operands and errors of clenshaw_step_raw.
+pf_status ham_step(const Ham* H, int prec, int s, const void* V, const void* B1, const void* B2, void* out,
+                   double a, double alpha, double beta, cudaStream_t st, int cta_cap = 0);
 // One filter application W = P(H~) V (K steps) with its own two auxiliary blocks.
 struct FilterItem {
   const Ham* H = nullptr;

@@ -541,7 +541,6 @@ static pf_status measure_block_steps(const Ham* H, int prec, cudaStream_t st, st
   PF_TRY(buf.alloc(3 * blk, st));
   PF_CUDA(cudaMemsetAsync(buf.p, 0, 3 * blk, st));
   unsigned char* b = buf.as<unsigned char>();
-  const void* val = ham_vals(H, prec);
   cudaEvent_t e0, e1;
   PF_CUDA(cudaEventCreate(&e0));
   PF_CUDA(cudaEventCreate(&e1));
@@ -549,8 +548,7 @@ static pf_status measure_block_steps(const Ham* H, int prec, cudaStream_t st, st
   for (int c = 0; c < 4 && rc == PF_OK; ++c) {
     const int sc = kBlockCand[c];
     auto step = [&] {
-      return clenshaw_step_raw(H->D, H->row_ptr, H->col, val, prec, sc, b, b + blk, b + 2 * blk, b + 2 * blk, 0.5, 2.0,
-                               1.0, st);
+      return ham_step(H, prec, sc, b, b + blk, b + 2 * blk, b + 2 * blk, 0.5, 2.0, 1.0, st);
     };
     rc = step();   // warm-up
     cudaEventRecord(e0, st);
@@ -1491,7 +1489,7 @@ static pf_status polfed_solve_impl(Ham* H, double target_eps, int nev, int K, co
 struct Request {
   int64_t id = 0;
   pf_model m;
-  std::vector<double> h, mu, A, un;
+  std::vector<double> h, mu, A, un, E;
   std::vector<int32_t> nj;
   double eps = 0.5;
   int nev = 1;
@@ -1520,6 +1518,7 @@ static int64_t model_dim(const pf_model& m) {
   if (m.kind == PF_MODEL_XXZ) return (int64_t)C(m.L, m.N);
   if (m.kind == PF_MODEL_HUBBARD) return (int64_t)(C(m.L, m.N_up) * C(m.L, m.N_dn));
   if (m.kind == PF_MODEL_QSUN) return (int64_t)1 << (m.N + m.L);
+  if (m.kind == PF_MODEL_QREM) return (int64_t)1 << m.L;
   return 0;
 }
 
@@ -1528,10 +1527,13 @@ static int64_t model_dim(const pf_model& m) {
 static int64_t model_nnz_bound(const pf_model& m, int64_t D) {
   if (m.kind == PF_MODEL_XXZ) return D * (1 + m.L);
   if (m.kind == PF_MODEL_HUBBARD) return D * (1 + 2 * m.L);
+  if (m.kind == PF_MODEL_QREM) return D * (1 + m.L);
   return D * (((int64_t)1 << m.N) + m.L);
 }
 
-static size_t ham_bytes(int64_t D, int64_t nnz) { return (size_t)(D + 1) * 8 + (size_t)nnz * 24 + (size_t)D * 4; }
+// row_ptr, col + the four value arrays (H, H~ in FP64, FP32, pairs), the basis states, and
+// the structured mapping's diagonal in three forms
+static size_t ham_bytes(int64_t D, int64_t nnz) { return (size_t)(D + 1) * 8 + (size_t)nnz * 32 + (size_t)D * 24; }
 
 struct Server {
   pf_server_config cfg;
@@ -1581,6 +1583,7 @@ struct Server {
     p.A = r->A.empty() ? nullptr : r->A.data();
     p.u_noise = r->un.empty() ? nullptr : r->un.data();
     p.n_of_j = r->nj.empty() ? nullptr : r->nj.data();
+    p.E = r->E.empty() ? nullptr : r->E.data();
     r->t_admit = now_ms();
     PF_TRY(pf_build_basis(&r->m, &r->basis, s));
     PF_TRY(pf_build_hamiltonian(r->basis, &r->m, &p, &r->ham, s));
@@ -1659,6 +1662,9 @@ static pf_status copy_request(const pf_model* m, const pf_params* p, Request* r)
     r->A.assign(p->A, p->A + (size_t)nd * nd);
     r->un.assign(p->u_noise, p->u_noise + L);
     r->nj.assign(p->n_of_j, p->n_of_j + L);
+  } else if (m->kind == PF_MODEL_QREM) {
+    if (!p->E || L > 30) return PF_EINVAL;
+    r->E.assign(p->E, p->E + ((size_t)1 << L));
   } else {
     return PF_EINVAL;
   }

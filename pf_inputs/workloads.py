@@ -121,6 +121,8 @@ CONFIGS = {
             nev=100, eps=0.5, block=64, precision="f32"),
     5: dict(name="serving_mix", model="xxz", L=(14, 16, 18, 20, 22), W=(0.5, 8.0),
             eps=(0.2, 0.8), nev=(20, 50, 200), requests=2000, precision="f32"),
+    # the paper's GPU benchmark model (Eq. qrem), at a size one solve of which takes seconds
+    6: dict(name="qrem_L18", model="qrem", L=18, Gamma=1.0, nev=100, eps=0.5, block=32, precision="f32"),
 }
 
 
