@@ -632,7 +632,7 @@ def run_serving(args):
     s = args.serve_block
     # warm-up: a short stream of the smallest sector
     warm = pi.serving_stream(3, 100.0, Ls=(min(Ls),), nevs=(min(nevs),), seed=5900)
-    sv = pf.Server(block=s, precision="f32")
+    sv = pf.Server(block=s, precision="f32", refine_precision=args.refine_precision)
     run_stream(sv, warm)
     lib = pf.lib()
     n0 = lib.pf_kernel_launches()
@@ -664,7 +664,7 @@ def run_serving(args):
            "fp64_one_at_a_time": {"eigenpairs_per_s": good64 / span64, "p50_ms": float(np.percentile(lat, 50)),
                                   "p99_ms": float(np.percentile(lat, 99)), "service_s_total": sum(svc),
                                   "latency": "FIFO queue simulated from measured service times, same arrivals"},
-           "n_gpus": 1, "dtype": "f32+f32x2+f64", "data": "synthetic", "gpu_launches": int(launches),
+           "n_gpus": 1, "dtype": dtype_name(args), "data": "synthetic", "gpu_launches": int(launches),
            "clocks": clocks.summary(),
            "config": {"workload": f"serving_xxz_L{'-'.join(map(str, Ls))}_n{args.serve_n}_rate{args.serve_rate}",
                       "requests": args.serve_n, "rate_per_s": args.serve_rate, "L": Ls, "nev": nevs,

@@ -392,6 +392,7 @@ typedef struct {
   double res_tol;           /* acceptance ||Hu - Eu|| <= res_tol ||H||; 0 = 1e-9           */
   double bounds_tol;        /* spectral-bounds tolerance; 0 = 1e-10                         */
   uint64_t seed;            /* start-block seed; 0 = 2024                                   */
+  int32_t refine_precision; /* refinement filter arithmetic: PF_F64 (0) or PF_DF64          */
 } pf_server_config;
 typedef struct {
   int64_t id;

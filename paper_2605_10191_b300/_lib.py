@@ -72,7 +72,7 @@ class pf_solve_item(C.Structure):
 class pf_server_config(C.Structure):
     _fields_ = [("block", C.c_int32), ("precision", C.c_int32), ("max_active", C.c_int32),
                 ("mem_budget_bytes", C.c_int64), ("res_tol", C.c_double), ("bounds_tol", C.c_double),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("refine_precision", C.c_int32)]
 
 
 class pf_request_info(C.Structure):

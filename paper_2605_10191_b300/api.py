@@ -428,11 +428,11 @@ class Server:
     """Continuous-batching solve server (pf_server_*): submit requests, step, take results."""
 
     def __init__(self, block=32, precision="f32", max_active=64, mem_budget_bytes=0, res_tol=0.0, bounds_tol=0.0,
-                 seed=0, stream=None):
+                 seed=0, stream=None, refine_precision="f64"):
         _install_torch_allocator()
         cfg = L.pf_server_config(block=block, precision=L.PF_F64 if precision == "f64" else L.PF_F32,
                                  max_active=max_active, mem_budget_bytes=int(mem_budget_bytes), res_tol=res_tol,
-                                 bounds_tol=bounds_tol, seed=seed)
+                                 bounds_tol=bounds_tol, seed=seed, refine_precision=_prec_code(refine_precision))
         self._stream = stream
         h = C.c_void_p()
         check(lib().pf_server_create(C.byref(cfg), _stream(stream), C.byref(h)), "pf_server_create")

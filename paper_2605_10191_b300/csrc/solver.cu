@@ -1571,6 +1571,7 @@ struct Server {
     o.precision = cfg.precision;
     if (cfg.res_tol > 0) o.res_tol = cfg.res_tol;
     if (cfg.seed) o.seed = cfg.seed;
+    o.refine_precision = cfg.refine_precision;
     return o;
   }
   // Admission work, on the stream the executor gives the solve: basis, Hamiltonian, bounds,
@@ -1802,6 +1803,7 @@ pf_status pf_server_create(const pf_server_config* cfg, pf_stream_t stream, pf_s
         c.block == 32 || c.block == 64))
     return PF_EINVAL;
   if (c.precision != PF_F64 && c.precision != PF_F32) return PF_EINVAL;
+  if (c.refine_precision != PF_F64 && c.refine_precision != PF_DF64) return PF_EINVAL;
   if (c.max_active <= 0) c.max_active = 64;
   if (c.mem_budget_bytes < 0) return PF_EINVAL;
   if (c.mem_budget_bytes == 0) {
