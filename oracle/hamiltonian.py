@@ -15,6 +15,10 @@ XXZ (Eq. xxz, App. A):  H = J sum_i (S^x_i S^x_{i+1} + S^y_i S^y_{i+1}
   the one with both spins flipped, with element J/2 (from (S+S- + S-S+)/2).
   Diagonal: for each bond in order, +(J*Delta)*0.25 if parallel else
   -(J*Delta)*0.25; then for i = 0..L-1, +h_i*0.5 if up else -(h_i*0.5).
+  J1-J2 (Eq. j1j2) and J1-J2-J3 (Eq. j1j2j3): the same with bonds (i, i+2) of
+  coupling J2, Delta2 and (i, i+3) of J3, Delta3 (J1 = J, Delta1 = Delta).  Bonds
+  and diagonal terms run range by range (1, then 2, then 3), then the fields; a
+  range whose coupling is exactly 0 contributes no bonds.
 
 Quantum sun (Eq. qsun, App. A.2): dot of N spins in the top N bits, outer spin
   j in bit j (j = 0..L-1).  H_dot = gamma R'/sqrt(2^N + 1) with
@@ -91,34 +95,49 @@ def csr_from_terms(D, rows, cols, vals):
     return CSR(D=D, indptr=indptr, indices=cols, data=vals)
 
 
-def _bonds(L, bc):
-    nb = L if bc == PBC else L - 1
-    return [(i, (i + 1) % L) for i in range(nb)]
+def _bonds(L, bc, r=1):
+    """Bonds (i, i + r): i = 0..L-1 (indices mod L) under PBC, i = 0..L-1-r under OBC."""
+    nb = L if bc == PBC else max(L - r, 0)
+    return [(i, (i + r) % L) for i in range(nb)]
+
+
+def _coupling_ranges(p):
+    """(range, J_r, Delta_r) of Eq. xxz (r = 1), with Eq. j1j2's r = 2 and Eq. j1j2j3's r = 3
+    terms when their coupling is nonzero (J_1 = p.J, Delta_1 = p.Delta)."""
+    out = [(1, p.J, p.Delta)]
+    for r, Jr, Dr in ((2, getattr(p, "J2", 0.0), getattr(p, "Delta2", 1.0)),
+                      (3, getattr(p, "J3", 0.0), getattr(p, "Delta3", 1.0))):
+        if Jr != 0.0:
+            out.append((r, Jr, Dr))
+    return out
 
 
 def xxz_hamiltonian(p):
-    """Eq. xxz in the S^z_tot sector with p.N up spins."""
+    """Eq. xxz in the S^z_tot sector with p.N up spins, plus the next-nearest (Eq. j1j2) and
+    third-neighbour (Eq. j1j2j3) couplings when p.J2 / p.J3 are nonzero."""
     L = p.L
     states = _basis.xxz_basis(L, p.N)
     D = len(states)
-    bonds = _bonds(L, p.bc)
-    jdq = (p.J * p.Delta) * 0.25
+    ranges = [(_bonds(L, p.bc, r), Jr, Dr) for (r, Jr, Dr) in _coupling_ranges(p)]
     d = np.zeros(D)
-    for (i, j) in bonds:
-        par = ((states >> i) & 1) == ((states >> j) & 1)
-        d = d + np.where(par, jdq, -jdq)
+    for bonds, Jr, Dr in ranges:
+        jdq = (Jr * Dr) * 0.25
+        for (i, j) in bonds:
+            par = ((states >> i) & 1) == ((states >> j) & 1)
+            d = d + np.where(par, jdq, -jdq)
     for i in range(L):
         hi = p.h[i] * 0.5
         d = d + np.where(((states >> i) & 1) == 1, hi, -hi)
     rows, cols, vals = [np.arange(D)], [np.arange(D)], [d]
-    half_j = p.J * 0.5
-    for (i, j) in bonds:
-        anti = ((states >> i) & 1) != ((states >> j) & 1)
-        r = np.nonzero(anti)[0]
-        t = states[r] ^ ((1 << i) | (1 << j))
-        rows.append(r)
-        cols.append(_basis.row_of(states, t))
-        vals.append(np.full(len(r), half_j))
+    for bonds, Jr, Dr in ranges:
+        half_j = Jr * 0.5
+        for (i, j) in bonds:
+            anti = ((states >> i) & 1) != ((states >> j) & 1)
+            r = np.nonzero(anti)[0]
+            t = states[r] ^ ((1 << i) | (1 << j))
+            rows.append(r)
+            cols.append(_basis.row_of(states, t))
+            vals.append(np.full(len(r), half_j))
     H = csr_from_terms(D, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
     H.states = states
     return H

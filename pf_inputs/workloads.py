@@ -26,6 +26,10 @@ class XXZParams:
     seed: int = 0
     h: np.ndarray = field(default=None, repr=False)   # fields h_i, i = 0..L-1
     kind: int = XXZ
+    J2: float = 0.0             # next-nearest couplings (Eq. j1j2); 0 = none
+    Delta2: float = 1.0
+    J3: float = 0.0             # third-neighbour couplings (Eq. j1j2j3); 0 = none
+    Delta3: float = 1.0
 
 
 @dataclass
@@ -82,6 +86,14 @@ def xxz_params(L, N=None, J=1.0, Delta=1.0, W=0.0, bc=PBC, seed=0):
     N = L // 2 if N is None else N
     h = W * (2.0 * uniform01(seed, np.arange(L)) - 1.0)
     return XXZParams(L=L, N=N, J=J, Delta=Delta, W=W, bc=bc, seed=seed, h=h)
+
+
+def j1j2_params(L, N=None, J1=1.0, J2=0.5, Delta1=1.0, Delta2=1.0, J3=0.0, Delta3=1.0, W=1.0, bc=PBC, seed=0):
+    """Eq. j1j2 (and Eq. j1j2j3 with J3 != 0); fields drawn as in xxz_params.  The paper's values:
+    J1 = 1, J2 = 0.5, Delta1 = Delta2 = 1, W = 1, and J3 = 0.225, Delta3 = 1."""
+    p = xxz_params(L, N=N, J=J1, Delta=Delta1, W=W, bc=bc, seed=seed)
+    p.J2, p.Delta2, p.J3, p.Delta3 = J2, Delta2, J3, Delta3
+    return p
 
 
 def qsun_params(N=3, L=15, g0=1.0, alpha=0.75, gamma=1.0, zeta=0.2, h0=1.0, wh=0.5, seed=0):

@@ -204,3 +204,45 @@ def test_qrem_energies_statistics():
     E = pi.qrem_params(L, seed=7).E
     assert abs(E.mean()) < 4 * np.sqrt(L / 2.0) / np.sqrt(E.size)
     assert abs(E.std() / np.sqrt(L / 2.0) - 1.0) < 0.03
+
+
+# ---------------------------------------------------------------- J1-J2 (Eq. j1j2) and J1-J2-J3 (Eq. j1j2j3)
+@pytest.mark.parametrize("L", [8, 10, 12])
+def test_j1j2_majumdar_ghosh_ground_state(L):
+    # at J2 = J1/2 (Delta1 = Delta2 = 1, no field, periodic, even L) the two dimer coverings are the
+    # exact ground states, with energy -3 J1 L / 8 (Majumdar & Ghosh 1969)
+    p = pi.j1j2_params(L, J1=1.0, J2=0.5, W=0.0)
+    w = np.linalg.eigvalsh(hm.build(p).dense())
+    assert abs(w[0] + 3.0 * L / 8.0) < 1e-10 and abs(w[1] + 3.0 * L / 8.0) < 1e-10
+    assert w[2] > w[1] + 1e-3
+
+
+@pytest.mark.parametrize("L", [7, 9])
+def test_range2_only_ring_is_a_relabelled_xxz_ring(L):
+    # J1 = 0, odd L: i -> 2i mod L maps the range-2 bonds onto a nearest-neighbour ring
+    J2, D2 = 0.8, 0.6
+    w2 = np.linalg.eigvalsh(hm.build(pi.j1j2_params(L, N=3, J1=0.0, J2=J2, Delta2=D2, W=0.0)).dense())
+    w1 = np.linalg.eigvalsh(hm.build(pi.xxz_params(L, N=3, J=J2, Delta=D2, W=0.0)).dense())
+    assert np.max(np.abs(w2 - w1)) < 1e-12
+
+
+@pytest.mark.parametrize("L,N,J3", [(12, 6, 0.0), (12, 6, 0.225), (11, 4, 0.225)])
+def test_j1j2j3_counts_and_trace_closed_forms(L, N, J3):
+    p = pi.j1j2_params(L, N=N, J3=J3, W=0.0)
+    H = hm.build(p)
+    D = math.comb(L, N)
+    ranges = [(1, 1.0, 1.0), (2, 0.5, 1.0)] + ([(3, J3, 1.0)] if J3 else [])
+    anti = 2 * math.comb(L - 2, N - 1)                     # states antiparallel on a given bond
+    par = math.comb(L - 2, N) + math.comb(L - 2, N - 2)
+    assert H.D == D and H.nnz == D + len(ranges) * L * anti
+    tr = sum(L * (Jr * Dr * 0.25) * (par - anti) for (_, Jr, Dr) in ranges)
+    assert abs(np.trace(H.dense()) - tr) < 1e-9
+    M = H.dense()
+    assert np.array_equal(M, M.T)
+
+
+def test_j1j2_reduces_to_xxz_when_J2_is_zero():
+    a = hm.build(pi.j1j2_params(10, J1=1.3, J2=0.0, Delta1=0.7, W=2.0, seed=5))
+    b = hm.build(pi.xxz_params(10, J=1.3, Delta=0.7, W=2.0, seed=5))
+    assert np.array_equal(a.indptr, b.indptr) and np.array_equal(a.indices, b.indices)
+    assert np.array_equal(a.data, b.data)
