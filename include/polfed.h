@@ -62,7 +62,9 @@ typedef enum { PF_F64 = 0, PF_F32 = 1, PF_DF64 = 2 } pf_precision;
 /* Model description (paper App. A).
  *  XXZ (Eq. xxz): L sites, N up spins (S^z_tot sector), couplings J, Delta, fields h_i.
  *     Bit i of a basis state is 1 when spin i is up; basis = L-bit integers with
- *     popcount N in ascending order; row = rank in that order.
+ *     popcount N in ascending order; row = rank in that order.  J2, Delta2 and J3,
+ *     Delta3 add the bonds (i, i+2) and (i, i+3) of the J1-J2 (Eq. j1j2) and
+ *     J1-J2-J3 (Eq. j1j2j3) chains; a zero coupling adds no bonds.
  *  Quantum sun (Eq. qsun): N dot spins in the top N bits, L outer spins in bits
  *     0..L-1; D = 2^(N+L), row = state.  H_dot = gamma (A + A^T)/sqrt(2)/sqrt(2^N+1);
  *     ray j couples dot spin n(j) and outer spin j with g0 alpha^(j + u_noise_j)/4.
@@ -81,6 +83,8 @@ typedef struct {
   double t, U;      /* Hubbard                                          */
   double g0, alpha, gamma; /* quantum sun                               */
   double Gamma;     /* QREM transverse field                            */
+  double J2, Delta2;  /* XXZ: next-nearest couplings, Eq. j1j2 (J2 = 0: none)   */
+  double J3, Delta3;  /* XXZ: third-neighbour couplings, Eq. j1j2j3 (J3 = 0: none) */
 } pf_model;
 
 /* Disorder and random couplings, host arrays (copied during the call).          */

@@ -19,7 +19,8 @@ class pf_model(C.Structure):
     _fields_ = [("kind", C.c_int32), ("L", C.c_int32), ("N", C.c_int32), ("N_up", C.c_int32),
                 ("N_dn", C.c_int32), ("bc", C.c_int32), ("J", C.c_double), ("Delta", C.c_double),
                 ("t", C.c_double), ("U", C.c_double), ("g0", C.c_double), ("alpha", C.c_double),
-                ("gamma", C.c_double), ("Gamma", C.c_double)]
+                ("gamma", C.c_double), ("Gamma", C.c_double), ("J2", C.c_double), ("Delta2", C.c_double),
+                ("J3", C.c_double), ("Delta3", C.c_double)]
 
 
 class pf_params(C.Structure):

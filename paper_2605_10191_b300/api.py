@@ -114,6 +114,10 @@ class Model:
     alpha: float = 0.75
     gamma: float = 1.0
     Gamma: float = 1.0
+    J2: float = 0.0
+    Delta2: float = 1.0
+    J3: float = 0.0
+    Delta3: float = 1.0
     h: object = None
     mu: object = None
     A: object = None
@@ -126,7 +130,8 @@ class Model:
         """From a parameter record with the attribute names of pf_inputs.workloads."""
         k = p.kind
         if k == L.PF_MODEL_XXZ:
-            return Model(kind=k, L=p.L, N=p.N, bc=p.bc, J=p.J, Delta=p.Delta, h=p.h)
+            return Model(kind=k, L=p.L, N=p.N, bc=p.bc, J=p.J, Delta=p.Delta, h=p.h, J2=getattr(p, "J2", 0.0),
+                         Delta2=getattr(p, "Delta2", 1.0), J3=getattr(p, "J3", 0.0), Delta3=getattr(p, "Delta3", 1.0))
         if k == L.PF_MODEL_QSUN:
             return Model(kind=k, L=p.L, N=p.N, g0=p.g0, alpha=p.alpha, gamma=p.gamma, h=p.h, A=p.A,
                          u_noise=p.u_noise, n_of_j=p.n_of_j)
@@ -139,7 +144,8 @@ class Model:
     def c_model(self):
         return L.pf_model(kind=self.kind, L=self.L, N=self.N, N_up=self.N_up, N_dn=self.N_dn, bc=self.bc,
                           J=self.J, Delta=self.Delta, t=self.t, U=self.U, g0=self.g0, alpha=self.alpha,
-                          gamma=self.gamma, Gamma=self.Gamma)
+                          gamma=self.gamma, Gamma=self.Gamma, J2=self.J2, Delta2=self.Delta2, J3=self.J3,
+                          Delta3=self.Delta3)
 
 
 class Basis:

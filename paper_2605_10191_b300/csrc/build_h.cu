@@ -159,10 +159,14 @@ static pf_status build_basis_impl(const pf_model* m, Basis** out, cudaStream_t s
 }
 
 // ------------------------------------------------------------------ Hamiltonian
-#define PF_MAX_ROW_TERMS 72
+#define PF_MAX_ROW_TERMS 104   // XXZ with three bond ranges at L = 32: 1 + 3 L terms
 
 struct DevModel {
   int kind, L, N, nbonds;
+  // XXZ bond ranges q = 0..nranges-1: nbr[q] bonds (i, i + rr[q] mod L) with jdqr = J Delta / 4 and
+  // halfJr = J / 2 of that range
+  int nranges, nbr[3], rr[3];
+  double jdqr[3], halfJr[3];
   int64_t Dd;                 // Hubbard: down-table length
   double jdq, halfJ, negt, U;
   double negG;                // QREM: -Gamma
@@ -221,20 +225,22 @@ __device__ void gen_row(const DevModel& M, int64_t row, RowTerms& T) {
   if (M.kind == PF_MODEL_XXZ) {
     uint32_t s = M.states[row];
     double d = 0.0;
-    for (int b = 0; b < M.nbonds; ++b) {
-      int i = b, j = (b + 1) % L;
-      bool par = ((s >> i) & 1u) == ((s >> j) & 1u);
-      d = __dadd_rn(d, par ? M.jdq : -M.jdq);
-    }
+    for (int q = 0; q < M.nranges; ++q)
+      for (int b = 0; b < M.nbr[q]; ++b) {
+        int i = b, j = (b + M.rr[q]) % L;
+        bool par = ((s >> i) & 1u) == ((s >> j) & 1u);
+        d = __dadd_rn(d, par ? M.jdqr[q] : -M.jdqr[q]);
+      }
     for (int i = 0; i < L; ++i) d = __dadd_rn(d, ((s >> i) & 1u) ? M.hhalf[i] : -M.hhalf[i]);
     T.push(row, d);
-    for (int b = 0; b < M.nbonds; ++b) {
-      int i = b, j = (b + 1) % L;
-      if (((s >> i) & 1u) != ((s >> j) & 1u)) {
-        uint32_t t = s ^ ((1u << i) | (1u << j));
-        T.push((int64_t)rank_state(t, M.binom), M.halfJ);
+    for (int q = 0; q < M.nranges; ++q)
+      for (int b = 0; b < M.nbr[q]; ++b) {
+        int i = b, j = (b + M.rr[q]) % L;
+        if (((s >> i) & 1u) != ((s >> j) & 1u)) {
+          uint32_t t = s ^ ((1u << i) | (1u << j));
+          T.push((int64_t)rank_state(t, M.binom), M.halfJr[q]);
+        }
       }
-    }
   } else if (M.kind == PF_MODEL_QSUN) {
     const int nd = 1 << M.N;
     uint32_t s = (uint32_t)row;
@@ -374,6 +380,17 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
     if (!p->h) return PF_EINVAL;
     M.jdq = (m->J * m->Delta) * 0.25;
     M.halfJ = m->J * 0.5;
+    // bond ranges as the oracle lists them: range 1 always, ranges 2 and 3 when their J != 0
+    M.nranges = 0;
+    const double Jr[3] = {m->J, m->J2, m->J3}, Dr[3] = {m->Delta, m->Delta2, m->Delta3};
+    for (int q = 0; q < 3; ++q) {
+      if (q > 0 && Jr[q] == 0.0) continue;
+      M.rr[M.nranges] = q + 1;
+      M.nbr[M.nranges] = (m->bc == PF_BC_PERIODIC) ? L : (L - (q + 1) > 0 ? L - (q + 1) : 0);
+      M.jdqr[M.nranges] = (Jr[q] * Dr[q]) * 0.25;
+      M.halfJr[M.nranges] = Jr[q] * 0.5;
+      ++M.nranges;
+    }
     hh.resize(L);
     for (int i = 0; i < L; ++i) hh[i] = p->h[i] * 0.5;
     M.states = b->states;

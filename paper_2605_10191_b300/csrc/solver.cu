@@ -1525,7 +1525,7 @@ static int64_t model_dim(const pf_model& m) {
 // Stored entries per row, an upper bound: the diagonal plus one per bond (XXZ), two per bond
 // (Hubbard), the dot block plus one per outer spin (quantum sun).
 static int64_t model_nnz_bound(const pf_model& m, int64_t D) {
-  if (m.kind == PF_MODEL_XXZ) return D * (1 + m.L);
+  if (m.kind == PF_MODEL_XXZ) return D * (1 + m.L * (1 + (m.J2 != 0.0) + (m.J3 != 0.0)));
   if (m.kind == PF_MODEL_HUBBARD) return D * (1 + 2 * m.L);
   if (m.kind == PF_MODEL_QREM) return D * (1 + m.L);
   return D * (((int64_t)1 << m.N) + m.L);
