@@ -120,3 +120,23 @@ def test_server_failing_request_is_isolated(pf):
     with pytest.raises(pf.PolfedError):
         sv.submit(pf.Model.from_params(good[1][0]), 1.5, 4)         # eps outside [0, 1]
     sv.close()
+
+
+@pytest.mark.parametrize("k", [19, 22])
+def test_low_degree_many_pair_requests_converge(pf, k):
+    """Requests of the serving stream (2 req/s, nev in {20, 50, 200}) with nev = 200 and K = 40-57:
+    a reserve block joining after a pass that still gained 4-8x brought a spurious Ritz pair into
+    the returned set; they must converge, and at L = 14 match dense diagonalisation."""
+    from oracle import hamiltonian as oh, dense
+    rq = pi.serving_stream(24, 2.0, Ls=(14, 16, 18), nevs=(20, 50, 200))[k]
+    p = rq["params"]
+    H = pf.Hamiltonian.from_params(p)
+    H.spectral_bounds()
+    K = H.choose_K(rq["eps"], rq["nev"])
+    r = H.solve(rq["eps"], rq["nev"], K, block=16, precision="f32", return_vectors=False, raise_on_notconv=False)
+    hn = r.report["hnorm"]
+    assert r.status == 0 and np.max(r.resid) <= 1e-9 * hn
+    if p.L == 14:
+        w, _ = dense.eigh_dense(oh.build(p))
+        lam = w[0] + rq["eps"] * (w[-1] - w[0])
+        assert np.max(np.abs(r.evals - w[dense.nearest(w, lam, rq["nev"])])) <= 1e-10 * max(abs(w[0]), abs(w[-1]))
