@@ -280,8 +280,11 @@ typedef struct {
   int32_t block;          /* s: 1..64, power of two; 0 = 32; < 0 = pf_autotune_block  */
   int32_t precision;      /* pf_precision of the filter recurrence                   */
   int32_t nev_guard;      /* Ritz pairs converged; 0 = ceil(1.5 nev)                  */
-  int32_t check_first;    /* first check at this block step; 0 = rule (see DESIGN)   */
-  int32_t check_every;    /* check interval in block steps; 0 = rule                 */
+  int32_t check_first;    /* first check at this block step; 0 = ceil(m / 2), m the
+                             expected Krylov blocks (20.427 s + 1.696 nev_g) / s      */
+  int32_t check_every;    /* check interval in block steps; 0 = ceil(m / 10), checked
+                             sooner when the largest residual of the last two checks,
+                             extrapolated geometrically, reaches tol sooner            */
   int32_t max_blocks;     /* Krylov budget in blocks; 0 = from eta                    */
   double eta;             /* over-allocation of the expected Krylov size; 0 = 1.5    */
   double tol;             /* P-space tolerance on ||B tau|| (FP64 filter); 0 = 1e-10 */
