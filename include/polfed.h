@@ -305,6 +305,8 @@ typedef struct {
   double refine_guard_lock;/* refinement locks a pair outside the returned set (guard,
                              reserve) once its residual is <= this x res_tol ||H||;
                              0 = 10, < 0 = never (returned pairs lock at 0.5)          */
+  double refine_lock;     /* refinement locks a returned pair once its residual is <=
+                             this x res_tol ||H|| (at most 1); 0 = 0.9                 */
   int32_t refine_precision;/* arithmetic of the refinement filter: PF_F64 (the default)
                              or PF_DF64 (pair-float on the FP32 units, about 2x faster
                              steps); Gram-Schmidt, Rayleigh-Ritz and the residual check
