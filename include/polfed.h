@@ -304,7 +304,7 @@ typedef struct {
                              the first pass (default: one joins per stalled pass)     */
   double refine_guard_lock;/* refinement locks a pair outside the returned set (guard,
                              reserve) once its residual is <= this x res_tol ||H||;
-                             0 = 10, < 0 = never (returned pairs lock at 0.5)          */
+                             0 = 10, < 0 = never (returned pairs: refine_lock)         */
   double refine_lock;     /* refinement locks a returned pair once its residual is <=
                              this x res_tol ||H|| (at most 1); 0 = 0.9                 */
   int32_t refine_precision;/* arithmetic of the refinement filter: PF_F64 (the default)
