@@ -86,6 +86,21 @@ def test_solve_xxz_L12_matches_dense(pf, precision):
         assert res.report["filter_steps_f64"] > 0 or res.report["refine_passes"] == 0
 
 
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("s", [1, 2])
+def test_scalar_and_narrow_lanczos_match_dense(pf, precision, s):
+    """Scalar Lanczos (s = 1, the paper's single-vector input) and s = 2 through the same path."""
+    p = pi.xxz_params(10, W=1.5, seed=1010)
+    Ho, w, U = _dense(p)
+    hn = max(abs(w[0]), abs(w[-1]))
+    Hg = pf.Hamiltonian.from_params(p)
+    Hg.spectral_bounds()
+    lam = w[0] + 0.5 * (w[-1] - w[0])
+    K = Hg.choose_K(0.5, 6)
+    res = Hg.solve(0.5, 6, K, block=s, precision=precision, target_abs=lam)
+    _check_solution(res, w, U, lam, 6, hn)
+
+
 @pytest.mark.parametrize("s", [4, 16])
 def test_solve_other_models_match_dense(pf, s):
     for p in (pi.qsun_params(N=3, L=8, seed=3001), pi.hubbard_params(7, 3, 3, U=1.0, W=4.0, seed=4001)):
