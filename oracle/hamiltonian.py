@@ -38,12 +38,23 @@ Fermi-Hubbard (not in the paper; open chain):
   Diagonal: for i = 0..L-1, + U*(n_up_i*n_dn_i); then for i = 0..L-1,
   + mu_i*(n_up_i + n_dn_i) (the occupations as doubles).
 
+U(1) quantum sun (Eq. qsun:U1, App. A.2): the sector of M up spins among the N + L
+  bits (dot in the top N), rows in ascending state order as for XXZ.  R' = A + A^T
+  with the elements between dot states of different popcount set to zero; H_dot =
+  R' c with c = gamma / sqrt(T / D), T = sum over dot states a (ascending), then b
+  (ascending) with popcount(b) = popcount(a), of binom(L, M - popcount(a)) *
+  (R'_ab * R'_ab), so that Tr(H_dot^2) / D = gamma^2 on the sector.  Ray j flips the
+  antiparallel pair (dot spin n(j), outer spin j) with element (g0 * alpha**u_j) * 0.5
+  (S^x S^x + S^y S^y).  Diagonal: H_dot[a, a], then the outer fields as above.
+
 QREM (Eq. qrem, App. A): H = sum_alpha E_alpha |alpha><alpha| - Gamma sum_i sigma^x_i on
   the full space of L spins, row = state.  sigma^x_i flips bit i with element 1, so
   state alpha couples to alpha ^ (1 << i) with element -Gamma for i = 0..L-1.
   Diagonal: E_alpha.
 """
 from dataclasses import dataclass
+import math
+
 import numpy as np
 import scipy.sparse as sp
 
@@ -187,6 +198,61 @@ def qsun_hamiltonian(p):
     return H
 
 
+def qsun_u1_dot_matrix(p):
+    """H_dot of Eq. qsun:U1 on the 2^N dot states (zero between different popcounts), normalised
+    numerically on the sector of p.M up spins: Tr(H_dot^2) / D = gamma^2."""
+    N, L, M = p.N, p.L, p.M
+    nd = 1 << N
+    A = np.asarray(p.A, dtype=np.float64)
+    S = A + A.T
+    pc = _basis.popcount(np.arange(nd))
+    S = np.where(pc[:, None] == pc[None, :], S, 0.0)
+    T = 0.0
+    for a in range(nd):
+        w = float(math.comb(L, M - int(pc[a]))) if 0 <= M - int(pc[a]) <= L else 0.0
+        for b in range(nd):
+            if pc[b] == pc[a]:
+                T = T + w * (S[a, b] * S[a, b])
+    D = math.comb(N + L, M)
+    return S * (p.gamma / math.sqrt(T / D))
+
+
+def qsun_u1_hamiltonian(p):
+    """Eq. qsun:U1 in the sector of p.M up spins among N + L."""
+    N, L, M = p.N, p.L, p.M
+    nd = 1 << N
+    states = _basis.fixed_popcount_states(N + L, M)
+    D = len(states)
+    dot = states >> L
+    outer = states & ((1 << L) - 1)
+    hd = qsun_u1_dot_matrix(p)
+    d = hd[dot, dot].copy()
+    for j in range(L):
+        hj = p.h[j] * 0.5
+        d = d + np.where(((states >> j) & 1) == 1, hj, -hj)
+    rows_all = np.arange(D)
+    rows, cols, vals = [rows_all], [rows_all], [d]
+    pcd = _basis.popcount(dot)
+    pcb = _basis.popcount(np.arange(nd))
+    for b in range(nd):
+        m = (dot != b) & (pcd == pcb[b])
+        rows.append(rows_all[m])
+        cols.append(_basis.row_of(states, (b << L) | outer[m]))
+        vals.append(hd[dot[m], b])
+    u = np.arange(L, dtype=np.float64) + p.u_noise
+    coef = (p.g0 * np.power(p.alpha, u)) * 0.5
+    for j in range(L):
+        bd = L + int(p.n_of_j[j])
+        anti = ((states >> bd) & 1) != ((states >> j) & 1)
+        r = rows_all[anti]
+        rows.append(r)
+        cols.append(_basis.row_of(states, states[anti] ^ ((1 << bd) | (1 << j))))
+        vals.append(np.full(len(r), coef[j]))
+    H = csr_from_terms(D, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+    H.states = states
+    return H
+
+
 def _between_mask(i, j):
     lo, hi = min(i, j), max(i, j)
     return ((1 << hi) - 1) & ~((1 << (lo + 1)) - 1)
@@ -242,5 +308,7 @@ def qrem_hamiltonian(p):
 
 
 def build(p):
-    """Dispatch on the parameter record's model kind (0 XXZ, 1 quantum sun, 2 Hubbard, 3 QREM)."""
-    return {0: xxz_hamiltonian, 1: qsun_hamiltonian, 2: hubbard_hamiltonian, 3: qrem_hamiltonian}[p.kind](p)
+    """Dispatch on the parameter record's model kind (0 XXZ, 1 quantum sun, 2 Hubbard, 3 QREM,
+    4 U(1) quantum sun)."""
+    return {0: xxz_hamiltonian, 1: qsun_hamiltonian, 2: hubbard_hamiltonian, 3: qrem_hamiltonian,
+            4: qsun_u1_hamiltonian}[p.kind](p)

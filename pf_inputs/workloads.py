@@ -11,7 +11,7 @@ import numpy as np
 
 from .rng import uniform01, normals
 
-XXZ, QSUN, HUBBARD, QREM = 0, 1, 2, 3
+XXZ, QSUN, HUBBARD, QREM, QSUN_U1 = 0, 1, 2, 3, 4
 PBC, OBC = 0, 1
 
 
@@ -48,6 +48,7 @@ class QSunParams:
     n_of_j: np.ndarray = field(default=None, repr=False)   # dot spin coupled to j
     h: np.ndarray = field(default=None, repr=False)        # fields h_j
     kind: int = QSUN
+    M: int = 0                  # U(1) variant: up spins among N + L (the sector)
 
 
 @dataclass
@@ -107,6 +108,15 @@ def qsun_params(N=3, L=15, g0=1.0, alpha=0.75, gamma=1.0, zeta=0.2, h0=1.0, wh=0
     h = h0 + wh * (2.0 * u[2 * L:] - 1.0)
     return QSunParams(N=N, L=L, g0=g0, alpha=alpha, gamma=gamma, zeta=zeta, h0=h0, wh=wh,
                       seed=seed, A=A, u_noise=u_noise, n_of_j=n_of_j, h=h)
+
+
+def qsun_u1_params(N=3, L=15, M=None, g0=1.0, alpha=0.75, gamma=1.0, zeta=0.2, h0=1.0, wh=0.5, seed=0):
+    """Eq. qsun:U1: the draws of qsun_params (same order), in the sector of M up spins among N + L
+    (default (N + L) // 2)."""
+    p = qsun_params(N=N, L=L, g0=g0, alpha=alpha, gamma=gamma, zeta=zeta, h0=h0, wh=wh, seed=seed)
+    p.kind = QSUN_U1
+    p.M = (N + L) // 2 if M is None else M
+    return p
 
 
 def hubbard_params(L, N_up=None, N_dn=None, t=1.0, U=1.0, W=0.0, bc=OBC, seed=0):

@@ -246,3 +246,67 @@ def test_j1j2_reduces_to_xxz_when_J2_is_zero():
     b = hm.build(pi.xxz_params(10, J=1.3, Delta=0.7, W=2.0, seed=5))
     assert np.array_equal(a.indptr, b.indptr) and np.array_equal(a.indices, b.indices)
     assert np.array_equal(a.data, b.data)
+
+
+# ---------------------------------------------------------------- U(1) quantum sun (Eq. qsun:U1)
+def _u1(N, L, M, **kw):
+    p = pi.qsun_u1_params(N=N, L=L, M=M, seed=kw.pop("seed", 9))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("N,L,M", [(3, 5, 4), (2, 6, 3), (3, 4, 2)])
+def test_qsun_u1_dot_normalisation_and_block_spectrum(N, L, M):
+    # g0 = 0, no fields: H = H_dot restricted to the sector.  Tr(H^2)/D = gamma^2 (the numerical
+    # normalisation), and the spectrum is that of H_dot's popcount-p blocks, each eigenvalue
+    # repeated binom(L, M - p) times.
+    p = _u1(N, L, M, g0=0.0, h=np.zeros(L), gamma=1.3)
+    Hm = hm.build(p).dense()
+    D = math.comb(N + L, M)
+    assert Hm.shape == (D, D)
+    assert abs(np.trace(Hm @ Hm) / D - 1.3 ** 2) < 1e-12
+    hd = hm.qsun_u1_dot_matrix(p)
+    pc = basis.popcount(np.arange(1 << N))
+    ref = []
+    for q in range(N + 1):
+        if not 0 <= M - q <= L:
+            continue
+        blk = np.nonzero(pc == q)[0]
+        ev = np.linalg.eigvalsh(hd[np.ix_(blk, blk)])
+        ref.extend(np.repeat(ev, math.comb(L, M - q)))
+    assert np.max(np.abs(np.linalg.eigvalsh(Hm) - np.sort(ref))) < 1e-12
+
+
+def test_qsun_u1_single_excitation_star_closed_form():
+    # one up spin, no dot term, no fields: the rays hop the excitation between the dot spin and
+    # outer spin j with t_j = g0 alpha^u_j / 2, a star graph: eigenvalues +-sqrt(sum t_j^2), 0 (L-1 times)
+    N, L = 1, 6
+    p = _u1(N, L, 1, gamma=0.0, h=np.zeros(L), n_of_j=np.zeros(L, dtype=np.int64))
+    t = 0.5 * p.g0 * np.power(p.alpha, np.arange(L) + p.u_noise)
+    w = np.linalg.eigvalsh(hm.build(p).dense())
+    r = np.sqrt(np.sum(t * t))
+    assert np.allclose(w, np.sort(np.concatenate([[-r, r], np.zeros(L - 1)])), atol=1e-14)
+
+
+def test_qsun_u1_fields_rays_and_counts():
+    N, L, M = 3, 6, 4
+    p = _u1(N, L, M, seed=21)
+    H = hm.build(p)
+    D = math.comb(N + L, M)
+    st = H.states
+    assert H.D == D and np.array_equal(st, basis.fixed_popcount_states(N + L, M))
+    Mx = H.dense()
+    assert np.array_equal(Mx, Mx.T)
+    # every element conserves the total popcount (automatic in the sector) and the rays carry
+    # (g0 alpha^u_j) / 2 between states differing in bits L + n(j) and j only
+    coef = (p.g0 * np.power(p.alpha, np.arange(L) + p.u_noise)) * 0.5
+    for r in range(D):
+        for j0 in range(H.indptr[r], H.indptr[r + 1]):
+            c = H.indices[j0]
+            x = int(st[r] ^ st[c])
+            if c == r or (x >> L) == int(st[r] >> L) ^ int(st[c] >> L) and (x & ((1 << L) - 1)) == 0:
+                continue                     # diagonal or a dot-only element
+            j = [k for k in range(L) if (x >> k) & 1]
+            assert len(j) == 1 and x == (1 << j[0]) | (1 << (L + int(p.n_of_j[j[0]])))
+            assert H.data[j0] == coef[j[0]]
