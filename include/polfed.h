@@ -45,7 +45,9 @@ typedef enum {
   PF_EBREAKDOWN = 7 /* Cholesky-QR breakdown the recovery path could not repair       */
 } pf_status;
 
-typedef enum { PF_MODEL_XXZ = 0, PF_MODEL_QSUN = 1, PF_MODEL_HUBBARD = 2, PF_MODEL_QREM = 3 } pf_model_kind;
+typedef enum {
+  PF_MODEL_XXZ = 0, PF_MODEL_QSUN = 1, PF_MODEL_HUBBARD = 2, PF_MODEL_QREM = 3, PF_MODEL_QSUN_U1 = 4
+} pf_model_kind;
 typedef enum { PF_BC_PERIODIC = 0, PF_BC_OPEN = 1 } pf_boundary;
 /* Arithmetic of a filter (Clenshaw) step.
  *  PF_F64   double blocks, FP64 values and arithmetic.
@@ -71,6 +73,11 @@ typedef enum { PF_F64 = 0, PF_F32 = 1, PF_DF64 = 2 } pf_precision;
  *  Fermi-Hubbard (not in the paper): L sites, N_up / N_dn fermions, hopping t,
  *     interaction U, potentials mu_i; row = rank_up * D_dn + rank_dn; Jordan-Wigner
  *     order: all up modes, then all down modes.
+ *  U(1) quantum sun (Eq. qsun:U1): the quantum sun's N dot and L outer spins in the
+ *     sector of N_up up spins among N + L (rows as for XXZ over N + L bits); the dot
+ *     matrix keeps only popcount-conserving elements and is normalised on the sector
+ *     (Tr(H_dot^2)/D = gamma^2); rays S^x S^x + S^y S^y flip antiparallel pairs with
+ *     g0 alpha^u_j / 2.
  *  QREM (Eq. qrem): L spins, full space D = 2^L, row = state; diagonal E_alpha,
  *     single spin flips alpha -> alpha ^ (1 << i) with element -Gamma.              */
 typedef struct {

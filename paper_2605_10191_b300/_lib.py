@@ -9,7 +9,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpolfed.so")
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ENOTCONV, PF_ETIMEOUT, PF_ECUDA, PF_ESTATE, PF_EBREAKDOWN = range(8)
-PF_MODEL_XXZ, PF_MODEL_QSUN, PF_MODEL_HUBBARD, PF_MODEL_QREM = 0, 1, 2, 3
+PF_MODEL_XXZ, PF_MODEL_QSUN, PF_MODEL_HUBBARD, PF_MODEL_QREM, PF_MODEL_QSUN_U1 = 0, 1, 2, 3, 4
 PF_MAP_CSR, PF_MAP_STRUCTURED = 0, 1
 PF_F64, PF_F32, PF_DF64 = 0, 1, 2
 PF_FORM_AUTO, PF_FORM_STEPS, PF_FORM_GRAPH = -1, 0, -2

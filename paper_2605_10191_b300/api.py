@@ -139,6 +139,9 @@ class Model:
             return Model(kind=k, L=p.L, N_up=p.N_up, N_dn=p.N_dn, bc=p.bc, t=p.t, U=p.U, mu=p.mu)
         if k == L.PF_MODEL_QREM:
             return Model(kind=k, L=p.L, Gamma=p.Gamma, E=p.E)
+        if k == L.PF_MODEL_QSUN_U1:
+            return Model(kind=k, L=p.L, N=p.N, N_up=p.M, g0=p.g0, alpha=p.alpha, gamma=p.gamma, h=p.h, A=p.A,
+                         u_noise=p.u_noise, n_of_j=p.n_of_j)
         raise ValueError(f"unknown model kind {k}")
 
     def c_model(self):

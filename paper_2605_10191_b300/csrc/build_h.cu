@@ -122,6 +122,9 @@ static pf_status build_basis_impl(const pf_model* m, Basis** out, cudaStream_t s
   } else if (m->kind == PF_MODEL_QREM) {
     if (L < 1 || L > 30) { delete b; return PF_EINVAL; }
     b->D = (int64_t)1 << L;
+  } else if (m->kind == PF_MODEL_QSUN_U1) {
+    if (L < 1 || m->N < 1 || m->N > 5 || m->N + L > 32 || m->N_up < 0 || m->N_up > m->N + L) { delete b; return PF_EINVAL; }
+    b->D = (int64_t)binom_h(m->N + L, m->N_up);
   } else {
     delete b;
     return PF_EINVAL;
@@ -133,18 +136,22 @@ static pf_status build_basis_impl(const pf_model* m, Basis** out, cudaStream_t s
   if (!b->binom) { delete b; return PF_ENOMEM; }
   cudaError_t e = cudaMemcpyAsync(b->binom, tab, sizeof(tab), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) { set_cuda_error(e, "binom upload"); dev_free(b->binom, st); delete b; return PF_ECUDA; }
-  int64_t nst = (m->kind == PF_MODEL_XXZ) ? b->D : (m->kind == PF_MODEL_HUBBARD ? b->D_up + b->D_dn : 0);
+  int64_t nst = (m->kind == PF_MODEL_XXZ || m->kind == PF_MODEL_QSUN_U1)
+                    ? b->D
+                    : (m->kind == PF_MODEL_HUBBARD ? b->D_up + b->D_dn : 0);
   if (nst > 0) {
     b->states = (uint32_t*)dev_alloc(nst * sizeof(uint32_t), st);
     if (!b->states) { dev_free(b->binom, st); delete b; return PF_ENOMEM; }
     if (m->kind == PF_MODEL_XXZ) {
       unrank_kernel<<<(unsigned)ceil_div(b->D, 256), 256, 0, st>>>(b->states, b->D, L, m->N, b->binom);
+    } else if (m->kind == PF_MODEL_QSUN_U1) {
+      unrank_kernel<<<(unsigned)ceil_div(b->D, 256), 256, 0, st>>>(b->states, b->D, m->N + L, m->N_up, b->binom);
     } else {
       unrank_kernel<<<(unsigned)ceil_div(b->D_up, 256), 256, 0, st>>>(b->states, b->D_up, L, m->N_up, b->binom);
       unrank_kernel<<<(unsigned)ceil_div(b->D_dn, 256), 256, 0, st>>>(b->states + b->D_up, b->D_dn, L, m->N_dn,
                                                                        b->binom);
     }
-    PF_COUNT(m->kind == PF_MODEL_XXZ ? 1 : 2);
+    PF_COUNT(m->kind == PF_MODEL_HUBBARD ? 2 : 1);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
       set_cuda_error(e, "unrank_kernel");
@@ -255,6 +262,23 @@ __device__ void gen_row(const DevModel& M, int64_t row, RowTerms& T) {
       uint32_t flip = (1u << (L + M.nj[j])) | (1u << j);
       T.push((int64_t)(s ^ flip), M.coef[j]);
     }
+  } else if (M.kind == PF_MODEL_QSUN_U1) {
+    const int nd = 1 << M.N;
+    const uint32_t s = M.states[row];
+    const uint32_t a = s >> L;
+    const uint32_t outer = s & ((1u << L) - 1u);
+    double d = M.hdot[a * nd + a];
+    for (int j = 0; j < L; ++j) d = __dadd_rn(d, ((s >> j) & 1u) ? M.hhalf[j] : -M.hhalf[j]);
+    T.push(row, d);
+    const int pa = __popc(a);
+    for (int q = 0; q < nd; ++q)
+      if ((uint32_t)q != a && __popc(q) == pa)
+        T.push((int64_t)rank_state(((uint32_t)q << L) | outer, M.binom), M.hdot[a * nd + q]);
+    for (int j = 0; j < L; ++j) {
+      const int bd = L + M.nj[j];
+      if (((s >> bd) & 1u) != ((s >> j) & 1u))
+        T.push((int64_t)rank_state(s ^ ((1u << bd) | (1u << j)), M.binom), M.coef[j]);
+    }
   } else if (M.kind == PF_MODEL_QREM) {
     T.push(row, M.E[row]);
     for (int i = 0; i < L; ++i) T.push((int64_t)((uint32_t)row ^ (1u << i)), M.negG);
@@ -363,7 +387,8 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
   if (!b || !m || !p || !out) return PF_EINVAL;
   *out = nullptr;
   if (m->kind != b->m.kind || m->L != b->m.L || m->N != b->m.N ||
-      (m->kind == PF_MODEL_HUBBARD && (m->N_up != b->m.N_up || m->N_dn != b->m.N_dn)))
+      (m->kind == PF_MODEL_HUBBARD && (m->N_up != b->m.N_up || m->N_dn != b->m.N_dn)) ||
+      (m->kind == PF_MODEL_QSUN_U1 && m->N_up != b->m.N_up))
     return PF_EINVAL;
   const int L = m->L;
   DevModel M;
@@ -412,6 +437,39 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
       nj[j] = p->n_of_j[j];
       if (nj[j] < 0 || nj[j] >= m->N) return PF_EINVAL;
     }
+  } else if (m->kind == PF_MODEL_QSUN_U1) {
+    if (!p->h || !p->A || !p->u_noise || !p->n_of_j) return PF_EINVAL;
+    M.nbonds = 0;
+    const int nd = 1 << m->N, Mup = m->N_up;
+    // popcount-conserving part of A + A^T, normalised on the sector: T = sum over a, then b with
+    // popcount(b) = popcount(a), of binom(L, M - popcount(a)) (S_ab S_ab); c = gamma / sqrt(T / D)
+    double T = 0.0;
+    for (int a = 0; a < nd; ++a) {
+      const int pa = __builtin_popcount(a);
+      const double w = (Mup - pa >= 0 && Mup - pa <= L) ? (double)binom_h(L, Mup - pa) : 0.0;
+      for (int q = 0; q < nd; ++q)
+        if (__builtin_popcount(q) == pa) {
+          const double sv = p->A[a * nd + q] + p->A[q * nd + a];
+          T = T + w * (sv * sv);
+        }
+    }
+    if (!(T > 0.0)) return PF_EINVAL;
+    const double c = m->gamma / sqrt(T / (double)b->D);
+    hdot.assign((size_t)nd * nd, 0.0);
+    for (int a = 0; a < nd; ++a)
+      for (int q = 0; q < nd; ++q)
+        if (__builtin_popcount(q) == __builtin_popcount(a)) hdot[a * nd + q] = (p->A[a * nd + q] + p->A[q * nd + a]) * c;
+    hh.resize(L);
+    coef.resize(L);
+    nj.resize(L);
+    for (int j = 0; j < L; ++j) {
+      hh[j] = p->h[j] * 0.5;
+      double u = (double)j + p->u_noise[j];
+      coef[j] = (m->g0 * pow(m->alpha, u)) * 0.5;
+      nj[j] = p->n_of_j[j];
+      if (nj[j] < 0 || nj[j] >= m->N) return PF_EINVAL;
+    }
+    M.states = b->states;
   } else if (m->kind == PF_MODEL_QREM) {
     if (!p->E) return PF_EINVAL;
     M.nbonds = 0;

@@ -1547,6 +1547,7 @@ static int64_t model_dim(const pf_model& m) {
   if (m.kind == PF_MODEL_HUBBARD) return (int64_t)(C(m.L, m.N_up) * C(m.L, m.N_dn));
   if (m.kind == PF_MODEL_QSUN) return (int64_t)1 << (m.N + m.L);
   if (m.kind == PF_MODEL_QREM) return (int64_t)1 << m.L;
+  if (m.kind == PF_MODEL_QSUN_U1) return (int64_t)C(m.N + m.L, m.N_up);
   return 0;
 }
 
@@ -1684,7 +1685,7 @@ static pf_status copy_request(const pf_model* m, const pf_params* p, Request* r)
   } else if (m->kind == PF_MODEL_HUBBARD) {
     if (!p->mu) return PF_EINVAL;
     r->mu.assign(p->mu, p->mu + L);
-  } else if (m->kind == PF_MODEL_QSUN) {
+  } else if (m->kind == PF_MODEL_QSUN || m->kind == PF_MODEL_QSUN_U1) {
     if (!p->h || !p->A || !p->u_noise || !p->n_of_j || m->N < 1 || m->N > 10) return PF_EINVAL;
     const int nd = 1 << m->N;
     r->h.assign(p->h, p->h + L);
