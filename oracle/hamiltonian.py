@@ -162,9 +162,16 @@ def qsun_dot_matrix(p):
     return (A + A.T) * c
 
 
+def _alpha_pow(alpha, u):
+    """alpha**u_j term by term with the C library's pow (math.pow), so that the coupling of each
+    ray is one correctly rounded evaluation; numpy's vectorised power may differ in the last bit."""
+    return np.array([math.pow(alpha, float(x)) for x in u])
+
+
 def qsun_ray_coefficients(p):
+    """g0 alpha^u_j / 4, u_j = j + noise_j (Eq. qsun; S^x S^x has element 1/4)."""
     u = np.arange(p.L, dtype=np.float64) + p.u_noise
-    return (p.g0 * np.power(p.alpha, u)) * 0.25
+    return (p.g0 * _alpha_pow(p.alpha, u)) * 0.25
 
 
 def qsun_hamiltonian(p):
@@ -240,7 +247,7 @@ def qsun_u1_hamiltonian(p):
         cols.append(_basis.row_of(states, (b << L) | outer[m]))
         vals.append(hd[dot[m], b])
     u = np.arange(L, dtype=np.float64) + p.u_noise
-    coef = (p.g0 * np.power(p.alpha, u)) * 0.5
+    coef = (p.g0 * _alpha_pow(p.alpha, u)) * 0.5
     for j in range(L):
         bd = L + int(p.n_of_j[j])
         anti = ((states >> bd) & 1) != ((states >> j) & 1)
