@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--refine-precision", default="f64", choices=["f64", "df64"],
                     help="arithmetic of the refinement filter: FP64 (the workload's definition) or pair-float")
+    ap.add_argument("--k-from", default=None, choices=["gauss", "kpm"],
+                    help="model mode: the filter degree from the Gaussian DOS or the KPM DOS (default: KPM for the "
+                         "quantum suns, Gaussian otherwise)")
     ap.add_argument("--mapping", default="structured", choices=["structured", "csr"],
                     help="model mode, QREM: how the steps read H~ (generated bit-flip columns or the CSR)")
     ap.add_argument("--no-variant", action="store_true",
@@ -60,8 +63,9 @@ def parse():
     ap.add_argument("--no-pipeline", dest="pipeline", action="store_false")
     ap.add_argument("--L", type=int, default=L_SITES, help="solve mode: chain length (default: the L=20 workload)")
     ap.add_argument("--nev", type=int, default=NEV, help="solve mode: eigenpairs per solve")
-    ap.add_argument("--config", type=int, default=3, choices=[1, 3, 4, 6],
-                    help="model mode: workload 1 (XXZ L=12), 3 (quantum sun N=3 L=15) or 4 (Hubbard L=12)")
+    ap.add_argument("--config", type=int, default=3, choices=[1, 3, 4, 6, 7, 8],
+                    help="model mode: workload 1 (XXZ L=12), 3 (quantum sun N=3 L=15), 4 (Hubbard L=12), 6 (QREM L=18), "
+                         "7 (U(1) quantum sun N=3 L=15 M=9) or 8 (J1-J2-J3 L=20)")
     ap.add_argument("--mode", default="solve", choices=["solve", "batch", "serving", "model"],
                     help="solve: the L=20 workload; batch: many small solves together vs one at a time; "
                          "serving: a Poisson request stream through the continuous-batching server")
@@ -559,10 +563,19 @@ def run_model(args):
                                          seed=pi.config_seed(args.config, r))
     elif c["model"] == "qrem":
         mk = lambda r: pi.qrem_params(c["L"], Gamma=c["Gamma"], seed=pi.config_seed(args.config, r))
+    elif c["model"] == "qsun_u1":
+        mk = lambda r: pi.qsun_u1_params(N=c["N"], L=c["L"], M=c["M"], g0=c["g0"], alpha=c["alpha"],
+                                         gamma=c["gamma"], seed=pi.config_seed(args.config, r))
+    elif c["model"] == "j1j2":
+        mk = lambda r: pi.j1j2_params(c["L"], J2=c["J2"], J3=c["J3"], W=c["W"], seed=pi.config_seed(args.config, r))
     else:
         mk = lambda r: pi.xxz_params(c["L"], W=c["W"], seed=pi.config_seed(args.config, r))
     prec = args.precision
     nev, s, eps = c["nev"], c["block"], c["eps"]
+    # the quantum suns' densities of states are far from the Gaussian of Eq. dos_gaussian: there K
+    # comes from the KPM density (with the Gaussian, the U(1) sun at r = 2 got K = 3336 against
+    # 2098, its filter window held fewer than nev_g levels, and the refinement stalled)
+    kmode = args.k_from or ("kpm" if c["model"] in ("qsun", "qsun_u1") else "gauss")
 
     def one(r):
         st = torch.cuda.current_stream()
@@ -571,8 +584,14 @@ def run_model(args):
         H = pf.Hamiltonian.from_params(mk(r))
         if c["model"] == "qrem":
             H.set_mapping(args.mapping)
-        H.spectral_bounds()
-        K = H.choose_K(eps, nev)
+        emin, emax, _, _ = H.spectral_bounds()
+        if kmode == "kpm":
+            # degree from the kernel-polynomial DOS at the target (Sec. 3.3, Eq. condition_for_K)
+            Ec, dE = H.rescaled()[:2]
+            mu = H.kpm_moments(N=512, R=32, seed=pi.config_seed(args.config, r))
+            K = pf.choose_K_kpm(mu, (emin + eps * (emax - emin) - Ec) / dE, nev)
+        else:
+            K = H.choose_K(eps, nev)
         res = H.solve(eps, nev, K, block=s, precision=prec, return_vectors=False, raise_on_notconv=False,
                       refine_precision=args.refine_precision)
         e1.record(st)
@@ -593,7 +612,7 @@ def run_model(args):
     D, nnz = rec[0]["D"], rec[0]["nnz"]
     out = {"metric": METRIC, "mode": "model", "value": good / t, "unit": "eigenpairs/s", "higher_is_better": True,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(rec), "dtype": dtype_name(args),
-           "data": "synthetic", "config": {"workload": c["name"], "D": D, "nnz": nnz, "nev": nev, "block": s,
+           "data": "synthetic", "config": {"workload": c["name"], "D": D, "nnz": nnz, "nev": nev, "block": s, "K_from": kmode,
                                            "target_eps": eps, "K": [x["K"] for x in rec]},
            "eigenpairs_at_tol": good, "solves": len(rec), "clocks": clocks.summary(),
            "phases_ms": {k: statistics.mean(x["rep"][k] for x in rec)

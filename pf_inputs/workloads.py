@@ -145,6 +145,12 @@ CONFIGS = {
             eps=(0.2, 0.8), nev=(20, 50, 200), requests=2000, precision="f32"),
     # the paper's GPU benchmark model (Eq. qrem), at a size one solve of which takes seconds
     6: dict(name="qrem_L18", model="qrem", L=18, Gamma=1.0, nev=100, eps=0.5, block=32, precision="f32"),
+    # the U(1) quantum sun (Eq. qsun:U1) in its half-filled sector, and the J1-J2-J3 chain (Eq. j1j2j3)
+    # with the paper's couplings
+    7: dict(name="qsun_u1_N3_L15_M9", model="qsun_u1", N=3, L=15, M=9, g0=1.0, alpha=0.75, gamma=1.0,
+            nev=50, eps=0.5, block=16, precision="f32"),
+    8: dict(name="j1j2j3_L20", model="j1j2", L=20, J2=0.5, J3=0.225, W=1.0, nev=100, eps=0.5, block=32,
+            precision="f32"),
 }
 
 

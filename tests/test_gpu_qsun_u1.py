@@ -42,3 +42,17 @@ def test_qsun_u1_solve_matches_dense(pf, precision):
     assert r.status == 0
     assert np.max(np.abs(r.evals - w[dense.nearest(w, lam, nev)])) <= 1e-10 * hn
     assert np.max(r.resid) <= 1e-9 * hn
+
+
+def test_qsun_u1_kpm_degree_converges(pf):
+    """A realisation whose Gaussian-DOS degree is too large (K = 3336: fewer than nev_g levels in the
+    window, the refinement stalls) converges with the degree from the KPM density (K = 2098)."""
+    p = pi.qsun_u1_params(N=3, L=15, M=9, seed=pi.config_seed(7, 2))
+    H = pf.Hamiltonian.from_params(p)
+    emin, emax, _, _ = H.spectral_bounds()
+    Ec, dE = H.rescaled()[:2]
+    mu = H.kpm_moments(N=512, R=32, seed=pi.config_seed(7, 2))
+    K = pf.choose_K_kpm(mu, (emin + 0.5 * (emax - emin) - Ec) / dE, 50)
+    assert K < H.choose_K(0.5, 50)
+    r = H.solve(0.5, 50, K, block=16, precision="f32", return_vectors=False, raise_on_notconv=False)
+    assert r.status == 0 and np.max(r.resid) <= 1e-9 * r.report["hnorm"]
