@@ -265,7 +265,7 @@ pf_status pf_filter_tune(const pf_ham* H, int32_t prec, int32_t s, int32_t K, in
  * be re-entered from its own hooks, loops that forbid allocation calls).  The two D x s
  * auxiliary blocks come from one fixed device array of 32 MiB inside the library, which
  * every GPU that loads the library keeps until the process exits.
- *  - Limit: 2 * D * s * w <= 32 MiB, w = 8 (PF_F64) or 4 (PF_F32), each block rounded up
+ *  - Limit: 2 * D * s * w <= 32 MiB, w = 8 (PF_F64, PF_DF64) or 4 (PF_F32), each block rounded up
  *    to 256 bytes; larger requests return PF_EINVAL without touching the GPU.
  *  - The first call on a device looks up the array's device address (a CUDA symbol
  *    query, no allocation) and caches it; make that first call before any stream capture.
