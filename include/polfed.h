@@ -165,10 +165,13 @@ pf_status pf_spectral_bounds(pf_ham* H, double tol, double* emin, double* emax, 
 pf_status pf_set_rescale(pf_ham* H, double Ec, double dE, pf_stream_t stream);
 /* How the Clenshaw steps read H~ (custom mappings, Sec. 5.7-5.8).
  *  PF_MAP_CSR         the stored CSR arrays (every model; the default except QREM).
- *  PF_MAP_STRUCTURED  QREM only (its default): a row's columns r ^ (1 << i) are generated
- *                     in registers in ascending order and every off-diagonal element is the
- *                     one value -Gamma / dE; only the diagonal is read.  The FMA sequence is
- *                     the CSR step's, so both mappings give the same bits.
+ *  PF_MAP_STRUCTURED  QREM (its default): a row's columns r ^ (1 << i) are generated in
+ *                     registers in ascending order and every off-diagonal element is the one
+ *                     value -Gamma / dE; only the diagonal is read.  Nearest-neighbour XXZ
+ *                     (J2 = J3 = 0, L >= 3; its default): FP32 steps read the CSR columns with
+ *                     the one off-diagonal value (J/2) / dE and the diagonal per row, not the
+ *                     value array (FP64 and pair-float steps keep the CSR form).  The FMA
+ *                     sequence is the CSR step's, so both mappings give the same bits.
  * Errors: PF_EINVAL (unknown mapping, or structured for another model).              */
 typedef enum { PF_MAP_CSR = 0, PF_MAP_STRUCTURED = 1 } pf_mapping;
 pf_status pf_ham_set_mapping(pf_ham* H, int32_t mapping);

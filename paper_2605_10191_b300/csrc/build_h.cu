@@ -383,6 +383,14 @@ static pf_status exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cuda
   return PF_OK;
 }
 
+// Models whose off-diagonal elements of H share one value, so that a structured mapping can drop
+// the value array: QREM (-Gamma, columns from bit flips) and the nearest-neighbour XXZ chain
+// (J / 2; with L >= 3 no two bonds couple the same pair of states).
+static bool structured_ok(const Ham* H) {
+  if (H->m.kind == PF_MODEL_QREM) return true;
+  return H->m.kind == PF_MODEL_XXZ && H->m.J2 == 0.0 && H->m.J3 == 0.0 && H->m.L >= 3;
+}
+
 static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_params* p, Ham** out, cudaStream_t st) {
   if (!b || !m || !p || !out) return PF_EINVAL;
   *out = nullptr;
@@ -551,7 +559,7 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
     delete H;
     return PF_ECUDA;
   }
-  H->mapping = m->kind == PF_MODEL_QREM ? PF_MAP_STRUCTURED : PF_MAP_CSR;
+  H->mapping = structured_ok(H) ? PF_MAP_STRUCTURED : PF_MAP_CSR;
   *out = H;
   return PF_OK;
 }
@@ -590,9 +598,9 @@ pf_status set_rescale(Ham* H, double Ec, double dE, cudaStream_t st) {
   rescale_kernel<<<(unsigned)ceil_div(H->D, 256), 256, 0, st>>>(H->D, H->row_ptr, H->col, H->val, Ec, dE, H->val_t,
                                                                  H->val32, H->val_df);
   PF_LAUNCH_CHECK("rescale_kernel");
-  if (H->m.kind == PF_MODEL_QREM) {
-    // structured mapping: every off-diagonal element of H~ is -Gamma / dE (the value the
-    // rescale kernel computes for each of them), the diagonal is kept per row
+  if (structured_ok(H)) {
+    // structured mapping: every off-diagonal element of H~ is -Gamma / dE (QREM) or (J / 2) / dE
+    // (XXZ), the value the rescale kernel computes for each of them; the diagonal is kept per row
     if (!H->diag_t) {
       H->diag_t = (double*)dev_alloc(H->D * sizeof(double), st);
       H->diag32 = (float*)dev_alloc(H->D * sizeof(float), st);
@@ -602,7 +610,7 @@ pf_status set_rescale(Ham* H, double Ec, double dE, cudaStream_t st) {
     diag_copy_kernel<<<(unsigned)ceil_div(H->D, 256), 256, 0, st>>>(H->D, H->row_ptr, H->col, H->val_t, H->val32,
                                                                     H->val_df, H->diag_t, H->diag32, H->diag_df);
     PF_LAUNCH_CHECK("diag_copy_kernel");
-    H->off_t = (-H->m.Gamma) / dE;
+    H->off_t = H->m.kind == PF_MODEL_QREM ? (-H->m.Gamma) / dE : (H->m.J * 0.5) / dE;
   }
   H->has_rescale = 1;
   return PF_OK;
@@ -772,7 +780,7 @@ pf_status pf_ham_set_mapping(pf_ham* hh, int32_t mapping) {
     H->mapping = PF_MAP_CSR;
     return PF_OK;
   }
-  if (mapping == PF_MAP_STRUCTURED && H->m.kind == PF_MODEL_QREM) {
+  if (mapping == PF_MAP_STRUCTURED && structured_ok(H)) {
     H->mapping = PF_MAP_STRUCTURED;
     return PF_OK;
   }

@@ -306,11 +306,14 @@ __device__ __forceinline__ void row_epilogue(int64_t off, const T (&acc)[E], boo
 // all execution forms produce the same bits: the SpMM accumulates in column order, four
 // entries per round, and the epilogue is fma(alpha, acc, fma(a, v, -beta q)) (or
 // fma(alpha, acc, a v) without B2).  L2ONLY selects ld.global.cg for B1 and B2.
-template <typename T, int S, bool L2ONLY, int SP, int B2M>
-__device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_t* __restrict__ rp,
-                                             const int32_t* __restrict__ col, const T* __restrict__ val,
-                                             const T* __restrict__ V, const T* B1, const T* B2, T* out, T a,
-                                             T alpha, T beta) {
+// VS selects where a stored element's value comes from: 0 = the CSR value array; 1 = constant
+// off-diagonal (the XXZ chain's J/(2 dE)): g for every column but the row's own, whose value is
+// diag[row] (the structured mapping; the values are those the CSR stores, so the bits agree).
+template <typename T, int S, bool L2ONLY, int SP, int B2M, int VS>
+__device__ __forceinline__ void clenshaw_row_vs(int64_t row, int lane, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                const T* __restrict__ V, const T* B1, const T* B2, T* out, T a,
+                                                T alpha, T beta, const T* __restrict__ diag, T g) {
   using Sh = Shape<T, S>;
   constexpr int E = Sh::E;
   const int64_t off = row * S + lane * E;
@@ -326,9 +329,15 @@ __device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_
   if (spmm) {
     int64_t j = rp[row];
     const int64_t end = rp[row + 1];
+    T dr = g;
+    if constexpr (VS == 1) dr = ld_val(diag + row);
+    auto hv = [&](int64_t jj, int c) -> T {
+      if constexpr (VS == 1) return (int64_t)c == row ? dr : g;
+      else return ld_val(val + jj);
+    };
     for (; j + 4 <= end; j += 4) {
       int c0 = __ldg(col + j), c1 = __ldg(col + j + 1), c2 = __ldg(col + j + 2), c3 = __ldg(col + j + 3);
-      T h0 = ld_val(val + j), h1 = ld_val(val + j + 1), h2 = ld_val(val + j + 2), h3 = ld_val(val + j + 3);
+      T h0 = hv(j, c0), h1 = hv(j + 1, c1), h2 = hv(j + 2, c2), h3 = hv(j + 3, c3);
       Vec<T, E> b0 = ldb(B1 + (int64_t)c0 * S + lane * E);
       Vec<T, E> b1 = ldb(B1 + (int64_t)c1 * S + lane * E);
       Vec<T, E> b2 = ldb(B1 + (int64_t)c2 * S + lane * E);
@@ -343,13 +352,21 @@ __device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_
     }
     for (; j < end; ++j) {
       int c0 = __ldg(col + j);
-      T h0 = ld_val(val + j);
+      T h0 = hv(j, c0);
       Vec<T, E> b0 = ldb(B1 + (int64_t)c0 * S + lane * E);
 #pragma unroll
       for (int e = 0; e < E; ++e) acc[e] = fmadd(h0, b0.x[e], acc[e]);
     }
   }
   row_epilogue<T, E, L2ONLY, B2M>(off, acc, hb2, V, B2, out, a, alpha, beta);
+}
+
+template <typename T, int S, bool L2ONLY, int SP, int B2M>
+__device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_t* __restrict__ rp,
+                                             const int32_t* __restrict__ col, const T* __restrict__ val,
+                                             const T* __restrict__ V, const T* B1, const T* B2, T* out, T a,
+                                             T alpha, T beta) {
+  clenshaw_row_vs<T, S, L2ONLY, SP, B2M, 0>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta, nullptr, T(0));
 }
 
 // One Clenshaw step over a D x s block.  rows_per_cta = 0: thread group g owns row g (one
@@ -484,6 +501,35 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) qrem_step_kernel(in
   }
 }
 
+// Structured mapping of the XXZ chain: the CSR's columns with the constant off-diagonal value g and
+// the per-row diagonal, no value array (clenshaw_row_vs with VS = 1); same bits as the CSR step.
+template <typename T, int S, int SP, int B2M>
+__global__ void __launch_bounds__(256, step_min_blocks<T>()) cconst_step_kernel(int64_t D, const int64_t* __restrict__ rp,
+                                                                                const int32_t* __restrict__ col,
+                                                                                const T* __restrict__ diag, T g,
+                                                                                const T* __restrict__ V,
+                                                                                const T* __restrict__ B1, const T* B2,
+                                                                                T* out, T a, T alpha, T beta,
+                                                                                int64_t rows_per_cta) {
+  using Sh = Shape<T, S>;
+  constexpr int G = Sh::G;
+  const int lane = (int)(threadIdx.x % G);
+  if (rows_per_cta > 0) {
+    const int64_t r0 = blockIdx.x * rows_per_cta;
+    const int64_t r1 = r0 + rows_per_cta < D ? r0 + rows_per_cta : D;
+    for (int64_t row = r0 + threadIdx.x / G; row < r1; row += 256 / G)
+      clenshaw_row_vs<T, S, false, SP, B2M, 1>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, diag, g);
+  } else if (rows_per_cta < 0) {
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
+    for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; row < D; row += groups)
+      clenshaw_row_vs<T, S, false, SP, B2M, 1>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, diag, g);
+  } else {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    if (row < D)
+      clenshaw_row_vs<T, S, false, SP, B2M, 1>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, diag, g);
+  }
+}
+
 // Launch shape of a step over `rows` rows: FP32 and pair-float steps use one wave of contiguous
 // row ranges (they are bound by their neighbour gathers, which the ranges keep in L1); FP64 steps
 // are bound by the FP64 pipe and keep one row per thread group.  cta_cap > 0 limits the CTAs
@@ -529,6 +575,12 @@ template <typename T, int S, int SP, int B2M>
 static StepShape qrem_shape(int64_t rows, int cta_cap = 0) {
   static const int nsm = device_sms();
   static const int occ = kernel_occupancy(qrem_step_kernel<T, S, SP, B2M>);
+  return shape_for<T, S>(rows, cta_cap, nsm, occ);
+}
+template <typename T, int S, int SP, int B2M>
+static StepShape cconst_shape(int64_t rows, int cta_cap = 0) {
+  static const int nsm = device_sms();
+  static const int occ = kernel_occupancy(cconst_step_kernel<T, S, SP, B2M>);
   return shape_for<T, S>(rows, cta_cap, nsm, occ);
 }
 
@@ -589,62 +641,88 @@ pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* co
   return PF_EINVAL;
 }
 
-// Structured-mapping (QREM) step launches: same shapes, validation and operands as the CSR step.
-template <typename T, int S, int SP, int B2M>
-static void launch_qrem_form(int64_t D, int L, const T* diag, T g, const T* V, const T* B1, const T* B2, T* out,
-                             T a, T alpha, T beta, cudaStream_t st, int cap) {
-  const StepShape sh = qrem_shape<T, S, SP, B2M>(D, cap);
-  qrem_step_kernel<T, S, SP, B2M><<<sh.grid, 256, 0, st>>>(D, L, diag, g, V, B1, B2, out, a, alpha, beta,
-                                                          sh.rows_per_cta);
+// Structured-mapping step launches (QREM bit flips, or XXZ constant off-diagonal): same shapes,
+// validation and operands as the CSR step.  The structure argument is L for QREM and the CSR
+// (row pointers, columns) for XXZ.
+struct StructArgs {
+  int L;
+  const int64_t* rp;
+  const int32_t* col;
+};
+template <bool QREM, typename T, int S, int SP, int B2M>
+static void launch_struct_form(int64_t D, StructArgs sa, const T* diag, T g, const T* V, const T* B1, const T* B2,
+                               T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
+  if constexpr (QREM) {
+    const StepShape sh = qrem_shape<T, S, SP, B2M>(D, cap);
+    qrem_step_kernel<T, S, SP, B2M><<<sh.grid, 256, 0, st>>>(D, sa.L, diag, g, V, B1, B2, out, a, alpha, beta,
+                                                            sh.rows_per_cta);
+  } else {
+    const StepShape sh = cconst_shape<T, S, SP, B2M>(D, cap);
+    cconst_step_kernel<T, S, SP, B2M><<<sh.grid, 256, 0, st>>>(D, sa.rp, sa.col, diag, g, V, B1, B2, out, a, alpha,
+                                                              beta, sh.rows_per_cta);
+  }
 }
-template <typename T, int S>
-static pf_status launch_qrem_s(int64_t D, int L, const T* diag, T g, const T* V, const T* B1, const T* B2, T* out,
-                               T a, T alpha, T beta, cudaStream_t st, int cap) {
+template <bool QREM, typename T, int S>
+static pf_status launch_struct_s(int64_t D, StructArgs sa, const T* diag, T g, const T* V, const T* B1, const T* B2,
+                                 T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
   const bool spmm = alpha != T(0);
   const bool hb2 = beta != T(0);
-  if (spmm && hb2) launch_qrem_form<T, S, 1, 1>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-  else if (spmm) launch_qrem_form<T, S, 1, 0>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-  else if (hb2) launch_qrem_form<T, S, 0, 1>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-  else launch_qrem_form<T, S, 0, 0>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-  PF_LAUNCH_CHECK("qrem_step_kernel");
+  if (spmm && hb2) launch_struct_form<QREM, T, S, 1, 1>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+  else if (spmm) launch_struct_form<QREM, T, S, 1, 0>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+  else if (hb2) launch_struct_form<QREM, T, S, 0, 1>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+  else launch_struct_form<QREM, T, S, 0, 0>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+  PF_LAUNCH_CHECK(QREM ? "qrem_step_kernel" : "cconst_step_kernel");
   return PF_OK;
 }
-template <typename T>
-static pf_status launch_qrem(int s, int64_t D, int L, const T* diag, T g, const T* V, const T* B1, const T* B2,
-                             T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
+template <bool QREM, typename T>
+static pf_status launch_struct(int s, int64_t D, StructArgs sa, const T* diag, T g, const T* V, const T* B1,
+                               const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
   switch (s) {
-    case 1: return launch_qrem_s<T, 1>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 2: return launch_qrem_s<T, 2>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 4: return launch_qrem_s<T, 4>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 8: return launch_qrem_s<T, 8>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 16: return launch_qrem_s<T, 16>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 32: return launch_qrem_s<T, 32>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 64: return launch_qrem_s<T, 64>(D, L, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 1: return launch_struct_s<QREM, T, 1>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 2: return launch_struct_s<QREM, T, 2>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 4: return launch_struct_s<QREM, T, 4>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 8: return launch_struct_s<QREM, T, 8>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 16: return launch_struct_s<QREM, T, 16>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 32: return launch_struct_s<QREM, T, 32>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 64: return launch_struct_s<QREM, T, 64>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
   }
   return PF_EINVAL;
 }
+template <typename T>
+static pf_status launch_structured(const Ham* H, int s, const T* diag, T g, const T* V, const T* B1, const T* B2,
+                                   T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
+  const StructArgs sa{H->m.L, H->row_ptr, H->col};
+  if (H->m.kind == PF_MODEL_QREM)
+    return launch_struct<true, T>(s, H->D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+  return launch_struct<false, T>(s, H->D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+}
 
-// One step of H~ through the handle's mapping: the CSR arrays, or the structured QREM rows.
+// One step of H~ through the handle's mapping: the CSR arrays, or the structured rows (QREM bit
+// flips; XXZ constant off-diagonal).
 pf_status ham_step(const Ham* H, int prec, int s, const void* V, const void* B1, const void* B2, void* out,
                    double a, double alpha, double beta, cudaStream_t st, int cta_cap) {
-  if (H->mapping != PF_MAP_STRUCTURED || !H->diag_t)
+  // XXZ: only the FP32 step takes the structured form (26.7 against 28.8 us at L = 20, s = 32);
+  // FP64 (bound by its pipe, 145.4 against 145.6 us) and pair-float (73.5 against 73.0 us) keep
+  // the CSR form.  The bits are the same either way.
+  const bool csr_form = H->mapping != PF_MAP_STRUCTURED || !H->diag_t ||
+                        (H->m.kind == PF_MODEL_XXZ && prec != PF_F32);
+  if (csr_form)
     return clenshaw_step_raw(H->D, H->row_ptr, H->col, ham_vals(H, prec), prec, s, V, B1, B2, out, a, alpha, beta,
                              st, cta_cap);
   if (!valid_s(s) || !V || !out) return PF_EINVAL;
   if (alpha != 0.0 && !B1) return PF_EINVAL;
   if (beta != 0.0 && !B2) return PF_EINVAL;
   if (beta != 0.0 && beta != 1.0) return PF_EINVAL;
-  const int64_t D = H->D;
-  const int L = H->m.L;
   if (prec == PF_F64)
-    return launch_qrem<double>(s, D, L, H->diag_t, H->off_t, (const double*)V, (const double*)B1,
-                               (const double*)B2, (double*)out, a, alpha, beta, st, cta_cap);
+    return launch_structured<double>(H, s, H->diag_t, H->off_t, (const double*)V, (const double*)B1,
+                                     (const double*)B2, (double*)out, a, alpha, beta, st, cta_cap);
   if (prec == PF_F32)
-    return launch_qrem<float>(s, D, L, H->diag32, (float)H->off_t, (const float*)V, (const float*)B1,
-                              (const float*)B2, (float*)out, (float)a, (float)alpha, (float)beta, st, cta_cap);
+    return launch_structured<float>(H, s, H->diag32, (float)H->off_t, (const float*)V, (const float*)B1,
+                                    (const float*)B2, (float*)out, (float)a, (float)alpha, (float)beta, st, cta_cap);
   if (prec == PF_DF64)
-    return launch_qrem<df2>(s, D, L, reinterpret_cast<const df2*>(H->diag_df), df2(H->off_t), (const df2*)V,
-                            (const df2*)B1, (const df2*)B2, (df2*)out, df2(a), df2(alpha), df2(beta), st, cta_cap);
+    return launch_structured<df2>(H, s, reinterpret_cast<const df2*>(H->diag_df), df2(H->off_t), (const df2*)V,
+                                  (const df2*)B1, (const df2*)B2, (df2*)out, df2(a), df2(alpha), df2(beta), st,
+                                  cta_cap);
   return PF_EINVAL;
 }
 
@@ -1051,6 +1129,10 @@ static void prepare_shapes_s() {
   qrem_shape<T, S, 1, 0>(1);
   qrem_shape<T, S, 0, 1>(1);
   qrem_shape<T, S, 1, 1>(1);
+  cconst_shape<T, S, 0, 0>(1);
+  cconst_shape<T, S, 1, 0>(1);
+  cconst_shape<T, S, 0, 1>(1);
+  cconst_shape<T, S, 1, 1>(1);
 }
 template <typename T>
 static void prepare_shapes(int s) {

@@ -146,8 +146,32 @@ def test_qrem_server_request(pf):
     assert np.max(np.abs(np.sort(r.evals) - np.sort(w[dense.nearest(w, lam, 10)]))) <= 1e-10 * hn
 
 
-def test_structured_mapping_rejected_for_other_models(pf):
-    H = pf.Hamiltonian.from_params(pi.xxz_params(8, W=1.0, seed=1))
+@pytest.mark.parametrize("mk", [lambda: pi.hubbard_params(6, 3, 3, U=1.0, W=1.0, seed=1),
+                                lambda: pi.qsun_params(N=2, L=6, seed=2),
+                                lambda: pi.j1j2_params(8, J2=0.5, W=1.0, seed=3)])
+def test_structured_mapping_rejected_for_other_models(pf, mk):
+    H = pf.Hamiltonian.from_params(mk())
     with pytest.raises(pf.PolfedError):
         H.set_mapping("structured")
     H.set_mapping("csr")
+
+
+@pytest.mark.parametrize("L,s,prec", [(12, 8, "f64"), (14, 32, "f32"), (14, 16, "df64"), (16, 32, "f32"),
+                                      (9, 1, "f64"), (10, 64, "f32")])
+def test_xxz_structured_step_and_filter_equal_csr(pf, L, s, prec):
+    """Nearest-neighbour XXZ: the CSR columns with the one off-diagonal value (J/2)/dE and the
+    per-row diagonal give the CSR step's bits, for single steps and whole filters."""
+    p = pi.xxz_params(L, W=2.0, seed=70 + L)
+    H = pf.Hamiltonian.from_params(p)
+    H.spectral_bounds()
+    V, B1, B2 = (_block((H.D, s), 800 + k, prec) for k in range(3))
+    c = pf.filter_coefficients(0.07, 33)
+    outs = {}
+    for mapping in ("csr", "structured"):
+        H.set_mapping(mapping)
+        o = torch.empty_like(V)
+        H.clenshaw_step(V, B1, B2, o, 0.0219, 2.0, 1.0)
+        outs[mapping] = (o, H.filter_apply(V, c))
+    torch.cuda.synchronize()
+    for a, b in zip(outs["csr"], outs["structured"]):
+        assert torch.equal(a, b)
