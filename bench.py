@@ -315,7 +315,7 @@ def run_kernel_only(args):
     w = 4 if args.kernel_precision == "f32" else 8
     # FP32 steps of this chain use the structured mapping (no value array); FP64 and pair-float the CSR
     byt = struct_step_bytes(D, H.nnz, s, w) if args.kernel_precision == "f32" else step_bytes(D, H.nnz, s, w)
-    print(json.dumps({"kernel": ("cconst_step_f32_s32" if args.kernel_precision == "f32"
+    print(json.dumps({"kernel": ("cstruct_step_f32_s32" if args.kernel_precision == "f32"
                                  else f"clenshaw_step_{args.kernel_precision}_s32"), "us_per_launch": 1e3 * ms,
                       "alg_bytes": byt, "GBps": byt / ms / 1e6, "launches": args.steps}))
 
@@ -427,13 +427,13 @@ def run_ours(args):
     roof = None
     if f32_n:
         # the FP32 steps of the nearest-neighbour XXZ chain run in its structured mapping
-        # (cconst_step_kernel: CSR columns, constant off-diagonal, per-row diagonal)
+        # (cstruct_step_kernel: CSR columns, constant off-diagonal, per-row diagonal)
         per = f32_ms / f32_n
         byt = struct_step_bytes(D, nnz, BLOCK, 4)
         ach = byt / per / 1e6
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": ncu_traffic("cconst_f32_xxz_L20_s32") if D == L20_D else None,
-                "kernel": "cconst_step_kernel<float,32>",
+                "traffic": ncu_traffic("cstruct_f32_xxz_L20_s32") if D == L20_D else None,
+                "kernel": "cstruct_step_kernel<float,32> (XXZ structured mapping)",
                 "us_per_launch": 1e3 * per, "alg_bytes_per_launch": byt, "peak_source": peak_kind}
     roof64 = refine_roofline(rec, D, nnz, args.refine_precision, peak, peak_kind)
     if roof64 is not None and D != L20_D:
@@ -633,11 +633,12 @@ def run_model(args):
                          for k in ("ms_filter_f32", "ms_filter_f64", "ms_orth", "ms_qr", "ms_check", "ms_extract",
                                    "ms_refine", "ms_total")}}
     structured = c["model"] == "qrem" and args.mapping == "structured"
-    xxz_struct = c["model"] == "xxz"
+    xxz_struct = c["model"] in ("xxz", "qsun")
     if structured:
         out["config"]["mapping"] = "structured (bit-flip columns generated in registers; diagonal read)"
     if xxz_struct:
-        out["config"]["mapping"] = "structured for FP32 steps (CSR columns, constant off-diagonal, diagonal read)"
+        out["config"]["mapping"] = ("structured for FP32 steps (CSR columns; values from the diagonal and "
+                                    + ("one off-diagonal constant)" if c["model"] == "xxz" else "the dot block and ray couplings)"))
 
     def alg_bytes(w):
         # QREM's structured mapping reads only the diagonal of the matrix; XXZ's FP32 steps the columns

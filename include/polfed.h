@@ -170,8 +170,10 @@ pf_status pf_set_rescale(pf_ham* H, double Ec, double dE, pf_stream_t stream);
  *                     value -Gamma / dE; only the diagonal is read.  Nearest-neighbour XXZ
  *                     (J2 = J3 = 0, L >= 3; its default): FP32 steps read the CSR columns with
  *                     the one off-diagonal value (J/2) / dE and the diagonal per row, not the
- *                     value array (FP64 and pair-float steps keep the CSR form).  The FMA
- *                     sequence is the CSR step's, so both mappings give the same bits.
+ *                     value array (FP64 and pair-float steps keep the CSR form).  Quantum sun
+ *                     (not its default: no faster): FP32 steps take each value from the
+ *                     diagonal, the dot block or the ray couplings by the two states' bits.
+ *                     The FMA sequence is the CSR step's, so both mappings give the same bits.
  * Errors: PF_EINVAL (unknown mapping, or structured for another model).              */
 typedef enum { PF_MAP_CSR = 0, PF_MAP_STRUCTURED = 1 } pf_mapping;
 pf_status pf_ham_set_mapping(pf_ham* H, int32_t mapping);

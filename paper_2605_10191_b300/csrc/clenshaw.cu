@@ -306,14 +306,23 @@ __device__ __forceinline__ void row_epilogue(int64_t off, const T (&acc)[E], boo
 // all execution forms produce the same bits: the SpMM accumulates in column order, four
 // entries per round, and the epilogue is fma(alpha, acc, fma(a, v, -beta q)) (or
 // fma(alpha, acc, a v) without B2).  L2ONLY selects ld.global.cg for B1 and B2.
-// VS selects where a stored element's value comes from: 0 = the CSR value array; 1 = constant
-// off-diagonal (the XXZ chain's J/(2 dE)): g for every column but the row's own, whose value is
-// diag[row] (the structured mapping; the values are those the CSR stores, so the bits agree).
+// VS selects the value source: 0 = the CSR value array; 1 = constant off-diagonal (the XXZ
+// chain's J/(2 dE)): g for every column but the row's own, whose value is diag[row]; 2 = the
+// quantum sun (row = state): diag[row] on the diagonal, the dot block's element when only dot bits
+// differ, else the coupling of ray j, j the one outer bit that differs.  The structured values are
+// those the CSR stores, so the bits agree with the CSR step.
+template <typename T> struct ValSrc {
+  const T* diag = nullptr;   // per-row diagonal of H~
+  T g = T(0);                // VS 1: the one off-diagonal value
+  const T* tab = nullptr;    // VS 2: the dot block of H~, 2^N x 2^N row-major
+  const T* coef = nullptr;   // VS 2: the ray couplings of H~, [L]
+  int L = 0, N = 0;          // VS 2: outer spins (bits 0..L-1) and dot spins (the bits above)
+};
 template <typename T, int S, bool L2ONLY, int SP, int B2M, int VS>
 __device__ __forceinline__ void clenshaw_row_vs(int64_t row, int lane, const int64_t* __restrict__ rp,
                                                 const int32_t* __restrict__ col, const T* __restrict__ val,
                                                 const T* __restrict__ V, const T* B1, const T* B2, T* out, T a,
-                                                T alpha, T beta, const T* __restrict__ diag, T g) {
+                                                T alpha, T beta, const ValSrc<T>& vsrc) {
   using Sh = Shape<T, S>;
   constexpr int E = Sh::E;
   const int64_t off = row * S + lane * E;
@@ -329,11 +338,20 @@ __device__ __forceinline__ void clenshaw_row_vs(int64_t row, int lane, const int
   if (spmm) {
     int64_t j = rp[row];
     const int64_t end = rp[row + 1];
-    T dr = g;
-    if constexpr (VS == 1) dr = ld_val(diag + row);
+    T dr = vsrc.g;
+    if constexpr (VS >= 1) dr = ld_val(vsrc.diag + row);
     auto hv = [&](int64_t jj, int c) -> T {
-      if constexpr (VS == 1) return (int64_t)c == row ? dr : g;
-      else return ld_val(val + jj);
+      if constexpr (VS == 1) {
+        return (int64_t)c == row ? dr : vsrc.g;
+      } else if constexpr (VS == 2) {
+        const uint32_t r = (uint32_t)row, x = r ^ (uint32_t)c;
+        const uint32_t om = (1u << vsrc.L) - 1u;
+        if (x == 0) return dr;
+        if ((x & om) == 0) return ld_val(vsrc.tab + (((r >> vsrc.L) << vsrc.N) + ((uint32_t)c >> vsrc.L)));
+        return ld_val(vsrc.coef + (__ffs(x & om) - 1));
+      } else {
+        return ld_val(val + jj);
+      }
     };
     for (; j + 4 <= end; j += 4) {
       int c0 = __ldg(col + j), c1 = __ldg(col + j + 1), c2 = __ldg(col + j + 2), c3 = __ldg(col + j + 3);
@@ -366,7 +384,7 @@ __device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_
                                              const int32_t* __restrict__ col, const T* __restrict__ val,
                                              const T* __restrict__ V, const T* B1, const T* B2, T* out, T a,
                                              T alpha, T beta) {
-  clenshaw_row_vs<T, S, L2ONLY, SP, B2M, 0>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta, nullptr, T(0));
+  clenshaw_row_vs<T, S, L2ONLY, SP, B2M, 0>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta, ValSrc<T>());
 }
 
 // One Clenshaw step over a D x s block.  rows_per_cta = 0: thread group g owns row g (one
@@ -501,16 +519,16 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) qrem_step_kernel(in
   }
 }
 
-// Structured mapping of the XXZ chain: the CSR's columns with the constant off-diagonal value g and
-// the per-row diagonal, no value array (clenshaw_row_vs with VS = 1); same bits as the CSR step.
-template <typename T, int S, int SP, int B2M>
-__global__ void __launch_bounds__(256, step_min_blocks<T>()) cconst_step_kernel(int64_t D, const int64_t* __restrict__ rp,
-                                                                                const int32_t* __restrict__ col,
-                                                                                const T* __restrict__ diag, T g,
-                                                                                const T* __restrict__ V,
-                                                                                const T* __restrict__ B1, const T* B2,
-                                                                                T* out, T a, T alpha, T beta,
-                                                                                int64_t rows_per_cta) {
+// Structured mappings that keep the CSR's columns but not its value array (clenshaw_row_vs): VS = 1,
+// the XXZ chain (constant off-diagonal, per-row diagonal); VS = 2, the quantum sun (diagonal, dot
+// block, ray couplings).  Same bits as the CSR step.
+template <typename T, int S, int SP, int B2M, int VS>
+__global__ void __launch_bounds__(256, step_min_blocks<T>()) cstruct_step_kernel(int64_t D, const int64_t* __restrict__ rp,
+                                                                                 const int32_t* __restrict__ col,
+                                                                                 ValSrc<T> vsrc, const T* __restrict__ V,
+                                                                                 const T* __restrict__ B1, const T* B2,
+                                                                                 T* out, T a, T alpha, T beta,
+                                                                                 int64_t rows_per_cta) {
   using Sh = Shape<T, S>;
   constexpr int G = Sh::G;
   const int lane = (int)(threadIdx.x % G);
@@ -518,15 +536,15 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) cconst_step_kernel(
     const int64_t r0 = blockIdx.x * rows_per_cta;
     const int64_t r1 = r0 + rows_per_cta < D ? r0 + rows_per_cta : D;
     for (int64_t row = r0 + threadIdx.x / G; row < r1; row += 256 / G)
-      clenshaw_row_vs<T, S, false, SP, B2M, 1>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, diag, g);
+      clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc);
   } else if (rows_per_cta < 0) {
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; row < D; row += groups)
-      clenshaw_row_vs<T, S, false, SP, B2M, 1>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, diag, g);
+      clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc);
   } else {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
     if (row < D)
-      clenshaw_row_vs<T, S, false, SP, B2M, 1>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, diag, g);
+      clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc);
   }
 }
 
@@ -577,10 +595,10 @@ static StepShape qrem_shape(int64_t rows, int cta_cap = 0) {
   static const int occ = kernel_occupancy(qrem_step_kernel<T, S, SP, B2M>);
   return shape_for<T, S>(rows, cta_cap, nsm, occ);
 }
-template <typename T, int S, int SP, int B2M>
-static StepShape cconst_shape(int64_t rows, int cta_cap = 0) {
+template <typename T, int S, int SP, int B2M, int VS>
+static StepShape cstruct_shape(int64_t rows, int cta_cap = 0) {
   static const int nsm = device_sms();
-  static const int occ = kernel_occupancy(cconst_step_kernel<T, S, SP, B2M>);
+  static const int occ = kernel_occupancy(cstruct_step_kernel<T, S, SP, B2M, VS>);
   return shape_for<T, S>(rows, cta_cap, nsm, occ);
 }
 
@@ -644,57 +662,54 @@ pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* co
 // Structured-mapping step launches (QREM bit flips, or XXZ constant off-diagonal): same shapes,
 // validation and operands as the CSR step.  The structure argument is L for QREM and the CSR
 // (row pointers, columns) for XXZ.
-struct StructArgs {
-  int L;
-  const int64_t* rp;
-  const int32_t* col;
-};
-template <bool QREM, typename T, int S, int SP, int B2M>
-static void launch_struct_form(int64_t D, StructArgs sa, const T* diag, T g, const T* V, const T* B1, const T* B2,
-                               T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
-  if constexpr (QREM) {
+enum { MAP_QREM = 0, MAP_XXZ = 1, MAP_QSUN = 2 };
+template <int KIND, typename T, int S, int SP, int B2M>
+static void launch_struct_form(const Ham* H, const ValSrc<T>& vs, const T* V, const T* B1, const T* B2, T* out, T a,
+                               T alpha, T beta, cudaStream_t st, int cap) {
+  const int64_t D = H->D;
+  if constexpr (KIND == MAP_QREM) {
     const StepShape sh = qrem_shape<T, S, SP, B2M>(D, cap);
-    qrem_step_kernel<T, S, SP, B2M><<<sh.grid, 256, 0, st>>>(D, sa.L, diag, g, V, B1, B2, out, a, alpha, beta,
+    qrem_step_kernel<T, S, SP, B2M><<<sh.grid, 256, 0, st>>>(D, H->m.L, vs.diag, vs.g, V, B1, B2, out, a, alpha, beta,
                                                             sh.rows_per_cta);
   } else {
-    const StepShape sh = cconst_shape<T, S, SP, B2M>(D, cap);
-    cconst_step_kernel<T, S, SP, B2M><<<sh.grid, 256, 0, st>>>(D, sa.rp, sa.col, diag, g, V, B1, B2, out, a, alpha,
-                                                              beta, sh.rows_per_cta);
+    constexpr int VS = KIND == MAP_XXZ ? 1 : 2;
+    const StepShape sh = cstruct_shape<T, S, SP, B2M, VS>(D, cap);
+    cstruct_step_kernel<T, S, SP, B2M, VS><<<sh.grid, 256, 0, st>>>(D, H->row_ptr, H->col, vs, V, B1, B2, out, a,
+                                                                    alpha, beta, sh.rows_per_cta);
   }
 }
-template <bool QREM, typename T, int S>
-static pf_status launch_struct_s(int64_t D, StructArgs sa, const T* diag, T g, const T* V, const T* B1, const T* B2,
-                                 T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
+template <int KIND, typename T, int S>
+static pf_status launch_struct_s(const Ham* H, const ValSrc<T>& vs, const T* V, const T* B1, const T* B2, T* out,
+                                 T a, T alpha, T beta, cudaStream_t st, int cap) {
   const bool spmm = alpha != T(0);
   const bool hb2 = beta != T(0);
-  if (spmm && hb2) launch_struct_form<QREM, T, S, 1, 1>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-  else if (spmm) launch_struct_form<QREM, T, S, 1, 0>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-  else if (hb2) launch_struct_form<QREM, T, S, 0, 1>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-  else launch_struct_form<QREM, T, S, 0, 0>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-  PF_LAUNCH_CHECK(QREM ? "qrem_step_kernel" : "cconst_step_kernel");
+  if (spmm && hb2) launch_struct_form<KIND, T, S, 1, 1>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+  else if (spmm) launch_struct_form<KIND, T, S, 1, 0>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+  else if (hb2) launch_struct_form<KIND, T, S, 0, 1>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+  else launch_struct_form<KIND, T, S, 0, 0>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+  PF_LAUNCH_CHECK(KIND == MAP_QREM ? "qrem_step_kernel" : "cstruct_step_kernel");
   return PF_OK;
 }
-template <bool QREM, typename T>
-static pf_status launch_struct(int s, int64_t D, StructArgs sa, const T* diag, T g, const T* V, const T* B1,
-                               const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
+template <int KIND, typename T>
+static pf_status launch_struct(int s, const Ham* H, const ValSrc<T>& vs, const T* V, const T* B1, const T* B2, T* out,
+                               T a, T alpha, T beta, cudaStream_t st, int cap) {
   switch (s) {
-    case 1: return launch_struct_s<QREM, T, 1>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 2: return launch_struct_s<QREM, T, 2>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 4: return launch_struct_s<QREM, T, 4>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 8: return launch_struct_s<QREM, T, 8>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 16: return launch_struct_s<QREM, T, 16>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 32: return launch_struct_s<QREM, T, 32>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 64: return launch_struct_s<QREM, T, 64>(D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 1: return launch_struct_s<KIND, T, 1>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 2: return launch_struct_s<KIND, T, 2>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 4: return launch_struct_s<KIND, T, 4>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 8: return launch_struct_s<KIND, T, 8>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 16: return launch_struct_s<KIND, T, 16>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 32: return launch_struct_s<KIND, T, 32>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 64: return launch_struct_s<KIND, T, 64>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
   }
   return PF_EINVAL;
 }
 template <typename T>
-static pf_status launch_structured(const Ham* H, int s, const T* diag, T g, const T* V, const T* B1, const T* B2,
+static pf_status launch_structured(const Ham* H, int s, const ValSrc<T>& vs, const T* V, const T* B1, const T* B2,
                                    T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
-  const StructArgs sa{H->m.L, H->row_ptr, H->col};
-  if (H->m.kind == PF_MODEL_QREM)
-    return launch_struct<true, T>(s, H->D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
-  return launch_struct<false, T>(s, H->D, sa, diag, g, V, B1, B2, out, a, alpha, beta, st, cap);
+  if (H->m.kind == PF_MODEL_QREM) return launch_struct<MAP_QREM, T>(s, H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+  if (H->m.kind == PF_MODEL_QSUN) return launch_struct<MAP_QSUN, T>(s, H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+  return launch_struct<MAP_XXZ, T>(s, H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
 }
 
 // One step of H~ through the handle's mapping: the CSR arrays, or the structured rows (QREM bit
@@ -705,7 +720,8 @@ pf_status ham_step(const Ham* H, int prec, int s, const void* V, const void* B1,
   // FP64 (bound by its pipe, 145.4 against 145.6 us) and pair-float (73.5 against 73.0 us) keep
   // the CSR form.  The bits are the same either way.
   const bool csr_form = H->mapping != PF_MAP_STRUCTURED || !H->diag_t ||
-                        (H->m.kind == PF_MODEL_XXZ && prec != PF_F32);
+                        ((H->m.kind == PF_MODEL_XXZ || H->m.kind == PF_MODEL_QSUN) && prec != PF_F32) ||
+                        (H->m.kind == PF_MODEL_QSUN && !H->qtab_t);
   if (csr_form)
     return clenshaw_step_raw(H->D, H->row_ptr, H->col, ham_vals(H, prec), prec, s, V, B1, B2, out, a, alpha, beta,
                              st, cta_cap);
@@ -713,16 +729,30 @@ pf_status ham_step(const Ham* H, int prec, int s, const void* V, const void* B1,
   if (alpha != 0.0 && !B1) return PF_EINVAL;
   if (beta != 0.0 && !B2) return PF_EINVAL;
   if (beta != 0.0 && beta != 1.0) return PF_EINVAL;
-  if (prec == PF_F64)
-    return launch_structured<double>(H, s, H->diag_t, H->off_t, (const double*)V, (const double*)B1,
-                                     (const double*)B2, (double*)out, a, alpha, beta, st, cta_cap);
-  if (prec == PF_F32)
-    return launch_structured<float>(H, s, H->diag32, (float)H->off_t, (const float*)V, (const float*)B1,
-                                    (const float*)B2, (float*)out, (float)a, (float)alpha, (float)beta, st, cta_cap);
-  if (prec == PF_DF64)
-    return launch_structured<df2>(H, s, reinterpret_cast<const df2*>(H->diag_df), df2(H->off_t), (const df2*)V,
-                                  (const df2*)B1, (const df2*)B2, (df2*)out, df2(a), df2(alpha), df2(beta), st,
-                                  cta_cap);
+  const int L = H->m.L, N = H->m.N;
+  if (prec == PF_F64) {
+    ValSrc<double> vs;
+    vs.diag = H->diag_t; vs.g = H->off_t; vs.tab = H->qtab_t; vs.coef = H->qtab_t ? H->qtab_t + H->qtab_n : nullptr;
+    vs.L = L; vs.N = N;
+    return launch_structured<double>(H, s, vs, (const double*)V, (const double*)B1, (const double*)B2, (double*)out,
+                                     a, alpha, beta, st, cta_cap);
+  }
+  if (prec == PF_F32) {
+    ValSrc<float> vs;
+    vs.diag = H->diag32; vs.g = (float)H->off_t; vs.tab = H->qtab32; vs.coef = H->qtab32 ? H->qtab32 + H->qtab_n : nullptr;
+    vs.L = L; vs.N = N;
+    return launch_structured<float>(H, s, vs, (const float*)V, (const float*)B1, (const float*)B2, (float*)out,
+                                    (float)a, (float)alpha, (float)beta, st, cta_cap);
+  }
+  if (prec == PF_DF64) {
+    ValSrc<df2> vs;
+    const df2* tab = reinterpret_cast<const df2*>(H->qtab_df);
+    vs.diag = reinterpret_cast<const df2*>(H->diag_df); vs.g = df2(H->off_t); vs.tab = tab;
+    vs.coef = tab ? tab + H->qtab_n : nullptr;
+    vs.L = L; vs.N = N;
+    return launch_structured<df2>(H, s, vs, (const df2*)V, (const df2*)B1, (const df2*)B2, (df2*)out, df2(a),
+                                  df2(alpha), df2(beta), st, cta_cap);
+  }
   return PF_EINVAL;
 }
 
@@ -1129,10 +1159,14 @@ static void prepare_shapes_s() {
   qrem_shape<T, S, 1, 0>(1);
   qrem_shape<T, S, 0, 1>(1);
   qrem_shape<T, S, 1, 1>(1);
-  cconst_shape<T, S, 0, 0>(1);
-  cconst_shape<T, S, 1, 0>(1);
-  cconst_shape<T, S, 0, 1>(1);
-  cconst_shape<T, S, 1, 1>(1);
+  cstruct_shape<T, S, 0, 0, 1>(1);
+  cstruct_shape<T, S, 1, 0, 1>(1);
+  cstruct_shape<T, S, 0, 1, 1>(1);
+  cstruct_shape<T, S, 1, 1, 1>(1);
+  cstruct_shape<T, S, 0, 0, 2>(1);
+  cstruct_shape<T, S, 1, 0, 2>(1);
+  cstruct_shape<T, S, 0, 1, 2>(1);
+  cstruct_shape<T, S, 1, 1, 2>(1);
 }
 template <typename T>
 static void prepare_shapes(int s) {

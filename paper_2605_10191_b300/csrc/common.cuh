@@ -104,6 +104,14 @@ struct Ham {
   float* diag32 = nullptr;
   float2* diag_df = nullptr;
   double off_t = 0.0;
+  // quantum sun: the dot block (2^N x 2^N) and the ray couplings (L) of H, kept on the host at
+  // build, and of H~ on the device after the rescale (one array per precision: qtab_n block
+  // entries, then the couplings)
+  std::vector<double> qs_hdot, qs_coef;
+  double* qtab_t = nullptr;
+  float* qtab32 = nullptr;
+  float2* qtab_df = nullptr;
+  int qtab_n = 0;
   int has_rescale = 0, has_bounds = 0;
   double Ec = 0, dE = 1, emin = 0, emax = 0, rmin = 0, rmax = 0, hnorm = 0;
   cudaStream_t st = 0;

@@ -147,7 +147,7 @@ def test_qrem_server_request(pf):
 
 
 @pytest.mark.parametrize("mk", [lambda: pi.hubbard_params(6, 3, 3, U=1.0, W=1.0, seed=1),
-                                lambda: pi.qsun_params(N=2, L=6, seed=2),
+                                lambda: pi.qsun_u1_params(N=2, L=6, M=4, seed=2),
                                 lambda: pi.j1j2_params(8, J2=0.5, W=1.0, seed=3)])
 def test_structured_mapping_rejected_for_other_models(pf, mk):
     H = pf.Hamiltonian.from_params(mk())
@@ -156,12 +156,15 @@ def test_structured_mapping_rejected_for_other_models(pf, mk):
     H.set_mapping("csr")
 
 
+@pytest.mark.parametrize("model", ["xxz", "qsun"])
 @pytest.mark.parametrize("L,s,prec", [(12, 8, "f64"), (14, 32, "f32"), (14, 16, "df64"), (16, 32, "f32"),
-                                      (9, 1, "f64"), (10, 64, "f32")])
-def test_xxz_structured_step_and_filter_equal_csr(pf, L, s, prec):
-    """Nearest-neighbour XXZ: the CSR columns with the one off-diagonal value (J/2)/dE and the
-    per-row diagonal give the CSR step's bits, for single steps and whole filters."""
-    p = pi.xxz_params(L, W=2.0, seed=70 + L)
+                                      (9, 1, "f64"), (10, 64, "f32"), (11, 4, "f32")])
+def test_csr_column_structured_step_and_filter_equal_csr(pf, model, L, s, prec):
+    """Structured mappings that keep the CSR columns: nearest-neighbour XXZ (one off-diagonal value
+    (J/2)/dE, per-row diagonal) and the quantum sun (diagonal, dot block, ray couplings) give the
+    CSR step's bits, for single steps and whole filters."""
+    p = (pi.xxz_params(L, W=2.0, seed=70 + L) if model == "xxz"
+         else pi.qsun_params(N=3, L=L - 3, seed=90 + L))
     H = pf.Hamiltonian.from_params(p)
     H.spectral_bounds()
     V, B1, B2 = (_block((H.D, s), 800 + k, prec) for k in range(3))
