@@ -272,8 +272,10 @@ pf_status pf_filter_tune(const pf_ham* H, int32_t prec, int32_t s, int32_t K, in
  * every GPU that loads the library keeps until the process exits.
  *  - Limit: 2 * D * s * w <= 32 MiB, w = 8 (PF_F64, PF_DF64) or 4 (PF_F32), each block rounded up
  *    to 256 bytes; larger requests return PF_EINVAL without touching the GPU.
- *  - The first call on a device looks up the array's device address (a CUDA symbol
- *    query, no allocation) and caches it; make that first call before any stream capture.
+ *  - Every call looks up the array's device address on the current device (a CUDA
+ *    symbol query, no allocation), so a context destroyed and re-created in the same
+ *    process (cudaDeviceReset) is picked up by the next call.  The first call on a device
+ *    may load the library's device code; make it before any stream capture.
  *  - All calls share the array and it keeps the last call's contents (nothing in it needs
  *    to start at zero).  Calls that can overlap on the GPU (other streams, other threads)
  *    race on it; serialise them.

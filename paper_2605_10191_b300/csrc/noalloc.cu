@@ -7,7 +7,6 @@
 // pf_filter_apply_noalloc takes the two blocks from one fixed device array instead, so it
 // calls no allocation routine at all.
 #include "common.cuh"
-#include <mutex>
 
 namespace pf {
 
@@ -17,22 +16,16 @@ namespace pf {
 #define PF_NOALLOC_SCRATCH_BYTES (32ull << 20)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[PF_NOALLOC_SCRATCH_BYTES];
 
-// In host code g_noalloc_scratch names a host-side shadow, not device memory, so the
-// device address is looked up once per device (with that device current) and cached.
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_ptr[64] = {nullptr};
-
+// In host code g_noalloc_scratch names a host-side shadow, not device memory.  The device
+// address is looked up on every call, with the caller's device current: the query allocates
+// nothing, costs far less than the K steps it precedes, and after cudaDeviceReset (or anything
+// else that destroys and re-creates the primary context, which reloads the module and can move
+// the array) the next call gets the new address instead of a stale one.
 static pf_status noalloc_scratch_address(void** out) {
-  int dev = 0;
-  PF_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return PF_EINVAL;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    PF_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  PF_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  if (!p) return PF_ECUDA;
+  *out = p;
   return PF_OK;
 }
 
