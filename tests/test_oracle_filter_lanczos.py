@@ -274,3 +274,124 @@ def test_kpm_choose_K_satisfies_condition():
     delta = dos.window_halfwidth(nev_g, float(kpm.dos_kpm(lam_t, mu)[0]))
     edge = lambda k: float(np.max(ch.filter_value(np.array([lam_t - delta, lam_t + delta]), lam_t, k)))
     assert edge(K) <= dos.OMEGA < edge(K - 1)
+
+
+# ---------------------------------------------------------------- Eq. dos_gaussian, Eq. Nev, K
+@pytest.mark.parametrize("mu,G,D", [(0.0, 0.2, 924), (-0.13, 0.071, 184756)])
+def test_gaussian_dos_normalisation_and_shape(mu, G, D):
+    """Eq. dos_gaussian is a density of D states: its integral is D, its mean mu~, its variance
+    G~^2, its peak D/(sqrt(2 pi) G~), and it falls to half the peak at mu~ +- G~ sqrt(2 ln 2).
+    Quadrature (trapezoid on a fine grid over +-12 G~), not the formula, gives the moments."""
+    x = np.linspace(mu - 12 * G, mu + 12 * G, 200001)
+    rho = dos.gaussian_dos(x, D, mu, G)
+    n0 = np.trapezoid(rho, x)
+    m1 = np.trapezoid(x * rho, x) / n0
+    m2 = np.trapezoid((x - m1) ** 2 * rho, x) / n0
+    assert abs(n0 - D) <= 1e-9 * D
+    assert abs(m1 - mu) <= 1e-9 * G
+    assert abs(math.sqrt(m2) - G) <= 1e-8 * G
+    assert abs(float(dos.gaussian_dos(mu, D, mu, G)) - D / (math.sqrt(2 * math.pi) * G)) <= 1e-12 * D / G
+    half = float(dos.gaussian_dos(mu + G * math.sqrt(2 * math.log(2)), D, mu, G))
+    assert abs(half / float(dos.gaussian_dos(mu, D, mu, G)) - 0.5) < 1e-12
+
+
+def test_window_holds_about_nev_g_levels():
+    """Eq. Nev with the Gaussian density of the exact moments: the window [lam~ - delta, lam~ + delta]
+    of the K rule holds about nev_g eigenvalues of a many-body spectrum (disordered XXZ L=14,
+    D = 3432, whose density is close to Gaussian); a lost factor 2 or sqrt(2 pi) in the density
+    would put 0.5x, 2x or 2.5x as many there.  Counted on the dense spectrum."""
+    H = hm.xxz_hamiltonian(pi.xxz_params(14, W=2.0, seed=1401))
+    w = np.linalg.eigvalsh(H.dense())
+    Ec, dE = 0.5 * (w[0] + w[-1]), 0.5 * (w[-1] - w[0]) * 1.001
+    Ht = ch.rescale(H, Ec, dE)
+    mu, G = dos.exact_moments(Ht)
+    wt = (w - Ec) / dE
+    for lam_t in (mu, mu + 0.5 * G, mu - 0.8 * G):
+        for nev_g in (30, 150):
+            delta = dos.window_halfwidth(nev_g, float(dos.gaussian_dos(lam_t, H.D, mu, G)))
+            n = int(np.sum(np.abs(wt - lam_t) <= delta))
+            assert 0.75 * nev_g <= n <= 1.3 * nev_g, (lam_t, nev_g, n)
+
+
+def test_choose_K_is_K_approx_of_that_window():
+    """choose_K = ceil(K_approx(lam~, delta)) with delta from Eq. Nev; the filter of that degree
+    takes the value Omega at lam~ +- delta within the K_approx accuracy (Eq. condition_for_K)."""
+    mu, G, D = 0.02, 0.15, 184756
+    for lam_t, nev_g in ((0.0, 150), (0.3, 75), (-0.4, 300)):
+        rho = float(dos.gaussian_dos(lam_t, D, mu, G))
+        delta = nev_g / (2.0 * rho)
+        K = dos.choose_K(lam_t, nev_g, D, mu, G)
+        assert K == math.ceil(2.655 * math.sqrt(1 - lam_t ** 2) / delta)
+        edge = ch.filter_value(np.array([lam_t - delta, lam_t + delta]), lam_t, K)
+        # the filter is symmetric in theta = arccos x, not in x: at low degree (K = 159 here) the
+        # two edges differ by ~0.01 to first order, their mean stays near Omega; a wrong
+        # constant in Eq. K_approx (or a lost factor in delta) moves both by 0.1 or more
+        assert abs(edge.mean() - dos.OMEGA) < 0.01 and np.all(np.abs(edge - dos.OMEGA) < 0.015)
+
+
+# ---------------------------------------------------------------- QR breakdown branch
+def _check_qr(W, Vprev, Q, R, deficient):
+    D, s = W.shape
+    assert np.abs(Q.T @ Q - np.eye(s)).max() < 1e-13                 # orthonormal, replacements too
+    if Vprev is not None:
+        assert np.abs(Vprev.T @ Q).max() < 1e-13                        # and orthogonal to the basis
+    # W - Vprev (Vprev^T W) = Q R exactly up to rounding: the replaced columns' rows of R carry
+    # no diagonal, the other entries reproduce W
+    Wp = W if Vprev is None else W - Vprev @ (Vprev.T @ W)
+    assert np.abs(Q @ R - Wp).max() < 1e-12 * max(1.0, np.abs(W).max())
+    assert np.all(np.tril(R, -1) == 0.0) and np.all(np.diag(R) >= 0.0)
+    for j in range(s):
+        if j in deficient:
+            assert R[j, j] == 0.0
+        else:
+            assert R[j, j] > 1e-6
+
+
+def test_gs_qr_breakdown_branch():
+    """gs_qr with rank-deficient blocks: a duplicated column, a zero column, and a column inside
+    the span of the previous basis.  Each deficient column gets a fresh unit vector orthogonal to
+    everything, with R[j, j] = 0; Q stays orthonormal and Q R reproduces the projected block."""
+    D, s = 200, 6
+    rng_cols = pi.uniform_pm_half(41, np.arange(D * s)).reshape(D, s)
+    Vprev, _ = np.linalg.qr(pi.uniform_pm_half(42, np.arange(D * 3)).reshape(D, 3))
+    W = rng_cols.copy()
+    W[:, 2] = W[:, 0]                      # duplicate of column 0
+    W[:, 4] = 0.0                          # zero column
+    W[:, 5] = Vprev @ np.array([0.3, -1.2, 0.7])   # inside span(Vprev): zero after projection
+    Q, R = lz.gs_qr(W, Vprev, seed=9, tag=1)
+    _check_qr(W, Vprev, Q, R, deficient={2, 4, 5})
+    # without a previous basis: two copies and a scaled copy
+    W2 = rng_cols[:, :4].copy()
+    W2[:, 1] = W2[:, 0]
+    W2[:, 3] = -2.5 * W2[:, 0]
+    Q2, R2 = lz.gs_qr(W2, None, seed=9, tag=0)
+    _check_qr(W2, None, Q2, R2, deficient={1, 3})
+    # the replacements are not a fixed vector: different tags (block steps) draw different ones
+    Q3, _ = lz.gs_qr(W2, None, seed=9, tag=5)
+    assert abs(float(Q3[:, 1] @ Q2[:, 1])) < 0.5
+
+
+def test_polfed_through_breakdown_matches_dense():
+    """A start block inside an invariant subspace (two exact eigenvectors far from the target):
+    the first filtered block lies in the span of the start block, so every column breaks down
+    and is replaced by fresh random vectors; the iteration then proceeds and still returns the
+    nev eigenvalues nearest lambda."""
+    H, w, U = _xxz12()
+    b = lz.lanczos_extrema(H)
+    Ec, dE = lz.padded_interval(b["emin"], b["emax"], b["rmin"], b["rmax"])
+    lam = b["emin"] + 0.5 * (b["emax"] - b["emin"])
+    Ht = ch.rescale(H, Ec, dE)
+    mu, G = dos.exact_moments(Ht)
+    nev = 10
+    K = dos.choose_K((lam - Ec) / dE, dos.guard_count(nev), H.D, mu, G)
+    V1 = U[:, [0, H.D - 1]].copy()        # the extreme eigenvectors: P V1 stays in their span
+    r = lz.polfed(H, lam, nev, K, 2, Ec, dE, V1=V1, return_state=True)
+    Vm = r["V"]
+    assert np.abs(Vm.T @ Vm - np.eye(Vm.shape[1])).max() < 1e-12
+    # the second block came from the breakdown: both of its B entries on the diagonal are zero
+    B1 = r["HL"][2:4, 0:2]
+    assert np.all(np.abs(np.diag(B1)) <= 1e-12)
+    sel = dense.nearest(w, lam, nev)
+    hn = np.abs(w).max()
+    assert np.max(np.abs(r["E"] - w[sel])) <= 1e-10 * hn
+    assert np.max(r["res"]) <= 1e-9 * hn
