@@ -39,6 +39,31 @@ WORKLOAD = "xxz_L20_D184756_nev100_s32_eps0.5"
 METRIC = "eigenpairs_per_s_at_residual_1e-9"
 
 
+# kernel-only workloads: (params factory, block width, mapping of the FP32 step, label)
+KERNEL_MODELS = {
+    "xxz20": ("xxz", 32, "XXZ L=20 periodic (D=184756)"),
+    "qsun": ("qsun", 16, "quantum sun N=3 L=15 (D=262144)"),
+    "hubbard": ("hubbard", 64, "Hubbard L=12 open, 6 up 6 down (D=853776)"),
+    "qrem18": ("qrem18", 32, "QREM L=18 (D=262144)"),
+    "qrem20": ("qrem20", 32, "QREM L=20 (D=1048576)"),
+}
+
+
+def kernel_model_params(name):
+    import pf_inputs as pi
+    if name == "xxz20":
+        return pi.xxz_params(L_SITES, W=W_LIST[0], seed=SEED0)
+    if name == "qsun":
+        c = pi.CONFIGS[3]
+        return pi.qsun_params(N=c["N"], L=c["L"], g0=c["g0"], alpha=c["alpha"], gamma=c["gamma"],
+                              seed=pi.config_seed(3, 0))
+    if name == "hubbard":
+        c = pi.CONFIGS[4]
+        return pi.hubbard_params(c["L"], c["N_up"], c["N_dn"], t=c["t"], U=c["U"], W=c["W"], seed=pi.config_seed(4, 0))
+    L = 18 if name == "qrem18" else 20
+    return pi.qrem_params(L, Gamma=1.0, seed=pi.config_seed(6, 0))
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -58,6 +83,8 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only time the fused Clenshaw step at the workload shape (profiling)")
     ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64", "df64"])
+    ap.add_argument("--kernel-model", default="xxz20", choices=list(KERNEL_MODELS),
+                    help="kernel-only: the workload whose step shape is timed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pipeline", action="store_true",
                     help="solve mode: the timed steps as one overlapped batch instead of one solve after another")
@@ -80,6 +107,13 @@ def parse():
     ap.add_argument("--serve-nev", default="20,50,200")
     ap.add_argument("--serve-block", type=int, default=16)
     ap.add_argument("--cpu-sample-steps", type=int, default=40)
+    ap.add_argument("--cpu-cores", type=int, default=0,
+                    help="oracle baseline: worker processes timed together (0 = every host core, at most 64)")
+    ap.add_argument("--no-fp64-plain", action="store_true",
+                    help="solve mode: skip the plain FP64 arm (one solve per realisation, FP64 filter throughout)")
+    ap.add_argument("--serving-sample", type=int, default=8,
+                    help="solve mode: requests of the serving-mix stream in the serving sub-record (0 = none)")
+    ap.add_argument("--serving-rate", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -111,6 +145,23 @@ def measured_peaks():
         d = json.load(open(p))
         return d.get("hbm_gbs", 6400.0), "measured"
     return 6400.0, "fallback"
+
+
+def percentiles(ms):
+    import numpy as np
+    return {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)), "unit": "ms"}
+
+
+def serving_mix_sample(n, rate, max_L=20, seed=5000):
+    """The first n requests of the serving-mix stream (L in 14..22, W ~ U[0.5, 8], eps ~ U[0.2, 0.8],
+    nev in {20, 50, 200}, Poisson arrivals at `rate`) with L <= max_L, at their stream arrival times.
+    An L = 22 request (D = 705,432) takes minutes even on its own, so it is left out of this sample."""
+    import pf_inputs as pi
+    out, m = [], 4 * n + 16
+    while len(out) < n:
+        out = [rq for rq in pi.serving_stream(m, rate, seed=seed) if rq["params"].L <= max_L][:n]
+        m *= 2
+    return out
 
 
 def step_bytes(D, nnz, s, w):
@@ -222,9 +273,10 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_sample(nsteps):
+def oracle_sample(nsteps, barrier=None):
     """Seconds per FP64 Clenshaw step of the oracle at the workload shape, the oracle's K,
-    and the number of filter steps of one solve (expected Krylov blocks x (K+1))."""
+    and the number of filter steps of one solve (expected Krylov blocks x (K+1)).  With a
+    barrier, the timed steps start when every worker of the group is ready."""
     import pf_inputs as pi
     from oracle import hamiltonian as oh, chebyshev as oc, dos as od, lanczos as ol
     p = pi.xxz_params(L_SITES, W=W_LIST[0], seed=SEED0)
@@ -247,6 +299,8 @@ def oracle_sample(nsteps):
         import contextlib
         one_core = contextlib.nullcontext()
     with one_core:
+        if barrier is not None:
+            barrier.wait()
         t0 = time.perf_counter()
         oc.clenshaw_apply(Ht, V, a)        # nsteps SpMM steps + the closing line
         dt = (time.perf_counter() - t0) / (nsteps + 1)
@@ -254,30 +308,82 @@ def oracle_sample(nsteps):
     return dt, K, blocks * (K + 1)
 
 
+def _oracle_proc(nsteps, barrier, q):
+    q.put(oracle_sample(nsteps, barrier))
+
+
+def host_cores(requested=0):
+    """Worker processes for the all-cores oracle baseline: every host core (at most 64, and at
+    most one per 1.5 GB of available memory), or the requested count."""
+    n = os.cpu_count() or 1
+    if requested > 0:
+        return min(requested, n), n
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        n_mem = max(1, int(avail // (1.5 * 2 ** 30)))
+    except (ValueError, OSError):
+        n_mem = n
+    return max(1, min(n, 64, n_mem)), n
+
+
+def oracle_rate(nsteps, cores):
+    """Eigenpairs/s of the oracle on `cores` host cores: one single-threaded worker process per
+    core, each timing nsteps Clenshaw steps of its own copy of the workload at the same time
+    (independent solves shard across cores without communication), summed over the workers.
+    Returns (rate, K, filter steps of one solve, seconds per step averaged over the workers)."""
+    if cores <= 1:
+        dt, K, n = oracle_sample(nsteps)
+        return NEV / (dt * n), K, n, dt
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")          # this process already holds a CUDA context
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        bar, q = ctx.Barrier(cores), ctx.Queue()
+        procs = [ctx.Process(target=_oracle_proc, args=(nsteps, bar, q)) for _ in range(cores)]
+        for pr in procs:
+            pr.start()
+        res = [q.get() for _ in procs]
+        for pr in procs:
+            pr.join()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    rate = sum(NEV / (dt * n) for dt, _, n in res)
+    return rate, res[0][1], res[0][2], statistics.mean(dt for dt, _, _ in res)
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return
     per_step = max(5, args.cpu_sample_steps // 2)
-    for _ in range(args.warmup):
-        oracle_sample(per_step)
-    secs, Ks, nsteps = [], [], []
+    cores, ncpu = host_cores(args.cpu_cores)
+    for _ in range(min(args.warmup, 1)):
+        oracle_sample(5)
+    rates, Ks, nsteps = [], [], []
     for _ in range(args.steps):
-        dt, K, n = oracle_sample(per_step)
-        secs.append(dt)
+        rate, K, n, _ = oracle_rate(per_step, cores)
+        rates.append(rate)
         Ks.append(K)
         nsteps.append(n)
-    t_solve = statistics.mean(secs) * statistics.mean(nsteps)
-    value = NEV / t_solve
-    sample = (f"{per_step} oracle Clenshaw steps per bench step (scipy CSR x {BLOCK}-column FP64 block, XXZ L=20, "
-              f"W={W_LIST[0]}), extrapolated to one solve of {int(statistics.mean(nsteps))} filter steps "
+    value = statistics.mean(rates)
+    t_solve = NEV / value
+    sample = (f"{per_step} oracle Clenshaw steps per bench step in each of {cores} single-threaded worker processes "
+              f"(host has {ncpu} cores; scipy CSR x {BLOCK}-column FP64 block, XXZ L=20, W={W_LIST[0]}), "
+              f"extrapolated to one solve of {int(statistics.mean(nsteps))} filter steps per worker "
               f"(expected Krylov blocks x (K+1)); orthogonalisation not counted")
     out = {"impl": "reference", "metric": METRIC, "value": value,
            "unit": "eigenpairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * t_solve, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "oracle": "plain FP64 numpy/scipy", "K": int(statistics.mean(Ks))},
-           "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": cores, "host_cores": ncpu,
+                            "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -288,10 +394,10 @@ def run_kernel_only(args):
     import pf_inputs as pi
     import paper_2605_10191_b300 as pf
     torch.cuda.set_device(0)
-    p = pi.xxz_params(L_SITES, W=W_LIST[0], seed=SEED0)
-    H = pf.Hamiltonian.from_params(p)
+    model = args.kernel_model
+    H = pf.Hamiltonian.from_params(kernel_model_params(model))
     H.spectral_bounds()
-    D, s = H.D, BLOCK
+    D, s = H.D, KERNEL_MODELS[model][1]
     dt = torch.float64 if args.kernel_precision == "f64" else torch.float32
     shape = (D, s, 2) if args.kernel_precision == "df64" else (D, s)
     g = torch.Generator(device="cuda").manual_seed(1)
@@ -313,10 +419,17 @@ def run_kernel_only(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     w = 4 if args.kernel_precision == "f32" else 8
-    # FP32 steps of this chain use the structured mapping (no value array); FP64 and pair-float the CSR
-    byt = struct_step_bytes(D, H.nnz, s, w) if args.kernel_precision == "f32" else step_bytes(D, H.nnz, s, w)
-    print(json.dumps({"kernel": ("cstruct_step_f32_s32" if args.kernel_precision == "f32"
-                                 else f"clenshaw_step_{args.kernel_precision}_s32"), "us_per_launch": 1e3 * ms,
+    # which step kernel runs: the XXZ chain's FP32 steps take the structured mapping (CSR columns
+    # and the diagonal, no value array), QREM's steps the generated bit-flip columns (diagonal
+    # only); everything else reads the CSR
+    if model.startswith("qrem"):
+        byt, kern = D * w + 4 * D * s * w, "qrem_step_kernel"
+    elif model == "xxz20" and args.kernel_precision == "f32":
+        byt, kern = struct_step_bytes(D, H.nnz, s, w), "cstruct_step_kernel"
+    else:
+        byt, kern = step_bytes(D, H.nnz, s, w), "clenshaw_step_kernel"
+    print(json.dumps({"kernel": f"{kern}<{args.kernel_precision},{s}>", "workload": KERNEL_MODELS[model][2],
+                      "D": D, "nnz": H.nnz, "block": s, "us_per_launch": 1e3 * ms,
                       "alg_bytes": byt, "GBps": byt / ms / 1e6, "launches": args.steps}))
 
 
@@ -340,7 +453,7 @@ def run_ours(args):
 
     pinned = torch.empty((NEV, math.comb(L_SITES, L_SITES // 2)), dtype=torch.float64, pin_memory=True)
 
-    def one_step(i, record, refine_precision=args.refine_precision):
+    def one_step(i, record, refine_precision=args.refine_precision, precision=args.precision):
         r = realisation(rank, world, i)
         p = pi.xxz_params(L_SITES, W=W_LIST[r], seed=SEED0 + r)
         st = torch.cuda.current_stream()
@@ -349,7 +462,7 @@ def run_ours(args):
         H = pf.Hamiltonian.from_params(p)
         H.spectral_bounds()
         K = H.choose_K(EPS, NEV)
-        res = H.solve(EPS, NEV, K, block=BLOCK, precision=args.precision, raise_on_notconv=False,
+        res = H.solve(EPS, NEV, K, block=BLOCK, precision=precision, raise_on_notconv=False,
                       refine_precision=refine_precision)
         ev[1].record(st)
         pinned.copy_(res.evecs.t(), non_blocking=True)     # D x nev (column-major) -> host
@@ -441,14 +554,14 @@ def run_ours(args):
     phase_keys = ("ms_filter_f32", "ms_filter_f64", "ms_orth", "ms_qr", "ms_check", "ms_extract", "ms_refine",
                   "ms_total")
     variant = None
-    if (world == 1 and not args.pipeline and args.precision == "f32" and args.refine_precision == "f64"
-            and not args.no_variant):
-        # the same solves with the refinement filter in pair-float on the FP32 units, timed the
-        # same way after the main region (reported beside `value`, not in it)
+    extras = world == 1 and not args.pipeline and args.precision == "f32"
+    if extras and args.refine_precision == "f64" and not args.no_variant:
+        # the same realisations with the refinement filter in pair-float on the FP32 units, one
+        # solve each, timed the same way after the main region (reported beside `value`, not in it)
         vrec = []
         with ClockSampler(local) as vclocks:
-            for i in range(args.steps):
-                one_step(args.warmup + i, vrec, "df64")
+            for i in range(len(W_LIST)):
+                one_step(i, vrec, "df64")
             torch.cuda.synchronize()
         v_dev = sum(x["dev_ms"] for x in vrec) / 1e3
         v_good = sum(x["good"] for x in vrec)
@@ -460,14 +573,44 @@ def run_ours(args):
                    "roofline_refine": refine_roofline(vrec, D, nnz, "df64", peak, peak_kind),
                    "phases_ms": {k: statistics.mean(x["rep"][k] for x in vrec) for k in phase_keys},
                    "residual_max_over_hnorm": max(x["rep"]["max_residual"] / x["rep"]["hnorm"] for x in vrec)}
+    fp64 = None
+    if extras and not args.no_fp64_plain:
+        # the plain FP64 GPU path (FP64 filter throughout, no refinement stage): one solve per
+        # realisation W = 1, 3, 5, timed the same way
+        frec = []
+        with ClockSampler(local) as fclocks:
+            for i in range(len(W_LIST)):
+                one_step(i, frec, "f64", "f64")
+            torch.cuda.synchronize()
+        f_dev = sum(x["dev_ms"] for x in frec) / 1e3
+        f_e2e = sum(x["e2e_ms"] for x in frec) / 1e3
+        f_good = sum(x["good"] for x in frec)
+        fp64 = {"value": f_good / f_dev, "unit": "eigenpairs/s", "e2e": f_good / f_e2e,
+                "ms_per_step": 1e3 * f_dev / len(frec), "dtype": "f64",
+                "precision": "FP64 filter, Lanczos, Rayleigh-Ritz throughout (no FP32 stage)",
+                "latency_ms": percentiles([x["e2e_ms"] for x in frec]), "K": [x["K"] for x in frec],
+                "realisation_W": [x["W"] for x in frec], "eigenpairs_at_tol": f_good, "solves": len(frec),
+                "clocks": fclocks.summary(),
+                "roofline_step": refine_roofline(frec, D, nnz, "f64", peak, peak_kind),
+                "phases_ms": {k: statistics.mean(x["rep"][k] for x in frec) for k in phase_keys},
+                "residual_max_over_hnorm": max(x["rep"]["max_residual"] / x["rep"]["hnorm"] for x in frec)}
+        if fp64["roofline_step"] is not None and D != L20_D:
+            fp64["roofline_step"]["traffic"] = None
+    serving = None
+    if extras and args.serving_sample > 0:
+        serving = serving_record(args.serving_sample, args.serving_rate, args.serve_block, args.refine_precision,
+                                 local)
     cpu = None
     if not args.no_cpu_baseline:
-        dt, K0, n = oracle_sample(args.cpu_sample_steps)
-        v = NEV / (dt * n)
-        cpu = {"value": v, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+        v1, K0, n, dt1 = oracle_rate(args.cpu_sample_steps, 1)
+        cores, ncpu = host_cores(args.cpu_cores)
+        vall, _, _, dtall = oracle_rate(args.cpu_sample_steps, cores) if cores > 1 else (v1, K0, n, dt1)
+        cpu = {"value": vall, "unit": "eigenpairs/s", "cores": cores, "host_cores": ncpu, "kind": "oracle",
                "sample": f"{args.cpu_sample_steps} oracle FP64 Clenshaw steps (scipy CSR x 32-column block, XXZ L=20) "
-                         f"extrapolated to one solve of {n} filter steps (expected Krylov blocks x (K+1), K={K0}); "
-                         f"orthogonalisation not counted"}
+                         f"in each of {cores} single-threaded worker processes timed together, extrapolated to "
+                         f"one solve of {n} filter steps per worker (expected Krylov blocks x (K+1), K={K0}); "
+                         f"orthogonalisation not counted",
+               "one_core": {"value": v1, "cores": 1, "s_per_step": dt1}, "s_per_step": dtall}
     out = {
         "metric": METRIC, "value": good / dev_s, "unit": "eigenpairs/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / len(rec),
@@ -485,6 +628,8 @@ def run_ours(args):
                    "eigenpairs_at_tol": good, "solves": len(rec) * world},
         "e2e": {"value": good / e2e_s, "unit": "eigenpairs/s", "h2d_bytes_per_step": rec[0]["h2d"],
                 "d2h_bytes_per_step": rec[0]["d2h"]},
+        "latency_ms": dict(percentiles([x["e2e_ms"] for x in rec]),
+                           of="each timed solve: basis, CSR, bounds, K, solve and the eigenvectors on the host"),
         "gpu_launches": int(launches),
         "roofline": roof, "roofline_refine": roof64, "cpu_baseline": cpu, "clocks": clk,
         "phases_ms": {k: statistics.mean(x["rep"][k] for x in rec) for k in phase_keys},
@@ -492,6 +637,8 @@ def run_ours(args):
         "residual_unrefined_max_over_hnorm": max(x["rep"]["max_residual_unrefined"] / x["rep"]["hnorm"]
                                                  for x in rec),
         "variant_refine_pairfloat": variant,
+        "fp64_plain": fp64,
+        "serving": serving,
     }
     print(json.dumps(out))
 
@@ -660,58 +807,57 @@ def run_model(args):
     print(json.dumps(out))
 
 
-def run_serving(args):
-    """Poisson request stream through the server vs plain FP64 solves one at a time."""
-    import numpy as np
-    import torch
+def serving_record(n, rate, block, refine_precision, gpu, Ls=None, nevs=None, max_L=20):
+    """The serving comparison on a bounded sample: the continuous-batching server (FP32 filter, FP64
+    Ritz/residual/refinement) against the plain FP64 path one request at a time in arrival order,
+    both driven live by the host clock on the same requests (latency = arrival to completion)."""
     import pf_inputs as pi
     import paper_2605_10191_b300 as pf
-    from paper_2605_10191_b300.serving import run_stream
-    torch.cuda.set_device(0)
-    Ls = tuple(int(x) for x in args.serve_L.split(","))
-    nevs = tuple(int(x) for x in args.serve_nev.split(","))
-    reqs = pi.serving_stream(args.serve_n, args.serve_rate, Ls=Ls, nevs=nevs)
-    s = args.serve_block
-    # warm-up: a short stream of the smallest sector
-    warm = pi.serving_stream(3, 100.0, Ls=(min(Ls),), nevs=(min(nevs),), seed=5900)
-    sv = pf.Server(block=s, precision="f32", refine_precision=args.refine_precision)
+    from paper_2605_10191_b300.serving import run_stream, run_one_at_a_time
+    if Ls is None:
+        reqs = serving_mix_sample(n, rate, max_L=max_L)
+        what = (f"the first {n} requests with L <= {max_L} of the serving-mix stream (seed 5000; L in 14..22, "
+                f"W ~ U[0.5, 8], eps ~ U[0.2, 0.8], nev in (20, 50, 200)) at {rate} req/s")
+    else:
+        reqs = pi.serving_stream(n, rate, Ls=Ls, nevs=nevs)
+        what = f"{n} requests, L in {Ls}, nev in {nevs}, {rate} req/s (seed 5000)"
+    warm = pi.serving_stream(3, 100.0, Ls=(14,), nevs=(20,), seed=5900)
+    sv = pf.Server(block=block, precision="f32", refine_precision=refine_precision)
     run_stream(sv, warm)
     lib = pf.lib()
     n0 = lib.pf_kernel_launches()
-    with ClockSampler(0) as clocks:
+    with ClockSampler(gpu) as clocks:
         r = run_stream(sv, reqs)
     launches = lib.pf_kernel_launches() - n0
     sv.close()
+    with ClockSampler(gpu) as clocks64:
+        f64 = run_one_at_a_time(reqs, block=block, precision="f64")
     summ = r.summary()
-    # plain FP64 path, one request at a time in arrival order; FIFO latencies from the measured
-    # service times and the same arrivals
-    svc, good64 = [], 0
-    for rq in reqs:
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        H, K, res = _solve_one(pf, rq["params"], rq["eps"], rq["nev"], s, "f64")
-        torch.cuda.synchronize()
-        svc.append(time.perf_counter() - t)
-        good64 += int(np.sum(res.resid <= RES_TOL * res.report["hnorm"]))
-        del H, res
-    fin, lat = 0.0, []
-    for rq, dt in zip(reqs, svc):
-        start = max(rq["t_arrival"], fin)
-        fin = start + dt
-        lat.append(1e3 * (fin - rq["t_arrival"]))
-    span64 = fin - reqs[0]["t_arrival"]
-    out = {"metric": "eigenpairs_per_s_at_residual_1e-9", "mode": "serving", "value": summ["eigenpairs_per_s"],
-           "unit": "eigenpairs/s", "higher_is_better": True, "p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"],
-           "serving": summ,
-           "fp64_one_at_a_time": {"eigenpairs_per_s": good64 / span64, "p50_ms": float(np.percentile(lat, 50)),
-                                  "p99_ms": float(np.percentile(lat, 99)), "service_s_total": sum(svc),
-                                  "latency": "FIFO queue simulated from measured service times, same arrivals"},
-           "n_gpus": 1, "dtype": dtype_name(args), "data": "synthetic", "gpu_launches": int(launches),
-           "clocks": clocks.summary(),
+    return {"value": summ["eigenpairs_per_s"], "unit": "eigenpairs/s", "p50_ms": summ["p50_ms"],
+            "p99_ms": summ["p99_ms"], "server": summ, "fp64_one_at_a_time": f64,
+            "gpu_launches": int(launches), "clocks": clocks.summary(), "clocks_fp64": clocks64.summary(),
+            "requests": [{"L": q["params"].L, "nev": q["nev"], "eps": round(q["eps"], 3), "W": round(q["params"].W, 3),
+                          "t_arrival_s": round(q["t_arrival"], 3)} for q in reqs],
+            "config": {"sample": what, "block": block, "refine": refine_precision,
+                       "timing": "host wall clock, arrival to completion, both arms live"}}
+
+
+def run_serving(args):
+    """Poisson request stream through the server vs plain FP64 solves one at a time."""
+    import torch
+    torch.cuda.set_device(0)
+    Ls = tuple(int(x) for x in args.serve_L.split(","))
+    nevs = tuple(int(x) for x in args.serve_nev.split(","))
+    rec = serving_record(args.serve_n, args.serve_rate, args.serve_block, args.refine_precision, 0, Ls=Ls, nevs=nevs)
+    out = {"metric": "eigenpairs_per_s_at_residual_1e-9", "mode": "serving", "value": rec["value"],
+           "unit": "eigenpairs/s", "higher_is_better": True, "p50_ms": rec["p50_ms"], "p99_ms": rec["p99_ms"],
+           "serving": rec["server"], "fp64_one_at_a_time": rec["fp64_one_at_a_time"],
+           "n_gpus": 1, "dtype": dtype_name(args), "data": "synthetic", "gpu_launches": rec["gpu_launches"],
+           "clocks": rec["clocks"], "requests": rec["requests"],
            "config": {"workload": f"serving_xxz_L{'-'.join(map(str, Ls))}_n{args.serve_n}_rate{args.serve_rate}",
                       "requests": args.serve_n, "rate_per_s": args.serve_rate, "L": Ls, "nev": nevs,
-                      "W": "U[0.5, 8]", "eps": "U[0.2, 0.8]", "block": s,
-                      "timing": "host wall clock, arrival to completion"}}
+                      "W": "U[0.5, 8]", "eps": "U[0.2, 0.8]", "block": args.serve_block,
+                      "timing": "host wall clock, arrival to completion, both arms live"}}
     print(json.dumps(out))
 
 

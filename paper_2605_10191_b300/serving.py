@@ -79,3 +79,43 @@ def run_stream(server: Server, requests, res_tol=1e-9):
     first = min(rq["t_arrival"] for rq in requests)
     return StreamResult(latencies_ms=lat, queue_ms=qms, statuses=st, eigenpairs=good, makespan_s=t_last - first,
                         steps=steps, peak_active=peak, results=[r for r, _ in out])
+
+
+def run_one_at_a_time(requests, block=16, precision="f64", refine_precision="f64", res_tol=1e-9):
+    """The same stream through a plain FIFO queue, one request at a time: each request starts when
+    it has arrived and the previous one has finished (basis, CSR, bounds, K and the solve), and its
+    latency is measured on the host clock from arrival to completion, as for the server."""
+    import torch
+    from .api import Hamiltonian
+    order = sorted(range(len(requests)), key=lambda k: requests[k]["t_arrival"])
+    lat = np.zeros(len(requests))
+    st = np.zeros(len(requests), dtype=np.int64)
+    good, service = 0, 0.0
+    t0 = time.perf_counter()
+    t_last = 0.0
+    for k in order:
+        rq = requests[k]
+        wait = rq["t_arrival"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        ts = time.perf_counter()
+        H = Hamiltonian.from_params(rq["params"])
+        H.spectral_bounds()
+        K = H.choose_K(rq["eps"], rq["nev"])
+        r = H.solve(rq["eps"], rq["nev"], K, block=block, precision=precision, return_vectors=False,
+                    raise_on_notconv=False, refine_precision=refine_precision)
+        torch.cuda.synchronize()
+        t_last = time.perf_counter() - t0
+        service += time.perf_counter() - ts
+        lat[k] = 1e3 * (t_last - rq["t_arrival"])
+        st[k] = r.status
+        hn = r.report["hnorm"]
+        good += int(np.sum(r.resid <= res_tol * hn)) if hn > 0 else 0
+        del H, r
+    first = min(rq["t_arrival"] for rq in requests)
+    span = t_last - first
+    return {"requests": int(len(requests)), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "eigenpairs": int(good),
+            "makespan_s": span, "eigenpairs_per_s": good / span if span > 0 else 0.0,
+            "failed": int(np.sum(st != 0)), "service_s_total": service,
+            "latency": "measured live: FIFO, one request at a time, host clock from arrival to completion"}

@@ -1,5 +1,5 @@
-"""CPU check of bench.py's reference arm: it runs the oracle on a bounded sample and prints one JSON
-line with the contract's keys (no GPU needed)."""
+"""CPU check of bench.py's reference arm: it runs the oracle on a bounded sample in parallel worker
+processes (one per core; two here) and prints one JSON line with the contract's keys (no GPU needed)."""
 import json
 import os
 import subprocess
@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def test_reference_arm_json_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--cpu-sample-steps", "4"], capture_output=True, text=True, timeout=600,
+                        "--warmup", "0", "--cpu-sample-steps", "4", "--cpu-cores", "2"], capture_output=True, text=True, timeout=600,
                        cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     line = [l for l in r.stdout.strip().splitlines() if l.startswith("{")][-1]
@@ -19,6 +19,7 @@ def test_reference_arm_json_line():
               "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 2
+    assert d["cpu_baseline"]["host_cores"] == os.cpu_count()
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"] == "xxz_L20_D184756_nev100_s32_eps0.5"
