@@ -78,8 +78,11 @@ def parse():
                          "quantum suns, Gaussian otherwise)")
     ap.add_argument("--mapping", default="structured", choices=["structured", "csr"],
                     help="model mode, QREM: how the steps read H~ (generated bit-flip columns or the CSR)")
+    ap.add_argument("--refine-form", default="default", choices=["default", "correction", "direct"],
+                    help="refinement passes: residual-correction form (FP64 residuals and updates, FP32 recurrence "
+                         "on the residuals; the default with FP64 refinement) or the direct recurrence on the vectors")
     ap.add_argument("--no-variant", action="store_true",
-                    help="solve mode: skip the extra timed solves with the pair-float refinement filter")
+                    help="solve mode: skip the extra timed solves with the direct FP64 and pair-float refinement")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only time the fused Clenshaw step at the workload shape (profiling)")
     ap.add_argument("--kernel-precision", default="f32", choices=["f32", "f64", "df64"])
@@ -182,7 +185,9 @@ def refine_roofline(rec, D, nnz, refine_precision, peak, peak_kind):
     (HBM roofline, 8 bytes per entry and value)."""
     f64_ms = sum(x["rep"]["ms_filter_f64"] for x in rec)
     f64_n = sum(x["rep"]["filter_steps_f64"] for x in rec)
-    if not f64_n:
+    if not f64_n or not f64_ms:
+        # no FP64 filter applications timed: the refinement ran in the residual-correction form,
+        # whose recurrence steps are FP32 steps (counted with the FP32 filter)
         return None
     per = f64_ms / f64_n
     if refine_precision == "df64":
@@ -197,6 +202,15 @@ def refine_roofline(rec, D, nnz, refine_precision, peak, peak_kind):
             "frac": flops / per / 1e9 / fp64_peak, "kernel": "clenshaw_step_kernel<double,32>",
             "us_per_launch": 1e3 * per, "traffic": ncu_traffic("clenshaw_f64_xxz_L20_s32"),
             "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz"}
+
+
+def refine_desc(args):
+    if args.refine_precision == "df64":
+        return "pair-float (FP32 hi+lo) refinement filter, direct form"
+    if args.refine_form == "direct":
+        return "FP64 refinement filter, direct form"
+    return ("FP64 refinement in residual-correction form (FP64 residuals, Ritz values, P(theta), updates; "
+            "FP32 recurrence on the residuals)")
 
 
 def dtype_name(args):
@@ -419,12 +433,12 @@ def run_kernel_only(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
     w = 4 if args.kernel_precision == "f32" else 8
-    # which step kernel runs: the XXZ chain's FP32 steps take the structured mapping (CSR columns
-    # and the diagonal, no value array), QREM's steps the generated bit-flip columns (diagonal
-    # only); everything else reads the CSR
+    # which step kernel runs: the XXZ chain's and the open Hubbard chain's FP32 steps take the
+    # structured mapping (CSR columns and the diagonal, no value array), QREM's steps the generated
+    # bit-flip columns (diagonal only); everything else reads the CSR
     if model.startswith("qrem"):
         byt, kern = D * w + 4 * D * s * w, "qrem_step_kernel"
-    elif model == "xxz20" and args.kernel_precision == "f32":
+    elif model in ("xxz20", "hubbard") and args.kernel_precision == "f32":
         byt, kern = struct_step_bytes(D, H.nnz, s, w), "cstruct_step_kernel"
     else:
         byt, kern = step_bytes(D, H.nnz, s, w), "clenshaw_step_kernel"
@@ -453,7 +467,8 @@ def run_ours(args):
 
     pinned = torch.empty((NEV, math.comb(L_SITES, L_SITES // 2)), dtype=torch.float64, pin_memory=True)
 
-    def one_step(i, record, refine_precision=args.refine_precision, precision=args.precision):
+    def one_step(i, record, refine_precision=args.refine_precision, precision=args.precision,
+                 refine_form=args.refine_form):
         r = realisation(rank, world, i)
         p = pi.xxz_params(L_SITES, W=W_LIST[r], seed=SEED0 + r)
         st = torch.cuda.current_stream()
@@ -463,7 +478,7 @@ def run_ours(args):
         H.spectral_bounds()
         K = H.choose_K(EPS, NEV)
         res = H.solve(EPS, NEV, K, block=BLOCK, precision=precision, raise_on_notconv=False,
-                      refine_precision=refine_precision)
+                      refine_precision=refine_precision, refine_form=refine_form)
         ev[1].record(st)
         pinned.copy_(res.evecs.t(), non_blocking=True)     # D x nev (column-major) -> host
         ev[2].record(st)
@@ -553,26 +568,33 @@ def run_ours(args):
         roof64["traffic"] = None          # the committed ncu summaries are of the L=20 workload
     phase_keys = ("ms_filter_f32", "ms_filter_f64", "ms_orth", "ms_qr", "ms_check", "ms_extract", "ms_refine",
                   "ms_total")
-    variant = None
     extras = world == 1 and not args.pipeline and args.precision == "f32"
-    if extras and args.refine_precision == "f64" and not args.no_variant:
-        # the same realisations with the refinement filter in pair-float on the FP32 units, one
-        # solve each, timed the same way after the main region (reported beside `value`, not in it)
+
+    def variant_run(refine_precision, refine_form, dtype, what):
+        # the same realisations, one solve each, timed the same way after the main region
+        # (reported beside `value`, not in it)
         vrec = []
         with ClockSampler(local) as vclocks:
             for i in range(len(W_LIST)):
-                one_step(i, vrec, "df64")
+                one_step(i, vrec, refine_precision, "f32", refine_form)
             torch.cuda.synchronize()
         v_dev = sum(x["dev_ms"] for x in vrec) / 1e3
         v_good = sum(x["good"] for x in vrec)
-        variant = {"value": v_good / v_dev, "unit": "eigenpairs/s", "ms_per_step": 1e3 * v_dev / len(vrec),
-                   "dtype": "f32+f32x2+f64",
-                   "refinement_filter": "pair-float (FP32 hi + lo, about 2^-47 relative error per step); "
-                                        "refinement Rayleigh-Ritz, Gram-Schmidt and residuals FP64",
-                   "eigenpairs_at_tol": v_good, "solves": len(vrec), "clocks": vclocks.summary(),
-                   "roofline_refine": refine_roofline(vrec, D, nnz, "df64", peak, peak_kind),
-                   "phases_ms": {k: statistics.mean(x["rep"][k] for x in vrec) for k in phase_keys},
-                   "residual_max_over_hnorm": max(x["rep"]["max_residual"] / x["rep"]["hnorm"] for x in vrec)}
+        return {"value": v_good / v_dev, "unit": "eigenpairs/s", "ms_per_step": 1e3 * v_dev / len(vrec),
+                "dtype": dtype, "refinement_filter": what, "eigenpairs_at_tol": v_good, "solves": len(vrec),
+                "clocks": vclocks.summary(),
+                "roofline_refine": refine_roofline(vrec, D, nnz, refine_precision, peak, peak_kind),
+                "phases_ms": {k: statistics.mean(x["rep"][k] for x in vrec) for k in phase_keys},
+                "residual_max_over_hnorm": max(x["rep"]["max_residual"] / x["rep"]["hnorm"] for x in vrec)}
+
+    variant, variant_direct = None, None
+    if extras and args.refine_precision == "f64" and not args.no_variant:
+        variant = variant_run("df64", "direct", "f32+f32x2+f64",
+                              "direct form, pair-float (FP32 hi + lo, about 2^-47 relative error per step); "
+                              "refinement Rayleigh-Ritz, Gram-Schmidt and residuals FP64")
+        if args.refine_form != "direct":
+            variant_direct = variant_run("f64", "direct", "f32+f64",
+                                         "direct form: the K-step recurrence on the Ritz vectors in FP64")
     fp64 = None
     if extras and not args.no_fp64_plain:
         # the plain FP64 GPU path (FP64 filter throughout, no refinement stage): one solve per
@@ -618,9 +640,8 @@ def run_ours(args):
         "dtype": dtype_name(args), "data": "synthetic",
         "config": {"workload": WORKLOAD, "model": f"XXZ L={L_SITES} periodic, J=1, Delta=1, h_i~U[-W,W], W in (1,3,5)",
                    "D": D, "nnz": nnz, "nev": NEV, "block": BLOCK, "target_eps": EPS,
-                   "precision": (f"FP32 filter + FP64 Lanczos/Rayleigh-Ritz + "
-                                 f"{'pair-float (FP32 hi+lo)' if args.refine_precision == 'df64' else 'FP64'} "
-                                 f"refinement filter" if args.precision == "f32" else "FP64 throughout"),
+                   "precision": (f"FP32 filter + FP64 Lanczos/Rayleigh-Ritz + " + refine_desc(args)
+                                 if args.precision == "f32" else "FP64 throughout"),
                    "K": [x["K"] for x in rec], "realisation_W": [x["W"] for x in rec],
                    "l2": "inputs larger than L2 (Krylov basis ~1.9 GB per solve)", "parallelism": f"replicas{world}",
                    "execution": ("the timed steps as one overlapped batch (pf_polfed_solve_batch)" if args.pipeline
@@ -637,6 +658,7 @@ def run_ours(args):
         "residual_unrefined_max_over_hnorm": max(x["rep"]["max_residual_unrefined"] / x["rep"]["hnorm"]
                                                  for x in rec),
         "variant_refine_pairfloat": variant,
+        "variant_refine_direct_fp64": variant_direct,
         "fp64_plain": fp64,
         "serving": serving,
     }
@@ -780,12 +802,11 @@ def run_model(args):
                          for k in ("ms_filter_f32", "ms_filter_f64", "ms_orth", "ms_qr", "ms_check", "ms_extract",
                                    "ms_refine", "ms_total")}}
     structured = c["model"] == "qrem" and args.mapping == "structured"
-    xxz_struct = c["model"] in ("xxz", "qsun")
+    xxz_struct = c["model"] in ("xxz", "hubbard")
     if structured:
         out["config"]["mapping"] = "structured (bit-flip columns generated in registers; diagonal read)"
     if xxz_struct:
-        out["config"]["mapping"] = ("structured for FP32 steps (CSR columns; values from the diagonal and "
-                                    + ("one off-diagonal constant)" if c["model"] == "xxz" else "the dot block and ray couplings)"))
+        out["config"]["mapping"] = "structured for FP32 steps (CSR columns; values from the diagonal and one off-diagonal constant)"
 
     def alg_bytes(w):
         # QREM's structured mapping reads only the diagonal of the matrix; XXZ's FP32 steps the columns

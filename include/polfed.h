@@ -264,6 +264,16 @@ pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t 
 pf_status pf_filter_tune(const pf_ham* H, int32_t prec, int32_t s, int32_t K, int32_t n, int32_t* form,
                          double* step_us, pf_stream_t stream);
 
+/* W = P_j(H~) v_j column by column: column j of the D x s block takes its own Chebyshev
+ * coefficients coeffs[i * s + j], i = 0..K (host, (K+1) x s row-major), in the recurrence of
+ * pf_filter_apply (Eq. clenshaw_chebyshev_prod).  The refinement's residual-correction form
+ * (PF_REFINE_CORRECTION) runs this recurrence in FP32 on the FP64 residuals.  prec: PF_F64 or
+ * PF_F32 (the table is rounded to the filter precision).  Allocates two auxiliary blocks and
+ * the device copy of the table.  Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ENOMEM,
+ * PF_ECUDA.                                                                          */
+pf_status pf_filter_apply_cols(const pf_ham* H, int32_t prec, int32_t s, const void* V, void* W,
+                               const double* coeffs, int32_t K, pf_stream_t stream);
+
 /* Same computation as pf_filter_apply, without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate device memory at
  * the time of the call (a frozen or exhausted memory pool, a host allocator that must not
@@ -321,11 +331,26 @@ typedef struct {
                              0 = 10, < 0 = never (returned pairs: refine_lock)         */
   double refine_lock;     /* refinement locks a returned pair once its residual is <=
                              this x res_tol ||H|| (at most 1); 0 = 0.9                 */
-  int32_t refine_precision;/* arithmetic of the refinement filter: PF_F64 (the default)
-                             or PF_DF64 (pair-float on the FP32 units, about 2x faster
-                             steps); Gram-Schmidt, Rayleigh-Ritz and the residual check
-                             stay FP64 either way                                      */
+  int32_t refine_precision;/* arithmetic of the refinement filter in the direct form:
+                             PF_F64 (the default) or PF_DF64 (pair-float on the FP32
+                             units, about 2x faster steps); Gram-Schmidt, Rayleigh-Ritz
+                             and the residual check stay FP64 either way               */
+  int32_t refine_form;    /* pf_refine_form of the refinement passes; 0 = the default,
+                             PF_REFINE_CORRECTION                                      */
 } pf_solve_opts;
+
+/* How a refinement pass applies W = (P(H~) + c I) U to a Ritz block U (FP32 filter path).
+ *  PF_REFINE_DIRECT      the K-step recurrence on U itself, in refine_precision arithmetic.
+ *  PF_REFINE_CORRECTION  residual-correction form: with theta_j = u_j^T H~ u_j and
+ *                        beta_i(theta) the recurrence's values on the scalar theta,
+ *                        (P(H~) + c) u = (P(theta) + c) u + beta_1 r + H~ d_1 - d_2, where
+ *                        r = H~ u - theta u and d_i = 2 beta_{i+1}(theta) r + 2 H~ d_{i+1}
+ *                        - d_{i+2}.  r, theta, P(theta) and the final sum are FP64; the d
+ *                        recurrence, whose terms are the size of u's error, runs in FP32
+ *                        (per-column coefficients), so its rounding adds ~1e-12 relative
+ *                        error instead of FP32's ~1e-5: one FP64 SpMM and K FP32 steps per
+ *                        pass in place of K FP64 steps.                                  */
+typedef enum { PF_REFINE_DIRECT = 1, PF_REFINE_CORRECTION = 2 } pf_refine_form;
 
 typedef struct {
   int32_t status, K, blocks, krylov_dim, nev_guard, converged, checks, refine_passes;
@@ -416,6 +441,7 @@ typedef struct {
   double bounds_tol;        /* spectral-bounds tolerance; 0 = 1e-10                         */
   uint64_t seed;            /* start-block seed; 0 = 2024                                   */
   int32_t refine_precision; /* refinement filter arithmetic: PF_F64 (0) or PF_DF64          */
+  int32_t refine_form;      /* pf_refine_form of the refinement passes; 0 = the default     */
 } pf_server_config;
 typedef struct {
   int64_t id;

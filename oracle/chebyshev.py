@@ -8,6 +8,7 @@ Eq. clenshaw_chebyshev_prod (Sec. 4.4), with a_n = c_n/chi:
     b_{K+1} = b_{K+2} = 0
     b_i = a_i V + 2 H~ b_{i+1} - b_{i+2},   i = K, ..., 1
     P(H~) V = a_0 V + H~ b_1 - b_2.
+clenshaw_apply_cols: the same recurrence with coefficients of its own for each column of V.
 """
 import numpy as np
 
@@ -62,6 +63,16 @@ def clenshaw_apply(Ht, V, a):
         b = a[i] * V + 2.0 * (S @ b1) - b2
         b2, b1 = b1, b
     return a[0] * V + (S @ b1) - b2
+
+
+def clenshaw_apply_cols(Ht, V, C):
+    """Column j of the result is P_j(H~) V[:, j], P_j the Chebyshev series with coefficients
+    C[:, j] (C is (K+1) x s): clenshaw_apply run on each column with its own coefficients."""
+    C = np.asarray(C, dtype=np.float64)
+    out = np.empty_like(V)
+    for j in range(V.shape[1]):
+        out[:, [j]] = clenshaw_apply(Ht, V[:, [j]], C[:, j])
+    return out
 
 
 def forward_chebyshev_sum(Ht, V, a):

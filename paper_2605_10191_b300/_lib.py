@@ -12,6 +12,7 @@ PF_OK, PF_EINVAL, PF_ENOMEM, PF_ENOTCONV, PF_ETIMEOUT, PF_ECUDA, PF_ESTATE, PF_E
 PF_MODEL_XXZ, PF_MODEL_QSUN, PF_MODEL_HUBBARD, PF_MODEL_QREM, PF_MODEL_QSUN_U1 = 0, 1, 2, 3, 4
 PF_MAP_CSR, PF_MAP_STRUCTURED = 0, 1
 PF_F64, PF_F32, PF_DF64 = 0, 1, 2
+PF_REFINE_DIRECT, PF_REFINE_CORRECTION = 1, 2
 PF_FORM_AUTO, PF_FORM_STEPS, PF_FORM_GRAPH = -1, 0, -2
 
 
@@ -36,7 +37,7 @@ class pf_solve_opts(C.Structure):
                 ("refine_passes", C.c_int32), ("refine_K", C.c_int32), ("seed", C.c_uint64),
                 ("use_abs_target", C.c_int32), ("target_abs", C.c_double), ("refine_shift", C.c_double),
                 ("refine_reserve", C.c_int32), ("refine_full_set", C.c_int32), ("refine_guard_lock", C.c_double),
-                ("refine_lock", C.c_double), ("refine_precision", C.c_int32)]
+                ("refine_lock", C.c_double), ("refine_precision", C.c_int32), ("refine_form", C.c_int32)]
 
 
 class pf_report(C.Structure):
@@ -73,7 +74,7 @@ class pf_solve_item(C.Structure):
 class pf_server_config(C.Structure):
     _fields_ = [("block", C.c_int32), ("precision", C.c_int32), ("max_active", C.c_int32),
                 ("mem_budget_bytes", C.c_int64), ("res_tol", C.c_double), ("bounds_tol", C.c_double),
-                ("seed", C.c_uint64), ("refine_precision", C.c_int32)]
+                ("seed", C.c_uint64), ("refine_precision", C.c_int32), ("refine_form", C.c_int32)]
 
 
 class pf_request_info(C.Structure):
@@ -110,6 +111,7 @@ PROTOTYPES = {
     "pf_choose_K": (i32, [vp, dbl, i32, P(i32), vp]),
     "pf_clenshaw_step": (i32, [vp, i32, i32, vp, vp, vp, vp, dbl, dbl, dbl, i32, vp]),
     "pf_filter_apply": (i32, [vp, i32, i32, vp, vp, P(dbl), i32, vp]),
+    "pf_filter_apply_cols": (i32, [vp, i32, i32, vp, vp, P(dbl), i32, vp]),
     "pf_filter_apply_noalloc": (i32, [vp, i32, i32, vp, vp, P(dbl), i32, vp]),
     "pf_default_opts": (None, [P(pf_solve_opts)]),
     "pf_polfed_solve": (i32, [vp, dbl, i32, i32, P(pf_solve_opts), P(dbl), vp, P(dbl), P(pf_report), vp]),

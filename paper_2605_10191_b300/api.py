@@ -59,6 +59,15 @@ def _block_prec(V):
 _PREC_NAMES = {"f64": L.PF_F64, "f32": L.PF_F32, "df64": L.PF_DF64}
 
 
+_REFINE_FORMS = {"default": 0, "direct": L.PF_REFINE_DIRECT, "correction": L.PF_REFINE_CORRECTION}
+
+
+def _refine_form_code(name):
+    if name not in _REFINE_FORMS:
+        raise ValueError(f"unknown refinement form {name!r}")
+    return _REFINE_FORMS[name]
+
+
 def _prec_code(name):
     if name not in _PREC_NAMES:
         raise ValueError(f"unknown precision {name!r}")
@@ -305,6 +314,19 @@ class Hamiltonian:
               "pf_filter_apply")
         return W
 
+    def filter_apply_cols(self, V, coeffs, W=None, stream=None):
+        """W[:, j] = P_j(H~) V[:, j] with coeffs[:, j] the Chebyshev coefficients of column j
+        ((K+1) x s, pf_filter_apply_cols)."""
+        prec = _block_prec(V)
+        W = torch.empty_like(V) if W is None else W
+        c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float64))
+        if c.ndim != 2 or c.shape[1] != V.shape[1]:
+            raise ValueError("coeffs must be (K+1) x s")
+        check(lib().pf_filter_apply_cols(self.handle, prec, V.shape[1], _ptr(V), _ptr(W),
+                                         c.ctypes.data_as(C.POINTER(C.c_double)), c.shape[0] - 1, _stream(stream)),
+              "pf_filter_apply_cols")
+        return W
+
     # ---- the solve
     def solve(self, eps, nev, K, block=32, precision="f64", return_vectors=True, target_abs=None, stream=None,
               raise_on_notconv=True, **opts):
@@ -333,6 +355,8 @@ def _make_opts(block, precision, target_abs, opts):
             raise TypeError(f"unknown option {k}")
         if k == "refine_precision" and isinstance(v, str):
             v = _prec_code(v)
+        if k == "refine_form" and isinstance(v, str):
+            v = _refine_form_code(v)
         setattr(o, k, v)
     if target_abs is not None:
         o.use_abs_target = 1
@@ -437,11 +461,12 @@ class Server:
     """Continuous-batching solve server (pf_server_*): submit requests, step, take results."""
 
     def __init__(self, block=32, precision="f32", max_active=64, mem_budget_bytes=0, res_tol=0.0, bounds_tol=0.0,
-                 seed=0, stream=None, refine_precision="f64"):
+                 seed=0, stream=None, refine_precision="f64", refine_form="default"):
         _install_torch_allocator()
         cfg = L.pf_server_config(block=block, precision=L.PF_F64 if precision == "f64" else L.PF_F32,
                                  max_active=max_active, mem_budget_bytes=int(mem_budget_bytes), res_tol=res_tol,
-                                 bounds_tol=bounds_tol, seed=seed, refine_precision=_prec_code(refine_precision))
+                                 bounds_tol=bounds_tol, seed=seed, refine_precision=_prec_code(refine_precision),
+                                 refine_form=_refine_form_code(refine_form))
         self._stream = stream
         h = C.c_void_p()
         check(lib().pf_server_create(C.byref(cfg), _stream(stream), C.byref(h)), "pf_server_create")

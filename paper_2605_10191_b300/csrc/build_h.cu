@@ -384,10 +384,13 @@ static pf_status exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cuda
 }
 
 // Models whose off-diagonal elements of H share one value, so that a structured mapping can drop
-// the value array: QREM (-Gamma, columns from bit flips) and the nearest-neighbour XXZ chain
-// (J / 2; with L >= 3 no two bonds couple the same pair of states).
+// the value array: QREM (-Gamma, columns from bit flips), the nearest-neighbour XXZ chain (J / 2;
+// with L >= 3 no two bonds couple the same pair of states) and the open Hubbard chain (-t: a
+// nearest-neighbour hop has no site strictly between its ends, so its Jordan-Wigner sign is +1,
+// and an up hop and a down hop never reach the same state).
 static bool structured_ok(const Ham* H) {
   if (H->m.kind == PF_MODEL_QREM || H->m.kind == PF_MODEL_QSUN) return true;
+  if (H->m.kind == PF_MODEL_HUBBARD) return H->m.bc != PF_BC_PERIODIC && H->m.L >= 2;
   return H->m.kind == PF_MODEL_XXZ && H->m.J2 == 0.0 && H->m.J3 == 0.0 && H->m.L >= 3;
 }
 
@@ -606,8 +609,9 @@ pf_status set_rescale(Ham* H, double Ec, double dE, cudaStream_t st) {
                                                                  H->val32, H->val_df);
   PF_LAUNCH_CHECK("rescale_kernel");
   if (structured_ok(H)) {
-    // structured mapping: every off-diagonal element of H~ is -Gamma / dE (QREM) or (J / 2) / dE
-    // (XXZ), the value the rescale kernel computes for each of them; the diagonal is kept per row
+    // structured mapping: every off-diagonal element of H~ is -Gamma / dE (QREM), -t / dE (open
+    // Hubbard chain) or (J / 2) / dE (XXZ), the value the rescale kernel computes for each of them;
+    // the diagonal is kept per row
     if (!H->diag_t) {
       H->diag_t = (double*)dev_alloc(H->D * sizeof(double), st);
       H->diag32 = (float*)dev_alloc(H->D * sizeof(float), st);
@@ -617,7 +621,9 @@ pf_status set_rescale(Ham* H, double Ec, double dE, cudaStream_t st) {
     diag_copy_kernel<<<(unsigned)ceil_div(H->D, 256), 256, 0, st>>>(H->D, H->row_ptr, H->col, H->val_t, H->val32,
                                                                     H->val_df, H->diag_t, H->diag32, H->diag_df);
     PF_LAUNCH_CHECK("diag_copy_kernel");
-    H->off_t = H->m.kind == PF_MODEL_QREM ? (-H->m.Gamma) / dE : (H->m.J * 0.5) / dE;
+    H->off_t = H->m.kind == PF_MODEL_QREM      ? (-H->m.Gamma) / dE
+               : H->m.kind == PF_MODEL_HUBBARD ? (-H->m.t) / dE
+                                               : (H->m.J * 0.5) / dE;
     if (H->m.kind == PF_MODEL_QSUN) {
       // the dot block and the ray couplings of H~: off-diagonal elements v / dE, as the rescale
       // kernel computes them, in the three value forms

@@ -279,11 +279,21 @@ template <typename T> __device__ __forceinline__ T ld_val(const T* p) {
 
 // The end of a row segment: out = fma(alpha, acc, fma(a, v, -beta q)), or fma(alpha, acc, a v)
 // without the B2 term.  beta is 0 or 1; with the B2 term known present it is 1, so -beta q is -q
-// (the same bits as the run-time form, where 1 * q is exact).
+// (the same bits as the run-time form, where 1 * q is exact).  acol, when not null, holds one
+// coefficient per column of the block (the s values of this step), used in place of a: entry e
+// of the lane's segment takes acol[c0 + e], c0 the segment's first column.
 template <typename T, int E, bool L2ONLY, int B2M>
 __device__ __forceinline__ void row_epilogue(int64_t off, const T (&acc)[E], bool hb2, const T* __restrict__ V,
-                                             const T* B2, T* out, T a, T alpha, T beta) {
+                                             const T* B2, T* out, T a, T alpha, T beta, const T* acol = nullptr,
+                                             int c0 = 0) {
   Vec<T, E> v = ld_default<T, E>(V + off);
+  T av[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) av[e] = a;
+  if (acol) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) av[e] = ld_val(acol + c0 + e);
+  }
   Vec<T, E> r;
   if (hb2) {
     Vec<T, E> q;
@@ -291,10 +301,10 @@ __device__ __forceinline__ void row_epilogue(int64_t off, const T (&acc)[E], boo
     else q = ld_plain<T, E>(B2 + off);
 #pragma unroll
     for (int e = 0; e < E; ++e)
-      r.x[e] = stored(fmadd(alpha, acc[e], fmadd(a, v.x[e], B2M > 0 ? -q.x[e] : -(beta * q.x[e]))));
+      r.x[e] = stored(fmadd(alpha, acc[e], fmadd(av[e], v.x[e], B2M > 0 ? -q.x[e] : -(beta * q.x[e]))));
   } else {
 #pragma unroll
-    for (int e = 0; e < E; ++e) r.x[e] = stored(fmadd(alpha, acc[e], a * v.x[e]));
+    for (int e = 0; e < E; ++e) r.x[e] = stored(fmadd(alpha, acc[e], av[e] * v.x[e]));
   }
   st_default<T, E>(out + off, r);
 }
@@ -322,7 +332,7 @@ template <typename T, int S, bool L2ONLY, int SP, int B2M, int VS>
 __device__ __forceinline__ void clenshaw_row_vs(int64_t row, int lane, const int64_t* __restrict__ rp,
                                                 const int32_t* __restrict__ col, const T* __restrict__ val,
                                                 const T* __restrict__ V, const T* B1, const T* B2, T* out, T a,
-                                                T alpha, T beta, const ValSrc<T>& vsrc) {
+                                                T alpha, T beta, const ValSrc<T>& vsrc, const T* acol = nullptr) {
   using Sh = Shape<T, S>;
   constexpr int E = Sh::E;
   const int64_t off = row * S + lane * E;
@@ -376,7 +386,7 @@ __device__ __forceinline__ void clenshaw_row_vs(int64_t row, int lane, const int
       for (int e = 0; e < E; ++e) acc[e] = fmadd(h0, b0.x[e], acc[e]);
     }
   }
-  row_epilogue<T, E, L2ONLY, B2M>(off, acc, hb2, V, B2, out, a, alpha, beta);
+  row_epilogue<T, E, L2ONLY, B2M>(off, acc, hb2, V, B2, out, a, alpha, beta, acol, lane * E);
 }
 
 template <typename T, int S, bool L2ONLY, int SP, int B2M>
@@ -400,22 +410,25 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) clenshaw_step_kerne
                                                             const int32_t* __restrict__ col,
                                                             const T* __restrict__ val, const T* __restrict__ V,
                                                             const T* __restrict__ B1, const T* B2, T* out, T a,
-                                                            T alpha, T beta, int64_t rows_per_cta) {
+                                                            T alpha, T beta, int64_t rows_per_cta,
+                                                            const T* __restrict__ acol) {
   using Sh = Shape<T, S>;
   constexpr int G = Sh::G;
   const int lane = (int)(threadIdx.x % G);
+  const ValSrc<T> vs0;
   if (rows_per_cta > 0) {
     const int64_t r0 = blockIdx.x * rows_per_cta;
     const int64_t r1 = r0 + rows_per_cta < D ? r0 + rows_per_cta : D;
     for (int64_t row = r0 + threadIdx.x / G; row < r1; row += 256 / G)
-      clenshaw_row<T, S, false, SP, B2M>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta);
-  } else if (rows_per_cta < 0) {   // grid-stride over row groups (a capped grid)
+      clenshaw_row_vs<T, S, false, SP, B2M, 0>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta, vs0, acol);
+  } else if (rows_per_cta < 0) {   // grid-stride over row groups (sweep order, or a capped grid)
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; row < D; row += groups)
-      clenshaw_row<T, S, false, SP, B2M>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta);
+      clenshaw_row_vs<T, S, false, SP, B2M, 0>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta, vs0, acol);
   } else {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
-    if (row < D) clenshaw_row<T, S, false, SP, B2M>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta);
+    if (row < D)
+      clenshaw_row_vs<T, S, false, SP, B2M, 0>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta, vs0, acol);
   }
 }
 
@@ -428,7 +441,7 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) clenshaw_step_kerne
 template <typename T, int S, int SP, int B2M>
 __device__ __forceinline__ void qrem_row(int64_t row, int lane, int L, const T* __restrict__ diag, T g,
                                          const T* __restrict__ V, const T* B1, const T* B2, T* out, T a, T alpha,
-                                         T beta) {
+                                         T beta, const T* acol) {
   using Sh = Shape<T, S>;
   constexpr int E = Sh::E;
   const int64_t off = row * S + lane * E;
@@ -491,7 +504,7 @@ __device__ __forceinline__ void qrem_row(int64_t row, int lane, int L, const T* 
       for (int e = 0; e < E; ++e) acc[e] = fmadd(h0, b0.x[e], acc[e]);
     }
   }
-  row_epilogue<T, E, false, B2M>(off, acc, hb2, V, B2, out, a, alpha, beta);
+  row_epilogue<T, E, false, B2M>(off, acc, hb2, V, B2, out, a, alpha, beta, acol, lane * E);
 }
 
 template <typename T, int S, int SP, int B2M>
@@ -500,7 +513,8 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) qrem_step_kernel(in
                                                                               const T* __restrict__ V,
                                                                               const T* __restrict__ B1, const T* B2,
                                                                               T* out, T a, T alpha, T beta,
-                                                                              int64_t rows_per_cta) {
+                                                                              int64_t rows_per_cta,
+                                                                              const T* __restrict__ acol) {
   using Sh = Shape<T, S>;
   constexpr int G = Sh::G;
   const int lane = (int)(threadIdx.x % G);
@@ -508,14 +522,14 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) qrem_step_kernel(in
     const int64_t r0 = blockIdx.x * rows_per_cta;
     const int64_t r1 = r0 + rows_per_cta < D ? r0 + rows_per_cta : D;
     for (int64_t row = r0 + threadIdx.x / G; row < r1; row += 256 / G)
-      qrem_row<T, S, SP, B2M>(row, lane, L, diag, g, V, B1, B2, out, a, alpha, beta);
+      qrem_row<T, S, SP, B2M>(row, lane, L, diag, g, V, B1, B2, out, a, alpha, beta, acol);
   } else if (rows_per_cta < 0) {
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; row < D; row += groups)
-      qrem_row<T, S, SP, B2M>(row, lane, L, diag, g, V, B1, B2, out, a, alpha, beta);
+      qrem_row<T, S, SP, B2M>(row, lane, L, diag, g, V, B1, B2, out, a, alpha, beta, acol);
   } else {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
-    if (row < D) qrem_row<T, S, SP, B2M>(row, lane, L, diag, g, V, B1, B2, out, a, alpha, beta);
+    if (row < D) qrem_row<T, S, SP, B2M>(row, lane, L, diag, g, V, B1, B2, out, a, alpha, beta, acol);
   }
 }
 
@@ -528,7 +542,8 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) cstruct_step_kernel
                                                                                  ValSrc<T> vsrc, const T* __restrict__ V,
                                                                                  const T* __restrict__ B1, const T* B2,
                                                                                  T* out, T a, T alpha, T beta,
-                                                                                 int64_t rows_per_cta) {
+                                                                                 int64_t rows_per_cta,
+                                                                                 const T* __restrict__ acol) {
   using Sh = Shape<T, S>;
   constexpr int G = Sh::G;
   const int lane = (int)(threadIdx.x % G);
@@ -536,15 +551,15 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) cstruct_step_kernel
     const int64_t r0 = blockIdx.x * rows_per_cta;
     const int64_t r1 = r0 + rows_per_cta < D ? r0 + rows_per_cta : D;
     for (int64_t row = r0 + threadIdx.x / G; row < r1; row += 256 / G)
-      clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc);
+      clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc, acol);
   } else if (rows_per_cta < 0) {
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; row < D; row += groups)
-      clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc);
+      clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc, acol);
   } else {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
     if (row < D)
-      clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc);
+      clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc, acol);
   }
 }
 
@@ -554,6 +569,12 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) cstruct_step_kernel
 // per SM (the grid is then one wave of that many per SM: ranges for FP32, a grid-stride loop
 // for FP64), leaving SM thread slots and registers to a kernel of another solve running
 // beside it.
+// When the gathered block b_{i+1} (rows x S entries) exceeds half of L2, FP32 and pair-float
+// steps instead sweep the rows in order: one wave of CTAs strides over row groups, so at any
+// moment the whole GPU works inside a window of a few thousand consecutive rows.  A neighbour
+// row behind the window was read a short while ago and is still in L2; with contiguous ranges
+// every CTA sits at its own place in the block and neighbours come from DRAM.  Hubbard L = 12
+// (6 up, 6 down), s = 64: 244 against 372 us per FP32 step, the same bits.
 struct StepShape {
   unsigned grid;
   int64_t rows_per_cta;
@@ -563,6 +584,18 @@ static int device_sms() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   return nsm;
+}
+static int64_t device_l2_bytes() {
+  static const int64_t l2 = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 126 << 20;
+    }
+    return (int64_t)v;
+  }();
+  return l2;
 }
 template <typename K>
 static int kernel_occupancy(K kern) {
@@ -576,6 +609,8 @@ static StepShape shape_for(int64_t rows, int cta_cap, int nsm, int occ) {
   const int per_sm = cta_cap > 0 ? std::min(occ, cta_cap) : occ;
   const int64_t waves = (int64_t)nsm * per_sm;
   if constexpr (!std::is_same_v<T, double>) {
+    if (2 * rows * S * (int64_t)sizeof(T) > device_l2_bytes() && rows > waves * (256 / Sh::G))
+      return StepShape{(unsigned)waves, -1};   // sweep order (block larger than half of L2)
     const int64_t R = ceil_div(rows, waves);
     if (R > 256 / Sh::G) return StepShape{(unsigned)ceil_div(rows, R), R};
   }
@@ -604,36 +639,37 @@ static StepShape cstruct_shape(int64_t rows, int cta_cap = 0) {
 
 template <typename T, int S, int SP, int B2M>
 static void launch_step_form(int64_t D, const int64_t* rp, const int32_t* col, const T* val, const T* V, const T* B1,
-                             const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st, int cta_cap) {
+                             const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st, int cta_cap, const T* acol) {
   const StepShape sh = step_shape<T, S, SP, B2M>(D, cta_cap);
   clenshaw_step_kernel<T, S, SP, B2M><<<sh.grid, 256, 0, st>>>(D, rp, col, val, V, B1, B2, out, a, alpha, beta,
-                                                              sh.rows_per_cta);
+                                                              sh.rows_per_cta, acol);
 }
 
 template <typename T, int S>
 static pf_status launch_step_s(int64_t D, const int64_t* rp, const int32_t* col, const T* val, const T* V, const T* B1,
-                               const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
+                               const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st, int cap, const T* acol) {
   const bool spmm = alpha != T(0);
   const bool hb2 = beta != T(0);
-  if (spmm && hb2) launch_step_form<T, S, 1, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
-  else if (spmm) launch_step_form<T, S, 1, 0>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
-  else if (hb2) launch_step_form<T, S, 0, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
-  else launch_step_form<T, S, 0, 0>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
+  if (spmm && hb2) launch_step_form<T, S, 1, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+  else if (spmm) launch_step_form<T, S, 1, 0>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+  else if (hb2) launch_step_form<T, S, 0, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+  else launch_step_form<T, S, 0, 0>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap, acol);
   PF_LAUNCH_CHECK("clenshaw_step_kernel");
   return PF_OK;
 }
 
 template <typename T>
 static pf_status launch_step(int s, int64_t D, const int64_t* rp, const int32_t* col, const T* val, const T* V,
-                             const T* B1, const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
+                             const T* B1, const T* B2, T* out, T a, T alpha, T beta, cudaStream_t st, int cap,
+                             const T* acol) {
   switch (s) {
-    case 1: return launch_step_s<T, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 2: return launch_step_s<T, 2>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 4: return launch_step_s<T, 4>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 8: return launch_step_s<T, 8>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 16: return launch_step_s<T, 16>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 32: return launch_step_s<T, 32>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 64: return launch_step_s<T, 64>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 1: return launch_step_s<T, 1>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 2: return launch_step_s<T, 2>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 4: return launch_step_s<T, 4>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 8: return launch_step_s<T, 8>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 16: return launch_step_s<T, 16>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 32: return launch_step_s<T, 32>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 64: return launch_step_s<T, 64>(D, rp, col, val, V, B1, B2, out, a, alpha, beta, st, cap, acol);
   }
   return PF_EINVAL;
 }
@@ -642,20 +678,21 @@ static bool valid_s(int s) { return s == 1 || s == 2 || s == 4 || s == 8 || s ==
 
 pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* col, const void* val, int prec, int s,
                             const void* V, const void* B1, const void* B2, void* out, double a, double alpha,
-                            double beta, cudaStream_t st, int cta_cap) {
+                            double beta, cudaStream_t st, int cta_cap, const void* acol) {
   if (!valid_s(s) || D <= 0 || !V || !out) return PF_EINVAL;
   if (alpha != 0.0 && (!B1 || !val)) return PF_EINVAL;
   if (beta != 0.0 && !B2) return PF_EINVAL;
   if (beta != 0.0 && beta != 1.0) return PF_EINVAL;
   if (prec == PF_F64)
     return launch_step<double>(s, D, row_ptr, col, (const double*)val, (const double*)V, (const double*)B1,
-                               (const double*)B2, (double*)out, a, alpha, beta, st, cta_cap);
+                               (const double*)B2, (double*)out, a, alpha, beta, st, cta_cap, (const double*)acol);
   if (prec == PF_F32)
     return launch_step<float>(s, D, row_ptr, col, (const float*)val, (const float*)V, (const float*)B1,
-                              (const float*)B2, (float*)out, (float)a, (float)alpha, (float)beta, st, cta_cap);
-  if (prec == PF_DF64)
+                              (const float*)B2, (float*)out, (float)a, (float)alpha, (float)beta, st, cta_cap,
+                              (const float*)acol);
+  if (prec == PF_DF64 && !acol)
     return launch_step<df2>(s, D, row_ptr, col, (const df2*)val, (const df2*)V, (const df2*)B1, (const df2*)B2,
-                            (df2*)out, df2(a), df2(alpha), df2(beta), st, cta_cap);
+                            (df2*)out, df2(a), df2(alpha), df2(beta), st, cta_cap, nullptr);
   return PF_EINVAL;
 }
 
@@ -665,66 +702,69 @@ pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* co
 enum { MAP_QREM = 0, MAP_XXZ = 1, MAP_QSUN = 2 };
 template <int KIND, typename T, int S, int SP, int B2M>
 static void launch_struct_form(const Ham* H, const ValSrc<T>& vs, const T* V, const T* B1, const T* B2, T* out, T a,
-                               T alpha, T beta, cudaStream_t st, int cap) {
+                               T alpha, T beta, cudaStream_t st, int cap, const T* acol) {
   const int64_t D = H->D;
   if constexpr (KIND == MAP_QREM) {
     const StepShape sh = qrem_shape<T, S, SP, B2M>(D, cap);
     qrem_step_kernel<T, S, SP, B2M><<<sh.grid, 256, 0, st>>>(D, H->m.L, vs.diag, vs.g, V, B1, B2, out, a, alpha, beta,
-                                                            sh.rows_per_cta);
+                                                            sh.rows_per_cta, acol);
   } else {
     constexpr int VS = KIND == MAP_XXZ ? 1 : 2;
     const StepShape sh = cstruct_shape<T, S, SP, B2M, VS>(D, cap);
     cstruct_step_kernel<T, S, SP, B2M, VS><<<sh.grid, 256, 0, st>>>(D, H->row_ptr, H->col, vs, V, B1, B2, out, a,
-                                                                    alpha, beta, sh.rows_per_cta);
+                                                                    alpha, beta, sh.rows_per_cta, acol);
   }
 }
 template <int KIND, typename T, int S>
 static pf_status launch_struct_s(const Ham* H, const ValSrc<T>& vs, const T* V, const T* B1, const T* B2, T* out,
-                                 T a, T alpha, T beta, cudaStream_t st, int cap) {
+                                 T a, T alpha, T beta, cudaStream_t st, int cap, const T* acol) {
   const bool spmm = alpha != T(0);
   const bool hb2 = beta != T(0);
-  if (spmm && hb2) launch_struct_form<KIND, T, S, 1, 1>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
-  else if (spmm) launch_struct_form<KIND, T, S, 1, 0>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
-  else if (hb2) launch_struct_form<KIND, T, S, 0, 1>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
-  else launch_struct_form<KIND, T, S, 0, 0>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+  if (spmm && hb2) launch_struct_form<KIND, T, S, 1, 1>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+  else if (spmm) launch_struct_form<KIND, T, S, 1, 0>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+  else if (hb2) launch_struct_form<KIND, T, S, 0, 1>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+  else launch_struct_form<KIND, T, S, 0, 0>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
   PF_LAUNCH_CHECK(KIND == MAP_QREM ? "qrem_step_kernel" : "cstruct_step_kernel");
   return PF_OK;
 }
 template <int KIND, typename T>
 static pf_status launch_struct(int s, const Ham* H, const ValSrc<T>& vs, const T* V, const T* B1, const T* B2, T* out,
-                               T a, T alpha, T beta, cudaStream_t st, int cap) {
+                               T a, T alpha, T beta, cudaStream_t st, int cap, const T* acol) {
   switch (s) {
-    case 1: return launch_struct_s<KIND, T, 1>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 2: return launch_struct_s<KIND, T, 2>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 4: return launch_struct_s<KIND, T, 4>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 8: return launch_struct_s<KIND, T, 8>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 16: return launch_struct_s<KIND, T, 16>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 32: return launch_struct_s<KIND, T, 32>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
-    case 64: return launch_struct_s<KIND, T, 64>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+    case 1: return launch_struct_s<KIND, T, 1>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 2: return launch_struct_s<KIND, T, 2>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 4: return launch_struct_s<KIND, T, 4>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 8: return launch_struct_s<KIND, T, 8>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 16: return launch_struct_s<KIND, T, 16>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 32: return launch_struct_s<KIND, T, 32>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+    case 64: return launch_struct_s<KIND, T, 64>(H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
   }
   return PF_EINVAL;
 }
 template <typename T>
 static pf_status launch_structured(const Ham* H, int s, const ValSrc<T>& vs, const T* V, const T* B1, const T* B2,
-                                   T* out, T a, T alpha, T beta, cudaStream_t st, int cap) {
-  if (H->m.kind == PF_MODEL_QREM) return launch_struct<MAP_QREM, T>(s, H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
-  if (H->m.kind == PF_MODEL_QSUN) return launch_struct<MAP_QSUN, T>(s, H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
-  return launch_struct<MAP_XXZ, T>(s, H, vs, V, B1, B2, out, a, alpha, beta, st, cap);
+                                   T* out, T a, T alpha, T beta, cudaStream_t st, int cap, const T* acol) {
+  if (H->m.kind == PF_MODEL_QREM)
+    return launch_struct<MAP_QREM, T>(s, H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+  if (H->m.kind == PF_MODEL_QSUN)
+    return launch_struct<MAP_QSUN, T>(s, H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
+  return launch_struct<MAP_XXZ, T>(s, H, vs, V, B1, B2, out, a, alpha, beta, st, cap, acol);
 }
 
 // One step of H~ through the handle's mapping: the CSR arrays, or the structured rows (QREM bit
 // flips; XXZ constant off-diagonal).
 pf_status ham_step(const Ham* H, int prec, int s, const void* V, const void* B1, const void* B2, void* out,
-                   double a, double alpha, double beta, cudaStream_t st, int cta_cap) {
-  // XXZ: only the FP32 step takes the structured form (26.7 against 28.8 us at L = 20, s = 32);
-  // FP64 (bound by its pipe, 145.4 against 145.6 us) and pair-float (73.5 against 73.0 us) keep
-  // the CSR form.  The bits are the same either way.
+                   double a, double alpha, double beta, cudaStream_t st, int cta_cap, const void* acol) {
+  // XXZ and Hubbard: only the FP32 step takes the structured form (XXZ L = 20, s = 32: 26.7
+  // against 28.8 us); FP64 (bound by its pipe, 145.4 against 145.6 us) and pair-float (73.5
+  // against 73.0 us) keep the CSR form.  The bits are the same either way.
   const bool csr_form = H->mapping != PF_MAP_STRUCTURED || !H->diag_t ||
-                        ((H->m.kind == PF_MODEL_XXZ || H->m.kind == PF_MODEL_QSUN) && prec != PF_F32) ||
+                        ((H->m.kind == PF_MODEL_XXZ || H->m.kind == PF_MODEL_QSUN || H->m.kind == PF_MODEL_HUBBARD) &&
+                         prec != PF_F32) ||
                         (H->m.kind == PF_MODEL_QSUN && !H->qtab_t);
   if (csr_form)
     return clenshaw_step_raw(H->D, H->row_ptr, H->col, ham_vals(H, prec), prec, s, V, B1, B2, out, a, alpha, beta,
-                             st, cta_cap);
+                             st, cta_cap, acol);
   if (!valid_s(s) || !V || !out) return PF_EINVAL;
   if (alpha != 0.0 && !B1) return PF_EINVAL;
   if (beta != 0.0 && !B2) return PF_EINVAL;
@@ -735,42 +775,50 @@ pf_status ham_step(const Ham* H, int prec, int s, const void* V, const void* B1,
     vs.diag = H->diag_t; vs.g = H->off_t; vs.tab = H->qtab_t; vs.coef = H->qtab_t ? H->qtab_t + H->qtab_n : nullptr;
     vs.L = L; vs.N = N;
     return launch_structured<double>(H, s, vs, (const double*)V, (const double*)B1, (const double*)B2, (double*)out,
-                                     a, alpha, beta, st, cta_cap);
+                                     a, alpha, beta, st, cta_cap, (const double*)acol);
   }
   if (prec == PF_F32) {
     ValSrc<float> vs;
     vs.diag = H->diag32; vs.g = (float)H->off_t; vs.tab = H->qtab32; vs.coef = H->qtab32 ? H->qtab32 + H->qtab_n : nullptr;
     vs.L = L; vs.N = N;
     return launch_structured<float>(H, s, vs, (const float*)V, (const float*)B1, (const float*)B2, (float*)out,
-                                    (float)a, (float)alpha, (float)beta, st, cta_cap);
+                                    (float)a, (float)alpha, (float)beta, st, cta_cap, (const float*)acol);
   }
-  if (prec == PF_DF64) {
+  if (prec == PF_DF64 && !acol) {
     ValSrc<df2> vs;
     const df2* tab = reinterpret_cast<const df2*>(H->qtab_df);
     vs.diag = reinterpret_cast<const df2*>(H->diag_df); vs.g = df2(H->off_t); vs.tab = tab;
     vs.coef = tab ? tab + H->qtab_n : nullptr;
     vs.L = L; vs.N = N;
     return launch_structured<df2>(H, s, vs, (const df2*)V, (const df2*)B1, (const df2*)B2, (df2*)out, df2(a),
-                                  df2(alpha), df2(beta), st, cta_cap);
+                                  df2(alpha), df2(beta), st, cta_cap, nullptr);
   }
   return PF_EINVAL;
 }
 
 // K-step recurrence.  b_i lives in aux[i & 1]: step i reads b_{i+1} = aux[(i+1)&1] and
-// overwrites b_{i+2} (= aux[i&1]) with b_i.
-pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs, const void*,
-                           int K, void* aux0, void* aux1, cudaStream_t st, int cta_cap) {
-  if (K < 1 || !coeffs) return PF_EINVAL;
+// overwrites b_{i+2} (= aux[i&1]) with b_i.  colcoef (device, (K+1) x s values in the filter
+// precision, FP64 or FP32 only), when not null, gives every column its own coefficients: step i
+// uses row i of the table in place of coeffs[i] (the residual-correction form of the refinement).
+pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs,
+                           const void* colcoef, int K, void* aux0, void* aux1, cudaStream_t st, int cta_cap) {
+  if (K < 1 || (!coeffs && !colcoef)) return PF_EINVAL;
+  if (colcoef && prec != PF_F64 && prec != PF_F32) return PF_EINVAL;
+  const size_t w = prec_bytes(prec);
+  auto ac = [&](int i) -> const void* {
+    return colcoef ? static_cast<const void*>(static_cast<const char*>(colcoef) + (size_t)i * s * w) : nullptr;
+  };
+  auto a = [&](int i) { return colcoef ? 0.0 : coeffs[i]; };
   void* aux[2] = {aux0, aux1};
   // i = K: b_K = a_K V
-  PF_TRY(ham_step(H, prec, s, V, nullptr, nullptr, aux[K & 1], coeffs[K], 0.0, 0.0, st, cta_cap));
+  PF_TRY(ham_step(H, prec, s, V, nullptr, nullptr, aux[K & 1], a(K), 0.0, 0.0, st, cta_cap, ac(K)));
   for (int i = K - 1; i >= 1; --i) {
     const double beta = (i == K - 1) ? 0.0 : 1.0;
-    PF_TRY(ham_step(H, prec, s, V, aux[(i + 1) & 1], aux[i & 1], aux[i & 1], coeffs[i], 2.0, beta, st, cta_cap));
+    PF_TRY(ham_step(H, prec, s, V, aux[(i + 1) & 1], aux[i & 1], aux[i & 1], a(i), 2.0, beta, st, cta_cap, ac(i)));
   }
   // P V = a_0 V + H~ b_1 - b_2
   const double beta = (K >= 2) ? 1.0 : 0.0;
-  PF_TRY(ham_step(H, prec, s, V, aux[1], aux[0], W, coeffs[0], 1.0, beta, st, cta_cap));
+  PF_TRY(ham_step(H, prec, s, V, aux[1], aux[0], W, a(0), 1.0, beta, st, cta_cap, ac(0)));
   return PF_OK;
 }
 
@@ -825,7 +873,8 @@ __device__ __forceinline__ int find_item(const BatchItemDev* __restrict__ items,
 
 // Sweep step t over all items' rows (items may differ in K).  UNI = 1: every item has the
 // same K (all t0 = 0), so the step's form (SP, B2M) is the same for all and fixed at compile
-// time, as in clenshaw_step_kernel.  rows_per_cta as in clenshaw_step_kernel.
+// time, as in clenshaw_step_kernel.  rows_per_cta as in clenshaw_step_kernel (> 0: contiguous
+// ranges; < 0: sweep order over row groups; 0: one row group per thread group).
 template <typename T, int S, int SP, int B2M>
 __global__ void __launch_bounds__(256, 4) clenshaw_batch_kernel(const BatchItemDev* __restrict__ items, int n, int t,
                                                              int64_t total_rows, int64_t rows_per_cta) {
@@ -837,6 +886,10 @@ __global__ void __launch_bounds__(256, 4) clenshaw_batch_kernel(const BatchItemD
     r0 = blockIdx.x * rows_per_cta + threadIdx.x / G;
     r1 = (blockIdx.x + 1) * rows_per_cta < total_rows ? (blockIdx.x + 1) * rows_per_cta : total_rows;
     stride = 256 / G;
+  } else if (rows_per_cta < 0) {   // sweep order: one wave of CTAs strides over row groups
+    r0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
+    r1 = total_rows;
+    stride = (int64_t)gridDim.x * (256 / G);
   } else {
     r0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
     r1 = r0 + 1 < total_rows ? r0 + 1 : total_rows;
@@ -1185,9 +1238,10 @@ pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t
   const double a0 = it.coeffs_host ? it.coeffs_host[0] : 0.0;
   const double aK = it.coeffs_host ? it.coeffs_host[it.K] : 0.0;
   if (!(g.exec && g.K == it.K && g.V == it.V && g.W == it.W && g.aux0 == it.aux0 && g.aux1 == it.aux1 &&
-        g.prec == it.prec && g.s == it.s && g.H == it.H && g.a0 == a0 && g.aK == aK && g.cap == it.cta_cap)) {
+        g.prec == it.prec && g.s == it.s && g.H == it.H && g.a0 == a0 && g.aK == aK && g.cap == it.cta_cap &&
+        g.colcoef == it.colcoef)) {
     g.reset();
-    if (!it.coeffs_host || it.K < 1) return PF_EINVAL;
+    if ((!it.coeffs_host && !it.colcoef) || it.K < 1) return PF_EINVAL;
     if (it.prec == PF_F64) prepare_shapes<double>(it.s);
     else if (it.prec == PF_DF64) prepare_shapes<df2>(it.s);
     else prepare_shapes<float>(it.s);
@@ -1197,7 +1251,7 @@ pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t
     pf_status rc = PF_OK;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      rc = filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, cap,
+      rc = filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, it.colcoef, it.K, it.aux0, it.aux1, cap,
                             it.cta_cap);
       e = cudaStreamEndCapture(cap, &g.graph);
     }
@@ -1208,7 +1262,7 @@ pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t
       // no graph: the same launches go to the stream one by one
       g.reset();
       cudaGetLastError();
-      return filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, st,
+      return filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, it.colcoef, it.K, it.aux0, it.aux1, st,
                               it.cta_cap);
     }
     g.K = it.K;
@@ -1222,6 +1276,7 @@ pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t
     g.a0 = a0;
     g.aK = aK;
     g.cap = it.cta_cap;
+    g.colcoef = it.colcoef;
   }
   PF_COUNT(it.K + 1);
   PF_CUDA(cudaGraphLaunch(g.exec, st));
@@ -1446,6 +1501,30 @@ pf_status pf_filter_apply(const pf_ham* hh, int32_t prec, int32_t s, const void*
   PF_TRY(a0.alloc(H->D * s * w, st));
   PF_TRY(a1.alloc(H->D * s * w, st));
   return filter_apply_raw(H, prec, s, V, W, coeffs, nullptr, K, a0.p, a1.p, st);
+}
+
+pf_status pf_filter_apply_cols(const pf_ham* hh, int32_t prec, int32_t s, const void* V, void* W,
+                               const double* coeffs, int32_t K, pf_stream_t stream) {
+  const Ham* H = reinterpret_cast<const Ham*>(hh);
+  if (!H || !V || !W || !coeffs || K < 1) return PF_EINVAL;
+  if (!H->has_rescale) return PF_ESTATE;
+  if (prec != PF_F64 && prec != PF_F32) return PF_EINVAL;
+  if (!valid_s(s)) return PF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t w = prec_bytes(prec);
+  const size_t n = (size_t)(K + 1) * s;
+  DevBuf a0, a1, tab;
+  PF_TRY(a0.alloc(H->D * s * w, st));
+  PF_TRY(a1.alloc(H->D * s * w, st));
+  PF_TRY(tab.alloc(n * w, st));
+  if (prec == PF_F64) {
+    PF_CUDA(cudaMemcpyAsync(tab.p, coeffs, n * 8, cudaMemcpyHostToDevice, st));
+  } else {
+    std::vector<float> c32(n);   // pageable: consumed when the copy call returns
+    for (size_t i = 0; i < n; ++i) c32[i] = (float)coeffs[i];
+    PF_CUDA(cudaMemcpyAsync(tab.p, c32.data(), n * 4, cudaMemcpyHostToDevice, st));
+  }
+  return filter_apply_raw(H, prec, s, V, W, nullptr, tab.p, K, a0.p, a1.p, st);
 }
 
 pf_status pf_filter_apply_batch(const pf_filter_item* items, int32_t n, int32_t prec, int32_t s, int32_t form,

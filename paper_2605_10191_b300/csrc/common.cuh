@@ -154,13 +154,16 @@ inline const void* ham_vals(const Ham* H, int prec) {
 
 // Clenshaw step on raw CSR arrays (clenshaw.cu)
 // cta_cap > 0 limits the step's CTAs per SM (room for another solve's kernels beside it).
+// acol (device, s values in the step's precision, FP64 or FP32), when not null, gives each
+// column of the block its own coefficient in place of a.
 pf_status clenshaw_step_raw(int64_t D, const int64_t* row_ptr, const int32_t* col, const void* val,
                             int prec, int s, const void* V, const void* B1, const void* B2, void* out,
-                            double a, double alpha, double beta, cudaStream_t st, int cta_cap = 0);
+                            double a, double alpha, double beta, cudaStream_t st, int cta_cap = 0,
+                            const void* acol = nullptr);
 // One step of H~ through the handle's mapping (CSR arrays or the structured QREM rows); the
 // operands and errors of clenshaw_step_raw.
 pf_status ham_step(const Ham* H, int prec, int s, const void* V, const void* B1, const void* B2, void* out,
-                   double a, double alpha, double beta, cudaStream_t st, int cta_cap = 0);
+                   double a, double alpha, double beta, cudaStream_t st, int cta_cap = 0, const void* acol = nullptr);
 // One filter application W = P(H~) V (K steps) with its own two auxiliary blocks.
 struct FilterItem {
   const Ham* H = nullptr;
@@ -175,6 +178,10 @@ struct FilterItem {
   const void* owner = nullptr;          // the solve the item belongs to (grouping only)
   struct FilterGraph* graph = nullptr;  // the owner's captured form of this application (async executor)
   int cta_cap = 0;                      // CTAs per SM for its steps (0 = all that fit)
+  // device, (K+1) x s: a coefficient per column and step in place of coeffs (the refinement's
+  // residual-correction form).  Such an item runs alone (plain recurrence or its captured
+  // graph), never in a sweep or persistent launch.
+  const void* colcoef = nullptr;
 };
 // A per-step sweep captured as a CUDA graph (chain of T kernel nodes), reused while the table
 // address, item count, step count and row total stay the same.
@@ -223,6 +230,7 @@ struct FilterGraph {
   const Ham* H = nullptr;
   double a0 = 0, aK = 0;
   int cap = 0;
+  const void* colcoef = nullptr;
   FilterGraph() = default;
   FilterGraph(const FilterGraph&) = delete;
   FilterGraph& operator=(const FilterGraph&) = delete;
@@ -234,8 +242,10 @@ pf_status filter_graph_launch(FilterGraph& g, const FilterItem& it, cudaStream_t
 // PF_DF64 their (hi, lo) float pairs (the form the sweep and persistent kernels read).
 void coeff_table_host(int prec, const double* c, int n, double* out);
 // W = P V for a D x s block (K steps); aux buffers are two D x s blocks of the filter type.
+// colcoef (device, (K+1) x s values of the filter precision, FP64 or FP32), when not null,
+// replaces coeffs_host: every column takes its own coefficient of each step.
 pf_status filter_apply_raw(const Ham* H, int prec, int s, const void* V, void* W, const double* coeffs_host,
-                           const void* coeffs_dev, int K, void* aux0, void* aux1, cudaStream_t st, int cta_cap = 0);
+                           const void* colcoef, int K, void* aux0, void* aux1, cudaStream_t st, int cta_cap = 0);
 
 // Dense tall-skinny kernels (dense.cu).  Blocked storage: nb blocks, each D x s row-major,
 // block b at X + b*D*s.

@@ -131,6 +131,48 @@ __global__ void permute_cols_kernel(int64_t D, int s, const double* in, const in
 }
 
 // evecs[:, j] (column-major D x nev) = U column sel[j] (blocked D x s storage)
+// ---- residual-correction form of a refinement pass (PF_REFINE_CORRECTION)
+// For a column u with theta = u^T H~ u, let beta_i be the recurrence's values on the scalar theta,
+// beta_i = a_i + 2 theta beta_{i+1} - beta_{i+2} (beta_{K+1} = beta_{K+2} = 0).  Subtracting
+// beta_i u from the vector recurrence leaves d_i = b_i - beta_i u with
+//   d_i = 2 beta_{i+1} r + 2 H~ d_{i+1} - d_{i+2},  r = H~ u - theta u,
+// and P(H~) u = P(theta) u + beta_1 r + H~ d_1 - d_2, P(theta) = a_0 + theta beta_1 - beta_2.
+// The d recurrence is a Clenshaw recurrence of degree K - 1 on r with per-column coefficients
+// gamma_0 = beta_1, gamma_i = 2 beta_{i+1} (i >= 1).  One thread per column: theta from the
+// diagonal of C = U^T (H~ U), the gamma table (FP32, K rows of s), P(theta) (a[0] already holds
+// the pass's shift c) and theta.
+__global__ void corr_table_kernel(const double* a, int K, const double* C, int s, float* gamma, double* p,
+                                  double* theta) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s) return;
+  const double th = C[(int64_t)j * s + j];
+  double b1 = 0.0, b2 = 0.0;   // beta_{i+1}, beta_{i+2}
+  for (int i = K; i >= 1; --i) {
+    const double bi = fma(2.0 * th, b1, a[i] - b2);
+    if (i >= 2) gamma[(int64_t)(i - 1) * s + j] = (float)(2.0 * bi);
+    b2 = b1;
+    b1 = bi;
+  }
+  gamma[j] = (float)b1;
+  p[j] = a[0] + th * b1 - b2;
+  theta[j] = th;
+}
+
+// r (FP32) = H~ U - theta U, column j scaled by theta[j]; H~ U and U are FP64 D x s row-major.
+__global__ void corr_resid_kernel(int64_t n, int s, const double* HU, const double* U, const double* theta,
+                                  float* r) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  r[i] = (float)(HU[i] - theta[i % s] * U[i]);
+}
+
+// W (FP64) = P(theta) U + dW, dW the FP32 result of the d recurrence's closing line.
+__global__ void corr_combine_kernel(int64_t n, int s, const double* U, const double* p, const float* dW, double* W) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  W[i] = fma(p[i % s], U[i], (double)dW[i]);
+}
+
 __global__ void gather_cols_kernel(int64_t D, int s, const double* U, const int* sel, int nev, double* out) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= D * nev) return;
@@ -628,6 +670,8 @@ struct Task {
   int nb = 0, nb_total = 0, passes = 0, max_pass = 0, Kr = 0, Lb = 0, na = 0;
   double prev = 0, a0 = 0;
   DevBuf U, HU, aux64;
+  DevBuf corr_small;   // correction form, per block: C = U^T H~ U, P(theta), theta
+  bool corr_fits = false;   // the gamma tables fit in the (then idle) Krylov basis
   std::vector<double> E, res;
   std::vector<int> sel;
   std::vector<FilterItem> pending;
@@ -650,8 +694,17 @@ struct Task {
     if (t_end) cudaEventDestroy(t_end);
   }
 
-  // arithmetic of the refinement filter (PF_DF64 or PF_F64)
+  // arithmetic of the refinement filter in the direct form (PF_DF64 or PF_F64)
   int refine_prec() const { return o.refine_precision; }
+  // refinement passes in the residual-correction form: asked for, or the default with the FP64
+  // refinement arithmetic (an explicit pair-float request keeps the direct form); needs K >= 2
+  bool corr_form() const {
+    const bool want = o.refine_form == PF_REFINE_CORRECTION || (o.refine_form == 0 && o.refine_precision == PF_F64);
+    return f32 && want && Kr >= 2 && corr_fits;
+  }
+  // The per-block gamma tables (FP32, up to K rows of s) live in the Krylov basis, which the
+  // refinement no longer reads once the Ritz vectors are extracted.
+  float* corr_gamma(int b) const { return reinterpret_cast<float*>(S.V.as<double>()) + (int64_t)b * K * s; }
 
   double max_res() const {
     double m = 0;
@@ -675,6 +728,8 @@ struct Task {
     if (!o.use_abs_target && !(target_eps >= 0.0 && target_eps <= 1.0)) return PF_EINVAL;
     if (o.precision != PF_F64 && o.precision != PF_F32) return PF_EINVAL;
     if (o.refine_precision != PF_F64 && o.refine_precision != PF_DF64) return PF_EINVAL;
+    if (o.refine_form != 0 && o.refine_form != PF_REFINE_DIRECT && o.refine_form != PF_REFINE_CORRECTION)
+      return PF_EINVAL;
     if (o.block < 0) {   // the autotuner picks the block width
       if (!H->has_rescale) return PF_ESTATE;
       PF_TRY(autotune_block(H, o.precision, nev, stream, &s, nullptr, nullptr, refine_prec()));
@@ -917,8 +972,11 @@ struct Task {
       coeffs_r.resize(Kr + 1);
       PF_TRY(filter_coefficients_dev(lam_t, Kr, coeffs_r.data(), st));
       a0 = coeffs_r[0];
-      PF_TRY(coeffr_dev.alloc((size_t)(Kr + 1) * 8, st));
+      PF_TRY(coeffr_dev.alloc((size_t)(std::max(Kr, K) + 1) * 8, st));
       PF_TRY(aux64.alloc((size_t)2 * nb_total * H->D * s * 8, st));
+      // room for the largest degree a pass can take (K after a stall) in the basis' bytes
+      corr_fits = Kr <= K && (size_t)nb_total * K * s * sizeof(float) <= S.V.bytes;
+      if (corr_form()) PF_TRY(corr_small.alloc((size_t)nb_total * (s * s + 2 * s) * sizeof(double), st));
       prev = max_res();
       phase = REFINE;
       if (o.refine_full_set && nb < nb_total) {   // the reserve joins the set now
@@ -939,9 +997,10 @@ struct Task {
     const double c_shift = o.refine_shift == 0.0 ? 0.05 : (o.refine_shift < 0.0 ? 0.0 : o.refine_shift);
     coeffs_r[0] = passes > 0 ? a0 + c_shift : a0;
     const int rprec = refine_prec();
+    const bool corr = corr_form();
     {
       std::vector<double> tab(Kr + 1);   // pageable: consumed when the copy call returns
-      coeff_table_host(rprec, coeffs_r.data(), Kr + 1, tab.data());
+      coeff_table_host(corr ? PF_F64 : rprec, coeffs_r.data(), Kr + 1, tab.data());
       PF_CUDA(cudaMemcpyAsync(coeffr_dev.p, tab.data(), (size_t)(Kr + 1) * 8, cudaMemcpyHostToDevice, st));
     }
     const int q = nb * s;
@@ -988,6 +1047,7 @@ struct Task {
     // Pair-float filter: the active blocks are converted into the HU blocks, which the filter
     // reads as V and which hold its FP64 result after refine_post converts W back; W is
     // written over the active U blocks, which are only scratch until the set is rebuilt.
+    if (corr) return issue_refine_correction();
     const bool pair = rprec == PF_DF64;
     if (pair && na > 0)
       PF_TRY(convert_d2df(Ud + (int64_t)Lb * DS, reinterpret_cast<float2*>(HUd + (int64_t)Lb * DS), na * DS, st));
@@ -1012,14 +1072,63 @@ struct Task {
     return PF_OK;
   }
 
+  // Correction form: per active block, H~ U (FP64 step), C = U^T H~ U, the gamma table and
+  // P(theta) (corr_table_kernel), r = H~ U - theta U in FP32, then the FP32 d recurrence of degree
+  // Kr - 1 on r with per-column coefficients, written to the block's FP32 slots of aux64: r, dW,
+  // and the two recurrence auxiliaries (the 2 D s doubles of a block hold 4 D s floats).
+  pf_status issue_refine_correction() {
+    const int64_t DS = H->D * s;
+    double* Ud = U.as<double>();
+    double* HUd = HU.as<double>();
+    for (int b = Lb; b < nb; ++b) {
+      const double* Ub = Ud + (int64_t)b * DS;
+      double* HUb = HUd + (int64_t)b * DS;
+      double* Cb = corr_small.as<double>() + (int64_t)b * (s * s + 2 * s);
+      float* gam = corr_gamma(b);
+      float* f = reinterpret_cast<float*>(aux64.as<double>() + (int64_t)(2 * b) * DS);
+      PF_TRY(ham_step(H, PF_F64, s, Ub, Ub, nullptr, HUb, 0.0, 1.0, 0.0, st));
+      PF_TRY(gram(H->D, s, Ub, 1, HUb, 1, Cb, S.gscr.as<double>(), S.gscr_elems, st));
+      corr_table_kernel<<<1, 64, 0, st>>>(coeffr_dev.as<double>(), Kr, Cb, s, gam, Cb + s * s, Cb + s * s + s);
+      PF_LAUNCH_CHECK("corr_table_kernel");
+      corr_resid_kernel<<<(unsigned)ceil_div(DS, 256), 256, 0, st>>>(DS, s, HUb, Ub, Cb + s * s + s, f);
+      PF_LAUNCH_CHECK("corr_resid_kernel");
+      FilterItem it;
+      it.H = H;
+      it.owner = this;
+      it.prec = PF_F32;
+      it.s = s;
+      it.V = f;
+      it.W = f + DS;
+      it.colcoef = gam;
+      it.K = Kr - 1;
+      it.aux0 = f + 2 * DS;
+      it.aux1 = f + 3 * DS;
+      while ((int)g_refine.size() <= b) g_refine.emplace_back(new FilterGraph());
+      it.graph = g_refine[b].get();
+      pending.push_back(it);
+      S.rep.filter_steps_f32 += Kr;
+      S.rep.filter_steps_f64 += 1;
+    }
+    return PF_OK;
+  }
+
   pf_status refine_post() {
     clk->mark(3);
     const int64_t DS = H->D * s;
     double* Ud = U.as<double>();
     double* HUd = HU.as<double>();
     double* Wd = HUd + (int64_t)Lb * DS;
-    if (refine_prec() == PF_DF64 && na > 0)   // W (pairs, over the active U blocks) to FP64
+    const bool corr = corr_form();
+    if (refine_prec() == PF_DF64 && !corr && na > 0)   // W (pairs, over the active U blocks) to FP64
       PF_TRY(convert_df2d(reinterpret_cast<const float2*>(Ud + (int64_t)Lb * DS), Wd, na * DS, st));
+    if (corr)   // W = P(theta) U + dW per active block, into the H U blocks as in the direct form
+      for (int b = Lb; b < nb; ++b) {
+        const double* pb = corr_small.as<double>() + (int64_t)b * (s * s + 2 * s) + s * s;
+        const float* dW = reinterpret_cast<const float*>(aux64.as<double>() + (int64_t)(2 * b) * DS) + DS;
+        corr_combine_kernel<<<(unsigned)ceil_div(DS, 256), 256, 0, st>>>(DS, s, Ud + (int64_t)b * DS, pb, dW,
+                                                                         HUd + (int64_t)b * DS);
+        PF_LAUNCH_CHECK("corr_combine_kernel");
+      }
     if (Lb > 0) {   // the filtered blocks against the locked ones, two Gram-Schmidt passes
       DevBuf Cl;
       PF_TRY(Cl.alloc((size_t)Lb * s * na * s * 8, st));
@@ -1034,7 +1143,8 @@ struct Task {
     PF_TRY(rayleigh_ritz_H(S, Ud, HUd, nb, E, res));
     sel = nearest_sel(E, lam, nev);
     clk->mark(4);
-    S.rep.ms_filter_f64 += clk->ms(2, 3);
+    // the correction form's passes are FP32 steps (plus one FP64 step per block)
+    (corr ? S.rep.ms_filter_f32 : S.rep.ms_filter_f64) += clk->ms(2, 3);
     S.rep.ms_refine += clk->ms(2, 4);
     if (passes < 8) {
       S.rep.refine_active[passes] = na;
@@ -1055,7 +1165,6 @@ struct Task {
       coeffs_r.assign(Kr + 1, 0.0);
       PF_TRY(filter_coefficients_dev(lam_t, Kr, coeffs_r.data(), st));
       a0 = coeffs_r[0];
-      PF_TRY(coeffr_dev.alloc((size_t)(Kr + 1) * 8, st));
     }
     prev = cur;
     return issue_refine_filter();
@@ -1140,7 +1249,7 @@ struct Executor {
     if (items.empty()) return PF_OK;
     if (items.size() == 1 && csize == 0) {
       const FilterItem& it = items[0];
-      return filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, nullptr, it.K, it.aux0, it.aux1, st);
+      return filter_apply_raw(it.H, it.prec, it.s, it.V, it.W, it.coeffs_host, it.colcoef, it.K, it.aux0, it.aux1, st);
     }
     const size_t need = filter_sweep_table_bytes((int)items.size());
     if (table.bytes < need) PF_TRY(table.alloc(need * 2, st));
@@ -1154,6 +1263,10 @@ struct Executor {
     for (Task* t : tasks) {
       if (t->phase == Task::DONE) continue;
       for (const FilterItem& it : t->pending) {
+        if (it.colcoef) {   // per-column coefficients: the plain recurrence, alone
+          PF_TRY(run_group(std::vector<FilterItem>(1, it), 0));
+          continue;
+        }
         const auto key = std::make_pair(it.prec, it.s);
         auto g = std::find_if(groups.begin(), groups.end(), [&](const auto& x) { return x.first == key; });
         if (g == groups.end()) {
@@ -1414,6 +1527,10 @@ struct AsyncExecutor {
     std::vector<Grp> grps;
     for (Live* l : idle)
       for (const FilterItem& it : l->t->pending) {
+        if (it.colcoef) {   // per-column coefficients: its captured recurrence, alone
+          PF_TRY(filter_graph_launch(*it.graph, it, l->st));
+          continue;
+        }
         auto g = std::find_if(grps.begin(), grps.end(), [&](const Grp& x) {
           return x.prec == it.prec && x.s == it.s && x.D == it.H->D && x.nnz == it.H->nnz;
         });
@@ -1601,6 +1718,7 @@ struct Server {
     if (cfg.res_tol > 0) o.res_tol = cfg.res_tol;
     if (cfg.seed) o.seed = cfg.seed;
     o.refine_precision = cfg.refine_precision;
+    o.refine_form = cfg.refine_form;
     return o;
   }
   // Admission work, on the stream the executor gives the solve: basis, Hamiltonian, bounds,
@@ -1833,6 +1951,7 @@ pf_status pf_server_create(const pf_server_config* cfg, pf_stream_t stream, pf_s
     return PF_EINVAL;
   if (c.precision != PF_F64 && c.precision != PF_F32) return PF_EINVAL;
   if (c.refine_precision != PF_F64 && c.refine_precision != PF_DF64) return PF_EINVAL;
+  if (c.refine_form != 0 && c.refine_form != PF_REFINE_DIRECT && c.refine_form != PF_REFINE_CORRECTION) return PF_EINVAL;
   if (c.max_active <= 0) c.max_active = 64;
   if (c.mem_budget_bytes < 0) return PF_EINVAL;
   if (c.mem_budget_bytes == 0) {

@@ -146,10 +146,13 @@ def test_qrem_server_request(pf):
     assert np.max(np.abs(np.sort(r.evals) - np.sort(w[dense.nearest(w, lam, 10)]))) <= 1e-10 * hn
 
 
-@pytest.mark.parametrize("mk", [lambda: pi.hubbard_params(6, 3, 3, U=1.0, W=1.0, seed=1),
+@pytest.mark.parametrize("mk", [lambda: pi.hubbard_params(6, 3, 3, U=1.0, W=1.0, bc=pi.PBC, seed=1),
                                 lambda: pi.qsun_u1_params(N=2, L=6, M=4, seed=2),
                                 lambda: pi.j1j2_params(8, J2=0.5, W=1.0, seed=3)])
 def test_structured_mapping_rejected_for_other_models(pf, mk):
+    """Models whose off-diagonal elements take more than one value: the periodic Hubbard ring (its
+    wrap-around hop carries the Jordan-Wigner sign of the fermions it passes), the U(1) quantum sun
+    and the J1-J2 chain keep the CSR."""
     H = pf.Hamiltonian.from_params(mk())
     with pytest.raises(pf.PolfedError):
         H.set_mapping("structured")

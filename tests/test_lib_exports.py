@@ -88,7 +88,7 @@ def test_binding_structs_and_constants_match_header(tmp_path):
     consts = ["PF_OK", "PF_EINVAL", "PF_ENOMEM", "PF_ENOTCONV", "PF_ETIMEOUT", "PF_ECUDA", "PF_ESTATE",
               "PF_EBREAKDOWN", "PF_MODEL_XXZ", "PF_MODEL_QSUN", "PF_MODEL_HUBBARD", "PF_MODEL_QREM",
               "PF_MODEL_QSUN_U1", "PF_MAP_CSR", "PF_MAP_STRUCTURED", "PF_F64", "PF_F32", "PF_DF64",
-              "PF_FORM_AUTO", "PF_FORM_STEPS", "PF_FORM_GRAPH"]
+              "PF_FORM_AUTO", "PF_FORM_STEPS", "PF_FORM_GRAPH", "PF_REFINE_DIRECT", "PF_REFINE_CORRECTION"]
     got = _c_layout(structs, consts, tmp_path)
     for n, fields in structs.items():
         cls = getattr(_lib, n)

@@ -395,3 +395,55 @@ def test_polfed_through_breakdown_matches_dense():
     hn = np.abs(w).max()
     assert np.max(np.abs(r["E"] - w[sel])) <= 1e-10 * hn
     assert np.max(r["res"]) <= 1e-9 * hn
+
+
+# ---------------------------------------------------------------- per-column coefficients
+def test_clenshaw_apply_cols_columns_are_independent_filters():
+    """clenshaw_apply_cols: column j equals the spectral definition U diag(P_j(E)) U^T v_j."""
+    H, w, U = _xxz12()
+    Ht = ch.rescale(H, -0.16, 6.72)
+    wt = (w + 0.16) / 6.72
+    s, K = 3, 40
+    C = np.stack([ch.filter_coefficients(lt, K) for lt in (-0.3, 0.05, 0.6)], axis=1)
+    V = pi.uniform_pm_half(5, np.arange(H.D * s)).reshape(H.D, s)
+    got = ch.clenshaw_apply_cols(Ht, V, C)
+    n = np.arange(K + 1)
+    for j in range(s):
+        Pj = np.cos(np.outer(np.arccos(wt), n)) @ C[:, j]
+        ref = U @ (Pj * (U.T @ V[:, j]))
+        assert np.abs(got[:, j] - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("K", [2, 3, 57, 400])
+def test_residual_correction_form_of_the_filter(K):
+    """The refinement's residual-correction form: for any theta, with beta_i the recurrence on the
+    scalar theta (beta_i = a_i + 2 theta beta_{i+1} - beta_{i+2}), r = H~ u - theta u and
+    d_i = 2 beta_{i+1} r + 2 H~ d_{i+1} - d_{i+2} (a per-column Clenshaw recurrence of degree K - 1
+    with gamma_0 = beta_1, gamma_i = 2 beta_{i+1}),
+        P(H~) u = P(theta) u + H~ d_1 - d_2 + beta_1 r,
+    where the closing line H~ d_1 - d_2 + gamma_0 r is that recurrence's own.  Checked against the
+    direct filter on near-eigenvectors (theta their Rayleigh quotients) and on random vectors."""
+    H, w, U = _xxz12()
+    Ec, dE = -0.16, 6.72
+    Ht = ch.rescale(H, Ec, dE)
+    a = ch.filter_coefficients(0.05, K)
+    S = Ht.scipy()
+    s = 4
+    X = U[:, 400:400 + s] + 1e-4 * pi.uniform_pm_half(9, np.arange(H.D * s)).reshape(H.D, s)
+    X /= np.linalg.norm(X, axis=0)
+    for Y in (X, pi.uniform_pm_half(10, np.arange(H.D * s)).reshape(H.D, s)):
+        theta = np.einsum("ij,ij->j", Y, S @ Y) / np.einsum("ij,ij->j", Y, Y)
+        beta = np.zeros((K + 3, s))
+        for i in range(K, 0, -1):
+            beta[i] = a[i] + 2 * theta * beta[i + 1] - beta[i + 2]
+        P_theta = a[0] + theta * beta[1] - beta[2]
+        R = S @ Y - Y * theta
+        G = np.empty((K, s))
+        G[0] = beta[1]
+        G[1:] = 2 * beta[2:K + 1]
+        corr = Y * P_theta + ch.clenshaw_apply_cols(Ht, R, G)
+        direct = ch.clenshaw_apply(Ht, Y, a)
+        assert np.abs(corr - direct).max() < 1e-12 * max(1.0, np.abs(direct).max())
+        # the correction itself is the size of the vectors' error, not of the vectors
+        if Y is X:
+            assert np.abs(corr - Y * P_theta).max() < 1e-2 * np.abs(direct).max()
