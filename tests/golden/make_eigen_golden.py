@@ -82,10 +82,11 @@ def write(name, c, res, seconds):
         f.write(f"# model: XXZ (Eq. xxz) L={c['L']} N={c['L'] // 2} periodic J=1 Delta=1 W={c['W']} seed={c['seed']}\n")
         f.write(f"# method: {res['method']}\n")
         f.write(f"# written by tests/golden/make_eigen_golden.py {name} in {seconds:.0f} s\n")
-        f.write(f"emin {res['emin']!r}\nemax {res['emax']!r}\nlambda {res['lam']!r}\nhnorm {res['hnorm']!r}\n")
+        for k, key in (("emin", "emin"), ("emax", "emax"), ("lambda", "lam"), ("hnorm", "hnorm")):
+            f.write(f"{k} {float(res[key])!r}\n")
         f.write("# E  residual/||H||\n")
         for e, r in zip(res["E"], res["r"]):
-            f.write(f"{e!r} {r:.3e}\n")
+            f.write(f"{float(e)!r} {float(r):.3e}\n")
     print("wrote", path, flush=True)
 
 

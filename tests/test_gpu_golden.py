@@ -1,0 +1,81 @@
+"""The whole eigenpair set at large sectors against stored oracle sets (Sec. 4.6: the nev eigenpairs
+nearest the target).
+
+The stored sets (tests/golden/xxz_*.txt) are written by tests/golden/make_eigen_golden.py, which
+runs only the oracle: dense diagonalisation at L=16 (D = 12,870), and at L=20 (D = 184,756; the
+three realisations of the benchmark) the oracle's FP64 POLFED from an independent start block.
+Each file lists more eigenvalues than a solve returns, by increasing distance from the oracle's
+lambda, so the test re-selects around the GPU's own lambda (the two lambdas differ only by the
+rounding of the extreme eigenvalues).
+
+Checks, with ||H|| the oracle's max(|Emin|, |Emax|):
+  * the GPU's lambda equals the oracle's within 1e-10 ||H||;
+  * every returned eigenvalue is within 1e-10 ||H|| of a distinct stored one;
+  * completeness: every stored eigenvalue nearer the GPU's lambda than the returned set's radius
+    (less the tolerance) is among the returned ones;
+  * every residual ||H u - E u|| <= 1e-9 ||H||.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import pf_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _num(x):
+    """A float written by repr: plain, or numpy's np.float64(...) form."""
+    return float(x[len("np.float64("):-1]) if x.startswith("np.float64(") else float(x)
+
+
+def load_golden(name):
+    head, E, r = {}, [], []
+    for line in open(os.path.join(GOLD, f"{name}.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        a, b = line.split()
+        if a in ("emin", "emax", "lambda", "hnorm"):
+            head[a] = _num(b)
+        else:
+            E.append(_num(a))
+            r.append(_num(b))
+    return head, np.array(E), np.array(r)
+
+
+def check_against_golden(evals, resid, lam_gpu, head, E, nev):
+    hn = head["hnorm"]
+    tol = 1e-10 * hn
+    assert abs(lam_gpu - head["lambda"]) <= tol
+    d = np.abs(E - lam_gpu)
+    order = np.lexsort((E, d))
+    assert len(E) > nev
+    radius = d[order[nev - 1]]
+    # the stored set must reach beyond the returned radius for completeness to be decidable
+    assert d[order[-1]] > radius + 2 * tol
+    assert len(evals) == nev
+    used = np.zeros(len(E), dtype=bool)
+    for e in evals:
+        k = int(np.argmin(np.where(used, np.inf, np.abs(E - e))))
+        assert abs(E[k] - e) <= tol, (e, E[k], abs(E[k] - e) / hn)
+        used[k] = True
+    must = d < radius - tol
+    assert np.all(used[must]), np.sort(E[must & ~used])
+    assert np.max(resid) <= 1e-9 * hn
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_xxz_L16_nev100_s32_against_dense(precision):
+    """XXZ L=16 (D = 12,870), nev = 100, s = 32, eps = 0.5: the benchmark's path (FP32 filter with
+    FP64 refinement) and the plain FP64 path against the dense oracle spectrum."""
+    import paper_2605_10191_b300 as pf
+    head, E, _ = load_golden("xxz_L16_W3")
+    H = pf.Hamiltonian.from_params(pi.xxz_params(16, W=3.0, seed=2001))
+    H.spectral_bounds()
+    K = H.choose_K(0.5, 100)
+    res = H.solve(0.5, 100, K, block=32, precision=precision, return_vectors=False)
+    assert res.status == 0
+    check_against_golden(res.evals, res.resid, res.report["lambda_"], head, E, 100)
