@@ -7,7 +7,7 @@
 //      and the rank-2 update A22 -= v w^T + w v^T of the full trailing block.
 //   2. Bisection with Sturm counts for each requested index (one thread per index).
 //   3. Inverse iteration on T - lambda I (tridiagonal LU with partial pivoting), one
-//      thread per cluster of close eigenvalues; members of a cluster are kept
+//      CTA per cluster of eigenvalues closer than 1e-6 ||T||; members of a cluster are kept
 //      orthogonal by modified Gram-Schmidt against the earlier members.
 //   4. Back-transformation z = H_0 H_1 ... H_{n-3} y, one CTA per eigenvector.
 #include "common.cuh"
@@ -488,11 +488,16 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
     double r = fabs(dh[i]) + (i > 0 ? fabs(eh[i - 1]) : 0.0) + (i < n - 1 ? fabs(eh[i]) : 0.0);
     tnorm = std::max(tnorm, r);
   }
-  // clusters: consecutive requested indices whose eigenvalues are within 1e-3 ||T||
+  // clusters: consecutive requested indices whose eigenvalues are within 1e-6 ||T||.  An eigenvalue
+  // separated from its neighbours by a gap g gets its vector from its own inverse iteration, accurate
+  // to ~eps ||T|| / g (2e-10 at g = 1e-6 ||T||; the Ritz vectors are rotated by a Rayleigh-Ritz in H
+  // afterwards); closer ones are kept orthogonal by Gram-Schmidt inside their cluster, which one CTA
+  // walks sequentially.  With LAPACK's 1e-3 ||T|| the top Ritz values of the filtered H_L (spaced
+  // ~3e-3 apart) chained into long clusters that serialised the whole step.
   std::vector<int> cs;
   cs.push_back(0);
   for (int i = 1; i < q; ++i) {
-    bool same = idx_host[i] == idx_host[i - 1] + 1 && (w_host[i] - w_host[i - 1]) <= 1e-3 * tnorm;
+    bool same = idx_host[i] == idx_host[i - 1] + 1 && (w_host[i] - w_host[i - 1]) <= 1e-6 * tnorm;
     if (!same) cs.push_back(i);
   }
   cs.push_back(q);
