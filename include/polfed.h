@@ -92,7 +92,19 @@ typedef struct {
   double Gamma;     /* QREM transverse field                            */
   double J2, Delta2;  /* XXZ: next-nearest couplings, Eq. j1j2 (J2 = 0: none)   */
   double J3, Delta3;  /* XXZ: third-neighbour couplings, Eq. j1j2j3 (J3 = 0: none) */
+  double phi;         /* XXZ: flux per bond; != 0 makes H complex Hermitian (needs
+                         J2 = J3 = 0 and L >= 3), see below                           */
 } pf_model;
+
+/* Complex-Hermitian ring (Sec. 2 allows complex-Hermitian H): with phi != 0 the XXZ hop of
+ * bond (i, j) is (J/2) e^{+i phi} S+_i S-_j + h.c. (element (J*0.5) cos(phi) +- i (J*0.5) sin(phi),
+ * + when the row's state has spin i up and j down; cos and sin from the host C library).  The
+ * Hamiltonian handle then holds the real symmetric embedding [[A, -B], [B, A]] of H = A + iB, of
+ * dimension 2 D (D the sector's states; pf_ham_info reports 2 D): row r < D carries A[r,c] at
+ * column c and -B[r,c] at D + c, row D + r carries B[r,c] at c and A[r,c] at D + c, exact zeros
+ * omitted except the diagonal.  Its spectrum is H's with every eigenvalue twice and [x; y] is an
+ * eigenvector exactly when x + iy is one of H, so every real entry point (bounds, K, filters,
+ * pf_polfed_solve) works on it unchanged; pf_polfed_solve_complex returns H's own eigenpairs.   */
 
 /* Disorder and random couplings, host arrays (copied during the call).          */
 typedef struct {
@@ -387,6 +399,24 @@ pf_status pf_polfed_solve(pf_ham* H, double target_eps, int32_t nev, int32_t K,
                           const pf_solve_opts* o, double* evals, double* evecs, double* resid,
                           pf_report* rep, pf_stream_t stream);
 
+/* The nev eigenpairs nearest the target of a complex-Hermitian H (Sec. 2: block Lanczos for
+ * complex-Hermitian matrices; the model's phi != 0, see pf_model).  The handle holds the real
+ * embedding M = [[A, -B], [B, A]] of H = A + iB, whose spectrum is H's with every eigenvalue
+ * twice; the call solves M for 2 nev pairs with pf_polfed_solve's path, matches the copies
+ * (consecutive values within res_tol ||H||) and returns one eigenpair of H per match: the copy
+ * with the smaller residual, its vector [x; y] as z = x + i y (||z|| = 1, ||H z - E z|| equals
+ * the copy's residual).  K is the degree for the embedded problem: pf_choose_K(H, eps, 2 nev)
+ * puts 2 nev values of M in the window, i.e. nev of H.
+ *   evals, resid : host [nev] (ascending).
+ *   evecs        : device, D x nev complex, column-major, each entry (re, im) FP64
+ *                  (2 D nev doubles; D the sector's dimension); may be NULL.
+ * Errors: those of pf_polfed_solve; PF_EINVAL for a real model; PF_EBREAKDOWN when the copies
+ * cannot be matched (H has a degenerate eigenvalue among the nev, which this path does not
+ * separate).                                                                          */
+pf_status pf_polfed_solve_complex(pf_ham* H, double target_eps, int32_t nev, int32_t K,
+                                  const pf_solve_opts* o, double* evals, double* evecs, double* resid,
+                                  pf_report* rep, pf_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * (a11) Batched solves: n independent problems (disorder realisations, sizes, targets)
  * solved together.  Every problem is a resumable solve holding its Lanczos state in device
@@ -456,7 +486,8 @@ typedef struct {
  * Errors: PF_EINVAL, PF_ECUDA.                                                      */
 pf_status pf_server_create(const pf_server_config* cfg, pf_stream_t stream, pf_server** out);
 /* Queue one request; m and p are copied (host).  id: host output.
- * Errors: PF_EINVAL (model, arrays, eps outside [0,1], nev outside [1, D]).          */
+ * Errors: PF_EINVAL (model, arrays, eps outside [0,1], nev outside [1, D]; a complex-
+ * Hermitian model, phi != 0, which goes through pf_polfed_solve_complex).           */
 pf_status pf_server_submit(pf_server* sv, const pf_model* m, const pf_params* p, double target_eps,
                            int32_t nev, int64_t* id);
 /* One step as above.  queued / active / finished: host outputs (may be NULL): requests

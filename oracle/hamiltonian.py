@@ -47,12 +47,15 @@ U(1) quantum sun (Eq. qsun:U1, App. A.2): the sector of M up spins among the N +
   antiparallel pair (dot spin n(j), outer spin j) with element (g0 * alpha**u_j) * 0.5
   (S^x S^x + S^y S^y).  Diagonal: H_dot[a, a], then the outer fields as above.
 
+XXZ ring with a flux phi per bond (complex Hermitian): each hop carries e^{+-i phi} (see
+  xxz_flux_hamiltonian); real_embedding gives the real symmetric [[A, -B], [B, A]] of H = A + iB.
+
 QREM (Eq. qrem, App. A): H = sum_alpha E_alpha |alpha><alpha| - Gamma sum_i sigma^x_i on
   the full space of L spins, row = state.  sigma^x_i flips bit i with element 1, so
   state alpha couples to alpha ^ (1 << i) with element -Gamma for i = 0..L-1.
   Diagonal: E_alpha.
 """
-from dataclasses import dataclass
+from dataclasses import dataclass, replace as dataclasses_replace
 import math
 
 import numpy as np
@@ -152,6 +155,50 @@ def xxz_hamiltonian(p):
     H = csr_from_terms(D, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
     H.states = states
     return H
+
+
+def xxz_flux_hamiltonian(p):
+    """Eq. xxz on a ring threaded by a flux p.phi per bond: a complex-Hermitian H (Sec. 2 allows
+    complex-Hermitian matrices).  The hop of bond (i, j) is (J/2) e^{+i phi} S+_i S-_j + h.c.: the
+    element of row state s is (J/2) e^{+i phi} when s has spin i up and j down, (J/2) e^{-i phi} when
+    it has i down and j up, with real part (J * 0.5) * cos(phi) and imaginary part +-((J * 0.5) *
+    sin(phi)) (the C library's cos and sin).  Diagonal as in xxz_hamiltonian.  complex128 values."""
+    Hr = xxz_hamiltonian(dataclasses_replace(p, phi=0.0))
+    states = Hr.states
+    rows = np.repeat(np.arange(Hr.D), np.diff(Hr.indptr))
+    cols = Hr.indices
+    half_j = p.J * 0.5
+    re, im = half_j * math.cos(p.phi), half_j * math.sin(p.phi)
+    data = Hr.data.astype(np.complex128)
+    off = rows != cols
+    # the one bond joining the row and column states, and which of its ends is up in the row state
+    x = states[rows[off]] ^ states[cols[off]]
+    lo = np.array([int(v).bit_length() - 1 for v in (x & -x)])       # lower bit of the flipped pair
+    hi = np.array([int(v).bit_length() - 1 for v in x])              # higher bit
+    wrap = (hi == p.L - 1) & (lo == 0) & (p.L > 2)                   # bond (L-1, 0): i = L-1, j = 0
+    i_bit = np.where(wrap, hi, lo)
+    up_i = ((states[rows[off]] >> i_bit) & 1) == 1
+    data[off] = re + 1j * np.where(up_i, im, -im)
+    H = CSR(D=Hr.D, indptr=Hr.indptr, indices=Hr.indices, data=data)
+    H.states = states
+    return H
+
+
+def real_embedding(Hc):
+    """The real symmetric form [[A, -B], [B, A]] (2D x 2D) of H = A + iB.  Row r < D holds A[r, c] at
+    column c and -B[r, c] at D + c; row D + r holds B[r, c] at c and A[r, c] at D + c; entries that are
+    exactly zero are not stored, the diagonal always is.  Its spectrum is that of H with every
+    eigenvalue twice, and [x; y] is an eigenvector exactly when x + iy is one of H."""
+    D = Hc.D
+    rows = np.repeat(np.arange(D), np.diff(Hc.indptr))
+    cols = Hc.indices
+    A, B = Hc.data.real.copy(), Hc.data.imag.copy()
+    keepA = (A != 0.0) | (rows == cols)
+    keepB = B != 0.0
+    r_all = np.concatenate([rows[keepA], rows[keepB], D + rows[keepB], D + rows[keepA]])
+    c_all = np.concatenate([cols[keepA], D + cols[keepB], cols[keepB], D + cols[keepA]])
+    v_all = np.concatenate([A[keepA], -B[keepB], B[keepB], A[keepA]])
+    return csr_from_terms(2 * D, r_all, c_all, v_all)
 
 
 def qsun_dot_matrix(p):
@@ -316,6 +363,9 @@ def qrem_hamiltonian(p):
 
 def build(p):
     """Dispatch on the parameter record's model kind (0 XXZ, 1 quantum sun, 2 Hubbard, 3 QREM,
-    4 U(1) quantum sun)."""
+    4 U(1) quantum sun).  An XXZ ring with a flux (p.phi != 0) is complex Hermitian; its real
+    embedding (the real symmetric matrix the solver works on) is returned."""
+    if p.kind == 0 and getattr(p, "phi", 0.0) != 0.0:
+        return real_embedding(xxz_flux_hamiltonian(p))
     return {0: xxz_hamiltonian, 1: qsun_hamiltonian, 2: hubbard_hamiltonian, 3: qrem_hamiltonian,
             4: qsun_u1_hamiltonian}[p.kind](p)

@@ -21,7 +21,7 @@ class pf_model(C.Structure):
                 ("N_dn", C.c_int32), ("bc", C.c_int32), ("J", C.c_double), ("Delta", C.c_double),
                 ("t", C.c_double), ("U", C.c_double), ("g0", C.c_double), ("alpha", C.c_double),
                 ("gamma", C.c_double), ("Gamma", C.c_double), ("J2", C.c_double), ("Delta2", C.c_double),
-                ("J3", C.c_double), ("Delta3", C.c_double)]
+                ("J3", C.c_double), ("Delta3", C.c_double), ("phi", C.c_double)]
 
 
 class pf_params(C.Structure):
@@ -115,6 +115,7 @@ PROTOTYPES = {
     "pf_filter_apply_noalloc": (i32, [vp, i32, i32, vp, vp, P(dbl), i32, vp]),
     "pf_default_opts": (None, [P(pf_solve_opts)]),
     "pf_polfed_solve": (i32, [vp, dbl, i32, i32, P(pf_solve_opts), P(dbl), vp, P(dbl), P(pf_report), vp]),
+    "pf_polfed_solve_complex": (i32, [vp, dbl, i32, i32, P(pf_solve_opts), P(dbl), vp, P(dbl), P(pf_report), vp]),
     "pf_start_block": (i32, [i64, i32, u64, vp, vp]),
     "pf_filter_apply_batch": (i32, [P(pf_filter_item), i32, i32, i32, i32, vp]),
     "pf_filter_tune": (i32, [vp, i32, i32, i32, i32, P(i32), P(dbl), vp]),

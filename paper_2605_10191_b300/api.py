@@ -127,6 +127,7 @@ class Model:
     Delta2: float = 1.0
     J3: float = 0.0
     Delta3: float = 1.0
+    phi: float = 0.0
     h: object = None
     mu: object = None
     A: object = None
@@ -140,7 +141,8 @@ class Model:
         k = p.kind
         if k == L.PF_MODEL_XXZ:
             return Model(kind=k, L=p.L, N=p.N, bc=p.bc, J=p.J, Delta=p.Delta, h=p.h, J2=getattr(p, "J2", 0.0),
-                         Delta2=getattr(p, "Delta2", 1.0), J3=getattr(p, "J3", 0.0), Delta3=getattr(p, "Delta3", 1.0))
+                         Delta2=getattr(p, "Delta2", 1.0), J3=getattr(p, "J3", 0.0), Delta3=getattr(p, "Delta3", 1.0),
+                         phi=getattr(p, "phi", 0.0))
         if k == L.PF_MODEL_QSUN:
             return Model(kind=k, L=p.L, N=p.N, g0=p.g0, alpha=p.alpha, gamma=p.gamma, h=p.h, A=p.A,
                          u_noise=p.u_noise, n_of_j=p.n_of_j)
@@ -157,7 +159,7 @@ class Model:
         return L.pf_model(kind=self.kind, L=self.L, N=self.N, N_up=self.N_up, N_dn=self.N_dn, bc=self.bc,
                           J=self.J, Delta=self.Delta, t=self.t, U=self.U, g0=self.g0, alpha=self.alpha,
                           gamma=self.gamma, Gamma=self.Gamma, J2=self.J2, Delta2=self.Delta2, J3=self.J3,
-                          Delta3=self.Delta3)
+                          Delta3=self.Delta3, phi=self.phi)
 
 
 class Basis:
@@ -328,6 +330,25 @@ class Hamiltonian:
         return W
 
     # ---- the solve
+    def solve_complex(self, eps, nev, K, block=32, precision="f64", return_vectors=True, target_abs=None, stream=None,
+                      raise_on_notconv=True, **opts):
+        """The nev eigenpairs of a complex-Hermitian model (phi != 0) nearest the target
+        (pf_polfed_solve_complex): evals, resid, and evecs as a (D, nev) complex128 tensor, D the
+        sector's dimension (the handle's D is 2 D, the real embedding)."""
+        o = _make_opts(block, precision, target_abs, opts)
+        evals = np.zeros(nev)
+        resid = np.zeros(nev)
+        Dc = self.D // 2
+        buf = torch.empty((nev, Dc, 2), dtype=torch.float64, device="cuda") if return_vectors else None
+        rep = L.pf_report()
+        st = lib().pf_polfed_solve_complex(self.handle, float(eps), int(nev), int(K), C.byref(o),
+                                           evals.ctypes.data_as(C.POINTER(C.c_double)), _ptr(buf),
+                                           resid.ctypes.data_as(C.POINTER(C.c_double)), C.byref(rep), _stream(stream))
+        if st not in (L.PF_OK, L.PF_ENOTCONV) or (st == L.PF_ENOTCONV and raise_on_notconv):
+            check(st, "pf_polfed_solve_complex")
+        evecs = torch.view_as_complex(buf).t() if buf is not None else None
+        return SolveResult(evals=evals, resid=resid, evecs=evecs, report=rep.as_dict(), status=st)
+
     def solve(self, eps, nev, K, block=32, precision="f64", return_vectors=True, target_abs=None, stream=None,
               raise_on_notconv=True, **opts):
         o = _make_opts(block, precision, target_abs, opts)

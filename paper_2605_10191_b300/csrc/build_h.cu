@@ -175,6 +175,9 @@ struct DevModel {
   int nranges, nbr[3], rr[3];
   double jdqr[3], halfJr[3];
   int64_t Dd;                 // Hubbard: down-table length
+  int flux;                   // XXZ ring with a flux: rows of the real embedding, 2 Dc of them
+  int64_t Dc;                 // the sector's dimension
+  double fre, fim;            // (J/2) cos(phi), (J/2) sin(phi)
   double jdq, halfJ, negt, U;
   double negG;                // QREM: -Gamma
   const double* E;            // QREM energies [2^L]
@@ -230,7 +233,10 @@ __device__ void gen_row(const DevModel& M, int64_t row, RowTerms& T) {
   T.n = 0;
   const int L = M.L;
   if (M.kind == PF_MODEL_XXZ) {
-    uint32_t s = M.states[row];
+    // with a flux, row R of the real embedding is part R / Dc of the sector's row R mod Dc
+    const int part = (M.flux && row >= M.Dc) ? 1 : 0;
+    const int64_t r = row - part * M.Dc;
+    uint32_t s = M.states[r];
     double d = 0.0;
     for (int q = 0; q < M.nranges; ++q)
       for (int b = 0; b < M.nbr[q]; ++b) {
@@ -240,6 +246,25 @@ __device__ void gen_row(const DevModel& M, int64_t row, RowTerms& T) {
       }
     for (int i = 0; i < L; ++i) d = __dadd_rn(d, ((s >> i) & 1u) ? M.hhalf[i] : -M.hhalf[i]);
     T.push(row, d);
+    if (M.flux) {
+      // hop of bond (i, j): A = (J/2) cos(phi); B = +-(J/2) sin(phi), + when spin i is up in s.
+      // Part 0 (row r): A at column c, -B at Dc + c; part 1 (row Dc + r): B at c, A at Dc + c.
+      for (int b = 0; b < M.nbr[0]; ++b) {
+        int i = b, j = (b + 1) % L;
+        if (((s >> i) & 1u) != ((s >> j) & 1u)) {
+          const int64_t c = (int64_t)rank_state(s ^ ((1u << i) | (1u << j)), M.binom);
+          const double B = ((s >> i) & 1u) ? M.fim : -M.fim;
+          if (part == 0) {
+            if (M.fre != 0.0) T.push(c, M.fre);
+            if (B != 0.0) T.push(M.Dc + c, -B);
+          } else {
+            if (B != 0.0) T.push(c, B);
+            if (M.fre != 0.0) T.push(M.Dc + c, M.fre);
+          }
+        }
+      }
+      return;
+    }
     for (int q = 0; q < M.nranges; ++q)
       for (int b = 0; b < M.nbr[q]; ++b) {
         int i = b, j = (b + M.rr[q]) % L;
@@ -389,6 +414,7 @@ static pf_status exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cuda
 // nearest-neighbour hop has no site strictly between its ends, so its Jordan-Wigner sign is +1,
 // and an up hop and a down hop never reach the same state).
 static bool structured_ok(const Ham* H) {
+  if (H->Dc > 0) return false;   // the real embedding of a complex H has two off-diagonal values
   if (H->m.kind == PF_MODEL_QREM || H->m.kind == PF_MODEL_QSUN) return true;
   if (H->m.kind == PF_MODEL_HUBBARD) return H->m.bc != PF_BC_PERIODIC && H->m.L >= 2;
   return H->m.kind == PF_MODEL_XXZ && H->m.J2 == 0.0 && H->m.J3 == 0.0 && H->m.L >= 3;
@@ -430,6 +456,13 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
     hh.resize(L);
     for (int i = 0; i < L; ++i) hh[i] = p->h[i] * 0.5;
     M.states = b->states;
+    if (m->phi != 0.0) {   // complex-Hermitian ring: rows of the real embedding
+      if (!std::isfinite(m->phi) || m->J2 != 0.0 || m->J3 != 0.0 || L < 3) return PF_EINVAL;
+      M.flux = 1;
+      M.Dc = b->D;
+      M.fre = M.halfJ * cos(m->phi);
+      M.fim = M.halfJ * sin(m->phi);
+    }
   } else if (m->kind == PF_MODEL_QSUN) {
     if (!p->h || !p->A || !p->u_noise || !p->n_of_j) return PF_EINVAL;
     M.nbonds = 0;
@@ -519,9 +552,10 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
 
   Ham* H = new Ham();
   H->m = *m;
-  H->D = b->D;
+  H->D = M.flux ? 2 * b->D : b->D;
+  H->Dc = M.flux ? b->D : 0;
   H->st = st;
-  const int64_t D = b->D;
+  const int64_t D = H->D;
   DevBuf counts;
   pf_status s = counts.alloc(D * sizeof(int64_t), st);
   if (s != PF_OK) { delete H; return s; }

@@ -91,6 +91,7 @@ struct Basis {
 struct Ham {
   pf_model m;
   int64_t D = 0, nnz = 0;
+  int64_t Dc = 0;               // complex-Hermitian model: its dimension (D = 2 Dc, the real embedding)
   int64_t* row_ptr = nullptr;   // device [D+1]
   int32_t* col = nullptr;       // device [nnz]
   double* val = nullptr;        // device [nnz], H

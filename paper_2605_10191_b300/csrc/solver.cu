@@ -1880,6 +1880,53 @@ pf_status pf_polfed_solve(pf_ham* hh, double target_eps, int32_t nev, int32_t K,
                            (cudaStream_t)stream);
 }
 
+// z = x + i y from column `col` of the real embedding's eigenvectors (2 Dc rows, column-major),
+// written as (re, im) pairs into column k of Z (Dc complex entries per column).
+__global__ void complex_column_kernel(int64_t Dc, const double* V2, int col, double* Z, int k) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= Dc) return;
+  const double* v = V2 + (int64_t)col * 2 * Dc;
+  Z[((int64_t)k * Dc + r) * 2] = v[r];
+  Z[((int64_t)k * Dc + r) * 2 + 1] = v[Dc + r];
+}
+
+pf_status pf_polfed_solve_complex(pf_ham* hh, double target_eps, int32_t nev, int32_t K, const pf_solve_opts* o,
+                                  double* evals, double* evecs, double* resid, pf_report* rep, pf_stream_t stream) {
+  Ham* H = reinterpret_cast<Ham*>(hh);
+  if (!H || !evals || !resid) return PF_EINVAL;
+  if (H->Dc <= 0 || nev < 1 || 2 * (int64_t)nev > H->D) return PF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  // every eigenvalue of H appears twice in the embedding: solve for 2 nev
+  const int n2 = 2 * nev;
+  std::vector<double> e2(n2), r2(n2);
+  DevBuf v2;
+  if (evecs) PF_TRY(v2.alloc((size_t)H->D * n2 * sizeof(double), st));
+  pf_report rp;
+  const pf_status s = polfed_solve_impl(H, target_eps, n2, K, o, e2.data(), evecs ? v2.as<double>() : nullptr,
+                                        r2.data(), &rp, st);
+  if (s != PF_OK && s != PF_ENOTCONV) return s;
+  if (rep) *rep = rp;
+  // the 2 nev values come ascending as pairs of copies; a pair whose copies disagree by more than
+  // the residual tolerance, or two pairs that coincide (a degenerate eigenvalue of H), cannot be
+  // matched to distinct eigenvectors of H
+  const double tol = (o && o->res_tol > 0 ? o->res_tol : 1e-9) * rp.hnorm;
+  for (int k = 0; k < nev; ++k) {
+    if (std::fabs(e2[2 * k + 1] - e2[2 * k]) > tol) return PF_EBREAKDOWN;
+    if (k + 1 < nev && e2[2 * k + 2] - e2[2 * k + 1] <= tol) return PF_EBREAKDOWN;
+  }
+  for (int k = 0; k < nev; ++k) {
+    const int c = r2[2 * k + 1] < r2[2 * k] ? 2 * k + 1 : 2 * k;   // the copy with the smaller residual
+    evals[k] = e2[c];
+    resid[k] = r2[c];
+    if (evecs) {
+      complex_column_kernel<<<(unsigned)ceil_div(H->Dc, 256), 256, 0, st>>>(H->Dc, v2.as<double>(), c, evecs, k);
+      PF_LAUNCH_CHECK("complex_column_kernel");
+    }
+  }
+  if (evecs) PF_CUDA(cudaStreamSynchronize(st));
+  return s;
+}
+
 pf_status pf_polfed_solve_batch(pf_solve_item* items, int32_t n, pf_stream_t stream) {
   if (n < 0 || (n > 0 && !items)) return PF_EINVAL;
   if (n == 0) return PF_OK;
@@ -1970,6 +2017,7 @@ pf_status pf_server_submit(pf_server* sv, const pf_model* m, const pf_params* p,
                            int64_t* id) {
   if (!sv || !m || !p || !id) return PF_EINVAL;
   if (!(target_eps >= 0.0 && target_eps <= 1.0) || nev < 1) return PF_EINVAL;
+  if (m->kind == PF_MODEL_XXZ && m->phi != 0.0) return PF_EINVAL;   // complex models: pf_polfed_solve_complex
   std::unique_ptr<Request> r(new Request());
   PF_TRY(copy_request(m, p, r.get()));
   const int64_t D = model_dim(*m);

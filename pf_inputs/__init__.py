@@ -9,9 +9,9 @@ with G = 0x9E3779B97F4A7C15.
 """
 from .rng import splitmix64, uniform01, uniform_pm_half, normals
 from .workloads import (XXZParams, QSunParams, HubbardParams, QREMParams, xxz_params, qsun_params,
-                        hubbard_params, qrem_params, j1j2_params, qsun_u1_params, CONFIGS, config_seed, serving_stream,
+                        hubbard_params, qrem_params, j1j2_params, xxz_flux_params, qsun_u1_params, CONFIGS, config_seed, serving_stream,
                         PBC, OBC)
 
 __all__ = ["splitmix64", "uniform01", "uniform_pm_half", "normals", "XXZParams",
            "QSunParams", "HubbardParams", "QREMParams", "xxz_params", "qsun_params", "hubbard_params",
-           "qrem_params", "j1j2_params", "qsun_u1_params", "CONFIGS", "config_seed", "serving_stream", "PBC", "OBC"]
+           "qrem_params", "j1j2_params", "xxz_flux_params", "qsun_u1_params", "CONFIGS", "config_seed", "serving_stream", "PBC", "OBC"]

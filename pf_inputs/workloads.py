@@ -30,6 +30,7 @@ class XXZParams:
     Delta2: float = 1.0
     J3: float = 0.0             # third-neighbour couplings (Eq. j1j2j3); 0 = none
     Delta3: float = 1.0
+    phi: float = 0.0            # flux per bond (complex-Hermitian ring); 0 = real
 
 
 @dataclass
@@ -87,6 +88,14 @@ def xxz_params(L, N=None, J=1.0, Delta=1.0, W=0.0, bc=PBC, seed=0):
     N = L // 2 if N is None else N
     h = W * (2.0 * uniform01(seed, np.arange(L)) - 1.0)
     return XXZParams(L=L, N=N, J=J, Delta=Delta, W=W, bc=bc, seed=seed, h=h)
+
+
+def xxz_flux_params(L, phi, N=None, J=1.0, Delta=1.0, W=0.0, bc=PBC, seed=0):
+    """The disordered XXZ ring threaded by a flux phi per bond (complex-Hermitian H); fields drawn as
+    in xxz_params."""
+    p = xxz_params(L, N=N, J=J, Delta=Delta, W=W, bc=bc, seed=seed)
+    p.phi = float(phi)
+    return p
 
 
 def j1j2_params(L, N=None, J1=1.0, J2=0.5, Delta1=1.0, Delta2=1.0, J3=0.0, Delta3=1.0, W=1.0, bc=PBC, seed=0):

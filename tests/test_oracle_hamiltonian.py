@@ -310,3 +310,60 @@ def test_qsun_u1_fields_rays_and_counts():
             j = [k for k in range(L) if (x >> k) & 1]
             assert len(j) == 1 and x == (1 << j[0]) | (1 << (L + int(p.n_of_j[j[0]])))
             assert abs(H.data[j0] - coef[j[0]]) <= 4e-16 * abs(coef[j[0]])
+
+
+# ---------------------------------------------------------------- complex Hermitian: XXZ ring with a flux
+def _twisted_xx_levels(L, N, phi, J=1.0):
+    """Free fermions of the XX ring with a flux phi per bond: Jordan-Wigner gives one-particle
+    energies J cos(k + phi), k = 2 pi (m + shift) / L with shift 1/2 for even N, 0 for odd N
+    (the fermions' boundary twist (-1)^(N-1))."""
+    shift = 0.5 if N % 2 == 0 else 0.0
+    levels = [J * math.cos(2.0 * math.pi * (m + shift) / L + phi) for m in range(L)]
+    return np.array(sorted(sum(c) for c in itertools.combinations(levels, N)))
+
+
+@pytest.mark.parametrize("L,N,phi", [(8, 4, 0.3), (9, 4, 1.1), (10, 5, -0.7), (8, 3, 2.0)])
+def test_flux_xx_ring_free_fermion_spectrum(L, N, phi):
+    p = pi.xxz_flux_params(L, phi, N=N, Delta=0.0, W=0.0)
+    Hc = hm.xxz_flux_hamiltonian(p)
+    A = Hc.dense()
+    assert np.abs(A - A.conj().T).max() == 0.0
+    w = np.linalg.eigvalsh(A)
+    assert np.abs(w - _twisted_xx_levels(L, N, phi)).max() < 1e-12
+    # a wrong direction of the phase on one bond breaks the closed form
+    assert np.abs(np.linalg.eigvalsh(hm.xxz_hamiltonian(pi.xxz_params(L, N=N, Delta=0.0)).dense())
+                  - _twisted_xx_levels(L, N, phi)).max() > 1e-3
+
+
+def test_flux_reduces_to_xxz_and_gauges_away_on_the_open_chain():
+    p0 = pi.xxz_params(10, W=2.0, seed=5)
+    H0 = hm.xxz_hamiltonian(p0)
+    Hz = hm.xxz_flux_hamiltonian(pi.xxz_flux_params(10, 0.0, W=2.0, seed=5))
+    assert np.array_equal(Hz.indices, H0.indices) and np.array_equal(Hz.data.real, H0.data)
+    assert np.all(Hz.data.imag == 0.0)
+    # on the open chain a flux is a gauge transformation: same spectrum as without it
+    po = pi.xxz_flux_params(9, 0.9, W=1.5, bc=pi.OBC, seed=6)
+    wo = np.linalg.eigvalsh(hm.xxz_flux_hamiltonian(po).dense())
+    w0 = np.linalg.eigvalsh(hm.xxz_hamiltonian(pi.xxz_params(9, W=1.5, bc=pi.OBC, seed=6)).dense())
+    assert np.abs(wo - w0).max() < 1e-12
+    # on the ring it is not: the spectrum moves
+    wr = np.linalg.eigvalsh(hm.xxz_flux_hamiltonian(pi.xxz_flux_params(9, 0.9, W=1.5, seed=6)).dense())
+    wr0 = np.linalg.eigvalsh(hm.xxz_hamiltonian(pi.xxz_params(9, W=1.5, seed=6)).dense())
+    assert np.abs(wr - wr0).max() > 1e-3
+
+
+def test_real_embedding_doubles_the_spectrum_and_maps_eigenvectors():
+    p = pi.xxz_flux_params(10, 0.45, W=2.5, seed=7)
+    Hc = hm.xxz_flux_hamiltonian(p)
+    M = hm.real_embedding(Hc)
+    assert M.D == 2 * Hc.D
+    Md = M.dense()
+    assert np.array_equal(Md, Md.T)
+    w, Z = np.linalg.eigh(Hc.dense())
+    wm = np.linalg.eigvalsh(Md)
+    assert np.abs(wm - np.repeat(w, 2)).max() < 1e-12 * np.abs(w).max()
+    for k in (0, 17, 100):
+        z = Z[:, k]
+        v = np.concatenate([z.real, z.imag])
+        assert np.abs(Md @ v - w[k] * v).max() < 1e-12 * np.abs(w).max()
+    assert hm.build(p).D == M.D and np.array_equal(hm.build(p).data, M.data)
