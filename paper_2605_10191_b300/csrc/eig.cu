@@ -2,16 +2,21 @@
 //
 // Used by the convergence checks (Eq. blocklan_criterion needs eigenvectors t_j of H_L)
 // and by the Rayleigh-Ritz steps.  Only selected eigenpairs are computed:
-//   1. Householder tridiagonalisation A = Q T Q^T (reflectors kept in A's columns),
-//      three or four launches per column: reflector, p = tau A22 v, w = p - (tau/2)(p.v) v,
-//      and the rank-2 update A22 -= v w^T + w v^T of the full trailing block.
-//   2. Bisection with Sturm counts for each requested index (one thread per index).
+//   1. Householder tridiagonalisation A = Q T Q^T (reflectors kept in A's columns): one
+//      thread-block-cluster launch for orders up to 400, above that four launches per column
+//      over the whole GPU: reflector, p = tau A22 v, w = p - (tau/2)(p.v) v, and the rank-2
+//      update A22 -= v w^T + w v^T of the full trailing block.
+//   2. Multisection with Sturm counts for each requested index (one warp, in a CTA of its
+//      own, per index).
 //   3. Inverse iteration on T - lambda I (tridiagonal LU with partial pivoting), one
 //      CTA per cluster of eigenvalues closer than 1e-6 ||T||; members of a cluster are kept
 //      orthogonal by modified Gram-Schmidt against the earlier members.
 //   4. Back-transformation z = H_0 H_1 ... H_{n-3} y, one CTA per eigenvector.
 #include "common.cuh"
+#include <cooperative_groups.h>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <algorithm>
 
 namespace pf {
@@ -199,6 +204,190 @@ __global__ void __launch_bounds__(PF_TRI_NT) tridiag_cluster_kernel(double* Aw, 
     }
     cluster_sync_all();
   }
+}
+
+// The tridiagonalisation for small orders in one thread-block cluster with the matrix in distributed
+// shared memory.  Column c lives in the shared memory of CTA c mod cs (its k-th column, k = c / cs),
+// for the whole reduction.  Per column j:
+//   1. the owner of column j forms the reflector from its copy (as house_kernel) and writes v, d, e,
+//      tau (v also into Aw's column j for the back-transformation);
+//   -- cluster barrier --
+//   2. every CTA copies v and tau from the owner's shared memory, forms p_c = tau A22[:, c] . v for
+//      its own columns c > j and stores each p_c into the p buffer of every CTA of the cluster;
+//   -- cluster barrier --
+//   3. every CTA forms g = p . v and w = p - (tau/2) g v from its full copies and applies the rank-2
+//      update A22 -= v w^T + w v^T to its own columns.
+// Two cluster barriers per column, and the matrix never leaves shared memory; the cluster kernel
+// below moves each phase's data through L2 and meets four times per column.  The barriers are
+// hardware barriers (no spin-waits).  Remote shared memory is read and written only between the
+// first and the last barrier, while every CTA of the cluster is resident.
+#define PF_TRI_DS_NT 512
+__global__ void __launch_bounds__(PF_TRI_DS_NT) tridiag_dsmem_kernel(double* Aw, int n, int ldc, double* d, double* e,
+                                                                   double* tau) {
+  extern __shared__ __align__(16) double ds[];
+  __shared__ double sh[32];
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned rank = cl.block_rank(), cs = cl.num_blocks();
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  double* cols = ds;                                 // ldc columns of n: column k*cs + rank at cols + k*n
+  double* vb = cols + (size_t)ldc * n;               // v, indexed by absolute row
+  double* pb = vb + n;                               // p, indexed by absolute column (every CTA's stores)
+  double* wb = pb + n;                               // w
+  double* tb = wb + n;                               // tau of the column this CTA owns now
+  for (int k = 0; k < ldc; ++k) {
+    const int c = k * (int)cs + (int)rank;
+    if (c < n)
+      for (int r = tid; r < n; r += PF_TRI_DS_NT) cols[(size_t)k * n + r] = Aw[(int64_t)c * n + r];
+  }
+  __syncthreads();
+  cluster_sync_all();
+  for (int j = 0; j + 2 < n; ++j) {
+    const int m = n - j - 1;
+    const unsigned owner = (unsigned)(j % (int)cs);
+    double* xown = cols + (size_t)(j / (int)cs) * n + j + 1;   // column j, rows j+1.. (owner's copy)
+    if (rank == owner) {   // reflector: H x = beta e1, H = I - tau v v^T, v_0 = 1
+      double sig = 0.0;
+      for (int i = 1 + tid; i < m; i += PF_TRI_DS_NT) sig += xown[i] * xown[i];
+      sig = block_sum(sig, sh);
+      const double alpha = xown[0];
+      double beta, t, scale;
+      if (sig == 0.0) {
+        beta = alpha;
+        t = 0.0;
+        scale = 0.0;
+      } else {
+        const double nrm = sqrt(alpha * alpha + sig);
+        beta = alpha <= 0.0 ? nrm : -nrm;
+        t = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      for (int i = 1 + tid; i < m; i += PF_TRI_DS_NT) xown[i] *= scale;
+      __syncthreads();
+      if (tid == 0) {
+        xown[0] = 1.0;
+        d[j] = cols[(size_t)(j / (int)cs) * n + j];
+        e[j] = beta;
+        tau[j] = t;
+        tb[0] = t;
+      }
+      __syncthreads();
+      for (int i = tid; i < m; i += PF_TRI_DS_NT) Aw[(int64_t)j * n + j + 1 + i] = xown[i];
+    }
+    cluster_sync_all();
+    {
+      const double* xo = cl.map_shared_rank(xown, owner);
+      for (int i = tid; i < m; i += PF_TRI_DS_NT) vb[j + 1 + i] = xo[i];
+    }
+    const double tj = *cl.map_shared_rank(tb, owner);
+    __syncthreads();
+    // p_c for the own columns c > j: one warp per column, the product stored into every CTA
+    const int k0 = (j + 1 - (int)rank + (int)cs - 1) / (int)cs;   // first own column index with c > j
+    for (int k = k0 + warp; k < ldc; k += PF_TRI_DS_NT / 32) {
+      const int c = k * (int)cs + (int)rank;
+      if (c >= n) break;
+      const double* col = cols + (size_t)k * n;
+      double acc = 0.0;
+      for (int l = j + 1 + lane; l < n; l += 32) acc = fma(col[l], vb[l], acc);
+      acc = warp_sum(acc);
+      if (lane < (int)cs) *cl.map_shared_rank(pb + c, (unsigned)lane) = tj * acc;
+    }
+    cluster_sync_all();
+    double g = 0.0;
+    for (int l = j + 1 + tid; l < n; l += PF_TRI_DS_NT) g = fma(pb[l], vb[l], g);
+    g = block_sum(g, sh);
+    const double cc = 0.5 * tj * g;
+    for (int l = j + 1 + tid; l < n; l += PF_TRI_DS_NT) wb[l] = pb[l] - cc * vb[l];
+    __syncthreads();
+    // rank-2 update over all (own column, row) pairs at once: with few rows per column a loop over
+    // the columns one after another left most threads idle (one CTA at n = 64: 18 us per column)
+    {
+      const int kend = (int)rank < n ? min(ldc, (n - 1 - (int)rank) / (int)cs + 1) : 0;   // own columns c < n
+      const int64_t tot = (int64_t)max(kend - k0, 0) * m;
+      for (int64_t idx = tid; idx < tot; idx += PF_TRI_DS_NT) {
+        const int k = k0 + (int)(idx / m), l = j + 1 + (int)(idx % m);
+        const int c = k * (int)cs + (int)rank;
+        cols[(size_t)k * n + l] -= vb[l] * wb[c] + wb[l] * vb[c];
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = 0; k < ldc; ++k) {
+    const int c = k * (int)cs + (int)rank;
+    if (c < n)
+      for (int r = tid; r < n; r += PF_TRI_DS_NT) Aw[(int64_t)c * n + r] = cols[(size_t)k * n + r];
+  }
+  cluster_sync_all();   // no CTA leaves while another may still read its shared memory
+}
+
+static size_t tridiag_dsmem_bytes(int n, int cs) {
+  const int ldc = (n + cs - 1) / cs;
+  return ((size_t)ldc * n + 3 * (size_t)n + 2) * sizeof(double);
+}
+
+// Cluster size for the distributed-shared-memory tridiagonalisation of order n (0: not possible):
+// the largest of 16, 8, 4, 2 whose per-CTA share of the matrix fits in shared memory and of which
+// the device runs a cluster.
+static int tridiag_dsmem_cluster_query(int n);
+static int tridiag_dsmem_cluster(int n) {
+  static std::mutex mu;
+  static std::map<int, int> memo;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = memo.find(n);
+  if (it != memo.end()) return it->second;
+  return memo[n] = tridiag_dsmem_cluster_query(n);
+}
+static int tridiag_dsmem_cluster_query(int n) {
+  static int smem_max = -1;
+  if (smem_max < 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) v = 0;
+    cudaGetLastError();
+    smem_max = v;
+  }
+  auto kern = tridiag_dsmem_kernel;
+  for (int c : {16, 8, 4, 2}) {
+    const size_t bytes = tridiag_dsmem_bytes(n, c);
+    if (bytes + 1024 > (size_t)smem_max) continue;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)c, 1, 1);
+    cfg.blockDim = dim3(PF_TRI_DS_NT, 1, 1);
+    cfg.dynamicSmemBytes = bytes;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) == cudaSuccess && ncl >= 1) return c;
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+static pf_status tridiag_dsmem(double* Aw, int n, double* d, double* e, double* tau, int cs, cudaStream_t st) {
+  const size_t bytes = tridiag_dsmem_bytes(n, cs);
+  PF_CUDA(cudaFuncSetAttribute(tridiag_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)cs, 1, 1);
+  cfg.blockDim = dim3(PF_TRI_DS_NT, 1, 1);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  PF_COUNT(1);
+  PF_CUDA(cudaLaunchKernelEx(&cfg, tridiag_dsmem_kernel, Aw, n, (n + cs - 1) / cs, d, e, tau));
+  return PF_OK;
 }
 
 // Largest cluster (16, else 8, 4, 2) the device can run for the fused tridiagonalisation;
@@ -447,8 +636,18 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
   const int64_t nn = (int64_t)n * n;
   eig_copy_kernel<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>(A, lda, n, Aw);
   PF_LAUNCH_CHECK("eig_copy_kernel");
-  const int ccs = n <= 1024 ? tridiag_cluster_size() : 0;
-  if (ccs > 0) {
+  // one cluster launch for small orders (bound by the latency of its per-column phases); above
+  // ~400 the four launches per column over the whole GPU are faster, since the O(n^3) update then
+  // dominates and the cluster holds 16 of 148 SMs (measured n = 448: 8.9 against 9.4 ms; 640:
+  // 13.2 against 17.2; 900: 20.1 against 34.6; 1400: 37.6 against 96.5)
+  // distributed shared memory up to n = 512 (n = 224: 2.7 against 3.4 ms for the L2-staged cluster
+  // form, 448: 7.1 against 9.1); at 640 the four launches per column over the whole GPU are faster
+  // (13.4 against 14.3 ms)
+  const int dcs = n <= 512 ? tridiag_dsmem_cluster(n) : 0;
+  const int ccs = (dcs == 0 && n <= 400) ? tridiag_cluster_size() : 0;
+  if (dcs > 0) {
+    PF_TRY(tridiag_dsmem(Aw, n, d, e, tau, dcs, st));
+  } else if (ccs > 0) {
     PF_TRY(tridiag_cluster(Aw, n, d, e, tau, p, ccs, st));
   } else {
     for (int j = 0; j + 2 < n; ++j) {
@@ -479,7 +678,9 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
   gl -= 2.0 * 2.2e-16 * tn * n + 1e-300;
   gu += 2.0 * 2.2e-16 * tn * n + 1e-300;
   const double pivmin = 2.3e-308 * std::max(1.0, maxe2);
-  bisect_kernel<<<(unsigned)ceil_div((int64_t)q * 32, 256), 256, 0, st>>>(d, e, n, idx_dev, q, w, gl, gu, pivmin);
+  // one warp per CTA: the Sturm counts are bound by the FP64 pipe, and q warps packed eight to a
+  // CTA ran on q / 8 SMs (n = 900, q = 150: 10.5 ms on 19 SMs)
+  bisect_kernel<<<(unsigned)q, 32, 0, st>>>(d, e, n, idx_dev, q, w, gl, gu, pivmin);
   PF_LAUNCH_CHECK("bisect_kernel");
   PF_CUDA(cudaMemcpyAsync(w_host, w, q * sizeof(double), cudaMemcpyDeviceToHost, st));
   PF_CUDA(cudaStreamSynchronize(st));
