@@ -302,7 +302,7 @@ def oracle_sample(nsteps, barrier=None):
     Ht = oc.rescale(H, Ec, dE)
     mu, G = od.exact_moments(Ht)
     lam_t = ((b["emin"] + EPS * (b["emax"] - b["emin"])) - Ec) / dE
-    nev_g = od.guard_count(NEV)
+    nev_g = od.guard_count(NEV, H.D)
     K = od.choose_K(lam_t, nev_g, H.D, mu, G)
     V = ol.start_block(H.D, BLOCK, 2024)
     a = oc.filter_coefficients(lam_t, nsteps)

@@ -204,7 +204,8 @@ pf_status pf_filter_coefficients(double lam_t, int32_t K, double* coeffs, pf_str
 
 /* Degree K from the Gaussian DOS with exact moments (Eq. dos_gaussian, Eq. Nev,
  * Eq. K_approx): K = ceil(2.655 sqrt(1 - lam~^2) * 2 rho(lam~) / nev_g),
- * nev_g = ceil(1.5 nev).  target_eps: lambda = Emin + eps (Emax - Emin).  Synchronises. */
+ * nev_g = ceil(g nev), g = 2.5 for D >= 100000, else 1.5.
+ * target_eps: lambda = Emin + eps (Emax - Emin).  Synchronises. */
 pf_status pf_choose_K(pf_ham* H, double target_eps, int32_t nev, int32_t* K, pf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
@@ -315,7 +316,8 @@ pf_status pf_filter_apply_noalloc(const pf_ham* H, int32_t prec, int32_t s, cons
 typedef struct {
   int32_t block;          /* s: 1..64, power of two; 0 = 32; < 0 = pf_autotune_block  */
   int32_t precision;      /* pf_precision of the filter recurrence                   */
-  int32_t nev_guard;      /* Ritz pairs converged; 0 = ceil(1.5 nev)                  */
+  int32_t nev_guard;      /* Ritz pairs converged; 0 = ceil(g nev),
+                             g = 2.5 for D >= 100000, else 1.5                      */
   int32_t check_first;    /* first check at this block step; 0 = ceil(m / 2), m the
                              expected Krylov blocks (20.427 s + 1.696 nev_g) / s      */
   int32_t check_every;    /* check interval in block steps; 0 = ceil(m / 10), checked
@@ -522,16 +524,18 @@ pf_status pf_kpm_dos(const double* mu, int32_t N, const double* x, int32_t nx, d
  * Errors: PF_EINVAL (eta outside [-1, 1]).                                          */
 pf_status pf_kpm_target(const double* mu, int32_t N, double eta, double* lam_t);
 /* K from Eq. condition_for_K with rho(lam~) from KPM: delta = nev_g / (2 rho) (Eq. Nev,
- * nev_g = ceil(1.5 nev)), then the smallest K in [K_approx/2, 2 K_approx] whose filter is at
- * most Omega = sin(2.655)/2.655 at both window edges lam~ +- delta (bisection).
+ * nev_g = ceil(g nev), g = 2.5 when mu_0 >= 100000, else 1.5), then the smallest K in
+ * [K_approx/2, 2 K_approx] whose filter is at most Omega = sin(2.655)/2.655 at both window
+ * edges lam~ +- delta (bisection).
  * Errors: PF_EINVAL (rho <= 0, lam_t outside (-1, 1)).                               */
 pf_status pf_choose_K_kpm(const double* mu, int32_t N, double lam_t, int32_t nev, int32_t* K);
 
 /* Block width from the autotuner: the step kernel is timed (8 steps on scratch blocks) for
  * s = 8, 16, 32, 64 and the width with the smallest predicted filter time is returned:
  * ceil(expectedkrylovdim(nev_g, s, 1) / s) x t_step(s) (Sec. 5.5's Krylov-size fit, nev_g =
- * ceil(1.5 nev)), plus for PF_F32 the FP64 refinement, 1.3 x 0.7 x ceil(nev_g / s) x t_step64(s)
- * (per unit degree); widths above nev_g (and above D/2) are skipped.  Timings are cached per
+ * ceil(g nev), g as for pf_choose_K), plus for PF_F32 the FP64 refinement,
+ * 1.3 x 0.7 x ceil(nev_g / s) x t_step64(s) (per unit degree); widths above nev_g (and above
+ * D/2) are skipped.  Timings are cached per
  * (device, D, nnz, precision).  A solve with block < 0 uses this choice.
  *   step_us, cost: host [4] (may be NULL): measured step time and predicted cost per candidate
  *   (0 = skipped).  Errors: PF_EINVAL, PF_ESTATE (H~ not set), PF_ENOMEM, PF_ECUDA.   */

@@ -118,7 +118,7 @@ def polfed(H, lam, nev, K, s, Ec, dE, tol=1e-10, seed=2024, eta=1.5, check_first
            check_every=None, V1=None, return_state=False):
     """Eigenpairs of H nearest the absolute energy lam (Sec. 4.6 workflow, steps 4-6)."""
     D = H.D
-    nev_g = min(guard_count(nev), D)
+    nev_g = min(guard_count(nev, D), D)
     Ht = rescale(H, Ec, dE)
     lam_t = (lam - Ec) / dE
     a = filter_coefficients(lam_t, K)

@@ -167,7 +167,7 @@ pf_status pf_choose_K_kpm(const double* mu, int32_t N, double lam_t, int32_t nev
   if (!mu || N < 1 || !K || nev < 1 || !(lam_t > -1.0 && lam_t < 1.0)) return PF_EINVAL;
   const double rho = kpm_rho(mu, N, lam_t);
   if (!(rho > 0.0)) return PF_EINVAL;
-  const int nev_g = (int)std::ceil(1.5 * nev);
+  const int nev_g = (int)std::ceil(guard_factor(mu[0]) * nev);   // mu_0 estimates D
   const double delta = nev_g / (2.0 * rho);
   const double k0 = 2.655 * std::sqrt(std::max(1.0 - lam_t * lam_t, 0.0)) / delta;
   int lo = std::max(1, (int)(k0 / 2)), hi = std::max(2, (int)std::ceil(2.0 * k0));

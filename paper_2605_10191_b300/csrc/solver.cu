@@ -441,12 +441,14 @@ static pf_status spectral_bounds_impl(Ham* H, double tol, cudaStream_t st) {
   return set_rescale(H, 0.5 * (hi + lo), 0.5 * (hi - lo), st);
 }
 
-// Guard factor: nev_g = ceil(1.5 nev) Ritz pairs of P are converged and the degree K is
-// chosen so that about nev_g eigenvalues lie above the cutoff.  The nev returned (nearest
-// lambda) then have filter values P >~ sinc(2.655 / 1.5) ~ 0.55, well above the magnitude
-// of the filter's negative sidelobe (~0.22), which is what the FP64 refinement must
-// contract relative to them.
-static const double kGuard = 1.5;
+// Guard factor (guard_factor, common.cuh): nev_g = ceil(g nev) Ritz pairs of P are converged and the
+// degree K is chosen so that about nev_g eigenvalues lie above the cutoff.  The nev returned
+// (nearest lambda) then have filter values P >~ sinc(2.655 / g) (0.55 at g = 1.5, 0.82 at 2.5),
+// above the magnitude of the filter's negative sidelobe (~0.22), which is what the refinement must
+// contract relative to them.  A larger guard lowers K (proportional to 1 / nev_g) faster than it
+// grows the Krylov space (20.4 s + 1.7 nev_g): filter-dominated solves (D >= 100,000) take g = 2.5
+// and need fewer steps in all; smaller ones, dominated by the Lanczos and Ritz work that grows
+// with nev_g, keep g = 1.5.
 
 static int expected_krylov_dim(int nev, int s, double eta) {
   return (int)std::ceil((20.427 * s + 1.696 * nev) * eta);
@@ -616,7 +618,7 @@ static pf_status autotune_block(const Ham* H, int prec, int nev, cudaStream_t st
   std::array<double, 4> us, us64;
   PF_TRY(measure_block_steps(H, prec, st, us));
   if (prec == PF_F32) PF_TRY(measure_block_steps(H, refine_prec, st, us64));
-  const int nev_g = std::max(nev, (int)std::ceil(1.5 * nev));
+  const int nev_g = std::max(nev, (int)std::ceil(guard_factor((double)H->D) * nev));
   double best = 0;
   int bs = 0;
   for (int c = 0; c < 4; ++c) {
@@ -741,7 +743,7 @@ struct Task {
     const double eta = o.eta > 0 ? o.eta : 1.5;
     tol = f32 ? (o.tol_f32 > 0 ? o.tol_f32 : 1e-7) : (o.tol > 0 ? o.tol : 1e-10);
     res_tol = o.res_tol > 0 ? o.res_tol : 1e-9;
-    nev_g = o.nev_guard > 0 ? o.nev_guard : (int)std::ceil(kGuard * nev);
+    nev_g = o.nev_guard > 0 ? o.nev_guard : (int)std::ceil(guard_factor((double)H->D) * nev);
     nev_g = std::max(nev_g, nev);
     if (nev_g > H->D) nev_g = (int)H->D;
     const int Mmax = (int)std::min<int64_t>(expected_krylov_dim(nev_g, s, eta), H->D);
@@ -1211,7 +1213,7 @@ struct Task {
 // state of solver_init, the Ritz set with H times it, and the FP32 path's refinement
 // auxiliaries, plus the transient Rayleigh-Ritz matrices.  Mirrors the allocations above.
 static size_t solve_state_bytes(int64_t D, int s, int nev, bool f32) {
-  int nev_g = std::max(nev, (int)std::ceil(kGuard * nev));
+  int nev_g = std::max(nev, (int)std::ceil(guard_factor((double)D) * nev));
   if (nev_g > D) nev_g = (int)D;
   const int Mmax = (int)std::min<int64_t>(expected_krylov_dim(nev_g, s, 1.5), D);
   int mb = std::max(2, Mmax / s);
@@ -1866,7 +1868,7 @@ pf_status pf_choose_K(pf_ham* hh, double target_eps, int32_t nev, int32_t* K, pf
   PF_TRY(ham_moments(H, &mu, &G, (cudaStream_t)stream));
   const double lam = H->emin + target_eps * (H->emax - H->emin);
   const double lt = (lam - H->Ec) / H->dE;
-  const int nev_g = (int)std::ceil(kGuard * nev);
+  const int nev_g = (int)std::ceil(guard_factor((double)H->D) * nev);
   const double rho = (double)H->D / (std::sqrt(2.0 * M_PI) * G) * std::exp(-(lt - mu) * (lt - mu) / (2.0 * G * G));
   const double delta = nev_g / (2.0 * rho);
   const double k = 2.655 * std::sqrt(std::max(1.0 - lt * lt, 0.0)) / delta;

@@ -65,7 +65,7 @@ def run_polfed(p, keep, s=1, seed=777):
     Ec, dE = ol.padded_interval(emin, emax, b["rmin"], b["rmax"])
     Ht = oc.rescale(H, Ec, dE)
     mu, G = od.exact_moments(Ht)
-    K = od.choose_K((lam - Ec) / dE, od.guard_count(keep), H.D, mu, G)
+    K = od.choose_K((lam - Ec) / dE, od.guard_count(keep, H.D), H.D, mu, G)
     out = ol.polfed(H, lam, keep, K, s, Ec, dE, tol=1e-10, seed=seed)
     order = by_distance(out["E"], lam)
     return dict(emin=emin, emax=emax, lam=lam, hnorm=hnorm, E=out["E"][order], r=out["res"][order] / hnorm,

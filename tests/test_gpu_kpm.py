@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import pf_inputs as pi
-from oracle import hamiltonian as oh, chebyshev as oc, dense, kpm
+from oracle import hamiltonian as oh, chebyshev as oc, dense, kpm, dos as od
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +47,7 @@ def test_kpm_dos_target_and_K_match_oracle(pf, setup):
     for eta in (-0.6, 0.3, 1.0):
         assert abs(pf.kpm_target(mu, eta) - kpm.offset_target(em, eta)) < 1e-12
     for lam_t, nev in ((em, 20), (0.2, 10), (-0.4, 30)):
-        assert pf.choose_K_kpm(mu, lam_t, nev) == kpm.choose_K(lam_t, int(np.ceil(1.5 * nev)), mu)
+        assert pf.choose_K_kpm(mu, lam_t, nev) == kpm.choose_K(lam_t, od.guard_count(nev, mu[0]), mu)
 
 
 def test_solve_at_maxdos_target(pf, setup):

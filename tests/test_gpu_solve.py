@@ -55,7 +55,7 @@ def test_moments_and_K_vs_oracle(pf):
     assert abs(mu - wt.mean()) < 1e-13 and abs(G - wt.std()) < 1e-12
     K = Hg.choose_K(0.5, 20)
     lam_t = ((emin + 0.5 * (emax - emin)) - Ec) / dE
-    assert K == od.choose_K(lam_t, od.guard_count(20), Ho.D, mu, G)
+    assert K == od.choose_K(lam_t, od.guard_count(20, Ho.D), Ho.D, mu, G)
 
 
 def _check_solution(res, w, U, lam, nev, hn):

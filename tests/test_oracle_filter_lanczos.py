@@ -133,7 +133,7 @@ def _solve_small(H, w, nev, s, eps, seed=2024, **kw):
     lam = b["emin"] + eps * (b["emax"] - b["emin"])
     Ht = ch.rescale(H, Ec, dE)
     mu, G = dos.exact_moments(Ht)
-    nev_g = dos.guard_count(nev)
+    nev_g = dos.guard_count(nev, H.D)
     K = dos.choose_K((lam - Ec) / dE, nev_g, H.D, mu, G)
     r = lz.polfed(H, lam, nev, K, s, Ec, dE, seed=seed, **kw)
     return r, lam
@@ -313,6 +313,24 @@ def test_window_holds_about_nev_g_levels():
             assert 0.75 * nev_g <= n <= 1.3 * nev_g, (lam_t, nev_g, n)
 
 
+def test_guard_rule_and_returned_edge_filter_value():
+    """The guard reading: nev_g = ceil(g nev), g = 1.5 below D = 100,000 and 2.5 from there on.  With
+    K from the window of nev_g levels, the nev-th level from the target sits at about
+    (nev / nev_g) delta, where a sinc-shaped filter of that window (value Omega at delta, the
+    reading of Eq. K_approx) is sinc(2.655 nev / nev_g): above 0.5 for either g, and above the
+    magnitude of the sidelobe minimum (-0.217) by more than 2x."""
+    assert dos.guard_count(10, 99999) == 15 and dos.guard_count(10, 100000) == 25
+    assert dos.guard_count(7, 12870) == 11 and dos.guard_count(7, 184756) == 18
+    x = np.linspace(4.0, 6.0, 20001)
+    side = float(np.min(np.sin(x) / x))
+    assert abs(side + 0.2172) < 1e-3
+    for D in (50000, 200000):
+        nev = 100
+        t = 2.655 * nev / dos.guard_count(nev, D)
+        edge = np.sin(t) / t
+        assert edge > 0.5 and edge > 2 * abs(side)
+
+
 def test_choose_K_is_K_approx_of_that_window():
     """choose_K = ceil(K_approx(lam~, delta)) with delta from Eq. Nev; the filter of that degree
     takes the value Omega at lam~ +- delta within the K_approx accuracy (Eq. condition_for_K)."""
@@ -383,7 +401,7 @@ def test_polfed_through_breakdown_matches_dense():
     Ht = ch.rescale(H, Ec, dE)
     mu, G = dos.exact_moments(Ht)
     nev = 10
-    K = dos.choose_K((lam - Ec) / dE, dos.guard_count(nev), H.D, mu, G)
+    K = dos.choose_K((lam - Ec) / dE, dos.guard_count(nev, H.D), H.D, mu, G)
     V1 = U[:, [0, H.D - 1]].copy()        # the extreme eigenvectors: P V1 stays in their span
     r = lz.polfed(H, lam, nev, K, 2, Ec, dE, V1=V1, return_state=True)
     Vm = r["V"]
