@@ -238,7 +238,7 @@ def ncu_traffic(kernel_tag):
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()
     if fields.get("source_sha256") != h or "traffic_bytes_per_launch" not in fields:
         return None
-    return float(fields["traffic_bytes_per_launch"])
+    return float(fields["traffic_bytes_per_launch"].split()[0])
 
 
 class ClockSampler:

@@ -398,10 +398,8 @@ __device__ __forceinline__ void clenshaw_row(int64_t row, int lane, const int64_
 }
 
 // One Clenshaw step over a D x s block.  rows_per_cta = 0: thread group g owns row g (one
-// row per G lanes).  rows_per_cta = R > 0: CTA b owns the contiguous rows [bR, (b+1)R) and
-// walks them in chunks of 256/G rows; the grid is one wave (SMs x resident CTAs), so each
-// SM's L1 serves the neighbour rows that fall inside its CTAs' ranges (for the XXZ chain in
-// rank order about half of all neighbours lie within +-200 rows).
+// row per G lanes).  rows_per_cta < 0: the grid (one wave, SMs x resident CTAs) strides over
+// groups of 256/G rows (the sweep order of shape_for).
 template <typename T> constexpr int step_min_blocks() {
   return is_df<T> ? PF_DF_MINB : sizeof(T) == 8 ? 8 : 6;
 }
@@ -416,12 +414,7 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) clenshaw_step_kerne
   constexpr int G = Sh::G;
   const int lane = (int)(threadIdx.x % G);
   const ValSrc<T> vs0;
-  if (rows_per_cta > 0) {
-    const int64_t r0 = blockIdx.x * rows_per_cta;
-    const int64_t r1 = r0 + rows_per_cta < D ? r0 + rows_per_cta : D;
-    for (int64_t row = r0 + threadIdx.x / G; row < r1; row += 256 / G)
-      clenshaw_row_vs<T, S, false, SP, B2M, 0>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta, vs0, acol);
-  } else if (rows_per_cta < 0) {   // grid-stride over row groups (sweep order, or a capped grid)
+  if (rows_per_cta < 0) {   // grid-stride over row groups (sweep order, or a capped grid)
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; row < D; row += groups)
       clenshaw_row_vs<T, S, false, SP, B2M, 0>(row, lane, rp, col, val, V, B1, B2, out, a, alpha, beta, vs0, acol);
@@ -518,12 +511,7 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) qrem_step_kernel(in
   using Sh = Shape<T, S>;
   constexpr int G = Sh::G;
   const int lane = (int)(threadIdx.x % G);
-  if (rows_per_cta > 0) {
-    const int64_t r0 = blockIdx.x * rows_per_cta;
-    const int64_t r1 = r0 + rows_per_cta < D ? r0 + rows_per_cta : D;
-    for (int64_t row = r0 + threadIdx.x / G; row < r1; row += 256 / G)
-      qrem_row<T, S, SP, B2M>(row, lane, L, diag, g, V, B1, B2, out, a, alpha, beta, acol);
-  } else if (rows_per_cta < 0) {
+  if (rows_per_cta < 0) {
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; row < D; row += groups)
       qrem_row<T, S, SP, B2M>(row, lane, L, diag, g, V, B1, B2, out, a, alpha, beta, acol);
@@ -547,12 +535,7 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) cstruct_step_kernel
   using Sh = Shape<T, S>;
   constexpr int G = Sh::G;
   const int lane = (int)(threadIdx.x % G);
-  if (rows_per_cta > 0) {
-    const int64_t r0 = blockIdx.x * rows_per_cta;
-    const int64_t r1 = r0 + rows_per_cta < D ? r0 + rows_per_cta : D;
-    for (int64_t row = r0 + threadIdx.x / G; row < r1; row += 256 / G)
-      clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc, acol);
-  } else if (rows_per_cta < 0) {
+  if (rows_per_cta < 0) {
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
     for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; row < D; row += groups)
       clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc, acol);
@@ -563,18 +546,18 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) cstruct_step_kernel
   }
 }
 
-// Launch shape of a step over `rows` rows: FP32 and pair-float steps use one wave of contiguous
-// row ranges (they are bound by their neighbour gathers, which the ranges keep in L1); FP64 steps
-// are bound by the FP64 pipe and keep one row per thread group.  cta_cap > 0 limits the CTAs
-// per SM (the grid is then one wave of that many per SM: ranges for FP32, a grid-stride loop
-// for FP64), leaving SM thread slots and registers to a kernel of another solve running
+// Launch shape of a step over `rows` rows.  FP32 and pair-float steps, bound by their neighbour
+// gathers, sweep the rows in order once there is more than one chunk of rows per CTA: one wave
+// of CTAs strides over 256/G-row groups, so at any moment the whole GPU works inside a window of
+// a few thousand consecutive rows.  A neighbour row behind the window was read a short while ago
+// and is still in L1 or L2.  Hubbard L = 12 (6 up, 6 down), s = 64: 244 against 372 us per FP32
+// step with one contiguous row range per CTA (there every CTA sits at its own place in a block
+// larger than half of L2 and neighbours come from DRAM); XXZ L = 20, s = 32, whose block fits in
+// L2: 25.2 against 26.7 us, L = 18: 9.4 against 10.0 us; the same bits in every shape.  FP64
+// steps are bound by the FP64 pipe and keep one row per thread group.  cta_cap > 0 limits the
+// CTAs per SM (the grid is then one wave of that many per SM: the sweep for FP32, a grid-stride
+// loop for FP64), leaving SM thread slots and registers to a kernel of another solve running
 // beside it.
-// When the gathered block b_{i+1} (rows x S entries) exceeds half of L2, FP32 and pair-float
-// steps instead sweep the rows in order: one wave of CTAs strides over row groups, so at any
-// moment the whole GPU works inside a window of a few thousand consecutive rows.  A neighbour
-// row behind the window was read a short while ago and is still in L2; with contiguous ranges
-// every CTA sits at its own place in the block and neighbours come from DRAM.  Hubbard L = 12
-// (6 up, 6 down), s = 64: 244 against 372 us per FP32 step, the same bits.
 struct StepShape {
   unsigned grid;
   int64_t rows_per_cta;
@@ -609,10 +592,7 @@ static StepShape shape_for(int64_t rows, int cta_cap, int nsm, int occ) {
   const int per_sm = cta_cap > 0 ? std::min(occ, cta_cap) : occ;
   const int64_t waves = (int64_t)nsm * per_sm;
   if constexpr (!std::is_same_v<T, double>) {
-    if (2 * rows * S * (int64_t)sizeof(T) > device_l2_bytes() && rows > waves * (256 / Sh::G))
-      return StepShape{(unsigned)waves, -1};   // sweep order (block larger than half of L2)
-    const int64_t R = ceil_div(rows, waves);
-    if (R > 256 / Sh::G) return StepShape{(unsigned)ceil_div(rows, R), R};
+    if (rows > waves * (256 / Sh::G)) return StepShape{(unsigned)waves, -1};   // sweep order
   }
   const int64_t classic = ceil_div(rows * Sh::G, 256);
   if (cta_cap > 0 && classic > waves) return StepShape{(unsigned)waves, -1};
@@ -873,8 +853,8 @@ __device__ __forceinline__ int find_item(const BatchItemDev* __restrict__ items,
 
 // Sweep step t over all items' rows (items may differ in K).  UNI = 1: every item has the
 // same K (all t0 = 0), so the step's form (SP, B2M) is the same for all and fixed at compile
-// time, as in clenshaw_step_kernel.  rows_per_cta as in clenshaw_step_kernel (> 0: contiguous
-// ranges; < 0: sweep order over row groups; 0: one row group per thread group).
+// time, as in clenshaw_step_kernel.  rows_per_cta as in clenshaw_step_kernel (< 0: sweep order
+// over row groups; 0: one row group per thread group).
 template <typename T, int S, int SP, int B2M>
 __global__ void __launch_bounds__(256, 4) clenshaw_batch_kernel(const BatchItemDev* __restrict__ items, int n, int t,
                                                              int64_t total_rows, int64_t rows_per_cta) {
@@ -882,11 +862,7 @@ __global__ void __launch_bounds__(256, 4) clenshaw_batch_kernel(const BatchItemD
   constexpr int G = Sh::G;
   const int lane = (int)(threadIdx.x % G);
   int64_t r0, r1, stride;
-  if (rows_per_cta > 0) {
-    r0 = blockIdx.x * rows_per_cta + threadIdx.x / G;
-    r1 = (blockIdx.x + 1) * rows_per_cta < total_rows ? (blockIdx.x + 1) * rows_per_cta : total_rows;
-    stride = 256 / G;
-  } else if (rows_per_cta < 0) {   // sweep order: one wave of CTAs strides over row groups
+  if (rows_per_cta < 0) {   // sweep order: one wave of CTAs strides over row groups
     r0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
     r1 = total_rows;
     stride = (int64_t)gridDim.x * (256 / G);
