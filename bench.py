@@ -3,7 +3,7 @@
 
 Workload (N=1): disordered XXZ chain, L=20 periodic, J=1, Delta=1, S^z_tot=0 sector
 (D=184756, nnz=2,129,556), 100 eigenpairs nearest eps=0.5, block width 32, FP32
-Chebyshev filter with FP64 Lanczos, Rayleigh-Ritz and refinement.  Step i solves
+Chebyshev filter, Lanczos Gram-Schmidt in pair-float, FP64 Rayleigh-Ritz and refinement.  Step i solves
 realisation r = (rank + i*world) mod 3 with W = (1, 3, 5)[r], seed 2000 + r.  A step is
 the whole path: basis and CSR build, spectral bounds, K, coefficients, block Lanczos,
 Ritz extraction, refinement.  The Krylov basis (~1.9 GB) is far larger than L2, so no
@@ -216,18 +216,26 @@ def refine_desc(args):
 
 
 def dtype_name(args):
-    """Arithmetic of the path: FP32 filter, pair-float (f32x2) or FP64 refinement filter, FP64
-    Lanczos and Rayleigh-Ritz; or FP64 throughout."""
+    """Arithmetic of the path: FP32 filter, pair-float (f32x2) Lanczos Gram-Schmidt and Ritz-vector
+    assembly, FP64 Lanczos coefficients, Rayleigh-Ritz and refinement; or FP64 throughout."""
     if getattr(args, "precision", "f32") != "f32":
         return "f64"
-    return "f32+f32x2+f64" if getattr(args, "refine_precision", "df64") == "df64" else "f32+f64"
+    return "f32+f32x2+f64"
+
+
+def step_source_sha256():
+    """Fingerprint of the step kernels' source: sha256 of csrc/clenshaw.cu followed by
+    csrc/pairfloat.cuh (the committed ncu summaries record it)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("clenshaw.cu", "pairfloat.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2605_10191_b300", "csrc", name), "rb").read())
+    return h.hexdigest()
 
 
 def ncu_traffic(kernel_tag):
     """Per-launch DRAM bytes from the committed ncu summary, if it matches the current source."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
-    src = os.path.join(ROOT, "paper_2605_10191_b300", "csrc", "clenshaw.cu")
     if not os.path.exists(path):
         return None
     fields = {}
@@ -235,8 +243,7 @@ def ncu_traffic(kernel_tag):
         if ":" in line:
             k, v = line.split(":", 1)
             fields[k.strip()] = v.strip()
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if fields.get("source_sha256") != h or "traffic_bytes_per_launch" not in fields:
+    if fields.get("source_sha256") != step_source_sha256() or "traffic_bytes_per_launch" not in fields:
         return None
     return float(fields["traffic_bytes_per_launch"].split()[0])
 
@@ -595,7 +602,7 @@ def run_ours(args):
                               "direct form, pair-float (FP32 hi + lo, about 2^-47 relative error per step); "
                               "refinement Rayleigh-Ritz, Gram-Schmidt and residuals FP64")
         if args.refine_form != "direct":
-            variant_direct = variant_run("f64", "direct", "f32+f64",
+            variant_direct = variant_run("f64", "direct", "f32+f32x2+f64",
                                          "direct form: the K-step recurrence on the Ritz vectors in FP64")
     fp64 = None
     if extras and not args.no_fp64_plain:
@@ -642,9 +649,12 @@ def run_ours(args):
         "dtype": dtype_name(args), "data": "synthetic",
         "config": {"workload": WORKLOAD, "model": f"XXZ L={L_SITES} periodic, J=1, Delta=1, h_i~U[-W,W], W in (1,3,5)",
                    "D": D, "nnz": nnz, "nev": NEV, "block": BLOCK, "target_eps": EPS,
-                   "precision": (f"FP32 filter + FP64 Lanczos/Rayleigh-Ritz + " + refine_desc(args)
+                   "precision": (f"FP32 filter + pair-float Lanczos Gram-Schmidt and Ritz-vector assembly "
+                                 f"+ FP64 Lanczos coefficients/Rayleigh-Ritz + " + refine_desc(args)
                                  if args.precision == "f32" else "FP64 throughout"),
                    "K": [x["K"] for x in rec], "realisation_W": [x["W"] for x in rec],
+                   "krylov_blocks": [x["rep"]["blocks"] for x in rec],
+                   "refine_passes": [x["rep"]["refine_passes"] for x in rec],
                    "l2": "inputs larger than L2 (Krylov basis ~1.9 GB per solve)", "parallelism": f"replicas{world}",
                    "execution": ("the timed steps as one overlapped batch (pf_polfed_solve_batch)" if args.pipeline
                                  else "one solve after another"),

@@ -37,7 +37,8 @@ class pf_solve_opts(C.Structure):
                 ("refine_passes", C.c_int32), ("refine_K", C.c_int32), ("seed", C.c_uint64),
                 ("use_abs_target", C.c_int32), ("target_abs", C.c_double), ("refine_shift", C.c_double),
                 ("refine_reserve", C.c_int32), ("refine_full_set", C.c_int32), ("refine_guard_lock", C.c_double),
-                ("refine_lock", C.c_double), ("refine_precision", C.c_int32), ("refine_form", C.c_int32)]
+                ("refine_lock", C.c_double), ("refine_precision", C.c_int32), ("refine_form", C.c_int32),
+                ("orth_precision", C.c_int32)]
 
 
 class pf_report(C.Structure):

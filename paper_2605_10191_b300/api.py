@@ -374,7 +374,7 @@ def _make_opts(block, precision, target_abs, opts):
     for k, v in opts.items():
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
-        if k == "refine_precision" and isinstance(v, str):
+        if k in ("refine_precision", "orth_precision") and isinstance(v, str):
             v = _prec_code(v)
         if k == "refine_form" and isinstance(v, str):
             v = _refine_form_code(v)

@@ -268,6 +268,13 @@ size_t gram_scratch_elems(int64_t D, int s, int nbX, int nbY);
 // Y may equal X only when nbX == nbY == 1.
 pf_status tsgemm(int64_t D, int s, const double* X, int nbX, const double* C, int ldc, double* Y, int nbY,
                  double alpha, double beta, cudaStream_t st);
+// The same two products in pair-float arithmetic on the FP32 units (operands and results FP64;
+// each product and sum carried as an unevaluated float pair, about 2^-47 relative to the sum of
+// the terms' magnitudes).  s = 16, 32, 64; other s run the FP64 kernels above.
+pf_status gram_df(int64_t D, int s, const double* X, int nbX, const double* Y, int nbY, double* C,
+                  double* scratch, size_t scratch_elems, cudaStream_t st);
+pf_status tsgemm_df(int64_t D, int s, const double* X, int nbX, const double* C, int ldc, double* Y, int nbY,
+                    double alpha, double beta, cudaStream_t st);
 // Column norms of R = A - B*diag(e) for nb blocks (norms[nb*s]); B may be NULL (then ||A||)
 pf_status colnorms(int64_t D, int s, const double* A, const double* B, const double* e, int nb, double* norms,
                    double* scratch, size_t scratch_elems, cudaStream_t st);

@@ -7,10 +7,14 @@
 //          memory; partial tiles are summed over chunks in a fixed order (deterministic).
 //  tsgemm  Y = beta Y + alpha X C, C of shape (nbX s) x (nbY s) row-major.  One CTA per
 //          (64-row tile, output block) streams the X blocks through shared memory.
+//  gram_df, tsgemm_df  the same products in pair-float arithmetic on the FP32 units: B300
+//          runs FP64 at 1/64 of the FP32 rate, and at s = 32 each basis entry feeds 32
+//          multiply-adds, so the FP64 kernels are bound by the FP64 pipe, not by memory.
 //  colnorms ||A[:,c] - e_c B[:,c]|| for every column of a blocked set.
 //  small_chol_inv / small_matmul  one-CTA Cholesky (with optional diagonal shift),
 //          triangular inverse and products for n <= 256.
 #include "common.cuh"
+#include "pairfloat.cuh"
 #include <cmath>
 
 namespace pf {
@@ -231,6 +235,165 @@ pf_status tsgemm(int64_t D, int s, const double* X, int nbX, const double* C, in
     case 64: return launch_tsgemm<64>(grid, st, D, X, nbX, C, ldc, Y, alpha, beta);
   }
   return PF_EINVAL;
+}
+
+// ------------------------------------------------------------------ pair-float gram / tsgemm
+// Each FP64 operand is split once, while it is staged in shared memory, into hi = rn(x) and
+// lo = rn(x - hi) (48 of its 53 bits).  A product accumulates by df_fma: the exact product of
+// the high parts (two_prod), the cross terms hi*lo and lo*hi, and a two_sum into the running
+// high part; the low parts collect in a float.  The result of a chain is the compensated dot
+// product of Ogita, Rump and Oishi (2005) with operands rounded to 48 bits.
+
+// gram_df: partial[chunk][bx][by][a][b] as in gram_partial.  256 threads as a 16 x 16 grid; a
+// thread owns the T x T outputs (ta + 16 i, tb + 16 j), T = S / 16.
+template <int S>
+__global__ void __launch_bounds__(GRAM_THREADS) gram_df_partial(int64_t D, const double* __restrict__ X, int nbX,
+                                                                const double* __restrict__ Y, int nbY,
+                                                                int64_t rows_per, double* __restrict__ part) {
+  constexpr int T = S / 16;
+  __shared__ df2 xs[GRAM_TR][S];
+  __shared__ df2 ys[GRAM_TR][S];
+  const int chunk = blockIdx.x, bx = blockIdx.y, by = blockIdx.z;
+  const double* Xb = X + (int64_t)bx * D * S;
+  const double* Yb = Y + (int64_t)by * D * S;
+  const int64_t r0 = (int64_t)chunk * rows_per;
+  int64_t r1 = r0 + rows_per;
+  if (r1 > D) r1 = D;
+  const int t = threadIdx.x, ta = t / 16, tb = t % 16;
+  df2 acc[T][T];
+#pragma unroll
+  for (int i = 0; i < T; ++i)
+#pragma unroll
+    for (int j = 0; j < T; ++j) acc[i][j] = df2(0.0f, 0.0f);
+  for (int64_t rt = r0; rt < r1; rt += GRAM_TR) {
+    const int nr = (int)((r1 - rt) < GRAM_TR ? (r1 - rt) : GRAM_TR);
+    for (int i = t; i < GRAM_TR * S; i += GRAM_THREADS) {
+      const int rr = i / S, cc = i % S;
+      double xv = 0.0, yv = 0.0;
+      if (rr < nr) {
+        xv = Xb[(rt + rr) * S + cc];
+        yv = Yb[(rt + rr) * S + cc];
+      }
+      xs[rr][cc] = df2(xv);
+      ys[rr][cc] = df2(yv);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int rr = 0; rr < GRAM_TR; ++rr) {
+      df2 xv[T], yv[T];
+#pragma unroll
+      for (int i = 0; i < T; ++i) xv[i] = xs[rr][ta + 16 * i];
+#pragma unroll
+      for (int j = 0; j < T; ++j) yv[j] = ys[rr][tb + 16 * j];
+#pragma unroll
+      for (int i = 0; i < T; ++i)
+#pragma unroll
+        for (int j = 0; j < T; ++j) acc[i][j] = df_fma(xv[i], yv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* P = part + (((int64_t)chunk * nbX + bx) * nbY + by) * (S * S);
+#pragma unroll
+  for (int i = 0; i < T; ++i)
+#pragma unroll
+    for (int j = 0; j < T; ++j) P[(ta + 16 * i) * S + tb + 16 * j] = (double)acc[i][j].hi + (double)acc[i][j].lo;
+}
+
+pf_status gram_df(int64_t D, int s, const double* X, int nbX, const double* Y, int nbY, double* C, double* scratch,
+                  size_t scratch_elems, cudaStream_t st) {
+  if (s != 16 && s != 32 && s != 64) return gram(D, s, X, nbX, Y, nbY, C, scratch, scratch_elems, st);
+  if (nbX < 1 || nbY < 1) return PF_EINVAL;
+  const int nchunk = gram_chunks(D, nbX, nbY);
+  if ((size_t)nchunk * nbX * nbY * s * s > scratch_elems) return PF_EINVAL;
+  if (nbX > 65535 || nbY > 65535) return PF_EINVAL;
+  const int64_t rows_per = ceil_div(D, nchunk);
+  dim3 grid(nchunk, nbX, nbY);
+  switch (s) {
+    case 16: gram_df_partial<16><<<grid, GRAM_THREADS, 0, st>>>(D, X, nbX, Y, nbY, rows_per, scratch); break;
+    case 32: gram_df_partial<32><<<grid, GRAM_THREADS, 0, st>>>(D, X, nbX, Y, nbY, rows_per, scratch); break;
+    default: gram_df_partial<64><<<grid, GRAM_THREADS, 0, st>>>(D, X, nbX, Y, nbY, rows_per, scratch); break;
+  }
+  PF_LAUNCH_CHECK("gram_df_partial");
+  const int64_t n = (int64_t)nbX * nbY * s * s;
+  gram_reduce<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(scratch, nchunk, nbX, nbY, s, C, nbY * s);
+  PF_LAUNCH_CHECK("gram_reduce");
+  return PF_OK;
+}
+
+// tsgemm_df: one CTA per (64-row tile, output block) as in tsgemm_kernel; thread t owns column
+// b = t % S of the rows t / S + i (256 / S).
+template <int S>
+__global__ void __launch_bounds__(TS_THREADS) tsgemm_df_kernel(int64_t D, const double* __restrict__ X, int nbX,
+                                                               const double* __restrict__ C, int ldc, double* Y,
+                                                               double alpha, double beta) {
+  constexpr int RSTEP = TS_THREADS / S;
+  constexpr int OPT = TS_TR / RSTEP;
+  extern __shared__ df2 tsd_smem[];
+  df2 (*xs)[S] = reinterpret_cast<df2 (*)[S]>(tsd_smem);
+  df2 (*cs)[S] = reinterpret_cast<df2 (*)[S]>(tsd_smem + TS_TR * S);
+  const int by = blockIdx.y;
+  const int64_t r0 = (int64_t)blockIdx.x * TS_TR;
+  const int t = threadIdx.x;
+  const int b = t % S, rbase = t / S;
+  df2 acc[OPT];
+#pragma unroll
+  for (int i = 0; i < OPT; ++i) acc[i] = df2(0.0f, 0.0f);
+  for (int bx = 0; bx < nbX; ++bx) {
+    const double* Xb = X + (int64_t)bx * D * S;
+    for (int i = t; i < TS_TR * S; i += TS_THREADS) {
+      const int rr = i / S, cc = i % S;
+      const int64_t r = r0 + rr;
+      xs[rr][cc] = df2(r < D ? Xb[r * S + cc] : 0.0);
+    }
+    for (int i = t; i < S * S; i += TS_THREADS) {
+      const int a = i / S, bb = i % S;
+      cs[a][bb] = df2(C[(int64_t)(bx * S + a) * ldc + by * S + bb]);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int a = 0; a < S; ++a) {
+      const df2 c = cs[a][b];
+#pragma unroll
+      for (int i = 0; i < OPT; ++i) acc[i] = df_fma(xs[rbase + i * RSTEP][a], c, acc[i]);
+    }
+    __syncthreads();
+  }
+  double* Yb = Y + (int64_t)by * D * S;
+#pragma unroll
+  for (int i = 0; i < OPT; ++i) {
+    const int64_t r = r0 + rbase + i * RSTEP;
+    if (r < D) {
+      const double y = beta != 0.0 ? beta * Yb[r * S + b] : 0.0;
+      Yb[r * S + b] = fma(alpha, (double)acc[i].hi + (double)acc[i].lo, y);
+    }
+  }
+}
+
+template <int S>
+static pf_status launch_tsgemm_df(dim3 grid, cudaStream_t st, int64_t D, const double* X, int nbX, const double* C,
+                                  int ldc, double* Y, double alpha, double beta) {
+  const int smem = (TS_TR * S + S * S) * (int)sizeof(df2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tsgemm_df_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) { set_cuda_error(e, "tsgemm_df smem attribute"); return PF_ECUDA; }
+    attr_set = true;
+  }
+  tsgemm_df_kernel<S><<<grid, TS_THREADS, smem, st>>>(D, X, nbX, C, ldc, Y, alpha, beta);
+  PF_LAUNCH_CHECK("tsgemm_df_kernel");
+  return PF_OK;
+}
+
+pf_status tsgemm_df(int64_t D, int s, const double* X, int nbX, const double* C, int ldc, double* Y, int nbY,
+                    double alpha, double beta, cudaStream_t st) {
+  if (s != 16 && s != 32 && s != 64) return tsgemm(D, s, X, nbX, C, ldc, Y, nbY, alpha, beta, st);
+  if (nbX < 1 || nbY < 1 || nbY > 65535) return PF_EINVAL;
+  dim3 grid((unsigned)ceil_div(D, TS_TR), nbY);
+  switch (s) {
+    case 16: return launch_tsgemm_df<16>(grid, st, D, X, nbX, C, ldc, Y, alpha, beta);
+    case 32: return launch_tsgemm_df<32>(grid, st, D, X, nbX, C, ldc, Y, alpha, beta);
+    default: return launch_tsgemm_df<64>(grid, st, D, X, nbX, C, ldc, Y, alpha, beta);
+  }
 }
 
 // ------------------------------------------------------------------ column norms

@@ -698,6 +698,8 @@ struct Task {
 
   // arithmetic of the refinement filter in the direct form (PF_DF64 or PF_F64)
   int refine_prec() const { return o.refine_precision; }
+  // Gram-Schmidt passes and Ritz-vector assembly in pair-float arithmetic (orth_precision)
+  bool orth_df() const { return o.orth_precision == PF_DF64 || (o.orth_precision == 0 && f32); }
   // refinement passes in the residual-correction form: asked for, or the default with the FP64
   // refinement arithmetic (an explicit pair-float request keeps the direct form); needs K >= 2
   bool corr_form() const {
@@ -732,6 +734,7 @@ struct Task {
     if (o.refine_precision != PF_F64 && o.refine_precision != PF_DF64) return PF_EINVAL;
     if (o.refine_form != 0 && o.refine_form != PF_REFINE_DIRECT && o.refine_form != PF_REFINE_CORRECTION)
       return PF_EINVAL;
+    if (o.orth_precision != 0 && o.orth_precision != PF_F64 && o.orth_precision != PF_DF64) return PF_EINVAL;
     if (o.block < 0) {   // the autotuner picks the block width
       if (!H->has_rescale) return PF_ESTATE;
       PF_TRY(autotune_block(H, o.precision, nev, stream, &s, nullptr, nullptr, refine_prec()));
@@ -839,8 +842,13 @@ struct Task {
     hl_store_kernel<<<1, 256, 0, st>>>(S.HL.as<double>(), S.Mcap, k, s, S.Ab, nullptr);
     PF_LAUNCH_CHECK("hl_store_kernel");
     for (int pass = 0; pass < 2; ++pass) {
-      PF_TRY(gram(D, s, S.V.as<double>(), k + 1, W, 1, S.Cg.as<double>(), S.gscr.as<double>(), S.gscr_elems, st));
-      PF_TRY(tsgemm(D, s, S.V.as<double>(), k + 1, S.Cg.as<double>(), s, W, 1, -1.0, 1.0, st));
+      if (orth_df()) {
+        PF_TRY(gram_df(D, s, S.V.as<double>(), k + 1, W, 1, S.Cg.as<double>(), S.gscr.as<double>(), S.gscr_elems, st));
+        PF_TRY(tsgemm_df(D, s, S.V.as<double>(), k + 1, S.Cg.as<double>(), s, W, 1, -1.0, 1.0, st));
+      } else {
+        PF_TRY(gram(D, s, S.V.as<double>(), k + 1, W, 1, S.Cg.as<double>(), S.gscr.as<double>(), S.gscr_elems, st));
+        PF_TRY(tsgemm(D, s, S.V.as<double>(), k + 1, S.Cg.as<double>(), s, W, 1, -1.0, 1.0, st));
+      }
     }
     clk->mark(2);
     // full: the basis spans the whole space, so B_{k+1} = 0 exactly.  cap: no room for
@@ -945,8 +953,8 @@ struct Task {
     PF_TRY(U.alloc((size_t)nb_total * H->D * s * 8, st));
     PF_TRY(HU.alloc((size_t)nb_total * H->D * s * 8, st));
     for (int b = 0; b < nb_total; ++b)
-      PF_TRY(tsgemm(H->D, s, S.V.as<double>(), R.blocks, S.Cg.as<double>() + b * s, qtot,
-                    U.as<double>() + (int64_t)b * H->D * s, 1, 1.0, 0.0, st));
+      PF_TRY((orth_df() ? tsgemm_df : tsgemm)(H->D, s, S.V.as<double>(), R.blocks, S.Cg.as<double>() + b * s, qtot,
+                                              U.as<double>() + (int64_t)b * H->D * s, 1, 1.0, 0.0, st));
     nb = qb;   // active Ritz blocks; blocks nb..nb_total-1 of U hold the reserve
     PF_TRY(rayleigh_ritz_H(S, U.as<double>(), HU.as<double>(), qb, E, res));
     sel = nearest_sel(E, lam, nev);
