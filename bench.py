@@ -243,7 +243,8 @@ def ncu_traffic(kernel_tag):
         if ":" in line:
             k, v = line.split(":", 1)
             fields[k.strip()] = v.strip()
-    if fields.get("source_sha256") != step_source_sha256() or "traffic_bytes_per_launch" not in fields:
+    if (fields.get("source_sha256", "").split() or [""])[0] != step_source_sha256() \
+            or "traffic_bytes_per_launch" not in fields:
         return None
     return float(fields["traffic_bytes_per_launch"].split()[0])
 
