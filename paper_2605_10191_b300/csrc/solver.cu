@@ -899,12 +899,21 @@ struct Task {
       }
       // Next check: every check_every block steps; with the default cadence, earlier when the
       // largest residual, extrapolated geometrically from the last two checks, reaches tol sooner
-      // (one step before the predicted block).  A block step at L = 20 costs ~4x a check.
+      // (one step before the predicted block).  A block step at L = 20 costs ~4x a check.  Where a
+      // check costs more than half the block steps between two checks (small sectors, many
+      // eigenpairs: XXZ L = 16, s = 16, nev = 200 checks at n ~ 400-1250 for 10-30 ms against ~1 ms
+      // per block), the next check moves to 3/4 of the extrapolated distance, or straight to the
+      // Krylov budget when the extrapolation lies beyond it.
       int step = check_every;
+      const double check_ms = clk->ms(4, 5);
+      const double block_ms = (S.rep.ms_filter_f32 + S.rep.ms_filter_f64 + S.rep.ms_orth + S.rep.ms_qr) / k;
       if (o.check_every <= 0 && prev_check_k > 0 && rmax < prev_check_r && rmax > tol) {
         const double rate = std::log(rmax / prev_check_r) / (double)(k - prev_check_k);
         const double need = std::log(tol / rmax) / rate;
         step = std::max(1, std::min(check_every, (int)std::ceil(need) - 1));
+        const int left = S.max_blocks - k;
+        if (need > check_every && check_ms > 0.5 * check_every * block_ms && left > check_every)
+          step = need >= left ? left : std::max(check_every, (int)(0.75 * need));
       }
       prev_check_k = k;
       prev_check_r = rmax;
