@@ -552,6 +552,21 @@ pf_status pf_autotune_block(pf_ham* H, int32_t precision, int32_t nev, int32_t* 
  * uniform = top 53 bits * 2^-53 (Steele, Lea & Flood 2014).  out: device double [D*s]. */
 pf_status pf_start_block(int64_t D, int32_t s, uint64_t seed, double* out, pf_stream_t stream);
 
+/* Selected eigenpairs of a dense real-symmetric matrix: the eigensolver the solve applies to the
+ * projected Lanczos matrix H_L at its convergence checks and its Ritz extraction (Sec. 4.6,
+ * Eq. blocklan_criterion).  Householder tridiagonalisation (one thread-block cluster up to n = 400,
+ * two launches per column over the GPU up to 1300, four above; the three forms give the same
+ * tridiagonal bit for bit), multisection with Sturm counts, inverse iteration (Gram-Schmidt within
+ * clusters closer than 1e-6 ||T||) and back-transformation, all FP64.
+ *   A: device, n x n row-major with leading dimension lda >= n; only (A + A^T) / 2 is used.
+ *   idx: host [q], indices into the ascending spectrum (0 = smallest), each in [0, n).
+ *   w: host [q], the eigenvalues of those indices.  Z: device, n x q, column k (leading dimension
+ *   ldz >= n) the unit eigenvector of w[k].  Allocates its workspace; synchronises the stream.
+ * Errors: PF_EINVAL (n < 1, q < 1, q > n, an index outside [0, n), lda or ldz < n, n > 25000),
+ * PF_ENOMEM, PF_ECUDA.                                                                     */
+pf_status pf_sym_eig_select(const double* A, int32_t lda, int32_t n, const int32_t* idx, int32_t q, double* w,
+                            double* Z, int32_t ldz, pf_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -118,6 +118,7 @@ PROTOTYPES = {
     "pf_polfed_solve": (i32, [vp, dbl, i32, i32, P(pf_solve_opts), P(dbl), vp, P(dbl), P(pf_report), vp]),
     "pf_polfed_solve_complex": (i32, [vp, dbl, i32, i32, P(pf_solve_opts), P(dbl), vp, P(dbl), P(pf_report), vp]),
     "pf_start_block": (i32, [i64, i32, u64, vp, vp]),
+    "pf_sym_eig_select": (i32, [vp, i32, i32, P(i32), i32, P(dbl), vp, i32, vp]),
     "pf_filter_apply_batch": (i32, [P(pf_filter_item), i32, i32, i32, i32, vp]),
     "pf_filter_tune": (i32, [vp, i32, i32, i32, i32, P(i32), P(dbl), vp]),
     "pf_polfed_solve_batch": (i32, [P(pf_solve_item), i32, vp]),

@@ -574,6 +574,23 @@ def filter_coefficients(lam_t, K, stream=None):
     return c
 
 
+def sym_eig_select(A, idx, stream=None):
+    """Eigenpairs of the symmetric n x n device matrix A (FP64) for the ascending-order indices idx
+    (pf_sym_eig_select, the H_L eigensolver): returns (w ndarray [q], Z tensor n x q)."""
+    n = A.shape[0]
+    if A.dtype != torch.float64 or not A.is_cuda or A.dim() != 2 or A.shape[1] != n:
+        raise ValueError("A must be a square float64 CUDA tensor")
+    A = A.contiguous()
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int32))
+    q = len(ix)
+    w = np.zeros(q)
+    Z = torch.empty((q, n), dtype=torch.float64, device="cuda")     # column k of the n x q result = row k
+    check(lib().pf_sym_eig_select(_ptr(A), n, n, ix.ctypes.data_as(C.POINTER(C.c_int32)), q,
+                                  w.ctypes.data_as(C.POINTER(C.c_double)), _ptr(Z), n, _stream(stream)),
+          "pf_sym_eig_select")
+    return w, Z.t()
+
+
 def start_block(D, s, seed, stream=None):
     out = torch.empty((D, s), dtype=torch.float64, device="cuda")
     check(lib().pf_start_block(int(D), int(s), C.c_uint64(seed), _ptr(out), _stream(stream)), "pf_start_block")

@@ -3,9 +3,9 @@
 // Used by the convergence checks (Eq. blocklan_criterion needs eigenvectors t_j of H_L)
 // and by the Rayleigh-Ritz steps.  Only selected eigenpairs are computed:
 //   1. Householder tridiagonalisation A = Q T Q^T (reflectors kept in A's columns): one
-//      thread-block-cluster launch for orders up to 400, above that four launches per column
-//      over the whole GPU: reflector, p = tau A22 v, w = p - (tau/2)(p.v) v, and the rank-2
-//      update A22 -= v w^T + w v^T of the full trailing block.
+//      thread-block-cluster launch for orders up to 400, up to 1300 two launches per column over
+//      the whole GPU (reflector and p = tau A22 v; w = p - (tau/2)(p.v) v and the rank-2 update
+//      A22 -= v w^T + w v^T of the full trailing block), above that four.
 //   2. Multisection with Sturm counts for each requested index (one warp, in a CTA of its
 //      own, per index).
 //   3. Inverse iteration on T - lambda I (tridiagonal LU with partial pivoting), one
@@ -118,6 +118,88 @@ __global__ void rank2_kernel(double* Aw, int n, int j, const double* p) {
   const double* w = p + n;
   double* a = Aw + (int64_t)(j + 1 + i) * n + j + 1 + l;
   *a -= v[l] * w[i] + w[l] * v[i];
+}
+
+// The same column step in two launches, for orders above the distributed-shared-memory kernel's
+// reach.  house_symv_kernel(j): every CTA forms the reflector of column j itself (the same block
+// sum as house_kernel, so the same bits in every CTA), its warps form p_i = tau A22[:, i] . v with v
+// read as x scaled on the fly, and CTA 0 stores d, e, tau and the scale and, first, finishes column
+// j - 1's stored reflector (x *= scale, x_0 = 1), which nothing reads any more.  wvec_rank2_kernel(j):
+// every CTA forms g = p . v (wvec_kernel's block sum) and applies the rank-2 update to its part of
+// A22 with w = p - (tau/2) g v.  Column j stays as it was until house_symv_kernel(j + 1) (or
+// tri_finish_kernel) scales it, so no CTA reads a column another CTA is rewriting.  The arithmetic,
+// operation for operation, is that of house/symv/wvec/rank2_kernel.
+__global__ void house_symv_kernel(double* Aw, int n, int j, double* d, double* e, double* tau, double* sc,
+                                  double* p) {
+  __shared__ double sh[32];
+  const int m = n - j - 1;
+  if (blockIdx.x == 0 && j > 0) {   // column j - 1's reflector: x *= scale, x_0 = 1 (as house_kernel)
+    const int mp = m + 1;
+    double* xp = Aw + (int64_t)(j - 1) * n + j;
+    const double scp = sc[j - 1];
+    for (int i = 1 + threadIdx.x; i < mp; i += blockDim.x) xp[i] *= scp;
+    if (threadIdx.x == 0) xp[0] = 1.0;
+  }
+  const double* x = Aw + (int64_t)j * n + j + 1;
+  double sig = 0.0;
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
+  sig = block_sum(sig, sh);
+  const double alpha = x[0];
+  double beta, t, scale;
+  if (sig == 0.0) {
+    beta = alpha;
+    t = 0.0;
+    scale = 0.0;
+  } else {
+    double nrm = sqrt(alpha * alpha + sig);
+    beta = alpha <= 0.0 ? nrm : -nrm;
+    t = (beta - alpha) / beta;
+    scale = 1.0 / (alpha - beta);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    d[j] = Aw[(int64_t)j * n + j];
+    e[j] = beta;
+    tau[j] = t;
+    sc[j] = scale;
+  }
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= m) return;
+  const double* col = Aw + (int64_t)(j + 1 + warp) * n + j + 1;
+  double s = 0.0;
+  for (int l = lane; l < m; l += 32) s = fma(col[l], l == 0 ? 1.0 : x[l] * scale, s);
+  s = warp_sum(s);
+  if (lane == 0) p[warp] = t * s;
+}
+
+// Column j's stored reflector after the last two-launch step (x *= scale, x_0 = 1).
+__global__ void reflector_store_kernel(double* Aw, int n, int j, const double* sc) {
+  const int m = n - j - 1;
+  double* x = Aw + (int64_t)j * n + j + 1;
+  const double scale = sc[j];
+  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] *= scale;
+  if (threadIdx.x == 0) x[0] = 1.0;
+}
+
+__global__ void wvec_rank2_kernel(double* Aw, int n, int j, const double* tau, const double* sc, const double* p) {
+  __shared__ double sh[32];
+  const int m = n - j - 1;
+  const double* x = Aw + (int64_t)j * n + j + 1;
+  const double scale = sc[j];
+  double g = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) g = fma(p[i], i == 0 ? 1.0 : x[i] * scale, g);
+  g = block_sum(g, sh);
+  const double c = 0.5 * tau[j] * g;
+  // grid-stride over the m x m entries: a few hundred CTAs, so that the redundant dot product
+  // above stays small next to the update
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)m * m;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / m), l = (int)(idx % m);
+    const double vi = i == 0 ? 1.0 : x[i] * scale, vl = l == 0 ? 1.0 : x[l] * scale;
+    const double wi = p[i] - c * vi, wl = p[l] - c * vl;
+    double* a = Aw + (int64_t)(j + 1 + i) * n + j + 1 + l;
+    *a -= vl * wi + wl * vi;
+  }
 }
 
 // The whole tridiagonalisation in one launch: one thread-block cluster of CS CTAs walks the
@@ -643,12 +725,29 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
   // distributed shared memory up to n = 512 (n = 224: 2.7 against 3.4 ms for the L2-staged cluster
   // form, 448: 7.1 against 9.1); at 640 the four launches per column over the whole GPU are faster
   // (13.4 against 14.3 ms)
-  const int dcs = n <= 512 ? tridiag_dsmem_cluster(n) : 0;
+  // two launches per column (house_symv + wvec_rank2, the same bits as the four below) from 400 to
+  // 1300: n = 448: 6.8 against 7.2 ms (DSMEM) and 9.0 (four launches); 640: 10.9 against 13.5;
+  // 900: 18.0 against 20.9; 1248: 31.4 against 32.2; at 1400 the four launches are ahead (38.6
+  // against 40.1) and at 320 the DSMEM kernel (4.2 against 4.5)
+  const int dcs = n <= 400 ? tridiag_dsmem_cluster(n) : 0;
   const int ccs = (dcs == 0 && n <= 400) ? tridiag_cluster_size() : 0;
   if (dcs > 0) {
     PF_TRY(tridiag_dsmem(Aw, n, d, e, tau, dcs, st));
   } else if (ccs > 0) {
     PF_TRY(tridiag_cluster(Aw, n, d, e, tau, p, ccs, st));
+  } else if (n <= 1300) {
+    double* sc = p + n;   // the reflectors' scales
+    for (int j = 0; j + 2 < n; ++j) {
+      const int m = n - j - 1;
+      house_symv_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Aw, n, j, d, e, tau, sc, p);
+      wvec_rank2_kernel<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)m * m, 256), 296), 256, 0, st>>>(Aw, n, j, tau,
+                                                                                                       sc, p);
+      PF_COUNT(2);
+    }
+    if (n >= 3) {
+      reflector_store_kernel<<<1, 256, 0, st>>>(Aw, n, n - 3, sc);
+      PF_COUNT(1);
+    }
   } else {
     for (int j = 0; j + 2 < n; ++j) {
       const int m = n - j - 1;
@@ -718,3 +817,19 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
 }
 
 }  // namespace pf
+
+using namespace pf;
+
+pf_status pf_sym_eig_select(const double* A, int32_t lda, int32_t n, const int32_t* idx, int32_t q, double* w,
+                            double* Z, int32_t ldz, pf_stream_t stream) {
+  if (!A || !idx || !w || !Z || n < 1 || n > 25000 || q < 1 || q > n || lda < n || ldz < n) return PF_EINVAL;
+  for (int i = 0; i < q; ++i)
+    if (idx[i] < 0 || idx[i] >= n) return PF_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = eig_workspace_bytes(n, q);
+  void* work = dev_alloc(bytes, st);
+  if (!work) return PF_ENOMEM;
+  const pf_status r = sym_eig_select(A, lda, n, idx, q, w, Z, ldz, work, bytes, st);
+  dev_free(work, st);
+  return r;
+}
