@@ -3,7 +3,7 @@ nearest the target).
 
 The stored sets (tests/golden/xxz_*.txt) are written by tests/golden/make_eigen_golden.py, which
 runs only the oracle: dense diagonalisation at L=16 (D = 12,870), and at L=20 (D = 184,756; the
-three realisations of the benchmark) the oracle's FP64 POLFED from an independent start block.
+benchmark's realisations) the oracle's FP64 POLFED from an independent start block.
 Each file lists more eigenvalues than a solve returns, by increasing distance from the oracle's
 lambda, so the test re-selects around the GPU's own lambda (the two lambdas differ only by the
 rounding of the extreme eigenvalues).
@@ -77,5 +77,21 @@ def test_xxz_L16_nev100_s32_against_dense(precision):
     H.spectral_bounds()
     K = H.choose_K(0.5, 100)
     res = H.solve(0.5, 100, K, block=32, precision=precision, return_vectors=False)
+    assert res.status == 0
+    check_against_golden(res.evals, res.resid, res.report["lambda_"], head, E, 100)
+
+
+@pytest.mark.parametrize("name,W,seed", [("xxz_L20_W3", 3.0, 2001)])
+def test_xxz_L20_benchmark_solve_against_oracle(name, W, seed):
+    """The benchmark's solve (XXZ L=20, D = 184,756, nev = 100, s = 32, FP32 filter with FP64 refinement)
+    against the oracle's FP64 POLFED set for the same realisation, found from an independent start
+    block with scalar Lanczos; the stored values are certified by the oracle's own residuals."""
+    import paper_2605_10191_b300 as pf
+    head, E, r = load_golden(name)
+    assert np.max(r) <= 1e-9
+    H = pf.Hamiltonian.from_params(pi.xxz_params(20, W=W, seed=seed))
+    H.spectral_bounds()
+    K = H.choose_K(0.5, 100)
+    res = H.solve(0.5, 100, K, block=32, precision="f32", return_vectors=False)
     assert res.status == 0
     check_against_golden(res.evals, res.resid, res.report["lambda_"], head, E, 100)
