@@ -81,7 +81,7 @@ def test_xxz_L16_nev100_s32_against_dense(precision):
     check_against_golden(res.evals, res.resid, res.report["lambda_"], head, E, 100)
 
 
-@pytest.mark.parametrize("name,W,seed", [("xxz_L20_W3", 3.0, 2001)])
+@pytest.mark.parametrize("name,W,seed", [("xxz_L20_W1", 1.0, 2000), ("xxz_L20_W3", 3.0, 2001)])
 def test_xxz_L20_benchmark_solve_against_oracle(name, W, seed):
     """The benchmark's solve (XXZ L=20, D = 184,756, nev = 100, s = 32, FP32 filter with FP64 refinement)
     against the oracle's FP64 POLFED set for the same realisation, found from an independent start
