@@ -12,7 +12,6 @@
 // fill pass produce the CSR arrays.  Diagonal sums use __dadd_rn/__dmul_rn so that no
 // multiply-add is contracted.
 #include "common.cuh"
-#include <algorithm>
 #include <cmath>
 
 namespace pf {
@@ -414,48 +413,6 @@ static pf_status exclusive_scan(const int64_t* in, int64_t n, int64_t* out, cuda
 // with L >= 3 no two bonds couple the same pair of states) and the open Hubbard chain (-t: a
 // nearest-neighbour hop has no site strictly between its ends, so its Jordan-Wigner sign is +1,
 // and an up hop and a down hop never reach the same state).
-// Reverse Cuthill-McKee order (Cuthill & McKee 1969; George 1971) of the graph on the n L-bit states
-// with k set bits (ascending, as the basis lists them) whose edges are open-chain nearest-neighbour
-// hops (bits i, i+1 differ).  Breadth-first search from a pseudo-peripheral state (the farthest one
-// found by two searches from the first), neighbours taken in increasing degree, then reversed.
-// perm[p] is the state visited p-th.  Used only as a traversal order of the sweep.
-static std::vector<int32_t> hop_graph_rcm(int L, int k) {
-  std::vector<uint32_t> st;
-  for (uint32_t x = 0; x < (1u << L); ++x)
-    if (__builtin_popcount(x) == k) st.push_back(x);
-  const int n = (int)st.size();
-  std::vector<std::vector<int>> adj(n);
-  for (int i = 0; i < n; ++i)
-    for (int b = 0; b + 1 < L; ++b)
-      if (((st[i] >> b) ^ (st[i] >> (b + 1))) & 1u) {
-        const uint32_t t = st[i] ^ (3u << b);
-        adj[i].push_back((int)(std::lower_bound(st.begin(), st.end(), t) - st.begin()));
-      }
-  auto bfs = [&](int root, std::vector<int>& order) {
-    std::vector<char> seen(n, 0);
-    order.clear();
-    order.push_back(root);
-    seen[root] = 1;
-    for (size_t h = 0; h < order.size(); ++h) {
-      std::vector<int> nb;
-      for (int v : adj[order[h]]) if (!seen[v]) { seen[v] = 1; nb.push_back(v); }
-      std::stable_sort(nb.begin(), nb.end(), [&](int a, int c) { return adj[a].size() < adj[c].size(); });
-      order.insert(order.end(), nb.begin(), nb.end());
-    }
-  };
-  std::vector<int> order;
-  int root = 0;
-  for (int it = 0; it < 2; ++it) { bfs(root, order); root = order.back(); }
-  bfs(root, order);
-  std::vector<int32_t> perm(n);
-  if ((int)order.size() != n) {   // the hop graph of a chain is connected; keep the identity otherwise
-    for (int i = 0; i < n; ++i) perm[i] = i;
-    return perm;
-  }
-  for (int p = 0; p < n; ++p) perm[p] = order[n - 1 - p];
-  return perm;
-}
-
 static bool structured_ok(const Ham* H) {
   if (H->Dc > 0) return false;   // the real embedding of a complex H has two off-diagonal values
   if (H->m.kind == PF_MODEL_QREM || H->m.kind == PF_MODEL_QSUN) return true;
@@ -643,26 +600,6 @@ static pf_status build_ham_impl(const Basis* b, const pf_model* m, const pf_para
   // lookups cost what the value array saves (34.9 against 34.7 us per FP32 step at N=3, L=15,
   // s=16), so it keeps the CSR unless asked
   H->mapping = (structured_ok(H) && m->kind != PF_MODEL_QSUN) ? PF_MAP_STRUCTURED : PF_MAP_CSR;
-  // open Hubbard chain: the sweep visits the slabs of D_dn rows (one up-spin state each) in reverse
-  // Cuthill-McKee order of the up-spin hopping graph (L = 12, 6 up: bandwidth 62 slabs against 252
-  // in rank order), so the slabs an up-spin hop reaches lie within ~30 MB of the sweep's position
-  if (structured_ok(H) && m->kind == PF_MODEL_HUBBARD && b->D_up > 1 && b->D_dn > 0) {
-    const std::vector<int32_t> perm = hop_graph_rcm(L, m->N_up);
-    if ((int64_t)perm.size() == b->D_up) {
-      H->slab_perm = (int32_t*)dev_alloc(perm.size() * sizeof(int32_t), st);
-      if (H->slab_perm) {
-        e = cudaMemcpyAsync(H->slab_perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the host vector goes out of scope
-        if (e != cudaSuccess) {
-          set_cuda_error(e, "slab order upload");
-          dev_free(H->slab_perm, st);
-          H->slab_perm = nullptr;
-        } else {
-          H->slab_rows = b->D_dn;
-        }
-      }
-    }
-  }
   if (m->kind == PF_MODEL_QSUN) {   // the value tables of the structured mapping
     H->qs_hdot = hdot;
     H->qs_coef = coef;
@@ -895,7 +832,6 @@ void pf_free_ham(pf_ham* hh) {
   dev_free(H->val_t, H->st);
   dev_free(H->val32, H->st);
   dev_free(H->val_df, H->st);
-  dev_free(H->slab_perm, H->st);
   dev_free(H->diag_t, H->st);
   dev_free(H->diag32, H->st);
   dev_free(H->diag_df, H->st);

@@ -282,8 +282,6 @@ template <typename T> struct ValSrc {
   const T* tab = nullptr;    // VS 2: the dot block of H~, 2^N x 2^N row-major
   const T* coef = nullptr;   // VS 2: the ray couplings of H~, [L]
   int L = 0, N = 0;          // VS 2: outer spins (bits 0..L-1) and dot spins (the bits above)
-  const int32_t* perm = nullptr;   // sweep order: slab perm[p] of slab rows is the p-th visited
-  int64_t slab = 0;
 };
 template <typename T, int S, bool L2ONLY, int SP, int B2M, int VS>
 __device__ __forceinline__ void clenshaw_row_vs(int64_t row, int lane, const int64_t* __restrict__ rp,
@@ -494,10 +492,8 @@ __global__ void __launch_bounds__(256, step_min_blocks<T>()) cstruct_step_kernel
   const int lane = (int)(threadIdx.x % G);
   if (rows_per_cta < 0) {
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x / G);
-    for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; g < D; g += groups) {
-      const int64_t row = vsrc.perm ? (int64_t)__ldg(vsrc.perm + g / vsrc.slab) * vsrc.slab + g % vsrc.slab : g;
+    for (int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G; row < D; row += groups)
       clenshaw_row_vs<T, S, false, SP, B2M, VS>(row, lane, rp, col, nullptr, V, B1, B2, out, a, alpha, beta, vsrc, acol);
-    }
   } else {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / G;
     if (row < D)
@@ -720,7 +716,6 @@ pf_status ham_step(const Ham* H, int prec, int s, const void* V, const void* B1,
     ValSrc<float> vs;
     vs.diag = H->diag32; vs.g = (float)H->off_t; vs.tab = H->qtab32; vs.coef = H->qtab32 ? H->qtab32 + H->qtab_n : nullptr;
     vs.L = L; vs.N = N;
-    vs.perm = H->slab_perm; vs.slab = H->slab_rows;
     return launch_structured<float>(H, s, vs, (const float*)V, (const float*)B1, (const float*)B2, (float*)out,
                                     (float)a, (float)alpha, (float)beta, st, cta_cap, (const float*)acol);
   }

@@ -123,11 +123,6 @@ struct Ham {
   float* qtab32 = nullptr;
   float2* qtab_df = nullptr;
   int qtab_n = 0;
-  // open Hubbard chain, structured FP32 step: the order in which the sweep visits the slabs of
-  // D_dn rows that share an up-spin state (a reverse Cuthill-McKee order of the up-spin hopping
-  // graph), so the slabs an up-spin hop reaches stay within a short window of the sweep
-  int32_t* slab_perm = nullptr;   // device [D / slab_rows]
-  int64_t slab_rows = 0;
   int has_rescale = 0, has_bounds = 0;
   double Ec = 0, dE = 1, emin = 0, emax = 0, rmin = 0, rmax = 0, hnorm = 0;
   cudaStream_t st = 0;
