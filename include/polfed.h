@@ -351,8 +351,9 @@ typedef struct {
                              and the residual check stay FP64 either way               */
   int32_t refine_form;    /* pf_refine_form of the refinement passes; 0 = the default,
                              PF_REFINE_CORRECTION                                      */
-  int32_t orth_precision; /* arithmetic of the Lanczos stage's two Gram-Schmidt passes
-                             and of the Ritz-vector assembly: PF_F64, or PF_DF64 (pair-
+  int32_t orth_precision; /* arithmetic of the Lanczos stage's two Gram-Schmidt passes,
+                             its Cholesky QR products and the Ritz-vector assembly:
+                             PF_F64, or PF_DF64 (pair-
                              float on the FP32 units, operands and results FP64, about
                              2^-47 relative to the terms' magnitudes; B300 runs FP64 at
                              1/64 of the FP32 rate); 0 = PF_DF64 with the PF_F32 filter,

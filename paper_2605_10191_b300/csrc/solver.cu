@@ -196,6 +196,7 @@ struct Solver {
   int* stat;
   pf_report rep;
   cudaEvent_t ev[2];
+  bool df = false;   // Cholesky QR's Gram product and update in pair-float (the FP32 path)
 };
 
 static pf_status solver_init(Solver& S, const Ham* H, int s, int max_blocks, int qmax, bool f32, cudaStream_t st) {
@@ -256,9 +257,9 @@ static pf_status chol_qr3(Solver& S, double* X, double* Q) {
   double* Rs[3] = {S.R1, S.R2, S.R3};
   double* src = X;
   for (int pass = 0; pass < 3; ++pass) {
-    PF_TRY(gram(S.D, s, src, 1, src, 1, S.Gb, S.gscr.as<double>(), S.gscr_elems, S.st));
+    PF_TRY((S.df ? gram_df : gram)(S.D, s, src, 1, src, 1, S.Gb, S.gscr.as<double>(), S.gscr_elems, S.st));
     PF_TRY(small_chol_inv(S.Gb, s, pass == 0 ? shift : 0.0, Rs[pass], S.Rib, S.stat, S.st));
-    PF_TRY(tsgemm(S.D, s, src, 1, S.Rib, s, S.tmp.as<double>(), 1, 1.0, 0.0, S.st));
+    PF_TRY((S.df ? tsgemm_df : tsgemm)(S.D, s, src, 1, S.Rib, s, S.tmp.as<double>(), 1, 1.0, 0.0, S.st));
     PF_CUDA(cudaMemcpyAsync(Q, S.tmp.p, (size_t)S.D * s * 8, cudaMemcpyDeviceToDevice, S.st));
     src = Q;
     int bad = 0;
@@ -769,6 +770,7 @@ struct Task {
     PF_CUDA(cudaEventRecord(t_begin, st));
     clk = new PhaseClock(st);
     PF_TRY(solver_init(S, H, s, max_blocks, std::max(qpad + q_reserve, nev_g), f32, st));
+    S.df = orth_df();
     coeffs.resize(K + 1);
     PF_TRY(filter_coefficients_dev(lam_t, K, coeffs.data(), st));
     PF_TRY(coeff_dev.alloc((size_t)(K + 1) * 8, st));
