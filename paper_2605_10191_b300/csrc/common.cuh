@@ -275,6 +275,10 @@ pf_status gram_df(int64_t D, int s, const double* X, int nbX, const double* Y, i
                   double* scratch, size_t scratch_elems, cudaStream_t st);
 pf_status tsgemm_df(int64_t D, int s, const double* X, int nbX, const double* C, int ldc, double* Y, int nbY,
                     double alpha, double beta, cudaStream_t st);
+// gram_df with Y already split into (hi, lo) float pairs by convert_d2df (s = 16, 32, 64 only):
+// the same result, with the Y blocks split once instead of once per X block.
+pf_status gram_df_ysplit(int64_t D, int s, const double* X, int nbX, const float2* Y, int nbY, double* C,
+                         double* scratch, size_t scratch_elems, cudaStream_t st);
 // Column norms of R = A - B*diag(e) for nb blocks (norms[nb*s]); B may be NULL (then ||A||)
 pf_status colnorms(int64_t D, int s, const double* A, const double* B, const double* e, int nb, double* norms,
                    double* scratch, size_t scratch_elems, cudaStream_t st);

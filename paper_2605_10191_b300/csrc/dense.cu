@@ -246,16 +246,21 @@ pf_status tsgemm(int64_t D, int s, const double* X, int nbX, const double* C, in
 
 // gram_df: partial[chunk][bx][by][a][b] as in gram_partial.  256 threads as a 16 x 16 grid; a
 // thread owns the T x T outputs (ta + 16 i, tb + 16 j), T = S / 16.
-template <int S>
+__device__ __forceinline__ df2 as_df(double x) { return df2(x); }
+__device__ __forceinline__ df2 as_df(float2 x) { return df2(x.x, x.y); }
+
+// TY = float2: Y given already split (hi, lo), as d2df_kernel splits it (the same pairs as
+// splitting here), so a Y block shared by every bx is split once, not once per CTA.
+template <int S, typename TY>
 __global__ void __launch_bounds__(GRAM_THREADS) gram_df_partial(int64_t D, const double* __restrict__ X, int nbX,
-                                                                const double* __restrict__ Y, int nbY,
+                                                                const TY* __restrict__ Y, int nbY,
                                                                 int64_t rows_per, double* __restrict__ part) {
   constexpr int T = S / 16;
   __shared__ df2 xs[GRAM_TR][S];
   __shared__ df2 ys[GRAM_TR][S];
   const int chunk = blockIdx.x, bx = blockIdx.y, by = blockIdx.z;
   const double* Xb = X + (int64_t)bx * D * S;
-  const double* Yb = Y + (int64_t)by * D * S;
+  const TY* Yb = Y + (int64_t)by * D * S;
   const int64_t r0 = (int64_t)chunk * rows_per;
   int64_t r1 = r0 + rows_per;
   if (r1 > D) r1 = D;
@@ -269,13 +274,14 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_df_partial(int64_t D, const
     const int nr = (int)((r1 - rt) < GRAM_TR ? (r1 - rt) : GRAM_TR);
     for (int i = t; i < GRAM_TR * S; i += GRAM_THREADS) {
       const int rr = i / S, cc = i % S;
-      double xv = 0.0, yv = 0.0;
+      double xv = 0.0;
+      TY yv{};
       if (rr < nr) {
         xv = Xb[(rt + rr) * S + cc];
         yv = Yb[(rt + rr) * S + cc];
       }
       xs[rr][cc] = df2(xv);
-      ys[rr][cc] = df2(yv);
+      ys[rr][cc] = as_df(yv);
     }
     __syncthreads();
 #pragma unroll 4
@@ -299,9 +305,9 @@ __global__ void __launch_bounds__(GRAM_THREADS) gram_df_partial(int64_t D, const
     for (int j = 0; j < T; ++j) P[(ta + 16 * i) * S + tb + 16 * j] = (double)acc[i][j].hi + (double)acc[i][j].lo;
 }
 
-pf_status gram_df(int64_t D, int s, const double* X, int nbX, const double* Y, int nbY, double* C, double* scratch,
-                  size_t scratch_elems, cudaStream_t st) {
-  if (s != 16 && s != 32 && s != 64) return gram(D, s, X, nbX, Y, nbY, C, scratch, scratch_elems, st);
+template <typename TY>
+static pf_status gram_df_any(int64_t D, int s, const double* X, int nbX, const TY* Y, int nbY, double* C,
+                             double* scratch, size_t scratch_elems, cudaStream_t st) {
   if (nbX < 1 || nbY < 1) return PF_EINVAL;
   const int nchunk = gram_chunks(D, nbX, nbY);
   if ((size_t)nchunk * nbX * nbY * s * s > scratch_elems) return PF_EINVAL;
@@ -309,15 +315,27 @@ pf_status gram_df(int64_t D, int s, const double* X, int nbX, const double* Y, i
   const int64_t rows_per = ceil_div(D, nchunk);
   dim3 grid(nchunk, nbX, nbY);
   switch (s) {
-    case 16: gram_df_partial<16><<<grid, GRAM_THREADS, 0, st>>>(D, X, nbX, Y, nbY, rows_per, scratch); break;
-    case 32: gram_df_partial<32><<<grid, GRAM_THREADS, 0, st>>>(D, X, nbX, Y, nbY, rows_per, scratch); break;
-    default: gram_df_partial<64><<<grid, GRAM_THREADS, 0, st>>>(D, X, nbX, Y, nbY, rows_per, scratch); break;
+    case 16: gram_df_partial<16, TY><<<grid, GRAM_THREADS, 0, st>>>(D, X, nbX, Y, nbY, rows_per, scratch); break;
+    case 32: gram_df_partial<32, TY><<<grid, GRAM_THREADS, 0, st>>>(D, X, nbX, Y, nbY, rows_per, scratch); break;
+    case 64: gram_df_partial<64, TY><<<grid, GRAM_THREADS, 0, st>>>(D, X, nbX, Y, nbY, rows_per, scratch); break;
+    default: return PF_EINVAL;
   }
   PF_LAUNCH_CHECK("gram_df_partial");
   const int64_t n = (int64_t)nbX * nbY * s * s;
   gram_reduce<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(scratch, nchunk, nbX, nbY, s, C, nbY * s);
   PF_LAUNCH_CHECK("gram_reduce");
   return PF_OK;
+}
+
+pf_status gram_df(int64_t D, int s, const double* X, int nbX, const double* Y, int nbY, double* C, double* scratch,
+                  size_t scratch_elems, cudaStream_t st) {
+  if (s != 16 && s != 32 && s != 64) return gram(D, s, X, nbX, Y, nbY, C, scratch, scratch_elems, st);
+  return gram_df_any<double>(D, s, X, nbX, Y, nbY, C, scratch, scratch_elems, st);
+}
+
+pf_status gram_df_ysplit(int64_t D, int s, const double* X, int nbX, const float2* Y, int nbY, double* C,
+                         double* scratch, size_t scratch_elems, cudaStream_t st) {
+  return gram_df_any<float2>(D, s, X, nbX, Y, nbY, C, scratch, scratch_elems, st);
 }
 
 // tsgemm_df: one CTA per (64-row tile, output block) as in tsgemm_kernel; thread t owns column

@@ -844,7 +844,14 @@ struct Task {
     hl_store_kernel<<<1, 256, 0, st>>>(S.HL.as<double>(), S.Mcap, k, s, S.Ab, nullptr);
     PF_LAUNCH_CHECK("hl_store_kernel");
     for (int pass = 0; pass < 2; ++pass) {
-      if (orth_df()) {
+      if (orth_df() && (s == 16 || s == 32 || s == 64)) {
+        // W split into float pairs once (into tmp, free until the QR), shared by every basis block
+        float2* W2 = reinterpret_cast<float2*>(S.tmp.p);
+        PF_TRY(convert_d2df(W, W2, D * s, st));
+        PF_TRY(gram_df_ysplit(D, s, S.V.as<double>(), k + 1, W2, 1, S.Cg.as<double>(), S.gscr.as<double>(),
+                              S.gscr_elems, st));
+        PF_TRY(tsgemm_df(D, s, S.V.as<double>(), k + 1, S.Cg.as<double>(), s, W, 1, -1.0, 1.0, st));
+      } else if (orth_df()) {
         PF_TRY(gram_df(D, s, S.V.as<double>(), k + 1, W, 1, S.Cg.as<double>(), S.gscr.as<double>(), S.gscr_elems, st));
         PF_TRY(tsgemm_df(D, s, S.V.as<double>(), k + 1, S.Cg.as<double>(), s, W, 1, -1.0, 1.0, st));
       } else {
