@@ -258,15 +258,17 @@ static pf_status chol_qr3(Solver& S, double* X, double* Q) {
   double* src = X;
   for (int pass = 0; pass < 3; ++pass) {
     PF_TRY((S.df ? gram_df : gram)(S.D, s, src, 1, src, 1, S.Gb, S.gscr.as<double>(), S.gscr_elems, S.st));
-    PF_TRY(small_chol_inv(S.Gb, s, pass == 0 ? shift : 0.0, Rs[pass], S.Rib, S.stat, S.st));
+    PF_TRY(small_chol_inv(S.Gb, s, pass == 0 ? shift : 0.0, Rs[pass], S.Rib, S.stat + pass, S.st));
     PF_TRY((S.df ? tsgemm_df : tsgemm)(S.D, s, src, 1, S.Rib, s, S.tmp.as<double>(), 1, 1.0, 0.0, S.st));
     PF_CUDA(cudaMemcpyAsync(Q, S.tmp.p, (size_t)S.D * s * 8, cudaMemcpyDeviceToDevice, S.st));
     src = Q;
-    int bad = 0;
-    PF_CUDA(cudaMemcpyAsync(&bad, S.stat, sizeof(int), cudaMemcpyDeviceToHost, S.st));
-    PF_CUDA(cudaStreamSynchronize(S.st));
-    if (bad) return PF_EBREAKDOWN;
   }
+  // one read of the three passes' status words (a failed pass substitutes 1 for a non-positive
+  // pivot, so the later passes run on finite values; Q and R are then discarded by the caller)
+  int bad[3] = {0, 0, 0};
+  PF_CUDA(cudaMemcpyAsync(bad, S.stat, sizeof(bad), cudaMemcpyDeviceToHost, S.st));
+  PF_CUDA(cudaStreamSynchronize(S.st));
+  if (bad[0] || bad[1] || bad[2]) return PF_EBREAKDOWN;
   // R = R3 R2 R1
   PF_TRY(small_matmul(S.R3, S.R2, S.T1, s, S.st));
   PF_TRY(small_matmul(S.T1, S.R1, S.Bb, s, S.st));
@@ -326,6 +328,8 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
   const int64_t D = S.D;
   PhaseClock clk(S.st);
   int k = 0;
+  int next_check = check_first, prev_k = 0;
+  double prev_r = 0.0;
   for (;;) {
     double* Vk = blockp(S, k);
     double* W = S.W.as<double>();
@@ -368,7 +372,7 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
     const int M = k * s;
     const bool last = (k + 1 > S.max_blocks) || exhausted;
     const bool enough = (select == 0 ? M >= 2 : M >= q) && M >= min_M;
-    const bool at_check = (k >= check_first && ((k - check_first) % check_every == 0)) || last;
+    const bool at_check = k >= next_check || last;
     if (enough && at_check) {
       std::vector<int> idx;
       if (select == 0) {
@@ -392,7 +396,11 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
       double scale = 1.0;
       if (tol_relative) scale = std::max(std::fabs(th.front()), std::fabs(th.back()));
       bool ok = true;
-      for (int i = 0; i < nq; ++i) ok = ok && (res[i] <= tol * scale);
+      double rmax = 0.0;
+      for (int i = 0; i < nq; ++i) {
+        ok = ok && (res[i] <= tol * scale);
+        rmax = std::max(rmax, res[i] / scale);
+      }
       if (ok || last) {
         out.blocks = k;
         out.converged = ok || full;
@@ -401,6 +409,24 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
         out.resid = res;
         break;
       }
+      // next check: every check_every blocks; earlier when the largest residual, extrapolated
+      // geometrically from the last two checks, reaches tol sooner; where a check costs more than
+      // half the block steps between two checks (the spectral-bounds Lanczos on H: a block step
+      // is one SpMM with s = 4), at 3/4 of the extrapolated distance or at the budget
+      int step = check_every;
+      if (prev_k > 0 && rmax < prev_r && rmax > tol) {
+        const double rate = std::log(rmax / prev_r) / (double)(k - prev_k);
+        const double need = std::log(tol / rmax) / rate;
+        step = std::max(1, std::min(check_every, (int)std::ceil(need) - 1));
+        const double check_ms = clk.ms(4, 5);
+        const double block_ms = (S.rep.ms_filter_f32 + S.rep.ms_filter_f64 + S.rep.ms_orth + S.rep.ms_qr) / k;
+        const int left = S.max_blocks - k;
+        if (need > check_every && check_ms > 0.5 * check_every * block_ms && left > check_every)
+          step = need >= left ? left : std::max(check_every, (int)(0.75 * need));
+      }
+      prev_k = k;
+      prev_r = rmax;
+      next_check = k + step;
     }
     if (last) {
       out.blocks = k;
@@ -411,8 +437,74 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
   return PF_OK;
 }
 
+// Dense copy of H (row-major D x D) from the CSR, FP64; A zeroed beforehand.
+__global__ void csr_to_dense_kernel(int64_t D, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                    const double* __restrict__ val, double* A) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= D) return;
+  for (int64_t j = rp[r]; j < rp[r + 1]; ++j) A[r * D + col[j]] += val[j];
+}
+
+// ||H z_c - w_c z_c|| for the columns z_c of Z (column-major, D x q), one CTA per column.
+__global__ void csr_resid_kernel(int64_t D, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                 const double* __restrict__ val, const double* __restrict__ Z, const double* w,
+                                 double* res) {
+  __shared__ double sh[32];
+  const int c = blockIdx.x;
+  const double* z = Z + (int64_t)c * D;
+  double acc = 0.0;
+  for (int64_t r = threadIdx.x; r < D; r += blockDim.x) {
+    double h = 0.0;
+    for (int64_t j = rp[r]; j < rp[r + 1]; ++j) h = fma(val[j], z[col[j]], h);
+    const double d = h - w[c] * z[r];
+    acc = fma(d, d, acc);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) res[c] = sqrt(acc);
+}
+
+// The extremes of a small H (D <= 400) from its dense form: one call of the H_L eigensolver (the
+// thread-block-cluster tridiagonalisation) in place of a block Lanczos whose ~20 block steps and
+// checks each cost launch latency (XXZ L = 10, D = 252: ~12 ms).  The residuals are computed from
+// the CSR.
+static pf_status spectral_bounds_dense(Ham* H, cudaStream_t st) {
+  const int64_t D = H->D;
+  DevBuf A, work, Z, wr;
+  PF_TRY(A.alloc((size_t)D * D * 8, st));
+  PF_CUDA(cudaMemsetAsync(A.p, 0, (size_t)D * D * 8, st));
+  csr_to_dense_kernel<<<(unsigned)ceil_div(D, 128), 128, 0, st>>>(D, H->row_ptr, H->col, H->val, A.as<double>());
+  PF_LAUNCH_CHECK("csr_to_dense_kernel");
+  const size_t wb = eig_workspace_bytes((int)D, 2);
+  PF_TRY(work.alloc(wb, st));
+  PF_TRY(Z.alloc((size_t)D * 2 * 8, st));
+  PF_TRY(wr.alloc(4 * 8, st));
+  const int idx[2] = {0, (int)D - 1};
+  double w[2] = {0, 0}, res[2] = {0, 0};
+  PF_TRY(sym_eig_select(A.as<double>(), (int)D, (int)D, idx, 2, w, Z.as<double>(), (int)D, work.p, wb, st));
+  PF_CUDA(cudaMemcpyAsync(wr.as<double>(), w, sizeof(w), cudaMemcpyHostToDevice, st));
+  csr_resid_kernel<<<2, 256, 0, st>>>(D, H->row_ptr, H->col, H->val, Z.as<double>(), wr.as<double>(),
+                                       wr.as<double>() + 2);
+  PF_LAUNCH_CHECK("csr_resid_kernel");
+  PF_CUDA(cudaMemcpyAsync(res, wr.as<double>() + 2, sizeof(res), cudaMemcpyDeviceToHost, st));
+  PF_CUDA(cudaStreamSynchronize(st));
+  H->emin = w[0];
+  H->emax = w[1];
+  H->rmin = res[0];
+  H->rmax = res[1];
+  return PF_OK;
+}
+
 static pf_status spectral_bounds_impl(Ham* H, double tol, cudaStream_t st) {
   if (tol <= 0) tol = 1e-10;
+  if (H->D >= 4 && H->D <= 400) {
+    PF_TRY(spectral_bounds_dense(H, st));
+    H->hnorm = std::max(std::fabs(H->emin), std::fabs(H->emax));
+    H->has_bounds = 1;
+    const double de0 = 0.5 * (H->emax - H->emin);
+    const double lo = H->emin - H->rmin - 1e-3 * de0;
+    const double hi = H->emax + H->rmax + 1e-3 * de0;
+    return set_rescale(H, 0.5 * (hi + lo), 0.5 * (hi - lo), st);
+  }
   // Block width 4 (resolves extremal multiplicities up to 4).  When the whole space fits in
   // the Krylov budget (D <= 600), the width is a power of two dividing D, so the last block
   // completes the space and the extremes are then exact.

@@ -30,6 +30,9 @@ def _dense(p):
 
 
 @pytest.mark.parametrize("mk", [lambda: pi.xxz_params(12, W=2.0, seed=1001),
+                                lambda: pi.xxz_params(10, W=2.0, seed=1002),        # D = 252: the dense path
+                                lambda: pi.xxz_params(4, N=1, W=1.0, seed=1003),    # D = 4
+                                lambda: pi.xxz_params(8, N=4, W=1.5, seed=1004),    # D = 70
                                 lambda: pi.qsun_params(N=3, L=7, seed=3001),
                                 lambda: pi.hubbard_params(6, 3, 3, U=1.0, W=4.0, seed=4001)])
 def test_spectral_bounds_vs_dense(pf, mk):
