@@ -211,13 +211,14 @@ def refine_desc(args):
         return "pair-float (FP32 hi+lo) refinement filter, direct form"
     if args.refine_form == "direct":
         return "FP64 refinement filter, direct form"
-    return ("FP64 refinement in residual-correction form (FP64 residuals, Ritz values, P(theta), updates; "
-            "FP32 recurrence on the residuals)")
+    return ("refinement in residual-correction form (FP64 residuals, Ritz values, P(theta), updates; "
+            "FP32 recurrence on the residuals; Rayleigh-Ritz Gram and rotation products in pair-float)")
 
 
 def dtype_name(args):
-    """Arithmetic of the path: FP32 filter, pair-float (f32x2) Lanczos Gram-Schmidt and Ritz-vector
-    assembly, FP64 Lanczos coefficients, Rayleigh-Ritz and refinement; or FP64 throughout."""
+    """Arithmetic of the path: FP32 filter, pair-float (f32x2) dense tall-skinny products
+    (Gram-Schmidt, Cholesky QR, Ritz vectors, Rayleigh-Ritz), FP64 SpMMs, residuals and small
+    factorisations; or FP64 throughout."""
     if getattr(args, "precision", "f32") != "f32":
         return "f64"
     return "f32+f32x2+f64"
@@ -650,8 +651,9 @@ def run_ours(args):
         "dtype": dtype_name(args), "data": "synthetic",
         "config": {"workload": WORKLOAD, "model": f"XXZ L={L_SITES} periodic, J=1, Delta=1, h_i~U[-W,W], W in (1,3,5)",
                    "D": D, "nnz": nnz, "nev": NEV, "block": BLOCK, "target_eps": EPS,
-                   "precision": (f"FP32 filter + pair-float Lanczos Gram-Schmidt and Ritz-vector assembly "
-                                 f"+ FP64 Lanczos coefficients/Rayleigh-Ritz + " + refine_desc(args)
+                   "precision": (f"FP32 filter + pair-float dense tall-skinny products (Gram-Schmidt, Cholesky QR, "
+                                 f"Ritz vectors, Rayleigh-Ritz) + FP64 Lanczos coefficients, SpMMs, residuals + "
+                                 + refine_desc(args)
                                  if args.precision == "f32" else "FP64 throughout"),
                    "K": [x["K"] for x in rec], "realisation_W": [x["W"] for x in rec],
                    "krylov_blocks": [x["rep"]["blocks"] for x in rec],

@@ -351,8 +351,12 @@ typedef struct {
                              and the residual check stay FP64 either way               */
   int32_t refine_form;    /* pf_refine_form of the refinement passes; 0 = the default,
                              PF_REFINE_CORRECTION                                      */
-  int32_t orth_precision; /* arithmetic of the Lanczos stage's two Gram-Schmidt passes,
-                             its Cholesky QR products and the Ritz-vector assembly:
+  int32_t orth_precision; /* arithmetic of the dense tall-skinny products: the Lanczos
+                             stage's two Gram-Schmidt passes, its Cholesky QR products,
+                             the Ritz-vector assembly, and the Gram and rotation products
+                             of the Rayleigh-Ritz in H and of the refinement's
+                             orthonormalisation (SpMMs, residuals, the s x s and q x q
+                             factorisations and eigensolves stay FP64):
                              PF_F64, or PF_DF64 (pair-
                              float on the FP32 units, operands and results FP64, about
                              2^-47 relative to the terms' magnitudes; B300 runs FP64 at

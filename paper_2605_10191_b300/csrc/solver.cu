@@ -561,7 +561,7 @@ static pf_status rayleigh_ritz_H(Solver& S, double* U, double* HU, int nb, std::
   }
   DevBuf G;
   PF_TRY(G.alloc((size_t)q * q * 8, S.st));
-  PF_TRY(gram(D, s, U, nb, HU, nb, G.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
+  PF_TRY((S.df ? gram_df : gram)(D, s, U, nb, HU, nb, G.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
   std::vector<int> idx(q);
   std::iota(idx.begin(), idx.end(), 0);
   E.assign(q, 0.0);
@@ -581,7 +581,7 @@ static pf_status rayleigh_ritz_H(Solver& S, double* U, double* HU, int nb, std::
   PF_LAUNCH_CHECK("z_to_rowmajor_kernel");
   // U2 = U C into HU's storage, then copy back; HU recomputed from U2
   for (int b = 0; b < nb; ++b)
-    PF_TRY(tsgemm(D, s, U, nb, Cr.as<double>() + b * s, q, HU + (int64_t)b * D * s, 1,
+    PF_TRY((S.df ? tsgemm_df : tsgemm)(D, s, U, nb, Cr.as<double>() + b * s, q, HU + (int64_t)b * D * s, 1,
                   1.0, 0.0, S.st));
   PF_CUDA(cudaMemcpyAsync(U, HU, (size_t)nb * D * s * 8, cudaMemcpyDeviceToDevice, S.st));
   for (int b = 0; b < nb; ++b) {
@@ -613,11 +613,11 @@ static pf_status orthonormalise_set(Solver& S, double* U, double* T, int nb) {
   PF_TRY(st.alloc(16, S.st));
   const double u = 1.1102230246251565e-16;
   for (int pass = 0; pass < 2; ++pass) {
-    PF_TRY(gram(D, s, U, nb, U, nb, G.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
+    PF_TRY((S.df ? gram_df : gram)(D, s, U, nb, U, nb, G.as<double>(), S.gscr.as<double>(), S.gscr_elems, S.st));
     const double shift = pass == 0 ? 11.0 * ((double)D * q + (double)q * (q + 1)) * u : 0.0;
     PF_TRY(small_chol_inv(G.as<double>(), q, shift, R.as<double>(), Ri.as<double>(), st.as<int>(), S.st));
     for (int b = 0; b < nb; ++b)
-      PF_TRY(tsgemm(D, s, U, nb, Ri.as<double>() + b * s, q, T + (int64_t)b * D * s, 1, 1.0,
+      PF_TRY((S.df ? tsgemm_df : tsgemm)(D, s, U, nb, Ri.as<double>() + b * s, q, T + (int64_t)b * D * s, 1, 1.0,
                     0.0, S.st));
     PF_CUDA(cudaMemcpyAsync(U, T, (size_t)nb * D * s * 8, cudaMemcpyDeviceToDevice, S.st));
     int bad = 0;
@@ -1253,9 +1253,9 @@ struct Task {
       DevBuf Cl;
       PF_TRY(Cl.alloc((size_t)Lb * s * na * s * 8, st));
       for (int pass = 0; pass < 2; ++pass) {
-        PF_TRY(gram(H->D, s, Ud, Lb, Wd, na, Cl.as<double>(), S.gscr.as<double>(), S.gscr_elems, st));
+        PF_TRY((S.df ? gram_df : gram)(H->D, s, Ud, Lb, Wd, na, Cl.as<double>(), S.gscr.as<double>(), S.gscr_elems, st));
         for (int b = 0; b < na; ++b)
-          PF_TRY(tsgemm(H->D, s, Ud, Lb, Cl.as<double>() + b * s, na * s, Wd + (int64_t)b * DS, 1, -1.0, 1.0, st));
+          PF_TRY((S.df ? tsgemm_df : tsgemm)(H->D, s, Ud, Lb, Cl.as<double>() + b * s, na * s, Wd + (int64_t)b * DS, 1, -1.0, 1.0, st));
       }
     }
     PF_TRY(orthonormalise_set(S, Wd, Ud + (int64_t)Lb * DS, na));
