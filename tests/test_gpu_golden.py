@@ -10,7 +10,9 @@ rounding of the extreme eigenvalues).
 
 Checks, with ||H|| the oracle's max(|Emin|, |Emax|):
   * the GPU's lambda equals the oracle's within 1e-10 ||H||;
-  * every returned eigenvalue is within 1e-10 ||H|| of a distinct stored one;
+  * every returned eigenvalue is within 1e-10 ||H|| of a distinct stored one (stored values whose
+    oracle residual exceeds 1e-9 ||H|| are uncertified: W = 5 has one, 8.9e-4 ||H||, where the
+    oracle's Krylov budget ended; a returned value inside its residual window is accepted);
   * completeness: every stored eigenvalue nearer the GPU's lambda than the returned set's radius
     (less the tolerance) is among the returned ones;
   * every residual ||H u - E u|| <= 1e-9 ||H||.
@@ -46,22 +48,38 @@ def load_golden(name):
     return head, np.array(E), np.array(r)
 
 
-def check_against_golden(evals, resid, lam_gpu, head, E, nev):
+def check_against_golden(evals, resid, lam_gpu, head, E, nev, r=None):
+    """r: the stored values' residuals / ||H||.  Values above 1e-9 are uncertified Ritz values of the
+    oracle (its Lanczos ended before they converged): they are left out of the matching, and a GPU
+    eigenvalue that matches no certified value is accepted only inside such a value's residual
+    window |e - E_u| <= r_u ||H|| (a Ritz value with residual rho lies within rho of an eigenvalue),
+    at most two per uncertified value."""
     hn = head["hnorm"]
     tol = 1e-10 * hn
+    cert = np.ones(len(E), dtype=bool) if r is None else r <= 1e-9
+    Eu, ru = E[~cert], (r[~cert] if r is not None else np.zeros(0))
+    E = E[cert]
     assert abs(lam_gpu - head["lambda"]) <= tol
     d = np.abs(E - lam_gpu)
     order = np.lexsort((E, d))
-    assert len(E) > nev
-    radius = d[order[nev - 1]]
-    # the stored set must reach beyond the returned radius for completeness to be decidable
-    assert d[order[-1]] > radius + 2 * tol
+    assert len(E) + len(Eu) > nev
     assert len(evals) == nev
     used = np.zeros(len(E), dtype=bool)
+    in_window = np.zeros(len(Eu), dtype=int)
+    unmatched = []
     for e in evals:
         k = int(np.argmin(np.where(used, np.inf, np.abs(E - e))))
-        assert abs(E[k] - e) <= tol, (e, E[k], abs(E[k] - e) / hn)
-        used[k] = True
+        if abs(E[k] - e) <= tol:
+            used[k] = True
+            continue
+        w = np.nonzero(np.abs(Eu - e) <= ru * hn + tol)[0]
+        assert len(w) > 0, (e, E[k], abs(E[k] - e) / hn)
+        in_window[w[0]] += 1
+        unmatched.append(e)
+    assert np.all(in_window <= 2)
+    # completeness over the certified values nearer lambda than the returned set's radius
+    radius = np.max(np.abs(np.asarray(evals) - lam_gpu))
+    assert d[order[-1]] > radius + 2 * tol      # the stored set reaches beyond the returned radius
     must = d < radius - tol
     assert np.all(used[must]), np.sort(E[must & ~used])
     assert np.max(resid) <= 1e-9 * hn
@@ -81,17 +99,17 @@ def test_xxz_L16_nev100_s32_against_dense(precision):
     check_against_golden(res.evals, res.resid, res.report["lambda_"], head, E, 100)
 
 
-@pytest.mark.parametrize("name,W,seed", [("xxz_L20_W1", 1.0, 2000), ("xxz_L20_W3", 3.0, 2001)])
+@pytest.mark.parametrize("name,W,seed", [("xxz_L20_W1", 1.0, 2000), ("xxz_L20_W3", 3.0, 2001), ("xxz_L20_W5", 5.0, 2002)])
 def test_xxz_L20_benchmark_solve_against_oracle(name, W, seed):
     """The benchmark's solve (XXZ L=20, D = 184,756, nev = 100, s = 32, FP32 filter with FP64 refinement)
     against the oracle's FP64 POLFED set for the same realisation, found from an independent start
     block with scalar Lanczos; the stored values are certified by the oracle's own residuals."""
     import paper_2605_10191_b300 as pf
     head, E, r = load_golden(name)
-    assert np.max(r) <= 1e-9
+    assert np.sum(r > 1e-9) <= 1          # at most one uncertified value in a stored set (W = 5)
     H = pf.Hamiltonian.from_params(pi.xxz_params(20, W=W, seed=seed))
     H.spectral_bounds()
     K = H.choose_K(0.5, 100)
     res = H.solve(0.5, 100, K, block=32, precision="f32", return_vectors=False)
     assert res.status == 0
-    check_against_golden(res.evals, res.resid, res.report["lambda_"], head, E, 100)
+    check_against_golden(res.evals, res.resid, res.report["lambda_"], head, E, 100, r)
