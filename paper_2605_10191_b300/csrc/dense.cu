@@ -563,9 +563,90 @@ __global__ void small_chol_inv_kernel(const double* G, int n, double shift_rel, 
   if (t == 0) status[0] = bad;
 }
 
+// The same factorisation for n <= 64 with the matrix in shared memory.  Cholesky, right-looking: per
+// pivot k one thread forms r_kk = sqrt(a_kk) and its reciprocal, the trailing upper triangle takes
+// a_rc -= (a_kr / r_kk)(a_kc / r_kk) with the reciprocal, then row k is scaled.  The inverse X of the
+// upper-triangular R by rows from the bottom: once row k of X is final every row i < k takes
+// x_ic -= r_ik x_kc (c >= k), and row k - 1, final after that, is scaled by 1 / r_{k-1,k-1} in the same
+// pass, so one barrier per row remains.  The global-memory kernel above spent ~80 us at n = 32 on its
+// three barriers per pivot with every operand in L1 and its one-thread-per-column back substitution.
+#define PF_CHOL_SM_N 64
+__global__ void __launch_bounds__(256) small_chol_inv_sm_kernel(const double* G, int n, double shift_rel, double* R,
+                                                                double* Rinv, int* status) {
+  extern __shared__ __align__(16) double smc[];
+  __shared__ double tr_sh[32];
+  __shared__ int bad;
+  const int ld = n + 1;
+  double* A = smc;              // n x ld, row-major: the upper triangle becomes R
+  double* X = A + n * ld;       // R^{-1}
+  double* rdg = X + n * ld;     // 1 / r_kk
+  const int t = threadIdx.x;
+  if (t == 0) bad = 0;
+  double tr = 0.0;
+  for (int i = t; i < n; i += blockDim.x) tr += G[i * n + i];
+  tr = block_sum(tr, tr_sh);
+  const double shift = shift_rel * tr;
+  for (int i = t; i < n * n; i += blockDim.x) {
+    const int r = i / n, c = i % n;
+    A[r * ld + c] = c >= r ? 0.5 * (G[r * n + c] + G[c * n + r]) + (r == c ? shift : 0.0) : 0.0;
+    X[r * ld + c] = r == c ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (t == 0) {
+      double dk = A[k * ld + k];
+      if (!(dk > 0.0)) {
+        bad = 1;
+        dk = 1.0;
+      }
+      const double pk = sqrt(dk);
+      A[k * ld + k] = pk;
+      rdg[k] = 1.0 / pk;
+    }
+    __syncthreads();
+    const double rp = rdg[k];
+    const int m = n - k - 1;
+    for (int i = t; i < m * m; i += blockDim.x) {
+      const int r = k + 1 + i / m, c = k + 1 + i % m;
+      if (c >= r) A[r * ld + c] -= (A[k * ld + r] * rp) * (A[k * ld + c] * rp);
+    }
+    __syncthreads();
+    for (int j = k + 1 + t; j < n; j += blockDim.x) A[k * ld + j] *= rp;   // row k is read again only below
+  }
+  if (t == 0) X[(n - 1) * ld + n - 1] = rdg[n - 1];
+  __syncthreads();
+  for (int k = n - 1; k >= 1; --k) {
+    const int w = n - k;   // columns k..n-1
+    for (int i = t; i < k * w; i += blockDim.x) {
+      const int r = i / w, c = k + i % w;
+      double x = X[r * ld + c] - A[r * ld + k] * X[k * ld + c];
+      if (r == k - 1) x *= rdg[k - 1];
+      X[r * ld + c] = x;
+    }
+    if (t == 0) X[(k - 1) * ld + k - 1] = rdg[k - 1];
+    __syncthreads();
+  }
+  for (int i = t; i < n * n; i += blockDim.x) {
+    const int r = i / n, c = i % n;
+    R[i] = c >= r ? A[r * ld + c] : 0.0;
+    Rinv[i] = c >= r ? X[r * ld + c] : 0.0;
+  }
+  if (t == 0) status[0] = bad;
+}
+
 pf_status small_chol_inv(const double* G, int n, double shift_rel, double* R, double* Rinv, int* status,
                          cudaStream_t st) {
   if (n < 1 || n > 512) return PF_EINVAL;
+  if (n <= PF_CHOL_SM_N) {
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        small_chol_inv_sm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)((2 * PF_CHOL_SM_N * (PF_CHOL_SM_N + 1) + PF_CHOL_SM_N) * sizeof(double)));
+    PF_CUDA(attr);
+    const size_t smem = (size_t)(2 * n * (n + 1) + n) * sizeof(double);
+    small_chol_inv_sm_kernel<<<1, 256, smem, st>>>(G, n, shift_rel, R, Rinv, status);
+    PF_LAUNCH_CHECK("small_chol_inv_sm_kernel");
+    return PF_OK;
+  }
   small_chol_inv_kernel<<<1, 512, 0, st>>>(G, n, shift_rel, R, Rinv, status);
   PF_LAUNCH_CHECK("small_chol_inv_kernel");
   return PF_OK;

@@ -22,7 +22,7 @@
 namespace pf {
 
 struct EigLayout {
-  size_t aw, d, e, tau, p, w, y, lu, cl, total;
+  size_t aw, d, e, tau, p, w, y, lu, cl, sturm, total;
 };
 
 static EigLayout eig_layout(int n, int q) {
@@ -38,11 +38,18 @@ static EigLayout eig_layout(int n, int q) {
   L.y = take((size_t)n * q * 8);
   L.lu = take((size_t)q * 6 * n * 8);
   L.cl = take((size_t)(q + 2) * 4 * 2);
+  L.sturm = take((size_t)n * 16);   // e^2 (FP64), d and e^2 scaled (FP32)
   L.total = o;
   return L;
 }
 
 size_t eig_workspace_bytes(int nmax, int qmax) { return eig_layout(nmax, qmax).total; }
+
+// One entry of the rank-2 update A22 -= v w^T + w v^T (row l, column c); every form of the
+// tridiagonalisation calls this one expression, so all give the same bits.
+__device__ __forceinline__ double rank2_entry(double a, double vl, double wc, double wl, double vc) {
+  return a - (vl * wc + wl * vc);
+}
 
 // Aw (column-major n x n) = A (row-major, lda); A is symmetric.
 __global__ void eig_copy_kernel(const double* A, int lda, int n, double* Aw) {
@@ -117,7 +124,7 @@ __global__ void rank2_kernel(double* Aw, int n, int j, const double* p) {
   const double* v = Aw + (int64_t)j * n + j + 1;
   const double* w = p + n;
   double* a = Aw + (int64_t)(j + 1 + i) * n + j + 1 + l;
-  *a -= v[l] * w[i] + w[l] * v[i];
+  *a = rank2_entry(*a, v[l], w[i], w[l], v[i]);
 }
 
 // The same column step in two launches, for orders above the distributed-shared-memory kernel's
@@ -198,7 +205,7 @@ __global__ void wvec_rank2_kernel(double* Aw, int n, int j, const double* tau, c
     const double vi = i == 0 ? 1.0 : x[i] * scale, vl = l == 0 ? 1.0 : x[l] * scale;
     const double wi = p[i] - c * vi, wl = p[l] - c * vl;
     double* a = Aw + (int64_t)(j + 1 + i) * n + j + 1 + l;
-    *a -= vl * wi + wl * vi;
+    *a = rank2_entry(*a, vl, wi, wl, vi);
   }
 }
 
@@ -282,26 +289,30 @@ __global__ void __launch_bounds__(PF_TRI_NT) tridiag_cluster_kernel(double* Aw, 
     for (int i = gwarp; i < m; i += nwarps) {   // column i of A22 per warp, rows across the lanes
       double* col = Aw + (int64_t)(j + 1 + i) * n + j + 1;
       const double wi = ldcg(w + i), vi = ldcg(x + i);
-      for (int l = lane; l < m; l += 32) col[l] = ldcg(col + l) - (ldcg(x + l) * wi + ldcg(w + l) * vi);
+      for (int l = lane; l < m; l += 32) col[l] = rank2_entry(ldcg(col + l), ldcg(x + l), wi, ldcg(w + l), vi);
     }
     cluster_sync_all();
   }
 }
 
 // The tridiagonalisation for small orders in one thread-block cluster with the matrix in distributed
-// shared memory.  Column c lives in the shared memory of CTA c mod cs (its k-th column, k = c / cs),
-// for the whole reduction.  Per column j:
-//   1. the owner of column j forms the reflector from its copy (as house_kernel) and writes v, d, e,
-//      tau (v also into Aw's column j for the back-transformation);
+// shared memory, one cluster barrier per column.  Column c lives in the shared memory of CTA c mod cs
+// (its k-th column, k = c / cs), for the whole reduction.  Every CTA also holds its own copy of the
+// column being reduced.  Per column j:
+//   1. every CTA forms the reflector of column j from its copy (the same block sum and operations as
+//      house_kernel, so the same bits in every CTA); CTA 0 stores d, e, tau, and the owner of column
+//      j keeps v in its stored column for the back-transformation;
+//   2. every CTA forms p_c = tau A22[:, c] . v for its own columns c > j and stores each p_c into
+//      every CTA's p buffer; the owner of column j + 1 stores that column into every CTA's copy
+//      buffer;
 //   -- cluster barrier --
-//   2. every CTA copies v and tau from the owner's shared memory, forms p_c = tau A22[:, c] . v for
-//      its own columns c > j and stores each p_c into the p buffer of every CTA of the cluster;
-//   -- cluster barrier --
-//   3. every CTA forms g = p . v and w = p - (tau/2) g v from its full copies and applies the rank-2
-//      update A22 -= v w^T + w v^T to its own columns.
-// Two cluster barriers per column, and the matrix never leaves shared memory; the cluster kernel
-// below moves each phase's data through L2 and meets four times per column.  The barriers are
-// hardware barriers (no spin-waits).  Remote shared memory is read and written only between the
+//   3. every CTA forms g = p . v and w = p - (tau/2) g v and applies the rank-2 update
+//      A22 -= v w^T + w v^T to its own columns and to its copy of column j + 1 (the same expression,
+//      so the copy equals the owner's column bit for bit).
+// The p and copy buffers alternate between two halves by the parity of j: a CTA that has passed
+// column j's barrier writes the other half, which every CTA finished reading before it arrived at
+// that barrier.  The result is the tridiagonal of house/symv/wvec/rank2_kernel, bit for bit.  The
+// barriers are hardware barriers (no spin-waits); remote shared memory is written only between the
 // first and the last barrier, while every CTA of the cluster is resident.
 #define PF_TRI_DS_NT 512
 __global__ void __launch_bounds__(PF_TRI_DS_NT) tridiag_dsmem_kernel(double* Aw, int n, int ldc, double* d, double* e,
@@ -314,56 +325,52 @@ __global__ void __launch_bounds__(PF_TRI_DS_NT) tridiag_dsmem_kernel(double* Aw,
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   double* cols = ds;                                 // ldc columns of n: column k*cs + rank at cols + k*n
   double* vb = cols + (size_t)ldc * n;               // v, indexed by absolute row
-  double* pb = vb + n;                               // p, indexed by absolute column (every CTA's stores)
-  double* wb = pb + n;                               // w
-  double* tb = wb + n;                               // tau of the column this CTA owns now
+  double* wb = vb + n;                               // w
+  double* pb = wb + n;                               // p of column j in pb + (j & 1) * n (every CTA's stores)
+  double* xb = pb + 2 * (size_t)n;                   // column j of the partly reduced matrix in xb + (j & 1) * n
   for (int k = 0; k < ldc; ++k) {
     const int c = k * (int)cs + (int)rank;
     if (c < n)
       for (int r = tid; r < n; r += PF_TRI_DS_NT) cols[(size_t)k * n + r] = Aw[(int64_t)c * n + r];
   }
+  for (int r = tid; r < n; r += PF_TRI_DS_NT) xb[r] = Aw[r];
   __syncthreads();
   cluster_sync_all();
   for (int j = 0; j + 2 < n; ++j) {
     const int m = n - j - 1;
-    const unsigned owner = (unsigned)(j % (int)cs);
-    double* xown = cols + (size_t)(j / (int)cs) * n + j + 1;   // column j, rows j+1.. (owner's copy)
-    if (rank == owner) {   // reflector: H x = beta e1, H = I - tau v v^T, v_0 = 1
-      double sig = 0.0;
-      for (int i = 1 + tid; i < m; i += PF_TRI_DS_NT) sig += xown[i] * xown[i];
-      sig = block_sum(sig, sh);
-      const double alpha = xown[0];
-      double beta, t, scale;
-      if (sig == 0.0) {
-        beta = alpha;
-        t = 0.0;
-        scale = 0.0;
-      } else {
-        const double nrm = sqrt(alpha * alpha + sig);
-        beta = alpha <= 0.0 ? nrm : -nrm;
-        t = (beta - alpha) / beta;
-        scale = 1.0 / (alpha - beta);
-      }
-      for (int i = 1 + tid; i < m; i += PF_TRI_DS_NT) xown[i] *= scale;
-      __syncthreads();
-      if (tid == 0) {
-        xown[0] = 1.0;
-        d[j] = cols[(size_t)(j / (int)cs) * n + j];
+    const double* xc = xb + (size_t)(j & 1) * n;
+    // 1. reflector: H x = beta e1, H = I - tau v v^T, v_0 = 1, x = rows j+1.. of column j
+    double sig = 0.0;
+    for (int i = 1 + tid; i < m; i += PF_TRI_DS_NT) sig += xc[j + 1 + i] * xc[j + 1 + i];
+    sig = block_sum(sig, sh);
+    const double alpha = xc[j + 1];
+    double beta, t, scale;
+    if (sig == 0.0) {
+      beta = alpha;
+      t = 0.0;
+      scale = 0.0;
+    } else {
+      const double nrm = sqrt(alpha * alpha + sig);
+      beta = alpha <= 0.0 ? nrm : -nrm;
+      t = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    for (int i = 1 + tid; i < m; i += PF_TRI_DS_NT) vb[j + 1 + i] = xc[j + 1 + i] * scale;
+    if (tid == 0) {
+      vb[j + 1] = 1.0;
+      if (rank == 0) {
+        d[j] = xc[j];
         e[j] = beta;
         tau[j] = t;
-        tb[0] = t;
       }
-      __syncthreads();
-      for (int i = tid; i < m; i += PF_TRI_DS_NT) Aw[(int64_t)j * n + j + 1 + i] = xown[i];
     }
-    cluster_sync_all();
-    {
-      const double* xo = cl.map_shared_rank(xown, owner);
-      for (int i = tid; i < m; i += PF_TRI_DS_NT) vb[j + 1 + i] = xo[i];
-    }
-    const double tj = *cl.map_shared_rank(tb, owner);
     __syncthreads();
-    // p_c for the own columns c > j: one warp per column, the product stored into every CTA
+    if (rank == (unsigned)(j % (int)cs)) {
+      double* own = cols + (size_t)(j / (int)cs) * n;
+      for (int i = tid; i < m; i += PF_TRI_DS_NT) own[j + 1 + i] = vb[j + 1 + i];
+    }
+    // 2. p_c for the own columns c > j: one warp per column, the product stored into every CTA
+    double* pj = pb + (size_t)(j & 1) * n;
     const int k0 = (j + 1 - (int)rank + (int)cs - 1) / (int)cs;   // first own column index with c > j
     for (int k = k0 + warp; k < ldc; k += PF_TRI_DS_NT / 32) {
       const int c = k * (int)cs + (int)rank;
@@ -372,25 +379,40 @@ __global__ void __launch_bounds__(PF_TRI_DS_NT) tridiag_dsmem_kernel(double* Aw,
       double acc = 0.0;
       for (int l = j + 1 + lane; l < n; l += 32) acc = fma(col[l], vb[l], acc);
       acc = warp_sum(acc);
-      if (lane < (int)cs) *cl.map_shared_rank(pb + c, (unsigned)lane) = tj * acc;
+      if (lane < (int)cs) *cl.map_shared_rank(pj + c, (unsigned)lane) = t * acc;
+    }
+    // the owner of column j + 1 hands its rows j+1.. to every CTA (the next reflector's input)
+    if (j + 3 < n && rank == (unsigned)((j + 1) % (int)cs)) {
+      const double* own = cols + (size_t)((j + 1) / (int)cs) * n;
+      double* dst = xb + (size_t)((j + 1) & 1) * n;
+      for (int i = tid; i < m * (int)cs; i += PF_TRI_DS_NT) {
+        const int r = i / m, row = j + 1 + i % m;
+        *cl.map_shared_rank(dst + row, (unsigned)r) = own[row];
+      }
     }
     cluster_sync_all();
+    // 3. w = p - (tau/2)(p.v) v and the rank-2 update
     double g = 0.0;
-    for (int l = j + 1 + tid; l < n; l += PF_TRI_DS_NT) g = fma(pb[l], vb[l], g);
+    for (int l = j + 1 + tid; l < n; l += PF_TRI_DS_NT) g = fma(pj[l], vb[l], g);
     g = block_sum(g, sh);
-    const double cc = 0.5 * tj * g;
-    for (int l = j + 1 + tid; l < n; l += PF_TRI_DS_NT) wb[l] = pb[l] - cc * vb[l];
+    const double cc = 0.5 * t * g;
+    for (int l = j + 1 + tid; l < n; l += PF_TRI_DS_NT) wb[l] = pj[l] - cc * vb[l];
     __syncthreads();
-    // rank-2 update over all (own column, row) pairs at once: with few rows per column a loop over
-    // the columns one after another left most threads idle (one CTA at n = 64: 18 us per column)
+    // over all (own column, row) pairs at once: with few rows per column a loop over the columns one
+    // after another left most threads idle (one CTA at n = 64: 18 us per column)
     {
       const int kend = (int)rank < n ? min(ldc, (n - 1 - (int)rank) / (int)cs + 1) : 0;   // own columns c < n
       const int64_t tot = (int64_t)max(kend - k0, 0) * m;
       for (int64_t idx = tid; idx < tot; idx += PF_TRI_DS_NT) {
         const int k = k0 + (int)(idx / m), l = j + 1 + (int)(idx % m);
         const int c = k * (int)cs + (int)rank;
-        cols[(size_t)k * n + l] -= vb[l] * wb[c] + wb[l] * vb[c];
+        double* a = cols + (size_t)k * n + l;
+        *a = rank2_entry(*a, vb[l], wb[c], wb[l], vb[c]);
       }
+    }
+    if (j + 3 < n) {
+      double* xn = xb + (size_t)((j + 1) & 1) * n;
+      for (int l = j + 1 + tid; l < n; l += PF_TRI_DS_NT) xn[l] = rank2_entry(xn[l], vb[l], wb[j + 1], wb[l], vb[j + 1]);
     }
     __syncthreads();
   }
@@ -399,12 +421,12 @@ __global__ void __launch_bounds__(PF_TRI_DS_NT) tridiag_dsmem_kernel(double* Aw,
     if (c < n)
       for (int r = tid; r < n; r += PF_TRI_DS_NT) Aw[(int64_t)c * n + r] = cols[(size_t)k * n + r];
   }
-  cluster_sync_all();   // no CTA leaves while another may still read its shared memory
+  cluster_sync_all();   // no CTA leaves while another may still write its shared memory
 }
 
 static size_t tridiag_dsmem_bytes(int n, int cs) {
   const int ldc = (n + cs - 1) / cs;
-  return ((size_t)ldc * n + 3 * (size_t)n + 2) * sizeof(double);
+  return ((size_t)ldc * n + 6 * (size_t)n) * sizeof(double);
 }
 
 // Cluster size for the distributed-shared-memory tridiagonalisation of order n (0: not possible):
@@ -529,38 +551,81 @@ __global__ void tri_finish_kernel(const double* Aw, int n, double* d, double* e,
   tau[n - 2] = 0.0;
 }
 
-// Sturm count: number of eigenvalues of T below x.
-__device__ int sturm_count(const double* d, const double* e, int n, double x, double pivmin) {
+// Sturm count: number of eigenvalues of T below x, from the pivots of the LDL^T factorisation of
+// T - x I (e2[i] = e[i]^2); pivmin guards tiny pivots.
+template <typename T>
+__device__ int sturm_count(const T* d, const T* e2, int n, T x, T pivmin) {
   int cnt = 0;
-  double q = d[0] - x;
+  T q = d[0] - x;
   if (fabs(q) < pivmin) q = -pivmin;
-  if (q < 0) ++cnt;
+  if (q < T(0)) ++cnt;
   for (int i = 1; i < n; ++i) {
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    q = d[i] - x - e2[i - 1] / q;
     if (fabs(q) < pivmin) q = -pivmin;
-    if (q < 0) ++cnt;
+    if (q < T(0)) ++cnt;
   }
   return cnt;
 }
 
-// Multisection, one warp per requested eigenvalue (index k of the ascending order): each
-// round the 32 lanes take Sturm counts at 32 evenly spaced points of (lo, hi] (lane 31 at
-// hi), and the warp keeps the sub-interval between the last point with fewer than k+1
-// eigenvalues below it and the first with at least k+1.  The interval shrinks 32-fold per
-// round (five bisection steps), so the sequential depth is a fifth of plain bisection.
-// [gl, gu] is the Gershgorin interval, widened by rounding; pivmin guards tiny pivots.
-__global__ void bisect_kernel(const double* d, const double* e, int n, const int* idx, int q, double* w, double gl,
-                              double gu, double pivmin) {
+// e2 = e^2 in FP64, and T scaled by sc (a power of two, so that ||T|| sc < 1) in FP32: df = d sc,
+// e2f = (e sc)^2.
+__global__ void sturm_prep_kernel(const double* d, const double* e, int n, double sc, double* e2, float* df,
+                                  float* e2f) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double ei = i < n - 1 ? e[i] : 0.0;
+  e2[i] = ei * ei;
+  df[i] = (float)(d[i] * sc);
+  const float ef = (float)(ei * sc);
+  e2f[i] = ef * ef;
+}
+
+// Multisection, one warp per requested eigenvalue (index k of the ascending order): each round the
+// 32 lanes take Sturm counts at 32 evenly spaced points of (lo, hi] (lane 31 at hi), and the warp
+// keeps the sub-interval between the last point with fewer than k+1 eigenvalues below it and the
+// first with at least k+1, a 32-fold shrink (five bisection steps) per round.
+//   - The first rounds count in FP32 on the scaled matrix until the interval is below delta.  An FP32
+//     count is the exact count of a matrix within ~9 eps_32 ||T|| of T (the backward error of the
+//     LDL^T recurrence, with the rounding of d, e and the shift), so the FP32 interval widened by
+//     delta (2^-17 ||T||, 14 times that) holds eigenvalue k of T.
+//   - The FP64 rounds continue from there to the rounding level.  Their first round places its points
+//     at both ends of the interval and, should the ends not bracket eigenvalue k, starts again from
+//     the Gershgorin interval [gl, gu] (widened by rounding).
+__global__ void bisect_kernel(const double* d, const double* e2, const float* df, const float* e2f, int n,
+                              const int* idx, int q, double* w, double gl, double gu, double pivmin, double sc,
+                              float pivminf, double delta) {
   const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= q) return;   // uniform per warp
   const int k = idx[warp];
-  double lo = gl, hi = gu;
+  float lof = __double2float_rd(gl * sc), hif = __double2float_ru(gu * sc);
+  const float deltaf = (float)(delta * sc);
+  for (int it = 0; it < 8 && hif - lof > deltaf; ++it) {
+    const float x = lane == 31 ? hif : lof + (hif - lof) * ((float)(lane + 1) / 32.0f);
+    const int cnt = sturm_count<float>(df, e2f, n, x, pivminf);
+    const unsigned mask = __ballot_sync(0xffffffffu, cnt >= k + 1);
+    const int first = mask ? __ffs(mask) - 1 : 31;
+    const float nhi = __shfl_sync(0xffffffffu, x, first);
+    const float nlo = first > 0 ? __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0) : lof;
+    if (nhi >= hif && nlo <= lof) break;
+    lof = nlo;
+    hif = nhi;
+  }
+  double lo = fmax(gl, (double)lof / sc - delta), hi = fmin(gu, (double)hif / sc + delta);
+  bool ends = true;
   for (int it = 0; it < 64; ++it) {
     if (hi - lo <= 2.2e-16 * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
-    const double x = lane == 31 ? hi : lo + (hi - lo) * ((double)(lane + 1) / 32.0);
-    const int cnt = sturm_count(d, e, n, x, pivmin);
+    const double x = lane == 31 ? hi : lo + (hi - lo) * (ends ? (double)lane / 31.0 : (double)(lane + 1) / 32.0);
+    const int cnt = sturm_count<double>(d, e2, n, x, pivmin);
     const unsigned mask = __ballot_sync(0xffffffffu, cnt >= k + 1);
+    if (ends) {
+      ends = false;
+      if ((mask & 1u) || !(mask >> 31)) {   // not a bracket of eigenvalue k: the whole interval
+        lo = gl;
+        hi = gu;
+        continue;
+      }
+    }
     const int first = mask ? __ffs(mask) - 1 : 31;
     const double nhi = __shfl_sync(0xffffffffu, x, first);
     const double nlo = first > 0 ? __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0) : lo;
@@ -580,18 +645,20 @@ __device__ __forceinline__ double hash_unit(uint64_t a) {
 }
 
 // One CTA per cluster [cs[c], cs[c+1]) of selected eigenvalues.  Thread 0 factors
-// T - lambda I (tridiagonal LU with partial pivoting) and runs the two triangular solves,
-// which are sequential; the whole CTA does the Gram-Schmidt against the cluster's earlier
-// members and the normalisation.
+// T - lambda I (tridiagonal LU with partial pivoting, the pivots kept as reciprocals) and runs the two
+// triangular solves, which are sequential recurrences (carried in registers); the whole CTA does the
+// Gram-Schmidt against the cluster's earlier members and the normalisation.  The factors live in
+// shared memory when smem_lu is set (6 n doubles of dynamic shared memory), else in lu.
 __global__ void inviter_kernel(const double* d, const double* e, int n, const double* w, const int* cs, int ncl,
-                               double* Y, double* lu, double tnorm) {
+                               double* Y, double* lu, double tnorm, int smem_lu) {
+  extern __shared__ __align__(16) double lus[];
   __shared__ double sh[32];
   const int c = blockIdx.x;
   if (c >= ncl) return;
   const int t = threadIdx.x;
-  double* dl = lu + (int64_t)c * 6 * n;
-  double* dd = dl + n;
-  double* du = dd + n;
+  double* dl = smem_lu ? lus : lu + (int64_t)c * 6 * n;
+  double* rd = dl + n;    // reciprocals of U's diagonal
+  double* du = rd + n;
   double* du2 = du + n;
   double* b = du2 + n;
   double* piv = b + n;    // 0/1 flags stored as doubles
@@ -605,36 +672,35 @@ __global__ void inviter_kernel(const double* d, const double* e, int n, const do
     double* y = Y + (int64_t)p * n;
     for (int i = t; i < n; i += blockDim.x) y[i] = hash_unit(((uint64_t)p << 32) ^ (uint64_t)i);
     if (t == 0) {
-      for (int i = 0; i < n; ++i) {
-        dd[i] = d[i] - lam;
-        if (i < n - 1) {
-          dl[i] = e[i];
-          du[i] = e[i];
-        }
-        du2[i] = 0.0;
-        piv[i] = 0.0;
-      }
+      // T - lam I = P L U: U has the diagonal 1/rd, the superdiagonals du, du2; L the multipliers dl
+      double di = d[0] - lam;   // running diagonal entry of row i
+      double ui = n > 1 ? e[0] : 0.0;   // running first superdiagonal entry of row i
       for (int i = 0; i < n - 1; ++i) {
-        if (fabs(dd[i]) >= fabs(dl[i])) {
-          double f = dd[i] != 0.0 ? dl[i] / dd[i] : 0.0;
+        const double sub = e[i];               // T(i+1, i)
+        const double dn = d[i + 1] - lam;      // T(i+1, i+1)
+        const double un = i < n - 2 ? e[i + 1] : 0.0;   // T(i+1, i+2)
+        if (fabs(di) >= fabs(sub)) {
+          const double f = di != 0.0 ? sub / di : 0.0;
           dl[i] = f;
-          dd[i + 1] -= f * du[i];
+          du[i] = ui;
+          du2[i] = 0.0;
+          piv[i] = 0.0;
+          rd[i] = di;
+          di = dn - f * ui;
+          ui = un;
         } else {
-          double f = dd[i] / dl[i];
-          dd[i] = dl[i];
+          const double f = di / sub;
           dl[i] = f;
-          double tmp = du[i];
-          du[i] = dd[i + 1];
-          dd[i + 1] = tmp - f * dd[i + 1];
-          if (i < n - 2) {
-            du2[i] = du[i + 1];
-            du[i + 1] = -f * du[i + 1];
-          }
+          du[i] = dn;
+          du2[i] = un;
           piv[i] = 1.0;
+          rd[i] = sub;
+          di = ui - f * dn;
+          ui = -f * un;
         }
       }
-      for (int i = 0; i < n; ++i)
-        if (dd[i] == 0.0) dd[i] = pertol > 0 ? pertol : 1e-300;
+      rd[n - 1] = di;
+      for (int i = 0; i < n; ++i) rd[i] = 1.0 / (rd[i] != 0.0 ? rd[i] : (pertol > 0 ? pertol : 1e-300));
     }
     __syncthreads();
     for (int it = 0; it < 4; ++it) {
@@ -642,19 +708,27 @@ __global__ void inviter_kernel(const double* d, const double* e, int n, const do
       __syncthreads();
       if (t == 0) {
         // L solve with the row interchanges
+        double bi = b[0];
         for (int i = 0; i < n - 1; ++i) {
+          const double bn = b[i + 1];
           if (piv[i] != 0.0) {
-            double tmp = b[i];
-            b[i] = b[i + 1];
-            b[i + 1] = tmp - dl[i] * b[i];
+            b[i] = bn;
+            bi = bi - dl[i] * bn;
           } else {
-            b[i + 1] -= dl[i] * b[i];
+            b[i] = bi;
+            bi = bn - dl[i] * bi;
           }
         }
+        b[n - 1] = bi;
         // U solve
-        b[n - 1] /= dd[n - 1];
-        if (n > 1) b[n - 2] = (b[n - 2] - du[n - 2] * b[n - 1]) / dd[n - 2];
-        for (int i = n - 3; i >= 0; --i) b[i] = (b[i] - du[i] * b[i + 1] - du2[i] * b[i + 2]) / dd[i];
+        double x1 = b[n - 1] * rd[n - 1], x2 = 0.0;
+        b[n - 1] = x1;
+        for (int i = n - 2; i >= 0; --i) {
+          const double x = (b[i] - du[i] * x1 - du2[i] * x2) * rd[i];
+          b[i] = x;
+          x2 = x1;
+          x1 = x;
+        }
       }
       __syncthreads();
       // orthogonalise against earlier members of the cluster (twice)
@@ -777,9 +851,20 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
   gl -= 2.0 * 2.2e-16 * tn * n + 1e-300;
   gu += 2.0 * 2.2e-16 * tn * n + 1e-300;
   const double pivmin = 2.3e-308 * std::max(1.0, maxe2);
+  // the FP32 rounds' scale: a power of two with tn sc in [0.5, 1)
+  int ex = 0;
+  std::frexp(tn, &ex);
+  const double sc = tn > 0.0 ? std::ldexp(1.0, -ex) : 1.0;
+  const float pivminf = 1.2e-38f * (float)std::max(1.0, maxe2 * sc * sc);
+  double* e2 = (double*)(wb + L.sturm);
+  float* df = (float*)(e2 + n);
+  float* e2f = df + n;
+  sturm_prep_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(d, e, n, sc, e2, df, e2f);
   // one warp per CTA: the Sturm counts are bound by the FP64 pipe, and q warps packed eight to a
   // CTA ran on q / 8 SMs (n = 900, q = 150: 10.5 ms on 19 SMs)
-  bisect_kernel<<<(unsigned)q, 32, 0, st>>>(d, e, n, idx_dev, q, w, gl, gu, pivmin);
+  bisect_kernel<<<(unsigned)q, 32, 0, st>>>(d, e2, df, e2f, n, idx_dev, q, w, gl, gu, pivmin, sc, pivminf,
+                                            std::ldexp(tn, -17));
+  PF_COUNT(1);   // sturm_prep_kernel
   PF_LAUNCH_CHECK("bisect_kernel");
   PF_CUDA(cudaMemcpyAsync(w_host, w, q * sizeof(double), cudaMemcpyDeviceToHost, st));
   PF_CUDA(cudaStreamSynchronize(st));
@@ -803,7 +888,16 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
   cs.push_back(q);
   const int ncl = (int)cs.size() - 1;
   PF_CUDA(cudaMemcpyAsync(cl, cs.data(), cs.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-  inviter_kernel<<<(unsigned)ncl, 256, 0, st>>>(d, e, n, w, cl, ncl, Y, lu, tnorm);
+  // the LU factors in shared memory up to n = 2000 (96 KB)
+  const int smem_lu = n <= 2000 ? 1 : 0;
+  const size_t lu_smem = smem_lu ? (size_t)6 * n * sizeof(double) : 0;
+  if (lu_smem > 48 * 1024) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+      cudaFuncSetAttribute(inviter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * 2000 * (int)sizeof(double));
+    });
+  }
+  inviter_kernel<<<(unsigned)ncl, 256, lu_smem, st>>>(d, e, n, w, cl, ncl, Y, lu, tnorm, smem_lu);
   PF_LAUNCH_CHECK("inviter_kernel");
   const size_t smem = (size_t)n * sizeof(double);
   if (smem > 48 * 1024) {
