@@ -45,10 +45,58 @@ static EigLayout eig_layout(int n, int q) {
 
 size_t eig_workspace_bytes(int nmax, int qmax) { return eig_layout(nmax, qmax).total; }
 
-// One entry of the rank-2 update A22 -= v w^T + w v^T (row l, column c); every form of the
-// tridiagonalisation calls this one expression, so all give the same bits.
+// One entry of the rank-2 update A22 -= v w^T + w v^T (row l, column c), as two FMAs; every form of
+// the tridiagonalisation calls this one expression.
 __device__ __forceinline__ double rank2_entry(double a, double vl, double wc, double wl, double vc) {
-  return a - (vl * wc + wl * vc);
+  return fma(-vl, wc, fma(-wl, vc, a));
+}
+
+// Deterministic block sum over blockDim.x threads of which only the first nact can hold a nonzero
+// term: warps beyond them skip their shuffle tree (their partial is +0, as block_sum would find), so the
+// result is block_sum's, bit for bit, without the idle warps' FP64 additions on the SM's slow FP64 pipe.
+__device__ double block_sum_act(double v, double* sh, int nact) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w < ((nact + 31) >> 5)) v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  double r = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0) r = warp_sum(r);
+  if (threadIdx.x == 0) sh[0] = r;
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Householder reflector of x (alpha = x_0, sig = sum_{i>=1} x_i^2): H x = beta e_0, H = I - tau v v^T with
+// v = x / (alpha - beta), v_0 = 1 (scale = 1 / (alpha - beta)).  Thread 0 evaluates the square root and
+// the two divisions and the block reads them from shared memory (rf, 3 doubles; the caller's next write
+// to rf follows a barrier): on B300 a division is ~1000 cycles of dependent FP64 operations, and every
+// warp of a 512-thread CTA evaluating them kept the SM's FP64 pipe busy for ~7000 cycles per column.
+struct Refl {
+  double beta, t, scale;
+};
+__device__ Refl reflector(double alpha, double sig, double* rf) {
+  if (threadIdx.x == 0) {
+    double beta, t, scale;
+    if (sig == 0.0) {
+      beta = alpha;
+      t = 0.0;
+      scale = 0.0;
+    } else {
+      const double nrm = sqrt(alpha * alpha + sig);
+      beta = alpha <= 0.0 ? nrm : -nrm;
+      t = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    rf[0] = beta;
+    rf[1] = t;
+    rf[2] = scale;
+  }
+  __syncthreads();
+  return Refl{rf[0], rf[1], rf[2]};
 }
 
 // Aw (column-major n x n) = A (row-major, lda); A is symmetric.
@@ -62,23 +110,14 @@ __global__ void eig_copy_kernel(const double* A, int lda, int n, double* Aw) {
 // Reflector for column j: x = Aw[j+1.., j].  H x = beta e1, H = I - tau v v^T, v_0 = 1.
 __global__ void house_kernel(double* Aw, int n, int j, double* d, double* e, double* tau) {
   __shared__ double sh[32];
+  __shared__ double rf[3];
   const int m = n - j - 1;
   double* x = Aw + (int64_t)j * n + j + 1;
   double sig = 0.0;
   for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
-  sig = block_sum(sig, sh);
-  const double alpha = x[0];
-  double beta, t, scale;
-  if (sig == 0.0) {
-    beta = alpha;
-    t = 0.0;
-    scale = 0.0;
-  } else {
-    double nrm = sqrt(alpha * alpha + sig);
-    beta = alpha <= 0.0 ? nrm : -nrm;
-    t = (beta - alpha) / beta;
-    scale = 1.0 / (alpha - beta);
-  }
+  sig = block_sum_act(sig, sh, m - 1);
+  const Refl rfl = reflector(x[0], sig, rf);
+  const double beta = rfl.beta, t = rfl.t, scale = rfl.scale;
   __syncthreads();
   for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] *= scale;
   if (threadIdx.x == 0) {
@@ -110,7 +149,7 @@ __global__ void wvec_kernel(const double* Aw, int n, int j, const double* tau, d
   const double* v = Aw + (int64_t)j * n + j + 1;
   double g = 0.0;
   for (int i = threadIdx.x; i < m; i += blockDim.x) g = fma(p[i], v[i], g);
-  g = block_sum(g, sh);
+  g = block_sum_act(g, sh, m);
   const double c = 0.5 * tau[j] * g;
   for (int i = threadIdx.x; i < m; i += blockDim.x) p[n + i] = p[i] - c * v[i];
 }
@@ -139,6 +178,7 @@ __global__ void rank2_kernel(double* Aw, int n, int j, const double* p) {
 __global__ void house_symv_kernel(double* Aw, int n, int j, double* d, double* e, double* tau, double* sc,
                                   double* p) {
   __shared__ double sh[32];
+  __shared__ double rf[3];
   const int m = n - j - 1;
   if (blockIdx.x == 0 && j > 0) {   // column j - 1's reflector: x *= scale, x_0 = 1 (as house_kernel)
     const int mp = m + 1;
@@ -150,19 +190,9 @@ __global__ void house_symv_kernel(double* Aw, int n, int j, double* d, double* e
   const double* x = Aw + (int64_t)j * n + j + 1;
   double sig = 0.0;
   for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
-  sig = block_sum(sig, sh);
-  const double alpha = x[0];
-  double beta, t, scale;
-  if (sig == 0.0) {
-    beta = alpha;
-    t = 0.0;
-    scale = 0.0;
-  } else {
-    double nrm = sqrt(alpha * alpha + sig);
-    beta = alpha <= 0.0 ? nrm : -nrm;
-    t = (beta - alpha) / beta;
-    scale = 1.0 / (alpha - beta);
-  }
+  sig = block_sum_act(sig, sh, m - 1);
+  const Refl rfl = reflector(x[0], sig, rf);
+  const double beta = rfl.beta, t = rfl.t, scale = rfl.scale;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     d[j] = Aw[(int64_t)j * n + j];
     e[j] = beta;
@@ -195,7 +225,7 @@ __global__ void wvec_rank2_kernel(double* Aw, int n, int j, const double* tau, c
   const double scale = sc[j];
   double g = 0.0;
   for (int i = threadIdx.x; i < m; i += blockDim.x) g = fma(p[i], i == 0 ? 1.0 : x[i] * scale, g);
-  g = block_sum(g, sh);
+  g = block_sum_act(g, sh, m);
   const double c = 0.5 * tau[j] * g;
   // grid-stride over the m x m entries: a few hundred CTAs, so that the redundant dot product
   // above stays small next to the update
@@ -227,6 +257,7 @@ __device__ __forceinline__ void cluster_sync_all() {
 __global__ void __launch_bounds__(PF_TRI_NT) tridiag_cluster_kernel(double* Aw, int n, double* d, double* e,
                                                                     double* tau, double* p) {
   __shared__ double sh[32];
+  __shared__ double rf[3];
   unsigned rank, cs;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
   asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(cs));
@@ -244,19 +275,9 @@ __global__ void __launch_bounds__(PF_TRI_NT) tridiag_cluster_kernel(double* Aw, 
         const double xi = ldcg(x + i);
         sig += xi * xi;
       }
-      sig = block_sum(sig, sh);
-      const double alpha = ldcg(x);
-      double beta, t, scale;
-      if (sig == 0.0) {
-        beta = alpha;
-        t = 0.0;
-        scale = 0.0;
-      } else {
-        const double nrm = sqrt(alpha * alpha + sig);
-        beta = alpha <= 0.0 ? nrm : -nrm;
-        t = (beta - alpha) / beta;
-        scale = 1.0 / (alpha - beta);
-      }
+      sig = block_sum_act(sig, sh, m - 1);
+      const Refl rfl = reflector(ldcg(x), sig, rf);
+      const double beta = rfl.beta, t = rfl.t, scale = rfl.scale;
       __syncthreads();
       for (int i = 1 + tid; i < m; i += PF_TRI_NT) x[i] = ldcg(x + i) * scale;
       if (tid == 0) {
@@ -280,7 +301,7 @@ __global__ void __launch_bounds__(PF_TRI_NT) tridiag_cluster_kernel(double* Aw, 
     // w = p - (tau/2)(p.v) v
     double g = 0.0;
     for (int i = tid; i < m; i += PF_TRI_NT) g = fma(ldcg(p + i), ldcg(x + i), g);
-    g = block_sum(g, sh);
+    g = block_sum_act(g, sh, m);
     const double c = 0.5 * tj * g;
     for (int i = gtid; i < m; i += nthr) p[n + i] = ldcg(p + i) - c * ldcg(x + i);
     cluster_sync_all();
@@ -319,6 +340,7 @@ __global__ void __launch_bounds__(PF_TRI_DS_NT) tridiag_dsmem_kernel(double* Aw,
                                                                    double* tau) {
   extern __shared__ __align__(16) double ds[];
   __shared__ double sh[32];
+  __shared__ double rf[3];
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const unsigned rank = cl.block_rank(), cs = cl.num_blocks();
@@ -342,19 +364,9 @@ __global__ void __launch_bounds__(PF_TRI_DS_NT) tridiag_dsmem_kernel(double* Aw,
     // 1. reflector: H x = beta e1, H = I - tau v v^T, v_0 = 1, x = rows j+1.. of column j
     double sig = 0.0;
     for (int i = 1 + tid; i < m; i += PF_TRI_DS_NT) sig += xc[j + 1 + i] * xc[j + 1 + i];
-    sig = block_sum(sig, sh);
-    const double alpha = xc[j + 1];
-    double beta, t, scale;
-    if (sig == 0.0) {
-      beta = alpha;
-      t = 0.0;
-      scale = 0.0;
-    } else {
-      const double nrm = sqrt(alpha * alpha + sig);
-      beta = alpha <= 0.0 ? nrm : -nrm;
-      t = (beta - alpha) / beta;
-      scale = 1.0 / (alpha - beta);
-    }
+    sig = block_sum_act(sig, sh, m - 1);
+    const Refl rfl = reflector(xc[j + 1], sig, rf);
+    const double beta = rfl.beta, t = rfl.t, scale = rfl.scale;
     for (int i = 1 + tid; i < m; i += PF_TRI_DS_NT) vb[j + 1 + i] = xc[j + 1 + i] * scale;
     if (tid == 0) {
       vb[j + 1] = 1.0;
@@ -394,8 +406,10 @@ __global__ void __launch_bounds__(PF_TRI_DS_NT) tridiag_dsmem_kernel(double* Aw,
     // 3. w = p - (tau/2)(p.v) v and the rank-2 update
     double g = 0.0;
     for (int l = j + 1 + tid; l < n; l += PF_TRI_DS_NT) g = fma(pj[l], vb[l], g);
-    g = block_sum(g, sh);
-    const double cc = 0.5 * t * g;
+    g = block_sum_act(g, sh, m);
+    if (tid == 0) rf[0] = 0.5 * t * g;   // once, not in every warp (FP64 pipe)
+    __syncthreads();
+    const double cc = rf[0];
     for (int l = j + 1 + tid; l < n; l += PF_TRI_DS_NT) wb[l] = pj[l] - cc * vb[l];
     __syncthreads();
     // over all (own column, row) pairs at once: with few rows per column a loop over the columns one
@@ -765,7 +779,7 @@ __global__ void backtransform_kernel(const double* Aw, const double* tau, int n,
     const double* v = Aw + (int64_t)j * n + j + 1;
     double g = 0.0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) g = fma(v[i], ys[j + 1 + i], g);
-    g = block_sum(g, sh);
+    g = block_sum_act(g, sh, m);
     const double f = t * g;
     for (int i = threadIdx.x; i < m; i += blockDim.x) ys[j + 1 + i] -= f * v[i];
     __syncthreads();
