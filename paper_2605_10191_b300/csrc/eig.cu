@@ -3,9 +3,10 @@
 // Used by the convergence checks (Eq. blocklan_criterion needs eigenvectors t_j of H_L)
 // and by the Rayleigh-Ritz steps.  Only selected eigenpairs are computed:
 //   1. Householder tridiagonalisation A = Q T Q^T (reflectors kept in A's columns): one
-//      thread-block-cluster launch for orders up to 400, up to 1300 two launches per column over
-//      the whole GPU (reflector and p = tau A22 v; w = p - (tau/2)(p.v) v and the rank-2 update
-//      A22 -= v w^T + w v^T of the full trailing block), above that four.
+//      thread-block-cluster launch with the matrix in distributed shared memory for orders up to
+//      ~620, up to 3000 two launches per column over the whole GPU (reflector, p = tau A22 v and
+//      w = p - (tau/2)(p.v) v; the rank-2 update A22 -= v w^T + w v^T of the full trailing block),
+//      above that four.
 //   2. Multisection with Sturm counts for each requested index (one warp, in a CTA of its
 //      own, per index).
 //   3. Inverse iteration on T - lambda I (tridiagonal LU with partial pivoting), one
@@ -22,7 +23,7 @@
 namespace pf {
 
 struct EigLayout {
-  size_t aw, d, e, tau, p, w, y, lu, cl, sturm, total;
+  size_t aw, d, e, tau, p, w, y, lu, cl, sturm, ticket, total;
 };
 
 static EigLayout eig_layout(int n, int q) {
@@ -33,12 +34,13 @@ static EigLayout eig_layout(int n, int q) {
   L.d = take((size_t)n * 8);
   L.e = take((size_t)n * 8);
   L.tau = take((size_t)n * 8);
-  L.p = take((size_t)2 * n * 8);
+  L.p = take((size_t)3 * n * 8);   // p, w, v of the two-launch column step
   L.w = take((size_t)q * 8);
   L.y = take((size_t)n * q * 8);
   L.lu = take((size_t)q * 6 * n * 8);
   L.cl = take((size_t)(q + 2) * 4 * 2);
   L.sturm = take((size_t)n * 16);   // e^2 (FP64), d and e^2 scaled (FP32)
+  L.ticket = take(16);
   L.total = o;
   return L;
 }
@@ -167,75 +169,83 @@ __global__ void rank2_kernel(double* Aw, int n, int j, const double* p) {
 }
 
 // The same column step in two launches, for orders above the distributed-shared-memory kernel's
-// reach.  house_symv_kernel(j): every CTA forms the reflector of column j itself (the same block
-// sum as house_kernel, so the same bits in every CTA), its warps form p_i = tau A22[:, i] . v with v
-// read as x scaled on the fly, and CTA 0 stores d, e, tau and the scale and, first, finishes column
-// j - 1's stored reflector (x *= scale, x_0 = 1), which nothing reads any more.  wvec_rank2_kernel(j):
-// every CTA forms g = p . v (wvec_kernel's block sum) and applies the rank-2 update to its part of
-// A22 with w = p - (tau/2) g v.  Column j stays as it was until house_symv_kernel(j + 1) (or
-// tri_finish_kernel) scales it, so no CTA reads a column another CTA is rewriting.  The arithmetic,
-// operation for operation, is that of house/symv/wvec/rank2_kernel.
-__global__ void house_symv_kernel(double* Aw, int n, int j, double* d, double* e, double* tau, double* sc,
-                                  double* p) {
+// reach (to n = 3000: v and w of a column in 48 KB of shared memory), with the arithmetic of house/symv/wvec/rank2_kernel operation for operation (the same bits).
+// house_symv_kernel(j): every CTA forms the reflector of column j itself (the same block sum as
+// house_kernel, so the same bits in every CTA) and v = x * scale (v_0 = 1) in shared memory, its warps
+// form p_i = tau A22[:, i] . v, and CTA 0 stores d, e, tau.  The CTA that finishes last (a ticket taken
+// after a fence; no CTA waits for another) forms g = p . v (wvec_kernel's block sum) and
+// w = p - (tau/2) g v, and stores v and w.  rank2_vw_kernel(j): every CTA stages v and w in shared
+// memory and applies the rank-2 update to its part of A22; CTA 0 stores v into column j for the
+// back-transformation (no launch reads column j after house_symv_kernel(j)).  Per update entry two
+// FMAs: the previous form rebuilt v and w from x in every entry, six FP64 operations.
+__global__ void house_symv_kernel(double* Aw, int n, int j, double* d, double* e, double* tau, double* p,
+                                  unsigned* ticket) {
+  extern __shared__ __align__(16) double vs[];   // v, m entries
   __shared__ double sh[32];
   __shared__ double rf[3];
+  __shared__ unsigned last;
   const int m = n - j - 1;
-  if (blockIdx.x == 0 && j > 0) {   // column j - 1's reflector: x *= scale, x_0 = 1 (as house_kernel)
-    const int mp = m + 1;
-    double* xp = Aw + (int64_t)(j - 1) * n + j;
-    const double scp = sc[j - 1];
-    for (int i = 1 + threadIdx.x; i < mp; i += blockDim.x) xp[i] *= scp;
-    if (threadIdx.x == 0) xp[0] = 1.0;
-  }
   const double* x = Aw + (int64_t)j * n + j + 1;
   double sig = 0.0;
   for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) sig += x[i] * x[i];
   sig = block_sum_act(sig, sh, m - 1);
   const Refl rfl = reflector(x[0], sig, rf);
   const double beta = rfl.beta, t = rfl.t, scale = rfl.scale;
+  for (int l = threadIdx.x; l < m; l += blockDim.x) vs[l] = l == 0 ? 1.0 : x[l] * scale;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     d[j] = Aw[(int64_t)j * n + j];
     e[j] = beta;
     tau[j] = t;
-    sc[j] = scale;
   }
+  __syncthreads();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= m) return;
-  const double* col = Aw + (int64_t)(j + 1 + warp) * n + j + 1;
-  double s = 0.0;
-  for (int l = lane; l < m; l += 32) s = fma(col[l], l == 0 ? 1.0 : x[l] * scale, s);
-  s = warp_sum(s);
-  if (lane == 0) p[warp] = t * s;
-}
-
-// Column j's stored reflector after the last two-launch step (x *= scale, x_0 = 1).
-__global__ void reflector_store_kernel(double* Aw, int n, int j, const double* sc) {
-  const int m = n - j - 1;
-  double* x = Aw + (int64_t)j * n + j + 1;
-  const double scale = sc[j];
-  for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] *= scale;
-  if (threadIdx.x == 0) x[0] = 1.0;
-}
-
-__global__ void wvec_rank2_kernel(double* Aw, int n, int j, const double* tau, const double* sc, const double* p) {
-  __shared__ double sh[32];
-  const int m = n - j - 1;
-  const double* x = Aw + (int64_t)j * n + j + 1;
-  const double scale = sc[j];
+  if (warp < m) {
+    const double* col = Aw + (int64_t)(j + 1 + warp) * n + j + 1;
+    double s = 0.0;
+    for (int l = lane; l < m; l += 32) s = fma(col[l], vs[l], s);
+    s = warp_sum(s);
+    if (lane == 0) p[warp] = t * s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
   double g = 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) g = fma(p[i], i == 0 ? 1.0 : x[i] * scale, g);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) g = fma(__ldcg(p + i), vs[i], g);
   g = block_sum_act(g, sh, m);
-  const double c = 0.5 * tau[j] * g;
-  // grid-stride over the m x m entries: a few hundred CTAs, so that the redundant dot product
-  // above stays small next to the update
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)m * m;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / m), l = (int)(idx % m);
-    const double vi = i == 0 ? 1.0 : x[i] * scale, vl = l == 0 ? 1.0 : x[l] * scale;
-    const double wi = p[i] - c * vi, wl = p[l] - c * vl;
+  if (threadIdx.x == 0) rf[0] = 0.5 * t * g;
+  __syncthreads();
+  const double c = rf[0];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    p[n + i] = __ldcg(p + i) - c * vs[i];
+    p[2 * n + i] = vs[i];
+  }
+  if (threadIdx.x == 0) *ticket = 0u;   // for the next column's launch
+}
+
+__global__ void rank2_vw_kernel(double* Aw, int n, int j, const double* p) {
+  extern __shared__ __align__(16) double vw[];   // v (m), then w (m)
+  const int m = n - j - 1;
+  double* vv = vw;
+  double* ww = vw + m;
+  for (int l = threadIdx.x; l < m; l += blockDim.x) {
+    vv[l] = p[2 * n + l];
+    ww[l] = p[n + l];
+  }
+  __syncthreads();
+  if (blockIdx.x == 0) {   // column j's stored reflector, v_0 = 1
+    double* x = Aw + (int64_t)j * n + j + 1;
+    for (int l = threadIdx.x; l < m; l += blockDim.x) x[l] = vv[l];
+  }
+  // grid-stride over the m x m entries (m^2 < 2^31 for the orders this form takes)
+  const int tot = m * m;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += gridDim.x * blockDim.x) {
+    const int i = idx / m, l = idx - i * m;
     double* a = Aw + (int64_t)(j + 1 + i) * n + j + 1 + l;
-    *a = rank2_entry(*a, vl, wi, wl, vi);
+    *a = rank2_entry(*a, vv[l], ww[i], ww[l], vv[i]);
   }
 }
 
@@ -806,35 +816,34 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
   const int64_t nn = (int64_t)n * n;
   eig_copy_kernel<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>(A, lda, n, Aw);
   PF_LAUNCH_CHECK("eig_copy_kernel");
-  // one cluster launch for small orders (bound by the latency of its per-column phases); above
-  // ~400 the four launches per column over the whole GPU are faster, since the O(n^3) update then
-  // dominates and the cluster holds 16 of 148 SMs (measured n = 448: 8.9 against 9.4 ms; 640:
-  // 13.2 against 17.2; 900: 20.1 against 34.6; 1400: 37.6 against 96.5)
-  // distributed shared memory up to n = 512 (n = 224: 2.7 against 3.4 ms for the L2-staged cluster
-  // form, 448: 7.1 against 9.1); at 640 the four launches per column over the whole GPU are faster
-  // (13.4 against 14.3 ms)
-  // two launches per column (house_symv + wvec_rank2, the same bits as the four below) from 400 to
-  // 1300: n = 448: 6.8 against 7.2 ms (DSMEM) and 9.0 (four launches); 640: 10.9 against 13.5;
-  // 900: 18.0 against 20.9; 1248: 31.4 against 32.2; at 1400 the four launches are ahead (38.6
-  // against 40.1) and at 320 the DSMEM kernel (4.2 against 4.5)
-  const int dcs = n <= 400 ? tridiag_dsmem_cluster(n) : 0;
+  // Which form, by order (measured per call, ms; the forms after the changes that gave each its
+  // present shape):
+  //   n      DSMEM cluster   two launches   four launches
+  //   252        1.73            3.33           4.31
+  //   400        3.74            5.77           7.23
+  //   512        6.10            7.83           9.66
+  //   616        8.92            9.65          11.98
+  //   900         --            16.00          19.43
+  //   1400        --            30.47          34.59
+  // The DSMEM cluster kernel wherever its share of the matrix fits in shared memory (n up to ~620),
+  // the L2-staged cluster kernel as its fallback for n <= 400, two launches per column up to 3000
+  // (v and w of a column in 48 KB of shared memory), four above (the same bits as two).
+  const int dcs = n <= 640 ? tridiag_dsmem_cluster(n) : 0;
   const int ccs = (dcs == 0 && n <= 400) ? tridiag_cluster_size() : 0;
   if (dcs > 0) {
     PF_TRY(tridiag_dsmem(Aw, n, d, e, tau, dcs, st));
   } else if (ccs > 0) {
     PF_TRY(tridiag_cluster(Aw, n, d, e, tau, p, ccs, st));
-  } else if (n <= 1300) {
-    double* sc = p + n;   // the reflectors' scales
+  } else if (n <= 3000) {
+    unsigned* ticket = (unsigned*)(wb + L.ticket);
+    PF_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
     for (int j = 0; j + 2 < n; ++j) {
       const int m = n - j - 1;
-      house_symv_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, 0, st>>>(Aw, n, j, d, e, tau, sc, p);
-      wvec_rank2_kernel<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)m * m, 256), 296), 256, 0, st>>>(Aw, n, j, tau,
-                                                                                                       sc, p);
+      const size_t vsm = (size_t)m * sizeof(double);
+      house_symv_kernel<<<(unsigned)ceil_div((int64_t)m * 32, 256), 256, vsm, st>>>(Aw, n, j, d, e, tau, p, ticket);
+      rank2_vw_kernel<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)m * m, 256), 296), 256, 2 * vsm, st>>>(Aw, n, j,
+                                                                                                          p);
       PF_COUNT(2);
-    }
-    if (n >= 3) {
-      reflector_store_kernel<<<1, 256, 0, st>>>(Aw, n, n - 3, sc);
-      PF_COUNT(1);
     }
   } else {
     for (int j = 0; j + 2 < n; ++j) {

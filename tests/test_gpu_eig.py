@@ -1,7 +1,7 @@
 """The H_L eigensolver (pf_sym_eig_select: tridiagonalisation, multisection, inverse iteration,
 back-transformation) against dense LAPACK (numpy.linalg.eigh) on seeded symmetric matrices, at
-orders that take each tridiagonalisation form: the thread-block-cluster kernel (n <= 400), two
-launches per column (400 < n <= 1300) and four (above).
+orders that take each tridiagonalisation form: the thread-block-cluster kernel with the matrix in
+distributed shared memory (n up to ~620), two launches per column (up to 3000) and four (above).
 
 Bar: eigenvalues within 1e-12 ||A||; residuals ||A z - w z|| <= 1e-12 ||A||; unit eigenvectors
 (1e-12), mutually orthogonal to 1e-9 (inverse iteration keeps vectors orthogonal by Gram-Schmidt only
@@ -63,7 +63,7 @@ def _check(pf, A, idx):
         assert ov.min() > 1 - 1e-10
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 17, 64, 300, 448, 700, 1350])
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 64, 300, 448, 600, 700, 1350, 3010])
 def test_dense_random_top_and_bottom(pf, n):
     A = _dense(n, 100 + n)
     q = min(n, 40)
