@@ -14,6 +14,7 @@
 //      orthogonal by modified Gram-Schmidt against the earlier members.
 //   4. Back-transformation z = H_0 H_1 ... H_{n-3} y, one CTA per eigenvector.
 #include "common.cuh"
+#include "pairfloat.cuh"
 #include <cooperative_groups.h>
 #include <cmath>
 #include <map>
@@ -39,7 +40,7 @@ static EigLayout eig_layout(int n, int q) {
   L.y = take((size_t)n * q * 8);
   L.lu = take((size_t)q * 6 * n * 8);
   L.cl = take((size_t)(q + 2) * 4 * 2);
-  L.sturm = take((size_t)n * 16);   // e^2 (FP64), d and e^2 scaled (FP32)
+  L.sturm = take((size_t)n * 32);   // e^2 (FP64), d and e^2 scaled (FP32 and pair-float)
   L.ticket = take(16);
   L.total = o;
   return L;
@@ -591,10 +592,48 @@ __device__ int sturm_count(const T* d, const T* e2, int n, T x, T pivmin) {
   return cnt;
 }
 
+// Pair-float a - b and a / b for the Sturm counts (stored form in, stored form out).  a - b: two_sum
+// of the high parts, the low parts added to its error, renormalised.  a / b: Dekker's division, the
+// FP32 quotient q1 of the high parts and the quotient of the remainder a - b q1 (formed with two_prod)
+// as the low part; about 2^-44 relative.
+__device__ __forceinline__ df2 dfe_sub(df2 a, df2 b) {
+  const float s = __fsub_rn(a.hi, b.hi);
+  const float w = __fsub_rn(s, a.hi);
+  float t = __fsub_rn(__fsub_rn(a.hi, __fsub_rn(s, w)), __fadd_rn(b.hi, w));
+  t = __fadd_rn(t, __fsub_rn(a.lo, b.lo));
+  return df_norm(df2(s, t));
+}
+__device__ __forceinline__ df2 dfe_div(df2 a, df2 b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const float p = __fmul_rn(b.hi, q1);
+  const float e = __fmaf_rn(b.hi, q1, -p);   // b.hi q1 = p + e exactly
+  float r = __fsub_rn(__fsub_rn(a.hi, p), e);
+  r = __fadd_rn(r, a.lo);
+  r = __fsub_rn(r, __fmul_rn(b.lo, q1));
+  return df_norm(df2(q1, __fdiv_rn(r, b.hi)));
+}
+
+// The Sturm count in pair-float on the scaled matrix (d and e^2 as pairs).  |e^2 / q| stays below
+// 1 / FLT_MIN because |q| >= pivmin = FLT_MIN max(1, max e^2); a non-finite pivot is taken as the
+// +infinity it stands for.
+__device__ int sturm_count_df(const df2* d, const df2* e2, int n, df2 x, float pivmin) {
+  int cnt = 0;
+  df2 q = dfe_sub(d[0], x);
+  if (fabsf(q.hi) < pivmin) q = df2(-pivmin, 0.0f);
+  if (q.hi < 0.0f) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = dfe_sub(dfe_sub(d[i], x), dfe_div(e2[i - 1], q));
+    if (!(fabsf(q.hi) <= 3.0e38f)) q = df2(3.0e38f, 0.0f);
+    if (fabsf(q.hi) < pivmin) q = df2(-pivmin, 0.0f);
+    if (q.hi < 0.0f) ++cnt;
+  }
+  return cnt;
+}
+
 // e2 = e^2 in FP64, and T scaled by sc (a power of two, so that ||T|| sc < 1) in FP32: df = d sc,
-// e2f = (e sc)^2.
+// e2f = (e sc)^2, and in pair-float: ddf = d sc, e2df = (e sc)^2.
 __global__ void sturm_prep_kernel(const double* d, const double* e, int n, double sc, double* e2, float* df,
-                                  float* e2f) {
+                                  float* e2f, df2* ddf, df2* e2df) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double ei = i < n - 1 ? e[i] : 0.0;
@@ -602,6 +641,8 @@ __global__ void sturm_prep_kernel(const double* d, const double* e, int n, doubl
   df[i] = (float)(d[i] * sc);
   const float ef = (float)(ei * sc);
   e2f[i] = ef * ef;
+  ddf[i] = df2(d[i] * sc);
+  e2df[i] = df2((ei * sc) * (ei * sc));
 }
 
 // Multisection, one warp per requested eigenvalue (index k of the ascending order): each round the
@@ -615,15 +656,51 @@ __global__ void sturm_prep_kernel(const double* d, const double* e, int n, doubl
 //   - The FP64 rounds continue from there to the rounding level.  Their first round places its points
 //     at both ends of the interval and, should the ends not bracket eigenvalue k, starts again from
 //     the Gershgorin interval [gl, gu] (widened by rounding).
-__global__ void bisect_kernel(const double* d, const double* e2, const float* df, const float* e2f, int n,
-                              const int* idx, int q, double* w, double gl, double gu, double pivmin, double sc,
-                              float pivminf, double delta) {
+// One multisection round of a warp on (lo, hi] with the count routine cnt_at(x): 32 points (lane 31 at
+// hi), or, with ends set, 32 points from lo to hi inclusive, and then false when the ends do not bracket
+// eigenvalue k (the caller starts again from the whole interval).  Returns false also when the round
+// made no progress at this resolution.
+template <typename CountAt>
+__device__ __forceinline__ bool multisection_round(double& lo, double& hi, bool ends, int k, int lane,
+                                                   CountAt cnt_at, bool& bracket_ok) {
+  const double x = lane == 31 ? hi : lo + (hi - lo) * (ends ? (double)lane / 31.0 : (double)(lane + 1) / 32.0);
+  const unsigned mask = __ballot_sync(0xffffffffu, cnt_at(x) >= k + 1);
+  bracket_ok = !ends || (!(mask & 1u) && (mask >> 31));
+  if (!bracket_ok) return false;
+  const int first = mask ? __ffs(mask) - 1 : 31;
+  const double nhi = __shfl_sync(0xffffffffu, x, first);
+  const double nlo = first > 0 ? __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0) : lo;
+  if (nhi >= hi && nlo <= lo) return false;
+  lo = nlo;
+  hi = nhi;
+  return true;
+}
+
+// Multisection, one warp per requested eigenvalue (index k of the ascending order): each round the
+// 32 lanes take Sturm counts at 32 evenly spaced points of (lo, hi] (lane 31 at hi), and the warp
+// keeps the sub-interval between the last point with fewer than k+1 eigenvalues below it and the
+// first with at least k+1, a 32-fold shrink (five bisection steps) per round.  The rounds run in three
+// precisions, each while the interval is wider than what the next can resolve cheaply:
+//   - FP32 on the scaled matrix until the interval is below delta32 = 2^-17 ||T||.  An FP32 count is the
+//     exact count of a matrix within ~9 eps_32 ||T|| of T (the backward error of the LDL^T recurrence,
+//     with the rounding of d, e and the shift), so the interval widened by delta32 (14 times that)
+//     holds eigenvalue k of T;
+//   - pair-float (about 2^-44) on the scaled matrix until the interval is below deltadf = 2^-38 ||T||,
+//     the same argument with eps = 2^-44 (a margin of ~8);
+//   - FP64 to the rounding level; an FP64 division is ~1000 cycles of dependent operations, a
+//     pair-float one ~100, so the FP64 rounds are kept to the last ~15 bits.
+// The first round of the pair-float and FP64 stages places its points at both ends of the widened
+// interval and, should they not bracket eigenvalue k, the stage starts again from the Gershgorin
+// interval [gl, gu] (widened by rounding).
+__global__ void bisect_kernel(const double* d, const double* e2, const float* df, const float* e2f, const df2* ddf,
+                              const df2* e2df, int n, const int* idx, int q, double* w, double gl, double gu,
+                              double pivmin, double sc, float pivminf, double delta32, double deltadf) {
   const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (warp >= q) return;   // uniform per warp
   const int k = idx[warp];
   float lof = __double2float_rd(gl * sc), hif = __double2float_ru(gu * sc);
-  const float deltaf = (float)(delta * sc);
+  const float deltaf = (float)(delta32 * sc);
   for (int it = 0; it < 8 && hif - lof > deltaf; ++it) {
     const float x = lane == 31 ? hif : lof + (hif - lof) * ((float)(lane + 1) / 32.0f);
     const int cnt = sturm_count<float>(df, e2f, n, x, pivminf);
@@ -635,27 +712,33 @@ __global__ void bisect_kernel(const double* d, const double* e2, const float* df
     lof = nlo;
     hif = nhi;
   }
-  double lo = fmax(gl, (double)lof / sc - delta), hi = fmin(gu, (double)hif / sc + delta);
-  bool ends = true;
+  double lo = fmax(gl, (double)lof / sc - delta32), hi = fmin(gu, (double)hif / sc + delta32);
+  auto count_df = [&](double x) { return sturm_count_df(ddf, e2df, n, df2(x * sc), pivminf); };
+  bool ends = true, ok = true;
+  for (int it = 0; it < 16 && hi - lo > deltadf; ++it) {
+    const bool moved = multisection_round(lo, hi, ends, k, lane, count_df, ok);
+    if (!ok) {
+      lo = gl;
+      hi = gu;
+    } else if (!moved) {
+      break;
+    }
+    ends = false;
+  }
+  lo = fmax(gl, lo - deltadf);
+  hi = fmin(gu, hi + deltadf);
+  auto count_d = [&](double x) { return sturm_count<double>(d, e2, n, x, pivmin); };
+  ends = true;
   for (int it = 0; it < 64; ++it) {
     if (hi - lo <= 2.2e-16 * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
-    const double x = lane == 31 ? hi : lo + (hi - lo) * (ends ? (double)lane / 31.0 : (double)(lane + 1) / 32.0);
-    const int cnt = sturm_count<double>(d, e2, n, x, pivmin);
-    const unsigned mask = __ballot_sync(0xffffffffu, cnt >= k + 1);
-    if (ends) {
-      ends = false;
-      if ((mask & 1u) || !(mask >> 31)) {   // not a bracket of eigenvalue k: the whole interval
-        lo = gl;
-        hi = gu;
-        continue;
-      }
+    const bool moved = multisection_round(lo, hi, ends, k, lane, count_d, ok);
+    if (!ok) {
+      lo = gl;
+      hi = gu;
+    } else if (!moved) {
+      break;
     }
-    const int first = mask ? __ffs(mask) - 1 : 31;
-    const double nhi = __shfl_sync(0xffffffffu, x, first);
-    const double nlo = first > 0 ? __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0) : lo;
-    if (nhi >= hi && nlo <= lo) break;   // no progress at this resolution
-    lo = nlo;
-    hi = nhi;
+    ends = false;
   }
   if (lane == 0) w[warp] = 0.5 * (lo + hi);
 }
@@ -882,11 +965,13 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
   double* e2 = (double*)(wb + L.sturm);
   float* df = (float*)(e2 + n);
   float* e2f = df + n;
-  sturm_prep_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(d, e, n, sc, e2, df, e2f);
+  df2* ddf = (df2*)(e2f + n);
+  df2* e2df = ddf + n;
+  sturm_prep_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(d, e, n, sc, e2, df, e2f, ddf, e2df);
   // one warp per CTA: the Sturm counts are bound by the FP64 pipe, and q warps packed eight to a
   // CTA ran on q / 8 SMs (n = 900, q = 150: 10.5 ms on 19 SMs)
-  bisect_kernel<<<(unsigned)q, 32, 0, st>>>(d, e2, df, e2f, n, idx_dev, q, w, gl, gu, pivmin, sc, pivminf,
-                                            std::ldexp(tn, -17));
+  bisect_kernel<<<(unsigned)q, 32, 0, st>>>(d, e2, df, e2f, ddf, e2df, n, idx_dev, q, w, gl, gu, pivmin, sc, pivminf,
+                                            std::ldexp(tn, -17), std::ldexp(tn, -38));
   PF_COUNT(1);   // sturm_prep_kernel
   PF_LAUNCH_CHECK("bisect_kernel");
   PF_CUDA(cudaMemcpyAsync(w_host, w, q * sizeof(double), cudaMemcpyDeviceToHost, st));
