@@ -313,6 +313,28 @@ struct PhaseClock {
   }
 };
 
+// Modelled device time (us) of a convergence check and of a block step, from sizes alone.  They
+// decide where the next check falls, which decides the Krylov dimension a solve stops at, so they
+// must not come from measured times: a solve sharing the GPU with others (a batch, the server) then
+// takes the same steps, and returns the same bits, as the same solve alone.  The rates are those the
+// kernels reach on B300: the Clenshaw step at ~4 TB/s of its algorithmic bytes (FP64: ~1 TFLOP/s on
+// the FP64 pipe), the Gram products at ~1 TFLOP/s, a floor of a few us per dependent launch; the
+// eigensolver's tridiagonalisation ~M (3 + 0.0135 M) us, the Sturm counts ~3 M us, inverse iteration
+// and back-transformation ~0.03 q M us, ~150 us of launches and host reads per check.
+static double model_check_us(int M, int q) {
+  return 150.0 + (double)M * (6.0 + 0.0135 * (double)M) + 0.03 * (double)q * (double)M;
+}
+static double model_block_us(const Ham* H, int s, int K, int k, bool fp64_step) {
+  const double D = (double)H->D, nnz = (double)H->nnz, ss = (double)s * (double)s;
+  const double w = fp64_step ? 8.0 : 4.0;
+  const double bytes = nnz * (w + 4.0) + 8.0 * (D + 1.0) + 4.0 * D * s * w;
+  double step = std::max(4.0, bytes / 4.0e6);
+  if (fp64_step) step = std::max(step, 2.0 * nnz * s / 1.0e6);
+  const double orth = std::max(24.0, 8.0 * (double)(k + 1) * ss * D / 1.0e6);
+  const double qr = std::max(60.0, 6.0 * ss * D / 1.0e6);
+  return (double)(K + 1) * step + orth + qr;
+}
+
 struct LanczosResult {
   int blocks = 0;      // number of Krylov blocks in the basis (M = blocks * s)
   bool converged = false;
@@ -412,16 +434,17 @@ static pf_status block_lanczos(Solver& S, OpKind op, const double* coeffs, int K
       // next check: every check_every blocks; earlier when the largest residual, extrapolated
       // geometrically from the last two checks, reaches tol sooner; where a check costs more than
       // half the block steps between two checks (the spectral-bounds Lanczos on H: a block step
-      // is one SpMM with s = 4), at 3/4 of the extrapolated distance or at the budget
+      // is one SpMM with s = 4), at 3/4 of the extrapolated distance or at the budget.  The costs
+      // are modelled from the sizes, never measured, so the steps taken do not depend on timing.
       int step = check_every;
       if (prev_k > 0 && rmax < prev_r && rmax > tol) {
         const double rate = std::log(rmax / prev_r) / (double)(k - prev_k);
         const double need = std::log(tol / rmax) / rate;
         step = std::max(1, std::min(check_every, (int)std::ceil(need) - 1));
-        const double check_ms = clk.ms(4, 5);
-        const double block_ms = (S.rep.ms_filter_f32 + S.rep.ms_filter_f64 + S.rep.ms_orth + S.rep.ms_qr) / k;
+        const double check_us = model_check_us(M, nq);
+        const double block_us = model_block_us(S.H, s, K, k, op != OP_FILTER32);
         const int left = S.max_blocks - k;
-        if (need > check_every && check_ms > 0.5 * check_every * block_ms && left > check_every)
+        if (need > check_every && check_us > 0.5 * check_every * block_us && left > check_every)
           step = need >= left ? left : std::max(check_every, (int)(0.75 * need));
       }
       prev_k = k;
@@ -1004,16 +1027,18 @@ struct Task {
       // check costs more than half the block steps between two checks (small sectors, many
       // eigenpairs: XXZ L = 16, s = 16, nev = 200 checks at n ~ 400-1250 for 10-30 ms against ~1 ms
       // per block), the next check moves to 3/4 of the extrapolated distance, or straight to the
-      // Krylov budget when the extrapolation lies beyond it.
+      // Krylov budget when the extrapolation lies beyond it.  Both costs are modelled from the
+      // sizes (model_check_us, model_block_us), never measured: the Krylov dimension a solve stops
+      // at, and so its result, must not depend on what else runs on the GPU.
       int step = check_every;
-      const double check_ms = clk->ms(4, 5);
-      const double block_ms = (S.rep.ms_filter_f32 + S.rep.ms_filter_f64 + S.rep.ms_orth + S.rep.ms_qr) / k;
       if (o.check_every <= 0 && prev_check_k > 0 && rmax < prev_check_r && rmax > tol) {
         const double rate = std::log(rmax / prev_check_r) / (double)(k - prev_check_k);
         const double need = std::log(tol / rmax) / rate;
         step = std::max(1, std::min(check_every, (int)std::ceil(need) - 1));
         const int left = S.max_blocks - k;
-        if (need > check_every && check_ms > 0.5 * check_every * block_ms && left > check_every)
+        const double check_us = model_check_us(M, nq);
+        const double block_us = model_block_us(H, s, K, k, !f32);
+        if (need > check_every && check_us > 0.5 * check_every * block_us && left > check_every)
           step = need >= left ? left : std::max(check_every, (int)(0.75 * need));
       }
       prev_check_k = k;
