@@ -204,7 +204,7 @@ pf_status pf_filter_coefficients(double lam_t, int32_t K, double* coeffs, pf_str
 
 /* Degree K from the Gaussian DOS with exact moments (Eq. dos_gaussian, Eq. Nev,
  * Eq. K_approx): K = ceil(2.655 sqrt(1 - lam~^2) * 2 rho(lam~) / nev_g),
- * nev_g = ceil(g nev), g = 2.5 for D >= 100000, else 1.5.
+ * nev_g = ceil(g nev), g = 3 for D >= 100000, else 1.5.
  * target_eps: lambda = Emin + eps (Emax - Emin).  Synchronises. */
 pf_status pf_choose_K(pf_ham* H, double target_eps, int32_t nev, int32_t* K, pf_stream_t stream);
 
@@ -317,7 +317,7 @@ typedef struct {
   int32_t block;          /* s: 1..64, power of two; 0 = 32; < 0 = pf_autotune_block  */
   int32_t precision;      /* pf_precision of the filter recurrence                   */
   int32_t nev_guard;      /* Ritz pairs converged; 0 = ceil(g nev),
-                             g = 2.5 for D >= 100000, else 1.5                      */
+                             g = 3 for D >= 100000, else 1.5                        */
   int32_t check_first;    /* first check at this block step; 0 = ceil(m / 2), m the
                              expected Krylov blocks (20.427 s + 1.696 nev_g) / s      */
   int32_t check_every;    /* check interval in block steps; 0 = ceil(m / 10), checked
@@ -535,7 +535,7 @@ pf_status pf_kpm_dos(const double* mu, int32_t N, const double* x, int32_t nx, d
  * Errors: PF_EINVAL (eta outside [-1, 1]).                                          */
 pf_status pf_kpm_target(const double* mu, int32_t N, double eta, double* lam_t);
 /* K from Eq. condition_for_K with rho(lam~) from KPM: delta = nev_g / (2 rho) (Eq. Nev,
- * nev_g = ceil(g nev), g = 2.5 when mu_0 >= 100000, else 1.5), then the smallest K in
+ * nev_g = ceil(g nev), g = 3 when mu_0 >= 100000, else 1.5), then the smallest K in
  * [K_approx/2, 2 K_approx] whose filter is at most Omega = sin(2.655)/2.655 at both window
  * edges lam~ +- delta (bisection).
  * Errors: PF_EINVAL (rho <= 0, lam_t outside (-1, 1)).                               */

@@ -46,19 +46,19 @@ def k_approx(lam_t, delta):
 
 
 def guard_count(nev, D):
-    """nev_g = ceil(g nev), g = 2.5 for D >= 100,000 and 1.5 below: Ritz pairs converged (and
+    """nev_g = ceil(g nev), g = 3 for D >= 100,000 and 1.5 below: Ritz pairs converged (and
     eigenvalues put above the cutoff by K).  Where only KPM moments are known, D is mu_0.
 
     The paper does not fix the margin.  Reading: the nev pairs nearest lambda must have filter
     values well above the magnitude of the filter's negative sidelobe (the sinc minimum,
     ~ -0.217, under the reading of Eq. K_approx used for OMEGA), since that ratio bounds how
     fast a refinement pass removes errors there; at g = 1.5 the returned edge sits at
-    P ~ sin(2.655/1.5)/(2.655/1.5) ~ 0.55, at g = 2.5 at ~ 0.82.  A larger guard lowers K
+    P ~ sin(2.655/1.5)/(2.655/1.5) ~ 0.55, at g = 3 at ~ 0.87.  A larger guard lowers K
     (~ 1/nev_g) faster than it grows the Krylov space (~ 20.4 s + 1.7 nev_g, the printed fit of
     Sec. 5.5), which pays where the filter's products dominate (large D); where the Lanczos and
     Ritz work, growing with nev_g, dominates (small D), the smaller margin is kept.
     """
-    g = 2.5 if D >= 100000 else 1.5
+    g = 3.0 if D >= 100000 else 1.5
     return int(math.ceil(g * nev))
 
 

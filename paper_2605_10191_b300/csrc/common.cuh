@@ -13,11 +13,11 @@
 namespace pf {
 // Guard nev_g = ceil(guard_factor(D) nev): the Ritz pairs converged, and the eigenvalues the degree
 // K puts above the filter's cutoff (Eq. Nev, Eq. K_approx).  Sectors of D >= 100,000, where the
-// filter's matrix products dominate a solve, take 2.5 (K falls as 1 / nev_g, the Krylov space
+// filter's matrix products dominate a solve, take 3 (K falls as 1 / nev_g, the Krylov space
 // grows only as 20.4 s + 1.7 nev_g); smaller ones, where the Lanczos and Ritz work dominates,
 // keep 1.5.  The KPM rule takes D as mu_0 (its estimate of Tr T_0).  The oracle's dos.guard_count
 // is the same rule.
-inline double guard_factor(double D) { return D >= 100000.0 ? 2.5 : 1.5; }
+inline double guard_factor(double D) { return D >= 100000.0 ? 3.0 : 1.5; }
 }  // namespace pf
 
 namespace pf {

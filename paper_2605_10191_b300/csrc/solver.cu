@@ -559,10 +559,10 @@ static pf_status spectral_bounds_impl(Ham* H, double tol, cudaStream_t st) {
 
 // Guard factor (guard_factor, common.cuh): nev_g = ceil(g nev) Ritz pairs of P are converged and the
 // degree K is chosen so that about nev_g eigenvalues lie above the cutoff.  The nev returned
-// (nearest lambda) then have filter values P >~ sinc(2.655 / g) (0.55 at g = 1.5, 0.82 at 2.5),
+// (nearest lambda) then have filter values P >~ sinc(2.655 / g) (0.55 at g = 1.5, 0.87 at 3),
 // above the magnitude of the filter's negative sidelobe (~0.22), which is what the refinement must
 // contract relative to them.  A larger guard lowers K (proportional to 1 / nev_g) faster than it
-// grows the Krylov space (20.4 s + 1.7 nev_g): filter-dominated solves (D >= 100,000) take g = 2.5
+// grows the Krylov space (20.4 s + 1.7 nev_g): filter-dominated solves (D >= 100,000) take g = 3
 // and need fewer steps in all; smaller ones, dominated by the Lanczos and Ritz work that grows
 // with nev_g, keep g = 1.5.
 

@@ -314,13 +314,13 @@ def test_window_holds_about_nev_g_levels():
 
 
 def test_guard_rule_and_returned_edge_filter_value():
-    """The guard reading: nev_g = ceil(g nev), g = 1.5 below D = 100,000 and 2.5 from there on.  With
+    """The guard reading: nev_g = ceil(g nev), g = 1.5 below D = 100,000 and 3 from there on.  With
     K from the window of nev_g levels, the nev-th level from the target sits at about
     (nev / nev_g) delta, where a sinc-shaped filter of that window (value Omega at delta, the
     reading of Eq. K_approx) is sinc(2.655 nev / nev_g): above 0.5 for either g, and above the
     magnitude of the sidelobe minimum (-0.217) by more than 2x."""
-    assert dos.guard_count(10, 99999) == 15 and dos.guard_count(10, 100000) == 25
-    assert dos.guard_count(7, 12870) == 11 and dos.guard_count(7, 184756) == 18
+    assert dos.guard_count(10, 99999) == 15 and dos.guard_count(10, 100000) == 30
+    assert dos.guard_count(7, 12870) == 11 and dos.guard_count(7, 184756) == 21
     x = np.linspace(4.0, 6.0, 20001)
     side = float(np.min(np.sin(x) / x))
     assert abs(side + 0.2172) < 1e-3
