@@ -559,9 +559,9 @@ pf_status pf_start_block(int64_t D, int32_t s, uint64_t seed, double* out, pf_st
 
 /* Selected eigenpairs of a dense real-symmetric matrix: the eigensolver the solve applies to the
  * projected Lanczos matrix H_L at its convergence checks and its Ritz extraction (Sec. 4.6,
- * Eq. blocklan_criterion).  Householder tridiagonalisation (one thread-block cluster up to n = 400,
- * two launches per column over the GPU up to 1300, four above; the three forms give the same
- * tridiagonal bit for bit), multisection with Sturm counts, inverse iteration (Gram-Schmidt within
+ * Eq. blocklan_criterion).  Householder tridiagonalisation (one thread-block cluster with the matrix
+ * in distributed shared memory up to n ~ 620, two launches per column over the GPU up to 3000, four
+ * above; every form gives the same tridiagonal bit for bit), multisection with Sturm counts, inverse iteration (Gram-Schmidt within
  * clusters closer than 1e-6 ||T||) and back-transformation, all FP64.
  *   A: device, n x n row-major with leading dimension lda >= n; only (A + A^T) / 2 is used.
  *   idx: host [q], indices into the ascending spectrum (0 = smallest), each in [0, n).

@@ -255,9 +255,9 @@ __global__ void rank2_vw_kernel(double* Aw, int n, int j, const double* p) {
 // the four phases of each column: the reflector (CTA 0, as house_kernel), p = tau A22 v (warps
 // of the whole cluster, as symv_kernel), w = p - (tau/2)(p.v) v (every CTA forms the dot in the
 // same order, then writes its slice, as wvec_kernel) and the rank-2 update (as rank2_kernel).
-// Data another CTA wrote is read with L2-only loads.  For H_L up to 1024 this replaces four
-// launches per column with one launch, so small solves (and many solves at once) are no longer
-// bound by launch latency.  No spin-waits: the barriers are hardware barriers.
+// Data another CTA wrote is read with L2-only loads.  One launch instead of four per column; it is
+// now the fallback (n <= 400) where the distributed-shared-memory form below cannot be launched.
+// No spin-waits: the barriers are hardware barriers.
 #define PF_TRI_NT 512
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
