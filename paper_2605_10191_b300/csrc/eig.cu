@@ -48,6 +48,25 @@ static EigLayout eig_layout(int n, int q) {
 
 size_t eig_workspace_bytes(int nmax, int qmax) { return eig_layout(nmax, qmax).total; }
 
+// A kernel's dynamic shared-memory limit is one value per kernel and device, shared by every host
+// thread.  Setting it to each call's own size lets a thread that lowers it (a smaller matrix) break
+// another thread's launch of a larger one in between; calls on distinct handles may run on different
+// threads.  This raises the limit to `bytes` when it is lower, never lowers it, and leaves sizes up to
+// the default 48 KB alone.
+static pf_status raise_smem_limit(const void* kern, size_t bytes) {
+  if (bytes <= (size_t)48 * 1024) return PF_OK;
+  int dev = 0;
+  PF_CUDA(cudaGetDevice(&dev));
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> limit;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[std::make_pair(kern, dev)];
+  if (bytes <= cur) return PF_OK;
+  PF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  cur = bytes;
+  return PF_OK;
+}
+
 // One entry of the rank-2 update A22 -= v w^T + w v^T (row l, column c), as two FMAs; every form of
 // the tridiagonalisation calls this one expression.
 __device__ __forceinline__ double rank2_entry(double a, double vl, double wc, double wl, double vc) {
@@ -480,7 +499,10 @@ static int tridiag_dsmem_cluster_query(int n) {
     const size_t bytes = tridiag_dsmem_bytes(n, c);
     if (bytes + 1024 > (size_t)smem_max) continue;
     cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (raise_smem_limit((const void*)kern, bytes) != PF_OK) {
+      cudaGetLastError();
+      continue;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)c, 1, 1);
     cfg.blockDim = dim3(PF_TRI_DS_NT, 1, 1);
@@ -501,7 +523,7 @@ static int tridiag_dsmem_cluster_query(int n) {
 
 static pf_status tridiag_dsmem(double* Aw, int n, double* d, double* e, double* tau, int cs, cudaStream_t st) {
   const size_t bytes = tridiag_dsmem_bytes(n, cs);
-  PF_CUDA(cudaFuncSetAttribute(tridiag_dsmem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  PF_TRY(raise_smem_limit((const void*)tridiag_dsmem_kernel, bytes));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)cs, 1, 1);
   cfg.blockDim = dim3(PF_TRI_DS_NT, 1, 1);
@@ -999,18 +1021,13 @@ pf_status sym_eig_select(const double* A, int lda, int n, const int* idx_host, i
   // the LU factors in shared memory up to n = 2000 (96 KB)
   const int smem_lu = n <= 2000 ? 1 : 0;
   const size_t lu_smem = smem_lu ? (size_t)6 * n * sizeof(double) : 0;
-  if (lu_smem > 48 * 1024) {
-    static std::once_flag once;
-    std::call_once(once, [] {
-      cudaFuncSetAttribute(inviter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * 2000 * (int)sizeof(double));
-    });
-  }
+  if (lu_smem > 48 * 1024) PF_TRY(raise_smem_limit((const void*)inviter_kernel, (size_t)6 * 2000 * sizeof(double)));
   inviter_kernel<<<(unsigned)ncl, 256, lu_smem, st>>>(d, e, n, w, cl, ncl, Y, lu, tnorm, smem_lu);
   PF_LAUNCH_CHECK("inviter_kernel");
   const size_t smem = (size_t)n * sizeof(double);
   if (smem > 48 * 1024) {
     if (smem > 200 * 1024) return PF_EINVAL;
-    PF_CUDA(cudaFuncSetAttribute(backtransform_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PF_TRY(raise_smem_limit((const void*)backtransform_kernel, smem));
   }
   backtransform_kernel<<<q, 256, smem, st>>>(Aw, tau, n, Y, Z, ldz);
   PF_LAUNCH_CHECK("backtransform_kernel");
