@@ -91,12 +91,12 @@ __global__ void unrank_kernel(uint32_t* out, int64_t n, int L, int N, const uint
 }
 
 static uint64_t binom_h(int n, int k) {
-  static uint64_t tab[33 * 33];
-  static bool init = false;
-  if (!init) {
-    host_binom(tab);
-    init = true;
-  }
+  // built once; the initialisation of a function-local static is thread-safe
+  static const std::vector<uint64_t> tab = [] {
+    std::vector<uint64_t> t(33 * 33);
+    host_binom(t.data());
+    return t;
+  }();
   if (n < 0 || k < 0 || n > 32 || k > 32) return 0;
   return tab[n * 33 + k];
 }

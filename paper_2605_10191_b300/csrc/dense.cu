@@ -210,12 +210,9 @@ template <int S>
 static pf_status launch_tsgemm(dim3 grid, cudaStream_t st, int64_t D, const double* X, int nbX, const double* C,
                                int ldc, double* Y, double alpha, double beta) {
   const int smem = (TS_TR * (S + 1) + S * S) * (int)sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tsgemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) { set_cuda_error(e, "tsgemm smem attribute"); return PF_ECUDA; }
-    attr_set = true;
-  }
+  // set once (a function-local static initialises exactly once, thread-safely); the size is fixed per S
+  static const cudaError_t attr = cudaFuncSetAttribute(tsgemm_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (attr != cudaSuccess) { set_cuda_error(attr, "tsgemm smem attribute"); return PF_ECUDA; }
   tsgemm_kernel<S><<<grid, TS_THREADS, smem, st>>>(D, X, nbX, C, ldc, Y, alpha, beta);
   PF_LAUNCH_CHECK("tsgemm_kernel");
   return PF_OK;
@@ -391,12 +388,9 @@ template <int S>
 static pf_status launch_tsgemm_df(dim3 grid, cudaStream_t st, int64_t D, const double* X, int nbX, const double* C,
                                   int ldc, double* Y, double alpha, double beta) {
   const int smem = (TS_TR * S + S * S) * (int)sizeof(df2);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tsgemm_df_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) { set_cuda_error(e, "tsgemm_df smem attribute"); return PF_ECUDA; }
-    attr_set = true;
-  }
+  // set once, as in launch_tsgemm
+  static const cudaError_t attr = cudaFuncSetAttribute(tsgemm_df_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (attr != cudaSuccess) { set_cuda_error(attr, "tsgemm_df smem attribute"); return PF_ECUDA; }
   tsgemm_df_kernel<S><<<grid, TS_THREADS, smem, st>>>(D, X, nbX, C, ldc, Y, alpha, beta);
   PF_LAUNCH_CHECK("tsgemm_df_kernel");
   return PF_OK;
