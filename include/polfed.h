@@ -18,7 +18,9 @@
  *    installed by pf_set_allocator (default: cudaMallocAsync / cudaFreeAsync).
  *  - Work is enqueued on the given stream.  Calls that return host scalars
  *    synchronise that stream before returning.  A handle must not be used by two
- *    threads at once; distinct handles are independent.
+ *    threads at once; distinct handles are independent: the library's process-wide
+ *    state (tuning caches, stream pools, kernel attributes) is guarded by locks or set
+ *    once, and kernel shared-memory limits are only ever raised.
  *  - Vector blocks are D x s, row-major (the s entries of a row are contiguous).
  */
 #ifndef POLFED_H
